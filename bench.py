@@ -1,0 +1,440 @@
+"""Benchmark: Stage-1 NTC training on the 250K-Gaussian, 20-view multi-view
+video workload (1352x1014, 4 views per launch), plus the rasterizer
+fwd+bwd throughput and the plain FP32 direct-optimisation path on the same
+GPU, and the FP64 CPU oracle on a bounded sample.
+
+One "step" is one Stage-1 iteration: NTC query of all Gaussians,
+transformation, projection + binning + sort + compositing of a batch of 4
+views, L1 + D-SSIM loss, backward into the hash table and MLP, Adam.  A
+frame is 150 iterations (Section 5.2); the headline value is seconds per
+frame.  Inputs are seeded synthetic scenes (the N3DV videos are not
+available) resident in HBM; the per-iteration working set (pair buffers of
+~0.5 GB) exceeds the 129 MB L2, so no flush is needed between iterations.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "NTC train s/frame @250K 3DGs, 20 views; raster fwd+bwd it/s vs FP32 plain"
+ITERS_PER_FRAME = 150
+CFG_INDEX = 3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mlp", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--small", action="store_true", help="a small scene (for profiling captures)")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_sample(scene, n_sample_gauss=None, views=1):
+    """Time the FP64 oracle's Stage-1 step on a bounded sample of the
+    workload: every Gaussian through the cache and transformation, and the
+    render + loss + backward of `views` of the 4 views of a batch.  Returns
+    (seconds per full 4-view iteration, description, threads)."""
+    import oracle
+    oracle.build()
+    cfg = scene.cfg
+    g = scene.prev
+    cams = scene.cams[:views]
+    og = oracle.Grid()
+    rng = np.random.default_rng(0)
+    from paper_2403_01444_gb300 import scenes
+    table = rng.uniform(-1e-4, 1e-4, size=(og.n_entries, 2))
+    Ws = scenes.random_mlp([32, 64, 64, 7], rng)
+    Ws[2][3] = np.abs(Ws[2][3]) + 1.0
+    p = oracle.NTCParams(og, table, Ws)
+    targets = np.random.default_rng(1).uniform(size=(views, 3, cfg.H, cfg.W))
+    t0 = time.perf_counter()
+    f = oracle.ntc_forward(p, g.mean, g.quat)
+    t_ntc_f = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    r = oracle.render(g, cams, f["mean"], f["quat"])
+    L, d_img, _ = oracle.loss_l1_dssim(r["img"], targets)
+    grads = oracle.raster_bwd(r["proj"], cfg.W, cfg.H, r["T_final"], r["last"], d_img)
+    dm, dq = oracle.project_bwd(g, cams, grads, mean=f["mean"], quat=f["quat"])
+    t_view = (time.perf_counter() - t0) / views
+    t0 = time.perf_counter()
+    d_raw7 = oracle.apply_bwd(g.mean, g.quat, f["raw7"], og.aabb, dm, dq)
+    dWs, d_enc = oracle.mlp_bwd(f["enc"], p.Ws, f["h1"], f["h2"], d_raw7)
+    oracle.encode_bwd(og, g.mean, d_enc)
+    t_ntc_b = time.perf_counter() - t0
+    per_iter = t_ntc_f + t_ntc_b + cfg.views_per_batch * t_view
+    desc = ("FP64 oracle, all %d Gaussians through NTC fwd/bwd + %d of the 4 views rendered, "
+            "loss, backward (%.1f s); per-iteration time = NTC + 4 x per-view time"
+            % (g.n, views, t_ntc_f + t_ntc_b + views * t_view))
+    return per_iter, desc, oracle.num_threads()
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2403_01444_gb300 import scenes
+    scene = scenes.make_scene(CFG_INDEX)
+    per_iter, desc, cores = oracle_sample(scene)
+    s_frame = per_iter * ITERS_PER_FRAME
+    line = {"impl": "reference", "metric": METRIC, "value": s_frame, "unit": "s/frame",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": per_iter * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(scene, "oracle"),
+            "cpu_baseline": {"value": s_frame, "unit": "s/frame", "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": s_frame, "unit": "s/frame", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(scene, parallelism):
+    cfg = scene.cfg
+    return {"workload": "ntc-stage1 250K Gaussians SH3, 20 cams 1352x1014, 4 views/launch, "
+                        "150 it/frame (synthetic N3DV stand-in)",
+            "gaussians": cfg.n_gauss, "sh_degree": cfg.sh_deg, "cameras": cfg.n_cams,
+            "width": cfg.W, "height": cfg.H, "views_per_step": cfg.views_per_batch,
+            "iters_per_frame": ITERS_PER_FRAME, "hash_grid": "16x2, 2^17, 16..1024",
+            "mlp": "32-64-64-7", "parallelism": parallelism,
+            "l2": "inputs larger than L2 (no flush)"}
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = "cuda"
+    from paper_2403_01444_gb300 import build as _b
+    _b.build()
+    from paper_2403_01444_gb300 import gs3, scenes
+    from paper_2403_01444_gb300.engine import NTC, DirectOpt, Rasterizer, Stage1, warmup
+    import oracle  # only for the grid size of the initial table (host integer layout)
+
+    if args.small:
+        scene = scenes.make_scene(CFG_INDEX, n_gauss=50_000, W=676, H=507)
+    else:
+        scene = scenes.make_scene(CFG_INDEX)
+    cfg = scene.cfg
+    W, H, Vb = cfg.W, cfg.H, cfg.views_per_batch
+    nb = cfg.n_cams // Vb
+    G = gs3.Gaussians.from_numpy(scene.prev)
+    Gt = gs3.Gaussians.from_numpy(scene.target)
+    cams_dev = gs3.cameras_to_device(scene.cams)
+    batch_cams = [gs3.camera_slice(cams_dev, b * Vb, Vb) for b in range(nb)]
+    # ground-truth views (rendered once by the FP32 rasterizer)
+    rt = Rasterizer(Gt.n, Vb, W, H, 1 << 24, dev)
+    targets = torch.empty(cfg.n_cams, 3, H, W, device=dev)
+    for b in range(nb):
+        rt.fit_capacity(Gt, batch_cams[b], margin=1.2)
+        targets[b * Vb:(b + 1) * Vb].copy_(rt.img)
+    del rt
+    torch.cuda.empty_cache()
+    # NTC: I-NGP-style init, then the warm-up towards the identity (Eq. 7)
+    precision = gs3.GS_MLP_BF16 if args.mlp == "bf16" else gs3.GS_MLP_FP32
+    rng = np.random.default_rng(7)
+    grid = gs3.hashgrid()
+    entries = gs3.ntc_hashgrid_entries(grid)
+    table = rng.uniform(-1e-4, 1e-4, size=(entries, 2)).astype(np.float32)
+    Ws = [w.astype(np.float32) for w in scenes.random_mlp([32, 64, 64, 7], rng)]
+    ntc = NTC(table, Ws, grid, precision, dev)
+    t0 = time.perf_counter()
+    wl = warmup(ntc, G, iters=1000)
+    torch.cuda.synchronize()
+    t_warm = time.perf_counter() - t0
+    warm_table, warm_mlp = ntc.table.p.clone(), ntc.mlp.p.clone()
+    st = Stage1(G, ntc, Vb, W, H, capacity=1 << 20)
+    counts = []
+    for b in range(nb):
+        counts.append(st.raster.fit_capacity(G, batch_cams[b], *st.transform(), margin=1.0))
+    st.raster.set_capacity(int(max(counts) * 1.3))
+    ntc.reset_to(warm_table, warm_mlp)
+    st.reset_state()
+
+    stream = torch.cuda.current_stream()
+    ev = {}
+
+    def step(i, record=False):
+        if i % ITERS_PER_FRAME == 0:
+            ntc.reset_to(warm_table, warm_mlp)  # every frame starts from the warm-up parameters
+        b = i % nb
+        cd, tg = batch_cams[b], targets[b * Vb:(b + 1) * Vb]
+        if not record:
+            st.step(cd, tg)
+            return
+        E = lambda k: ev.setdefault(k, []).append(torch.cuda.Event(enable_timing=True)) or ev[k][-1].record(stream)
+        E("t0")
+        st.transform()
+        E("t1")
+        gs3.gs_project(G, cd, Vb, W, H, st.raster.proj, st.mean_t, st.quat_t)
+        E("t2")
+        r = st.raster
+        gs3.gs_bin_sort(r.proj, G.n, Vb, W, H, r.capacity, r.vals, r.ranges, None, r.d_count, r.d_err, r.ws)
+        E("t3")
+        gs3.gs_raster_fwd(r.proj, G.n, Vb, W, H, r.bg, r.vals, r.ranges, r.img, r.T_final, r.last)
+        E("t4")
+        st.loss(r.img, tg)
+        E("t5")
+        gs3.gs_raster_bwd(r.proj, G.n, Vb, W, H, r.bg, r.vals, r.ranges, r.T_final, r.last,
+                          st.loss.d_img, r.grads, None)
+        E("t6")
+        gs3.gs_project_bwd(G, cd, Vb, W, H, r.grads, r.d_mean, r.d_quat, st.mean_t, st.quat_t)
+        E("t7")
+        gs3.ntc_apply_bwd(G.mean, G.quat, st.raw7, G.n, st.aabb, st.order, r.d_mean, r.d_quat, st.d_raw7)
+        gs3.ntc_mlp_bwd(st.enc, G.n, ntc.mlp_struct(), st.d_raw7, st.loss_scale_view(), ntc.mlp.g, st.d_enc)
+        gs3.ntc_encode_bwd(G.mean, G.n, ntc.grid, st.d_enc, ntc.table.g)
+        E("t8")
+        st.update()
+        E("t9")
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    gs3.lib().gs_launch_count.restype = ctypes_u64()
+    l0 = gs3.lib().gs_launch_count()
+    with ClockSampler(local) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(args.warmup, args.warmup + args.steps):
+            step(i)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    launches = gs3.lib().gs_launch_count() - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    st.raster.check()
+    ms_all = torch.tensor([ms], device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(ms_all, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(ms_all.item())
+    s_per_frame = ms_max * ITERS_PER_FRAME / 1e3 / world  # whole-job: frames of all ranks
+
+    # per-stage breakdown (separate, instrumented pass)
+    ev.clear()
+    for i in range(args.warmup + args.steps, args.warmup + args.steps + 10):
+        step(i, record=True)
+    torch.cuda.synchronize()
+    names = ["ntc_fwd", "project", "bin_sort", "raster_fwd", "loss", "raster_bwd", "project_bwd",
+             "ntc_bwd", "adam"]
+    stages = {}
+    for k, nm in enumerate(names):
+        a, b = ev["t%d" % k], ev["t%d" % (k + 1)]
+        stages[nm] = statistics.mean(x.elapsed_time(y) for x, y in zip(a, b))
+    pairs = int(st.raster.count())
+
+    # rasterizer fwd+bwd it/s: project + bin/sort + raster fwd + raster bwd + project bwd
+    raster_ms = sum(stages[k] for k in ("project", "bin_sort", "raster_fwd", "raster_bwd", "project_bwd"))
+
+    # roofline of the dominant kernel group
+    hbm, bf16, src = load_peaks()
+    dom = max(stages, key=stages.get)
+    roof = roofline_for(dom, stages[dom], pairs, G.n, Vb, W, H, cfg, hbm, src)
+
+    # plain FP32 direct optimisation on the same inputs and rasterizer
+    plain = None
+    if not args.no_plain:
+        do = DirectOpt(G, Vb, W, H, st.raster.capacity, device=dev)
+        for i in range(3):
+            do.step(batch_cams[i % nb], targets[(i % nb) * Vb:(i % nb + 1) * Vb])
+        torch.cuda.synchronize()
+        e0.record(stream)
+        kp = max(10, args.steps // 2)
+        for i in range(kp):
+            b = i % nb
+            do.step(batch_cams[b], targets[b * Vb:(b + 1) * Vb])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1) / kp
+        plain = {"s_per_frame": pms * ITERS_PER_FRAME / 1e3, "ms_per_iter": pms, "iters": kp}
+        del do
+
+    # end to end through the public API with host buffers: per step the batch's
+    # target views go host->device from pinned memory and the loss comes back
+    host_targets = targets.cpu().pin_memory()
+    dev_tg = torch.empty(Vb, 3, H, W, device=dev)
+    host_loss = torch.empty(1, pin_memory=True)
+    ke = max(10, args.steps // 2)
+    for i in range(2):
+        dev_tg.copy_(host_targets[0:Vb], non_blocking=True)
+        st.step(batch_cams[0], dev_tg)
+        host_loss.copy_(st.loss.d_loss, non_blocking=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(ke):
+        if i % ITERS_PER_FRAME == 0:
+            ntc.reset_to(warm_table, warm_mlp)
+        b = i % nb
+        dev_tg.copy_(host_targets[b * Vb:(b + 1) * Vb], non_blocking=True)
+        st.step(batch_cams[b], dev_tg)
+        host_loss.copy_(st.loss.d_loss, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / ke
+    h2d = Vb * 3 * H * W * 4
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        per_iter, desc, cores = oracle_sample(scene)
+        cpu = {"value": per_iter * ITERS_PER_FRAME, "unit": "s/frame", "cores": cores,
+               "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        clocks = clk.summary()
+        line = {"metric": METRIC, "value": s_per_frame, "unit": "s/frame", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+                "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+                "dtype": "mixed: f16 table, %s mlp, f32 raster" % args.mlp if precision == gs3.GS_MLP_BF16 else "f32",
+                "data": "synthetic", "config": config_dict(scene, "replicas%d" % world if world > 1 else "single"),
+                "train_it_per_s": 1e3 / ms_max,
+                "raster_fwd_bwd_it_per_s": 1e3 / raster_ms,
+                "raster_fwd_bwd_ms": raster_ms,
+                "plain_fp32_direct_opt": plain,
+                "speedup_vs_plain_per_iter": (plain["ms_per_iter"] / ms_max) if plain else None,
+                "stages_ms": {k: round(v, 4) for k, v in stages.items()},
+                "pairs_per_step": pairs, "warmup_loss": wl, "warmup_s": t_warm,
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_ms * ITERS_PER_FRAME / 1e3, "unit": "s/frame",
+                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4},
+                "gpu_launches": int(launches), "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+def ctypes_u64():
+    import ctypes
+    return ctypes.c_uint64
+
+
+def roofline_for(stage, ms, pairs, n, V, W, H, cfg, hbm_gbs, src):
+    """Algorithmic bytes of one launch of the stage's kernels (each logically
+    required read or write counted once) over its measured time."""
+    K = (cfg.sh_deg + 1) ** 2
+    px = V * W * H
+    per_gauss_params = 12 + 16 + 12 + 4 + 12 * K
+    bytes_ = {
+        "bin_sort": pairs * (12 + 24 + 8),              # key/val write, one sort r+w, range scan
+        "raster_fwd": pairs * 40 + px * 20,             # records + index per pair, outputs
+        "raster_bwd": pairs * 40 + px * 32 + n * V * 32,
+        "project": n * per_gauss_params + n * V * 44,
+        "project_bwd": n * per_gauss_params + n * V * 32 + n * 28,
+        "loss": px * 3 * 4 * 3,
+        "ntc_fwd": n * (12 + 16 + 28 + 28 + 64),
+        "ntc_bwd": n * (12 + 16 + 28 + 28 + 28 + 64),
+        "adam": (1647607 * 2 + 6592) * 30,
+    }.get(stage, 0)
+    achieved = bytes_ / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": stage, "achieved": achieved, "peak": hbm_gbs,
+            "unit": "GB/s", "frac": achieved / hbm_gbs, "traffic": None,
+            "algorithmic_bytes": bytes_, "ms": ms, "peak_source": src}
+
+
+def main():
+    args = parse()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,297 @@
+/*
+ * gs3.h -- C ABI of libgs3, the GB300 (sm_103a) kernels of one Stage-1
+ * training step of 3DGStream (arXiv 2403.01444): Neural Transformation Cache
+ * query (hash-grid encoding + tiny MLP, Section 4.1), transformation of the
+ * previous frame's Gaussians (Section 4.1), EWA projection with SH colour
+ * (Section 3.2, Eq. 2-3), tile binning + key sort, front-to-back alpha
+ * compositing (Section 3.2, Eq. 4), the L1 + D-SSIM loss (Eq. 6), the
+ * hand-written backward of all of them, and Adam (Suppl. A).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every function returns a gs_status (0 = GS_OK).  Invalid host arguments
+ *    return GS_ERR_INVALID_ARG before anything is launched; a failed launch
+ *    returns GS_ERR_CUDA (gs_last_error() gives the message).
+ *  - Array arguments are DEVICE pointers owned by the caller (allocated by
+ *    e.g. PyTorch).  The library never allocates or frees device memory;
+ *    scratch comes from a caller buffer sized by the matching *_workspace_size.
+ *    Struct arguments (gs_gaussians, gs_hashgrid, ...) are HOST structs whose
+ *    pointer fields are device pointers; they are read before the call returns.
+ *  - Every call is asynchronous on the given stream (a cudaStream_t; NULL is
+ *    the legacy default stream), takes no host synchronisation, and is safe to
+ *    capture in a CUDA graph.  Errors found on the device are written to a
+ *    caller-provided device word (d_err) and read at the caller's sync point.
+ *  - Layouts are row-major, FP32 unless stated.  N = number of Gaussians,
+ *    V = views in one launch, K = (sh_deg + 1)^2.  Images are planar
+ *    [V][3][H][W].  Per-(view, Gaussian) arrays are [V][N][...].
+ *  - Pixel (x, y) has its centre at (x + 0.5, y + 0.5).  Tiles are 16 x 16.
+ */
+#ifndef GS3_H
+#define GS3_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define GS_API __attribute__((visibility("default")))
+#else
+#define GS_API
+#endif
+
+typedef int gs_status;
+enum {
+    GS_OK = 0,
+    GS_ERR_INVALID_ARG = -1,
+    GS_ERR_CAPACITY = -2,   /* more tile intersections than the caller's buffers hold */
+    GS_ERR_CUDA = -3,
+    GS_ERR_TIMEOUT = -4,    /* a bounded device wait gave up */
+    GS_ERR_NONFINITE = -5
+};
+
+/* element types of typeless (void*) buffers */
+enum { GS_F32 = 0, GS_F16 = 1, GS_BF16 = 2, GS_NONE = 3 };
+
+typedef void *gs_stream; /* cudaStream_t */
+
+#define GS_TILE 16
+#define GS_MAX_VIEWS 64
+
+/* Gaussian set (Section 3.1, Eq. 1-2).  Device pointers. */
+typedef struct {
+    const float *mean;          /* [N][3] */
+    const float *quat;          /* [N][4] (w, x, y, z); normalised inside the projection */
+    const float *scale;         /* [N][3] positive scales (activation applied) */
+    const float *opacity_logit; /* [N]; opacity = sigmoid(logit) */
+    const float *sh;            /* [N][K][3] SH coefficients, degree sh_deg <= 3 */
+    int64_t n;
+    int32_t sh_deg;
+} gs_gaussians;
+
+/* Pinhole camera (OpenCV frame: +z forward, +y down). Passed as a DEVICE
+ * array [V] so that a captured graph reads the current views at replay. */
+typedef struct {
+    float viewmat[12]; /* world -> camera [R | t], row-major 3x4 */
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float campos[3];   /* camera centre in world coordinates */
+} gs_camera;
+
+/* Per-(view, Gaussian) projected records, device pointers, each [V][N][...]. */
+typedef struct {
+    float *mean2d;         /* [V][N][2] pixel coordinates */
+    float *conic_opacity;  /* [V][N][4] (A, B, C, opacity): inverse 2D covariance [[A,B],[B,C]] */
+    float *rgb;            /* [V][N][3] SH colour + 0.5, clamped at 0 */
+    float *depth;          /* [V][N] camera-space z */
+    int32_t *radius;       /* [V][N] ceil(3 sqrt(lambda_max)); 0 = culled */
+    int32_t *tiles_touched;/* [V][N] number of 16x16 tiles in the footprint rectangle */
+} gs_projected;
+
+/* Multi-resolution hash grid (Section 4.1; Suppl. A).  Level resolutions
+ * N_l = floor(n_min * b^l + 1e-6), b = exp((ln n_max - ln n_min) / (levels - 1)).
+ * Level l is a dense (N_l+1)^3 grid when that fits in 2^log2_table entries,
+ * else the I-NGP spatial hash.  Coordinates are normalised by the box aabb
+ * (min xyz, max xyz) and clamped to it.  Table layout: [entries][features]. */
+typedef struct {
+    int32_t levels;      /* L <= 16 */
+    int32_t features;    /* F == 2 */
+    int32_t log2_table;  /* log2 T */
+    int32_t n_min, n_max;
+    float aabb[6];
+} gs_hashgrid;
+
+/* MLP 32 -> 64 -> 64 -> 7, ReLU, no biases (Section 4.1 Eq. 5; Suppl. A).
+ * Weights are [out][in] row-major, concatenated W1 | W2 | W3 (6592 values). */
+enum { GS_MLP_FP32 = 0, GS_MLP_BF16 = 1 };
+typedef struct {
+    int32_t precision;   /* GS_MLP_FP32: SIMT FP32; GS_MLP_BF16: tcgen05 BF16 x BF16 -> FP32 */
+    const float *w_f32;  /* FP32 master weights (device) */
+    const void *w_bf16;  /* BF16 copy of the same layout (device), used when precision == BF16 */
+} gs_mlp;
+
+#define GS_MLP_IN 32
+#define GS_MLP_HIDDEN 64
+#define GS_MLP_OUT 7
+#define GS_MLP_PARAMS (64 * 32 + 64 * 64 + 7 * 64)
+
+/* Adam hyper-parameters (Suppl. A: lr 0.002). */
+typedef struct {
+    float lr, beta1, beta2, eps;
+} gs_adam;
+
+/* Training state kept in DEVICE memory, read and advanced by the kernels so a
+ * whole step needs no host round trip: dynamic loss scale, non-finite flag,
+ * number of applied Adam steps, clean steps since the last scale change. */
+typedef struct {
+    float loss_scale;
+    int32_t found_inf;
+    int32_t step;
+    int32_t clean_steps;
+} gs_train_state;
+
+/* ------------------------------------------------------------------ misc */
+
+/* Message of the last failing call in this thread ("" if none). */
+GS_API const char *gs_last_error(void);
+/* Library version, (major << 16) | minor. */
+GS_API int gs_version(void);
+/* Number of CUDA kernels this library has launched since it was loaded. */
+GS_API uint64_t gs_launch_count(void);
+
+/* ------------------------------------------------------------ projection */
+
+/* EWA projection and SH colour of every Gaussian into V views
+ * (Section 3.2, Eq. 2-3; colour Section 3.1).  Per (view, Gaussian):
+ *   t = R mu + t_w; cull if t_z <= 0.2
+ *   Sigma = R(q) diag(s)^2 R(q)^T; J = perspective Jacobian at t with
+ *   t_x/t_z, t_y/t_z clamped to 1.3x the half field of view
+ *   Sigma2d = J W Sigma W^T J^T + 0.3 I; cull if det <= 0
+ *   conic = Sigma2d^-1 (FP64 when the FP32 condition estimate exceeds 1e6)
+ *   radius = ceil(3 sqrt(lambda_max)), lambda_max = mid + sqrt(max(0.1, mid^2 - det))
+ *   mean2d = (fx t_x / t_z + cx, fy t_y / t_z + cy)
+ *   tile rect x in [floor((u - r)/16), floor((u + r + 15)/16)) clamped to the
+ *   image's tiles (same in y); an empty rect culls (radius = tiles_touched = 0)
+ *   rgb = max(0, sum_k Y_k(dir) sh_k + 0.5), dir = (mu - campos)/|mu - campos|
+ *   opacity = sigmoid(logit)
+ * All V views share width W and height H.  Overwrites every field of out. */
+GS_API gs_status gs_project(const gs_gaussians *g, const gs_camera *d_cams, int V, int W, int H,
+                     const gs_projected *out, gs_stream stream);
+
+/* Reverse of gs_project for mean and rotation (Section 4.1: in Stage 1 only
+ * the transformed mean and rotation receive gradients).  grads[V][N][8] holds
+ * dL/d(u, v, A, B, C, r, g, b) per (view, Gaussian) as written by
+ * gs_raster_bwd.  Overwrites d_mean[N][3] and d_quat[N][4] (gradient wrt the
+ * un-normalised input quaternion), summed over the V views. */
+GS_API gs_status gs_project_bwd(const gs_gaussians *g, const gs_camera *d_cams, int V, int W, int H,
+                         const float *grads, float *d_mean, float *d_quat, gs_stream stream);
+
+/* --------------------------------------------------------- binning + sort */
+
+/* Scratch bytes gs_bin_sort needs for n Gaussians, V views of W x H and room
+ * for `capacity` (Gaussian, tile) pairs. */
+GS_API size_t gs_bin_sort_workspace_size(int64_t n, int V, int W, int H, int64_t capacity);
+
+/* Tile binning and key sort (the tile pipeline of Section 3.2).  Every
+ * (view, Gaussian, tile of its rect) pair gets key = (view * tiles + tile) << 32
+ * | IEEE bits of its FP32 depth and value = Gaussian index; pairs are ordered by
+ * (key, value).  Writes vals[count] (sorted values), ranges[V * tiles][2]
+ * ([first, last+1) per tile, zeros when empty), *d_count (device int64) and,
+ * when keys != NULL, keys[count] (for checking).  Bit-exact and deterministic.
+ * If count > capacity, *d_err is set to GS_ERR_CAPACITY, nothing is written
+ * past capacity, and every range is empty; the caller regrows and reruns.
+ * ws: scratch of gs_bin_sort_workspace_size bytes, 256-byte aligned. */
+GS_API gs_status gs_bin_sort(const gs_projected *proj, int64_t n, int V, int W, int H, int64_t capacity,
+                      uint32_t *vals, uint32_t *ranges, uint64_t *keys, int64_t *d_count,
+                      int32_t *d_err, void *ws, size_t ws_bytes, gs_stream stream);
+
+/* ------------------------------------------------------------ compositing */
+
+/* Front-to-back alpha compositing (Section 3.2, Eq. 4), one 16x16 tile per
+ * block.  Per pixel, over its tile's sorted list: power = -(A dx^2 + C dy^2)/2
+ * - B dx dy with (dx, dy) = pixel centre - mean2d; skip if power > 0;
+ * alpha = min(0.99, opacity exp(power)); skip if alpha < 1/255; stop before a
+ * Gaussian that would take T below 1e-4; C += rgb alpha T; T *= 1 - alpha.
+ * Writes img[V][3][H][W] = C + T bg, T_final[V][H][W] and last[V][H][W] (1 +
+ * list position of the last Gaussian added, 0 if none). */
+GS_API gs_status gs_raster_fwd(const gs_projected *proj, int64_t n, int V, int W, int H, const float *bg,
+                        const uint32_t *vals, const uint32_t *ranges, float *img, float *T_final,
+                        int32_t *last, gs_stream stream);
+
+/* Reverse of gs_raster_fwd: walks each pixel's list back to front from
+ * `last`, recomputing T_i = T_{i+1} / (1 - alpha_i) from T_final (no per-pair
+ * state is stored).  Per-(view, Gaussian) gradients are reduced across each
+ * warp and each tile before one vector atomic per (Gaussian, tile).
+ * Overwrites grads[V][N][8] = dL/d(u, v, A, B, C, r, g, b) and, when non-NULL,
+ * d_opacity[V][N].  bg is a host array of 3 floats. */
+GS_API gs_status gs_raster_bwd(const gs_projected *proj, int64_t n, int V, int W, int H, const float *bg,
+                        const uint32_t *vals, const uint32_t *ranges, const float *T_final,
+                        const int32_t *last, const float *d_img, float *grads, float *d_opacity,
+                        gs_stream stream);
+
+/* ------------------------------------------------------------------- loss */
+
+GS_API size_t gs_loss_workspace_size(int planes, int H, int W);
+
+/* L = (1 - lambda) mean|I - I*| + lambda (1 - SSIM(I, I*)) (Eq. 6, lambda =
+ * 0.2), SSIM with an 11x11 Gaussian window (sigma 1.5), C1 = 0.01^2,
+ * C2 = 0.03^2, zero padding, mean over all planes and pixels.  img and target
+ * are [planes][H][W].  Writes d_img = dL/dI, *d_loss and, if non-NULL,
+ * *d_ssim (device floats). */
+GS_API gs_status gs_loss_l1_dssim(const float *img, const float *target, int planes, int H, int W,
+                           float lambda, float *d_img, float *d_loss, float *d_ssim, void *ws,
+                           size_t ws_bytes, gs_stream stream);
+
+/* ---------------------------------------------------- transformation cache */
+
+/* Number of table entries (rows) of the grid; < 0 on invalid arguments. */
+GS_API int64_t ntc_hashgrid_entries(const gs_hashgrid *grid);
+
+/* enc[n][L*F] = per level, trilinear interpolation of the 8 corner features
+ * around the normalised mean (Section 4.1).  table_dtype: GS_F16 or GS_F32;
+ * enc_dtype: GS_F32 or GS_BF16. */
+GS_API gs_status ntc_encode_fwd(const float *mean, int64_t n, const gs_hashgrid *grid, const void *table,
+                         int table_dtype, void *enc, int enc_dtype, gs_stream stream);
+
+/* d_table[entries][F] += trilinear-weighted scatter of d_enc[n][L*F]
+ * (FP32 atomics; the caller zeroes d_table between steps -- adam_step does). */
+GS_API gs_status ntc_encode_bwd(const float *mean, int64_t n, const gs_hashgrid *grid, const float *d_enc,
+                         float *d_table, gs_stream stream);
+
+/* raw7[n][7] = W3 relu(W2 relu(W1 enc)) (Section 4.1 Eq. 5).  enc_dtype
+ * GS_F32 or GS_BF16. */
+GS_API gs_status ntc_mlp_fwd(const void *enc, int enc_dtype, int64_t n, const gs_mlp *w, float *raw7,
+                      gs_stream stream);
+
+/* Reverse of ntc_mlp_fwd with d_raw7 multiplied by *d_scale (device float;
+ * NULL = 1): dW[6592] += sum over rows (FP32), d_enc[n][32] = dL/d enc
+ * (written when non-NULL). */
+GS_API gs_status ntc_mlp_bwd(const void *enc, int enc_dtype, int64_t n, const gs_mlp *w,
+                      const float *d_raw7, const float *d_scale, float *dW, float *d_enc,
+                      gs_stream stream);
+
+/* Transformation (Section 4.1): mean_out = mean + raw7[0:3];
+ * quat_out = norm(quat) x norm(raw7[3:7]) (order 0, the paper's product) or
+ * norm(raw7[3:7]) x norm(quat) (order 1); Hamilton product, (w, x, y, z);
+ * norm(v) = v / max(|v|, 1e-12).  Means outside grid->aabb are not moved and
+ * their rotation is only normalised (Suppl. A discards them). */
+GS_API gs_status ntc_apply(const float *mean, const float *quat, const float *raw7, int64_t n,
+                    const float *aabb, int order, float *mean_out, float *quat_out,
+                    gs_stream stream);
+
+/* Reverse of ntc_apply wrt raw7: overwrites d_raw7[n][7]. */
+GS_API gs_status ntc_apply_bwd(const float *mean, const float *quat, const float *raw7, int64_t n,
+                        const float *aabb, int order, const float *d_mean_out,
+                        const float *d_quat_out, float *d_raw7, gs_stream stream);
+
+/* Warm-up loss (Section 4.1 Eq. 7): mean over rows of |dmu|_1 - cos^2(norm(dq), (1,0,0,0)).
+ * Writes *d_loss (device float) and d_raw7[n][7] = dL/d raw7. */
+GS_API gs_status ntc_warmup_loss(const float *raw7, int64_t n, float *d_raw7, float *d_loss,
+                          gs_stream stream);
+
+/* ------------------------------------------------------------- optimiser */
+
+/* Sets d_state->found_inf = 1 if any of g[n] is not finite. */
+GS_API gs_status gs_check_finite(const float *g, int64_t n, gs_train_state *d_state, gs_stream stream);
+
+/* Bias-corrected Adam (Suppl. A) on p[n] with gradient g * (1 / loss_scale)
+ * and step number d_state->step + 1, skipped when d_state->found_inf is set.
+ * Zeroes g afterwards (ready for the next step's accumulation).  If shadow is
+ * non-NULL, writes the updated parameters converted to shadow_dtype (GS_F16 or
+ * GS_BF16).  All state (m, v) FP32, in place. */
+GS_API gs_status adam_step(float *p, float *g, float *m, float *v, int64_t n, const gs_adam *hp,
+                    const gs_train_state *d_state, void *shadow, int shadow_dtype,
+                    gs_stream stream);
+
+/* End of a step: on a non-finite gradient halve the loss scale and clear the
+ * flag; else count the step and double the scale after growth_interval clean
+ * steps (growth_interval <= 0 keeps the scale fixed). */
+GS_API gs_status gs_train_state_advance(gs_train_state *d_state, int growth_interval, gs_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS3_H */

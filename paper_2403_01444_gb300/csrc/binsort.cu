@@ -1,0 +1,532 @@
+// Tile binning and key sort (the tile pipeline of Section 3.2).
+//
+// The order required is that of the 64-bit key (view, tile, depth bits) with
+// ties by Gaussian index.  Instead of radix-sorting 64-bit keys of every
+// (Gaussian, tile) pair, the sort is split in two stable stages:
+//   1. the V*N (view, Gaussian) entries are sorted by (view, depth bits) --
+//      4 byte-digit passes on the FP32 depth bits plus one pass on the view;
+//   2. pairs are emitted in that order (each entry's tiles row-major) and
+//      stably sorted on the (view * tiles + tile) key alone, which needs
+//      ceil(log2(V * tiles) / 8) passes (2 for 4 views of 1352x1014).
+// Stage 2 keeps the depth order inside every tile, so the result equals the
+// full-key sort while moving 8 bytes per pair per pass over 2 passes instead
+// of 12 bytes over 6.  All passes are stable LSD byte passes of
+// reduce-then-scan form (histogram, one-block scan, ranked scatter): no
+// inter-block waits, deterministic output.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace gs3 {
+
+constexpr int RADIX = 256;
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_WARPS = SORT_THREADS / 32;
+constexpr int SORT_ITEMS = 16;
+constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;  // 4096 keys per block step
+constexpr int SORT_BLOCKS = kNumSMs * 4;              // fixed grid: n may live on the device
+constexpr int SCAN_THREADS = 1024;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+struct SortPass {
+    const uint32_t *kin, *vin;
+    uint32_t *kout, *vout;
+    const int64_t *d_n;  // device count (NULL: use n_host)
+    int64_t n_host;
+    int shift;
+    uint32_t div;        // != 0: digit = value / div (the view of a (view, Gaussian) entry)
+    uint32_t *hist;      // [RADIX][G]
+    int G;
+};
+
+__device__ __forceinline__ int64_t pass_n(const SortPass &s) { return s.d_n ? *s.d_n : s.n_host; }
+
+__device__ __forceinline__ void block_range(int64_t n, int G, int b, int64_t &beg, int64_t &end)
+{
+    int64_t tiles = (n + SORT_TILE - 1) / SORT_TILE;
+    int64_t per = (tiles + G - 1) / G;
+    beg = (int64_t)b * per * SORT_TILE;
+    end = min(n, beg + per * SORT_TILE);
+}
+
+__device__ __forceinline__ uint32_t digit_of(const SortPass &s, uint32_t k, uint32_t v)
+{
+    return s.div ? (v / s.div) : ((k >> s.shift) & (RADIX - 1));
+}
+
+__global__ void __launch_bounds__(SORT_THREADS) radix_hist_kernel(SortPass s)
+{
+    __shared__ uint32_t h[RADIX];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t beg, end;
+    block_range(pass_n(s), s.G, blockIdx.x, beg, end);
+    for (int64_t i = beg + threadIdx.x; i < end; i += SORT_THREADS) {
+        uint32_t d = s.div ? (s.vin[i] / s.div) : ((s.kin[i] >> s.shift) & (RADIX - 1));
+        atomicAdd(&h[d], 1u);
+    }
+    __syncthreads();
+    s.hist[threadIdx.x * s.G + blockIdx.x] = h[threadIdx.x];
+}
+
+// Exclusive scan, in place, of M u32 counters with one block.
+__global__ void __launch_bounds__(SCAN_THREADS) scan_u32_kernel(uint32_t *a, int M)
+{
+    __shared__ uint32_t s[SCAN_THREADS];
+    int per = (M + SCAN_THREADS - 1) / SCAN_THREADS;
+    int beg = threadIdx.x * per, end = min(M, beg + per);
+    uint32_t sum = 0;
+    for (int i = beg; i < end; ++i) sum += a[i];
+    s[threadIdx.x] = sum;
+    __syncthreads();
+    for (int o = 1; o < SCAN_THREADS; o <<= 1) {
+        uint32_t x = threadIdx.x >= o ? s[threadIdx.x - o] : 0u;
+        __syncthreads();
+        s[threadIdx.x] += x;
+        __syncthreads();
+    }
+    uint32_t run = s[threadIdx.x] - sum;
+    for (int i = beg; i < end; ++i) {
+        uint32_t x = a[i];
+        a[i] = run;
+        run += x;
+    }
+}
+
+__global__ void __launch_bounds__(SORT_THREADS) radix_scatter_kernel(SortPass s)
+{
+    __shared__ uint32_t s_off[RADIX];
+    __shared__ uint32_t s_tot[RADIX];
+    __shared__ uint32_t s_wh[SORT_WARPS][RADIX];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    int64_t beg, end;
+    block_range(pass_n(s), s.G, blockIdx.x, beg, end);
+    s_off[tid] = s.hist[tid * s.G + blockIdx.x];
+    for (int64_t t0 = beg; t0 < end; t0 += SORT_TILE) {
+        for (int k = tid; k < SORT_WARPS * RADIX; k += SORT_THREADS) (&s_wh[0][0])[k] = 0u;
+        __syncthreads();
+        uint32_t key[SORT_ITEMS], val[SORT_ITEMS], rank[SORT_ITEMS], dig[SORT_ITEMS];
+#pragma unroll
+        for (int j = 0; j < SORT_ITEMS; ++j) {
+            int64_t idx = t0 + (int64_t)warp * 32 * SORT_ITEMS + j * 32 + lane;
+            bool ok = idx < end;
+            key[j] = ok ? s.kin[idx] : 0u;
+            val[j] = ok ? s.vin[idx] : 0u;
+            uint32_t d = ok ? digit_of(s, key[j], val[j]) : (uint32_t)RADIX;
+            dig[j] = d;
+            unsigned peers = __match_any_sync(0xffffffffu, d);
+            uint32_t before = 0;
+            if (ok) before = s_wh[warp][d];
+            __syncwarp();
+            if (ok && lane == __ffs(peers) - 1) s_wh[warp][d] = before + __popc(peers);
+            __syncwarp();
+            rank[j] = before + __popc(peers & lt);
+        }
+        __syncthreads();
+        {
+            uint32_t run = 0;
+#pragma unroll
+            for (int w = 0; w < SORT_WARPS; ++w) {
+                uint32_t c = s_wh[w][tid];
+                s_wh[w][tid] = run;
+                run += c;
+            }
+            s_tot[tid] = run;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < SORT_ITEMS; ++j) {
+            uint32_t d = dig[j];
+            if (d < RADIX) {
+                uint32_t pos = s_off[d] + s_wh[warp][d] + rank[j];
+                s.kout[pos] = key[j];
+                s.vout[pos] = val[j];
+            }
+        }
+        __syncthreads();
+        s_off[tid] += s_tot[tid];
+    }
+}
+
+// ---------------------------------------------------------------- stage 1
+__global__ void depth_keys_kernel(const float *depth, const int32_t *radius, int64_t NV,
+                                  uint32_t *k, uint32_t *v)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NV) return;
+    // positive depths: IEEE bits are monotone; culled entries go last
+    k[i] = radius[i] > 0 ? __float_as_uint(depth[i]) : 0xffffffffu;
+    v[i] = (uint32_t)i;
+}
+
+// Number of tiles of every entry, in the sorted order (same rectangle rule as
+// the emission below and as gs_project's tiles_touched).
+__global__ void sorted_counts_kernel(const uint32_t *svals, const float2 *mean2d,
+                                     const int32_t *radius, int64_t NV, int tx, int ty,
+                                     int32_t *cnt)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NV) return;
+    uint32_t sv = svals[i];
+    int r = radius[sv];
+    int c = 0;
+    if (r > 0) {
+        float2 m = mean2d[sv];
+        int x0, y0, x1, y1;
+        tile_rect(m.x, m.y, r, tx, ty, x0, y0, x1, y1);
+        c = (x1 - x0) * (y1 - y0);
+    }
+    cnt[i] = c;
+}
+
+// ------------------------------------------------- scan of tile counts
+__device__ __forceinline__ int64_t block_scan_i64(int64_t x, int64_t *s_warp, int64_t &total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        s_warp[lane] = w;
+    }
+    __syncthreads();
+    int64_t before = warp > 0 ? s_warp[warp - 1] : 0;
+    total = s_warp[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before + inc - x;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) count_reduce_kernel(const int32_t *cnt, int64_t NV,
+                                                                    int64_t *bsum)
+{
+    __shared__ int64_t s_warp[32];
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+    int64_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k)
+        if (base + k < NV) sum += cnt[base + k];
+    int64_t total;
+    block_scan_i64(sum, s_warp, total);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+// Exclusive scan of the block sums; total count, capacity check, n_eff.
+__global__ void __launch_bounds__(SCAN_THREADS) count_top_kernel(int64_t *bsum, int nb,
+                                                                 int64_t capacity, int64_t *d_count,
+                                                                 int64_t *n_eff, int32_t *d_err)
+{
+    __shared__ int64_t s_warp[32];
+    int per = (nb + SCAN_THREADS - 1) / SCAN_THREADS;
+    int beg = threadIdx.x * per, end = min(nb, beg + per);
+    int64_t sum = 0;
+    for (int i = beg; i < end; ++i) sum += bsum[i];
+    int64_t total;
+    int64_t run = block_scan_i64(sum, s_warp, total);
+    for (int i = beg; i < end; ++i) {
+        int64_t x = bsum[i];
+        bsum[i] = run;
+        run += x;
+    }
+    if (threadIdx.x == 0) {
+        *d_count = total;
+        bool fits = total <= capacity;
+        *n_eff = fits ? total : 0;
+        if (!fits && d_err) atomicCAS(d_err, 0, (int32_t)GS_ERR_CAPACITY);
+    }
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) count_down_kernel(const int32_t *cnt, int64_t NV,
+                                                                  const int64_t *bsum,
+                                                                  int64_t *offsets)
+{
+    __shared__ int64_t s_warp[32];
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+    int64_t c[SCAN_ITEMS];
+    int64_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        c[k] = (base + k < NV) ? cnt[base + k] : 0;
+        sum += c[k];
+    }
+    int64_t total;
+    int64_t run = block_scan_i64(sum, s_warp, total) + bsum[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        if (base + k < NV) offsets[base + k] = run;
+        run += c[k];
+    }
+}
+
+// ------------------------------------------------------------- emission
+struct EmitParams {
+    const uint32_t *svals;  // sorted (view, Gaussian) entries: view * n + g
+    const int64_t *offsets;
+    const int64_t *n_eff;
+    const float2 *mean2d;
+    const int32_t *radius;
+    int64_t NV, n;
+    int tx, ty, tiles;
+    uint32_t *tkeys, *tvals;
+};
+
+// A warp's 32 consecutive entries own one contiguous output range; lanes
+// stride over it so the key/value stores are coalesced.
+__global__ void __launch_bounds__(256) emit_kernel(EmitParams e)
+{
+    if (*e.n_eff == 0) return;  // nothing to emit, or over capacity
+    const int lane = threadIdx.x & 31;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool ok = i < e.NV;
+    uint32_t sv = ok ? e.svals[i] : 0u;
+    int64_t off = ok ? e.offsets[i] : 0;
+    int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
+    if (ok) {
+        int r = e.radius[sv];
+        if (r > 0) {
+            float2 m = e.mean2d[sv];
+            tile_rect(m.x, m.y, r, e.tx, e.ty, x0, y0, x1, y1);
+        }
+    }
+    int w = x1 - x0;
+    int64_t cnt = (int64_t)w * (y1 - y0);
+    unsigned okmask = __ballot_sync(0xffffffffu, ok);
+    if (okmask == 0u) return;  // warp-uniform: the whole warp is past the end
+    int lastl = 31 - __clz(okmask);
+    // lanes past the end take the warp's end offset so offsets stay monotone
+    int64_t wend = __shfl_sync(0xffffffffu, off + cnt, lastl);
+    if (!ok) off = wend;
+    int64_t wbeg = __shfl_sync(0xffffffffu, off, 0);
+    uint32_t view = sv / (uint32_t)e.n;
+    uint32_t g = sv - view * (uint32_t)e.n;
+    uint32_t kbase = view * (uint32_t)e.tiles;
+    int64_t span = wend - wbeg;
+    for (int64_t k0 = 0; k0 < span; k0 += 32) {
+        int64_t o = wbeg + k0 + lane;
+        int src = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            int cand = src + step;
+            int64_t oc = __shfl_sync(0xffffffffu, off, cand);
+            if (oc <= o) src = cand;
+        }
+        int64_t so = __shfl_sync(0xffffffffu, off, src);
+        int sw = __shfl_sync(0xffffffffu, w, src);
+        int sx = __shfl_sync(0xffffffffu, x0, src);
+        int sy = __shfl_sync(0xffffffffu, y0, src);
+        uint32_t sk = __shfl_sync(0xffffffffu, kbase, src);
+        uint32_t sg = __shfl_sync(0xffffffffu, g, src);
+        if (o < wend) {
+            int local = (int)(o - so);
+            int ty = sy + local / sw;
+            int tx = sx + local - (local / sw) * sw;
+            e.tkeys[o] = sk + (uint32_t)(ty * e.tx + tx);
+            e.tvals[o] = sg;
+        }
+    }
+}
+
+__global__ void ranges_kernel(const uint32_t *tk, const int64_t *n_eff, uint32_t *ranges)
+{
+    int64_t n = *n_eff;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t k = tk[i];
+        if (i == 0 || tk[i - 1] != k) ranges[2 * (int64_t)k] = (uint32_t)i;
+        if (i == n - 1 || tk[i + 1] != k) ranges[2 * (int64_t)k + 1] = (uint32_t)(i + 1);
+    }
+}
+
+__global__ void keys64_kernel(const uint32_t *tk, const uint32_t *vals, const int64_t *n_eff,
+                              const float *depth, int64_t n, int tiles, uint64_t *keys)
+{
+    int64_t cnt = *n_eff;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t k = tk[i];
+        int64_t view = k / (uint32_t)tiles;
+        uint32_t db = __float_as_uint(depth[view * n + vals[i]]);
+        keys[i] = ((uint64_t)k << 32) | db;
+    }
+}
+
+// ------------------------------------------------------------- workspace
+struct BinWs {
+    uint32_t *dk[2], *dv[2];
+    int64_t *offsets, *bsum;
+    int32_t *cnt;
+    uint32_t *hist;
+    int64_t *n_eff;
+    uint32_t *tk[2], *tv;
+    size_t bytes;
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+static BinWs carve(void *base, int64_t NV, int64_t cap)
+{
+    BinWs w{};
+    char *p = reinterpret_cast<char *>(base);
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        char *r = p ? p + o : nullptr;
+        o += align256(bytes);
+        return r;
+    };
+    for (int k = 0; k < 2; ++k) w.dk[k] = reinterpret_cast<uint32_t *>(take(4 * NV));
+    for (int k = 0; k < 2; ++k) w.dv[k] = reinterpret_cast<uint32_t *>(take(4 * NV));
+    w.offsets = reinterpret_cast<int64_t *>(take(8 * (NV + 1)));
+    w.cnt = reinterpret_cast<int32_t *>(take(4 * NV));
+    w.bsum = reinterpret_cast<int64_t *>(take(8 * (ceil_div(NV, SCAN_TILE) + 1)));
+    w.hist = reinterpret_cast<uint32_t *>(take(4 * RADIX * SORT_BLOCKS));
+    w.n_eff = reinterpret_cast<int64_t *>(take(64));
+    for (int k = 0; k < 2; ++k) w.tk[k] = reinterpret_cast<uint32_t *>(take(4 * cap));
+    w.tv = reinterpret_cast<uint32_t *>(take(4 * cap));
+    w.bytes = o;
+    return w;
+}
+
+static gs_status run_pass(SortPass s, int64_t grid_items_hint, cudaStream_t st)
+{
+    (void)grid_items_hint;
+    note_launch();
+    radix_hist_kernel<<<s.G, SORT_THREADS, 0, st>>>(s);
+    note_launch();
+    scan_u32_kernel<<<1, SCAN_THREADS, 0, st>>>(s.hist, RADIX * s.G);
+    note_launch();
+    radix_scatter_kernel<<<s.G, SORT_THREADS, 0, st>>>(s);
+    return launch_status("radix pass");
+}
+
+}  // namespace gs3
+
+using namespace gs3;
+
+extern "C" size_t gs_bin_sort_workspace_size(int64_t n, int V, int W, int H, int64_t capacity)
+{
+    (void)W;
+    (void)H;
+    if (n < 0 || V < 1 || capacity < 0) return 0;
+    return carve(nullptr, n * V, capacity).bytes;
+}
+
+extern "C" gs_status gs_bin_sort(const gs_projected *proj, int64_t n, int V, int W, int H,
+                                 int64_t capacity, uint32_t *vals, uint32_t *ranges, uint64_t *keys,
+                                 int64_t *d_count, int32_t *d_err, void *ws, size_t ws_bytes,
+                                 gs_stream stream)
+{
+    GS_REQUIRE(proj && vals && ranges && d_count && ws, "gs_bin_sort: null argument");
+    GS_REQUIRE(n >= 0 && V >= 1 && V <= GS_MAX_VIEWS, "gs_bin_sort: bad n or V");
+    GS_REQUIRE(W > 0 && H > 0 && W <= 16384 && H <= 16384, "gs_bin_sort: bad image size");
+    GS_REQUIRE(n * V < (int64_t(1) << 32) - 1, "gs_bin_sort: n * V must fit in 32 bits");
+    GS_REQUIRE(capacity >= 0 && capacity < (int64_t(1) << 32) - 1,
+               "gs_bin_sort: capacity must fit in 32 bits");
+    GS_REQUIRE(aligned(ws, 256), "gs_bin_sort: workspace must be 256-byte aligned");
+    const int64_t NV = n * V;
+    BinWs w = carve(ws, NV, capacity);
+    GS_REQUIRE(ws_bytes >= w.bytes, "gs_bin_sort: workspace too small (%zu < %zu)", ws_bytes,
+               w.bytes);
+    cudaStream_t st = as_stream(stream);
+    const int tx = tiles_x_of(W), ty = tiles_y_of(H);
+    const int tiles = tx * ty;
+    const int64_t nkeys = (int64_t)V * tiles;
+    cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * nkeys, st);
+    if (NV == 0) {
+        cudaMemsetAsync(d_count, 0, sizeof(int64_t), st);
+        return launch_status("gs_bin_sort");
+    }
+    // ---- stage 1: (view, depth) order of the V*N entries
+    note_launch();
+    depth_keys_kernel<<<(int)ceil_div(NV, 256), 256, 0, st>>>(proj->depth, proj->radius, NV,
+                                                              w.dk[0], w.dv[0]);
+    int cur = 0;
+    int Gd = (int)std::min<int64_t>(SORT_BLOCKS, ceil_div(NV, SORT_TILE));
+    for (int pass = 0; pass < 4 + (V > 1 ? 1 : 0); ++pass) {
+        SortPass s{};
+        s.kin = w.dk[cur];
+        s.vin = w.dv[cur];
+        s.kout = w.dk[cur ^ 1];
+        s.vout = w.dv[cur ^ 1];
+        s.d_n = nullptr;
+        s.n_host = NV;
+        s.shift = pass < 4 ? 8 * pass : 0;
+        s.div = pass < 4 ? 0u : (uint32_t)n;
+        s.hist = w.hist;
+        s.G = Gd;
+        gs_status e = run_pass(s, NV, st);
+        if (e != GS_OK) return e;
+        cur ^= 1;
+    }
+    const uint32_t *svals = w.dv[cur];
+    // ---- offsets of every entry's pairs in that order
+    int nb = (int)ceil_div(NV, SCAN_TILE);
+    note_launch();
+    sorted_counts_kernel<<<(int)ceil_div(NV, 256), 256, 0, st>>>(
+        svals, reinterpret_cast<const float2 *>(proj->mean2d), proj->radius, NV, tx, ty, w.cnt);
+    note_launch();
+    count_reduce_kernel<<<nb, SCAN_THREADS, 0, st>>>(w.cnt, NV, w.bsum);
+    note_launch();
+    count_top_kernel<<<1, SCAN_THREADS, 0, st>>>(w.bsum, nb, capacity, d_count, w.n_eff, d_err);
+    note_launch();
+    count_down_kernel<<<nb, SCAN_THREADS, 0, st>>>(w.cnt, NV, w.bsum, w.offsets);
+    // ---- stage 2: emit pairs, stable sort on the tile key
+    int bits = 0;
+    while ((int64_t(1) << bits) < nkeys) ++bits;
+    int passes = (bits + 7) / 8;
+    EmitParams ep{};
+    ep.svals = svals;
+    ep.offsets = w.offsets;
+    ep.n_eff = w.n_eff;
+    ep.mean2d = reinterpret_cast<const float2 *>(proj->mean2d);
+    ep.radius = proj->radius;
+    ep.NV = NV;
+    ep.n = n;
+    ep.tx = tx;
+    ep.ty = ty;
+    ep.tiles = tiles;
+    ep.tkeys = w.tk[0];
+    ep.tvals = (passes % 2 == 0) ? vals : w.tv;
+    note_launch();
+    emit_kernel<<<(int)ceil_div(NV, 256), 256, 0, st>>>(ep);
+    gs_status e = launch_status("gs_bin_sort emit");
+    if (e != GS_OK) return e;
+    int kc = 0;
+    uint32_t *vcur = ep.tvals;
+    for (int pass = 0; pass < passes; ++pass) {
+        SortPass s{};
+        s.kin = w.tk[kc];
+        s.vin = vcur;
+        s.kout = w.tk[kc ^ 1];
+        s.vout = (vcur == vals) ? w.tv : vals;
+        s.d_n = w.n_eff;
+        s.n_host = 0;
+        s.shift = 8 * pass;
+        s.div = 0;
+        s.hist = w.hist;
+        s.G = SORT_BLOCKS;
+        e = run_pass(s, 0, st);
+        if (e != GS_OK) return e;
+        kc ^= 1;
+        vcur = s.vout;
+    }
+    note_launch();
+    ranges_kernel<<<kNumSMs * 8, 256, 0, st>>>(w.tk[kc], w.n_eff, ranges);
+    if (keys) {
+        note_launch();
+        keys64_kernel<<<kNumSMs * 8, 256, 0, st>>>(w.tk[kc], vals, w.n_eff, proj->depth, n, tiles,
+                                                   keys);
+    }
+    return launch_status("gs_bin_sort");
+}

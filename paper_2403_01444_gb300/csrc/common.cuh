@@ -1,0 +1,85 @@
+// Shared device/host helpers of libgs3 (status handling, launch checks).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <atomic>
+
+#include "../../include/gs3.h"
+
+namespace gs3 {
+
+// Thread-local message of the last failing call.
+void set_error(const char *fmt, ...);
+
+// Number of kernels this library has launched (all threads).
+inline std::atomic<uint64_t> &launch_counter()
+{
+    static std::atomic<uint64_t> c{0};
+    return c;
+}
+inline void note_launch() { launch_counter().fetch_add(1, std::memory_order_relaxed); }
+
+inline gs_status launch_status(const char *what)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error("%s: %s", what, cudaGetErrorString(e));
+        return GS_ERR_CUDA;
+    }
+    return GS_OK;
+}
+
+#define GS_REQUIRE(cond, ...)                                                                     \
+    do {                                                                                          \
+        if (!(cond)) {                                                                            \
+            ::gs3::set_error(__VA_ARGS__);                                                        \
+            return GS_ERR_INVALID_ARG;                                                            \
+        }                                                                                         \
+    } while (0)
+
+inline cudaStream_t as_stream(gs_stream s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+inline int tiles_x_of(int W) { return (W + GS_TILE - 1) / GS_TILE; }
+inline int tiles_y_of(int H) { return (H + GS_TILE - 1) / GS_TILE; }
+
+constexpr int kNumSMs = 152;  // GB300: 2 dies x 76 SMs
+
+// ------------------------------------------------------------------ device
+// Tile rectangle of a footprint: x in [floor((u - r)/16), floor((u + r + 15)/16)),
+// clamped to [0, tx].  floor(u - r) is taken exactly as floor of the
+// round-down FP32 difference (exact while |floor(u - r)| < 2^24), so the
+// result equals the real-number definition for any FP32 u.
+__device__ __forceinline__ int floor_div16_of_sum(float u, float r_signed)
+{
+    float s = r_signed < 0.f ? __fsub_rd(u, -r_signed) : __fadd_rd(u, r_signed);
+    s = fminf(fmaxf(s, -1.0e9f), 1.0e9f);
+    int f = (int)floorf(s);
+    return f >> 4;  // arithmetic shift: floor division by 16
+}
+
+__device__ __forceinline__ void tile_rect(float u, float v, int r, int tx, int ty, int &x0, int &y0,
+                                          int &x1, int &y1)
+{
+    x0 = min(tx, max(0, floor_div16_of_sum(u, -(float)r)));
+    x1 = min(tx, max(0, floor_div16_of_sum(u, (float)(r + GS_TILE - 1))));
+    y0 = min(ty, max(0, floor_div16_of_sum(v, -(float)r)));
+    y1 = min(ty, max(0, floor_div16_of_sum(v, (float)(r + GS_TILE - 1))));
+}
+
+__device__ __forceinline__ float warp_sum(float x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+}  // namespace gs3

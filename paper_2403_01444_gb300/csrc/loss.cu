@@ -1,0 +1,270 @@
+// L1 + D-SSIM loss and its gradient (Section 4.1, Eq. 6).
+// Pass 1 filters (x, y, x^2, y^2, xy) with the separable 11x11 Gaussian window
+// through shared memory, forms the SSIM map and the three per-pixel
+// coefficients of its derivative wrt (mu_x, E[x^2], E[xy]); pass 2 filters
+// those coefficients (the window is symmetric, so the adjoint is the same
+// filter) and assembles dL/dI; pass 3 reduces the block partial sums in FP64.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace gs3 {
+
+constexpr int LT = 32;          // output tile side
+constexpr int LH = 5;           // window half-width
+constexpr int LS = LT + 2 * LH; // staged tile side (42)
+constexpr int LTHREADS = 256;
+
+// Normalised 11-tap Gaussian window (sigma 1.5), built by each block in
+// shared memory (no constant-memory upload, so the call is capture-safe).
+__device__ __forceinline__ void build_window(float *w)
+{
+    if (threadIdx.x < 11) {
+        float s = 0.f;
+        for (int i = 0; i < 11; ++i) s += expf(-(float)((i - 5) * (i - 5)) / 4.5f);
+        int i = threadIdx.x;
+        w[i] = expf(-(float)((i - 5) * (i - 5)) / 4.5f) / s;
+    }
+}
+
+struct LossParams {
+    const float *x, *y;
+    int P, H, W;
+    float lam;
+    float *ca, *cb, *cc;  // per-pixel derivative coefficients
+    double *partial;      // [blocks][2]: sum of SSIM map, sum |x - y|
+    float *d_img;
+    float *d_loss, *d_ssim;
+    int nblocks;
+};
+
+__global__ void __launch_bounds__(LTHREADS) ssim_fwd_kernel(LossParams p)
+{
+    __shared__ float sx[LS][LS + 1], sy[LS][LS + 1];
+    __shared__ float hs[5][LS][LT + 1];
+    __shared__ double red[2][LTHREADS / 32];
+    __shared__ float c_win[11];
+    build_window(c_win);
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * LT, y0 = blockIdx.y * LT, pl = blockIdx.z;
+    const int64_t HW = (int64_t)p.H * p.W;
+    const float *X = p.x + pl * HW, *Y = p.y + pl * HW;
+    for (int i = tid; i < LS * LS; i += LTHREADS) {
+        int r = i / LS, c = i % LS;
+        int gy = y0 - LH + r, gx = x0 - LH + c;
+        bool in = gy >= 0 && gy < p.H && gx >= 0 && gx < p.W;
+        int64_t o = (int64_t)gy * p.W + gx;
+        sx[r][c] = in ? X[o] : 0.f;
+        sy[r][c] = in ? Y[o] : 0.f;
+    }
+    __syncthreads();
+    for (int i = tid; i < LS * LT; i += LTHREADS) {
+        int r = i / LT, c = i % LT;
+        float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, m4 = 0.f;
+#pragma unroll
+        for (int k = 0; k < 11; ++k) {
+            float a = sx[r][c + k], b = sy[r][c + k], w = c_win[k];
+            m0 = fmaf(w, a, m0);
+            m1 = fmaf(w, b, m1);
+            m2 = fmaf(w, a * a, m2);
+            m3 = fmaf(w, b * b, m3);
+            m4 = fmaf(w, a * b, m4);
+        }
+        hs[0][r][c] = m0;
+        hs[1][r][c] = m1;
+        hs[2][r][c] = m2;
+        hs[3][r][c] = m3;
+        hs[4][r][c] = m4;
+    }
+    __syncthreads();
+    const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
+    double ssum = 0.0, lsum = 0.0;
+    const int c = tid % LT;
+    for (int r = tid / LT; r < LT; r += LTHREADS / LT) {
+        int gy = y0 + r, gx = x0 + c;
+        if (gy >= p.H || gx >= p.W) continue;
+        float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
+#pragma unroll
+        for (int k = 0; k < 11; ++k) {
+            float w = c_win[k];
+            mx = fmaf(w, hs[0][r + k][c], mx);
+            my = fmaf(w, hs[1][r + k][c], my);
+            exx = fmaf(w, hs[2][r + k][c], exx);
+            eyy = fmaf(w, hs[3][r + k][c], eyy);
+            exy = fmaf(w, hs[4][r + k][c], exy);
+        }
+        float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
+        float n1 = 2.f * mx * my + C1, n2 = 2.f * sxy + C2;
+        float d1 = mx * mx + my * my + C1, d2 = sxx + syy + C2;
+        float idd = 1.f / (d1 * d2);
+        float s = n1 * n2 * idd;
+        float ds_dmx = 2.f * my * n2 * idd - s * 2.f * mx / d1;
+        float ds_dsxx = -s / d2;
+        float ds_dsxy = 2.f * n1 * idd;
+        int64_t o = pl * HW + (int64_t)gy * p.W + gx;
+        p.ca[o] = ds_dmx - 2.f * mx * ds_dsxx - my * ds_dsxy;
+        p.cb[o] = ds_dsxx;
+        p.cc[o] = ds_dsxy;
+        ssum += (double)s;
+        lsum += (double)fabsf(sx[r + LH][c + LH] - sy[r + LH][c + LH]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ssum += __shfl_xor_sync(0xffffffffu, ssum, o);
+        lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    }
+    if ((tid & 31) == 0) {
+        red[0][tid >> 5] = ssum;
+        red[1][tid >> 5] = lsum;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < LTHREADS / 32; ++w) {
+            a += red[0][w];
+            b += red[1][w];
+        }
+        int64_t bid = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        p.partial[2 * bid] = a;
+        p.partial[2 * bid + 1] = b;
+    }
+}
+
+__global__ void __launch_bounds__(LTHREADS) ssim_bwd_kernel(LossParams p)
+{
+    __shared__ float sa[LS][LS + 1], sb[LS][LS + 1], sc[LS][LS + 1];
+    __shared__ float hs[3][LS][LT + 1];
+    __shared__ float c_win[11];
+    build_window(c_win);
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * LT, y0 = blockIdx.y * LT, pl = blockIdx.z;
+    const int64_t HW = (int64_t)p.H * p.W;
+    for (int i = tid; i < LS * LS; i += LTHREADS) {
+        int r = i / LS, c = i % LS;
+        int gy = y0 - LH + r, gx = x0 - LH + c;
+        bool in = gy >= 0 && gy < p.H && gx >= 0 && gx < p.W;
+        int64_t o = pl * HW + (int64_t)gy * p.W + gx;
+        sa[r][c] = in ? p.ca[o] : 0.f;
+        sb[r][c] = in ? p.cb[o] : 0.f;
+        sc[r][c] = in ? p.cc[o] : 0.f;
+    }
+    __syncthreads();
+    for (int i = tid; i < LS * LT; i += LTHREADS) {
+        int r = i / LT, c = i % LT;
+        float m0 = 0.f, m1 = 0.f, m2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < 11; ++k) {
+            float w = c_win[k];
+            m0 = fmaf(w, sa[r][c + k], m0);
+            m1 = fmaf(w, sb[r][c + k], m1);
+            m2 = fmaf(w, sc[r][c + k], m2);
+        }
+        hs[0][r][c] = m0;
+        hs[1][r][c] = m1;
+        hs[2][r][c] = m2;
+    }
+    __syncthreads();
+    const float invM = 1.f / (float)((double)p.P * (double)HW);
+    const int c = tid % LT;
+    for (int r = tid / LT; r < LT; r += LTHREADS / LT) {
+        int gy = y0 + r, gx = x0 + c;
+        if (gy >= p.H || gx >= p.W) continue;
+        float fa = 0.f, fb = 0.f, fc = 0.f;
+#pragma unroll
+        for (int k = 0; k < 11; ++k) {
+            float w = c_win[k];
+            fa = fmaf(w, hs[0][r + k][c], fa);
+            fb = fmaf(w, hs[1][r + k][c], fb);
+            fc = fmaf(w, hs[2][r + k][c], fc);
+        }
+        int64_t o = pl * HW + (int64_t)gy * p.W + gx;
+        float xv = p.x[o], yv = p.y[o];
+        float diff = xv - yv;
+        float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
+        float dssim = fa + 2.f * xv * fb + yv * fc;
+        p.d_img[o] = ((1.f - p.lam) * sgn - p.lam * dssim) * invM;
+    }
+}
+
+__global__ void __launch_bounds__(1024) loss_final_kernel(LossParams p)
+{
+    __shared__ double red[2][32];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < p.nblocks; i += blockDim.x) {
+        a += p.partial[2 * i];
+        b += p.partial[2 * i + 1];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = a;
+        red[1][threadIdx.x >> 5] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sa = 0.0, sb = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            sa += red[0][w];
+            sb += red[1][w];
+        }
+        double M = (double)p.P * p.H * p.W;
+        double ssim = sa / M;
+        double loss = (1.0 - p.lam) * sb / M + p.lam * (1.0 - ssim);
+        *p.d_loss = (float)loss;
+        if (p.d_ssim) *p.d_ssim = (float)ssim;
+    }
+}
+
+static size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace gs3
+
+using namespace gs3;
+
+extern "C" size_t gs_loss_workspace_size(int planes, int H, int W)
+{
+    if (planes <= 0 || H <= 0 || W <= 0) return 0;
+    size_t px = (size_t)planes * H * W;
+    size_t nb = (size_t)ceil_div(W, LT) * ceil_div(H, LT) * planes;
+    return 3 * a256(4 * px) + a256(16 * nb);
+}
+
+extern "C" gs_status gs_loss_l1_dssim(const float *img, const float *target, int planes, int H,
+                                      int W, float lambda, float *d_img, float *d_loss,
+                                      float *d_ssim, void *ws, size_t ws_bytes, gs_stream stream)
+{
+    GS_REQUIRE(img && target && d_img && d_loss && ws, "gs_loss_l1_dssim: null argument");
+    GS_REQUIRE(planes > 0 && H > 0 && W > 0 && planes <= 65535, "gs_loss_l1_dssim: bad shape");
+    GS_REQUIRE(ws_bytes >= gs_loss_workspace_size(planes, H, W),
+               "gs_loss_l1_dssim: workspace too small");
+    GS_REQUIRE(aligned(ws, 256), "gs_loss_l1_dssim: workspace must be 256-byte aligned");
+    LossParams p{};
+    p.x = img;
+    p.y = target;
+    p.P = planes;
+    p.H = H;
+    p.W = W;
+    p.lam = lambda;
+    size_t px = (size_t)planes * H * W;
+    char *b = reinterpret_cast<char *>(ws);
+    p.ca = reinterpret_cast<float *>(b);
+    p.cb = reinterpret_cast<float *>(b + a256(4 * px));
+    p.cc = reinterpret_cast<float *>(b + 2 * a256(4 * px));
+    p.partial = reinterpret_cast<double *>(b + 3 * a256(4 * px));
+    p.d_img = d_img;
+    p.d_loss = d_loss;
+    p.d_ssim = d_ssim;
+    dim3 grid((unsigned)ceil_div(W, LT), (unsigned)ceil_div(H, LT), (unsigned)planes);
+    p.nblocks = (int)(grid.x * grid.y * grid.z);
+    cudaStream_t s = as_stream(stream);
+    note_launch();
+    ssim_fwd_kernel<<<grid, LTHREADS, 0, s>>>(p);
+    note_launch();
+    ssim_bwd_kernel<<<grid, LTHREADS, 0, s>>>(p);
+    note_launch();
+    loss_final_kernel<<<1, 1024, 0, s>>>(p);
+    return launch_status("gs_loss_l1_dssim");
+}

@@ -1,0 +1,310 @@
+"""Stage-1 training engine: device buffers and the kernel sequence of one
+training iteration of the Neural Transformation Cache (Section 4.1), the
+plain direct-optimisation comparator (Section 5.3, "Direct Opt."), the
+warm-up (Eq. 7) and a render helper.  All computation happens in libgs3;
+this module owns buffers, streams and the order of calls.
+"""
+from __future__ import annotations
+
+import math
+from typing import List, Optional
+
+import numpy as np
+import torch
+
+from . import gs3
+from .gs3 import Gaussians, Projected
+
+LAMBDA_DSSIM = 0.2          # Eq. 6
+NTC_LR = 0.002              # Suppl. A
+ADAM_BETAS = (0.9, 0.99)    # I-NGP's Adam constants (the paper's NTC follows I-NGP)
+ADAM_EPS = 1e-15
+
+
+def _i32(*shape, device="cuda"):
+    return torch.zeros(*shape, dtype=torch.int32, device=device)
+
+
+def _f32(*shape, device="cuda"):
+    return torch.zeros(*shape, dtype=torch.float32, device=device)
+
+
+class Rasterizer:
+    """Projection + binning + compositing (+ reverse) for V views of W x H."""
+
+    def __init__(self, n: int, V: int, W: int, H: int, capacity: int, device="cuda",
+                 bg=(0.0, 0.0, 0.0)):
+        self.n, self.V, self.W, self.H = n, V, W, H
+        self.device = device
+        self.bg = tuple(float(x) for x in bg)
+        self.tiles = math.ceil(W / gs3.TILE) * math.ceil(H / gs3.TILE)
+        self.proj = Projected.empty(V, n, device)
+        self.ranges = _i32(V * self.tiles, 2, device=device)
+        self.d_count = torch.zeros(1, dtype=torch.int64, device=device)
+        self.d_err = _i32(1, device=device)
+        self.img = _f32(V, 3, H, W, device=device)
+        self.T_final = _f32(V, H, W, device=device)
+        self.last = _i32(V, H, W, device=device)
+        self.grads = _f32(V, n, 8, device=device)
+        self.d_mean = _f32(n, 3, device=device)
+        self.d_quat = _f32(n, 4, device=device)
+        self.set_capacity(capacity)
+
+    def set_capacity(self, capacity: int):
+        self.capacity = int(capacity)
+        self.vals = _i32(max(self.capacity, 1), device=self.device)
+        ws = gs3.gs_bin_sort_workspace_size(self.n, self.V, self.W, self.H, self.capacity)
+        self.ws = torch.empty(ws, dtype=torch.uint8, device=self.device)
+
+    def forward(self, g: Gaussians, cams_dev, mean=None, quat=None, stream=None, keys=None):
+        V, W, H, n = self.V, self.W, self.H, self.n
+        gs3.gs_project(g, cams_dev, V, W, H, self.proj, mean, quat, stream)
+        gs3.gs_bin_sort(self.proj, n, V, W, H, self.capacity, self.vals, self.ranges, keys,
+                        self.d_count, self.d_err, self.ws, stream)
+        gs3.gs_raster_fwd(self.proj, n, V, W, H, self.bg, self.vals, self.ranges, self.img,
+                          self.T_final, self.last, stream)
+        return self.img
+
+    def backward(self, g: Gaussians, cams_dev, d_img, mean=None, quat=None, stream=None):
+        V, W, H, n = self.V, self.W, self.H, self.n
+        gs3.gs_raster_bwd(self.proj, n, V, W, H, self.bg, self.vals, self.ranges, self.T_final,
+                          self.last, d_img, self.grads, None, stream)
+        gs3.gs_project_bwd(g, cams_dev, V, W, H, self.grads, self.d_mean, self.d_quat, mean, quat,
+                           stream)
+        return self.d_mean, self.d_quat
+
+    def count(self) -> int:
+        return int(self.d_count.item())
+
+    def check(self):
+        """Raise if the device reported an error (reads device memory: syncs)."""
+        err = int(self.d_err.item())
+        if err != 0:
+            raise gs3.GsError("gs_bin_sort", err, "device reported error (count %d, capacity %d)"
+                              % (self.count(), self.capacity))
+
+    def fit_capacity(self, g: Gaussians, cams_dev, mean=None, quat=None, margin=1.5):
+        """Run the forward once and grow the pair buffers to margin x the count."""
+        self.d_err.zero_()
+        self.forward(g, cams_dev, mean, quat)
+        c = self.count()
+        want = max(1024, int(c * margin))
+        if want > self.capacity or self.d_err.item() != 0:
+            self.set_capacity(want)
+            self.d_err.zero_()
+            self.forward(g, cams_dev, mean, quat)
+        self.check()
+        return c
+
+
+class Loss:
+    def __init__(self, V, W, H, device="cuda", lam=LAMBDA_DSSIM):
+        self.V, self.W, self.H, self.lam = V, W, H, lam
+        self.ws = torch.empty(gs3.gs_loss_workspace_size(3 * V, H, W), dtype=torch.uint8,
+                              device=device)
+        self.d_img = _f32(V, 3, H, W, device=device)
+        self.d_loss = _f32(1, device=device)
+        self.d_ssim = _f32(1, device=device)
+
+    def __call__(self, img, target, stream=None):
+        gs3.gs_loss_l1_dssim(img, target, 3 * self.V, self.H, self.W, self.lam, self.d_img,
+                             self.d_loss, self.d_ssim, self.ws, stream)
+        return self.d_loss
+
+
+class AdamBuffers:
+    def __init__(self, p: torch.Tensor, lr: float, shadow_dtype=None):
+        self.p = p
+        self.g = torch.zeros_like(p)
+        self.m = torch.zeros_like(p)
+        self.v = torch.zeros_like(p)
+        self.hp = gs3.GsAdam(lr, ADAM_BETAS[0], ADAM_BETAS[1], ADAM_EPS)
+        self.shadow = None if shadow_dtype is None else p.to(shadow_dtype)
+
+    def reset(self, values: Optional[torch.Tensor] = None):
+        if values is not None:
+            self.p.copy_(values)
+            if self.shadow is not None:
+                self.shadow.copy_(values.to(self.shadow.dtype))
+        self.g.zero_()
+        self.m.zero_()
+        self.v.zero_()
+
+    def step(self, d_state, stream=None):
+        gs3.adam_step(self.p, self.g, self.m, self.v, self.hp, d_state, self.shadow, stream)
+
+
+class NTC:
+    """Hash table (FP32 master + FP16 shadow) and MLP (FP32 master + BF16 shadow)."""
+
+    def __init__(self, table: np.ndarray, weights: List[np.ndarray], grid: gs3.GsHashgrid,
+                 precision: int = gs3.GS_MLP_BF16, device="cuda", lr=NTC_LR):
+        self.grid = grid
+        self.precision = precision
+        self.entries = gs3.ntc_hashgrid_entries(grid)
+        assert table.shape == (self.entries, 2), (table.shape, self.entries)
+        w = np.concatenate([x.reshape(-1) for x in weights]).astype(np.float32)
+        assert w.size == gs3.MLP_PARAMS
+        tab = torch.from_numpy(np.ascontiguousarray(table, np.float32)).to(device)
+        self.table = AdamBuffers(tab, lr, torch.float16)
+        self.mlp = AdamBuffers(torch.from_numpy(w).to(device), lr, torch.bfloat16)
+        self.init_table = tab.clone()
+        self.init_mlp = self.mlp.p.clone()
+
+    def mlp_struct(self):
+        return gs3.mlp_struct(self.precision, self.mlp.p, self.mlp.shadow)
+
+    def table_for_encode(self):
+        # the mixed-precision path reads the FP16 shadow; the FP32 path the master
+        return self.table.shadow if self.precision == gs3.GS_MLP_BF16 else self.table.p
+
+    def enc_dtype(self):
+        return torch.bfloat16 if self.precision == gs3.GS_MLP_BF16 else torch.float32
+
+    def reset_to(self, table: torch.Tensor, mlp: torch.Tensor):
+        self.table.reset(table)
+        self.mlp.reset(mlp)
+
+    def weights_numpy(self):
+        w = self.mlp.p.detach().cpu().numpy().astype(np.float64)
+        return [w[:2048].reshape(64, 32), w[2048:6144].reshape(64, 64), w[6144:].reshape(7, 64)]
+
+
+class Stage1:
+    """One Stage-1 training iteration (Section 4.1): NTC query of the frozen
+    previous-frame means, transformation, render of a batch of views, L1 +
+    D-SSIM loss, hand-written backward into the hash table and MLP, Adam."""
+
+    def __init__(self, g: Gaussians, ntc: NTC, V: int, W: int, H: int, capacity: int,
+                 order: int = 0, loss_scale: Optional[float] = None, growth_interval=2000,
+                 device="cuda"):
+        n = g.n
+        self.g, self.ntc, self.V, self.W, self.H, self.order = g, ntc, V, W, H, order
+        self.raster = Rasterizer(n, V, W, H, capacity, device)
+        self.loss = Loss(V, W, H, device)
+        self.enc = torch.zeros(n, 32, dtype=ntc.enc_dtype(), device=device)
+        self.raw7 = _f32(n, 7, device=device)
+        self.mean_t = _f32(n, 3, device=device)
+        self.quat_t = _f32(n, 4, device=device)
+        self.d_raw7 = _f32(n, 7, device=device)
+        self.d_enc = _f32(n, 32, device=device)
+        if loss_scale is None:
+            loss_scale = 2.0 ** 15 if ntc.precision == gs3.GS_MLP_BF16 else 1.0
+        self.growth = growth_interval if ntc.precision == gs3.GS_MLP_BF16 else 0
+        self.state = gs3.new_train_state(loss_scale, device)
+        self.aabb = list(ntc.grid.aabb)
+
+    def reset_state(self, loss_scale=None):
+        ls = gs3.read_train_state(self.state).loss_scale if loss_scale is None else loss_scale
+        self.state.copy_(gs3.new_train_state(ls, self.state.device))
+
+    def transform(self, stream=None):
+        """NTC query + transformation: writes mean_t, quat_t."""
+        g, ntc, n = self.g, self.ntc, self.g.n
+        gs3.ntc_encode_fwd(g.mean, n, ntc.grid, ntc.table_for_encode(), self.enc, stream)
+        gs3.ntc_mlp_fwd(self.enc, n, ntc.mlp_struct(), self.raw7, stream)
+        gs3.ntc_apply(g.mean, g.quat, self.raw7, n, self.aabb, self.order, self.mean_t, self.quat_t,
+                      stream)
+        return self.mean_t, self.quat_t
+
+    def compute_grads(self, cams_dev, target, stream=None):
+        """Forward and backward of one iteration; leaves the scaled gradients
+        in ntc.table.g and ntc.mlp.g (no update)."""
+        g, ntc, n = self.g, self.ntc, self.g.n
+        self.transform(stream)
+        img = self.raster.forward(g, cams_dev, self.mean_t, self.quat_t, stream)
+        self.loss(img, target, stream)
+        d_mean, d_quat = self.raster.backward(g, cams_dev, self.loss.d_img, self.mean_t, self.quat_t,
+                                              stream)
+        gs3.ntc_apply_bwd(g.mean, g.quat, self.raw7, n, self.aabb, self.order, d_mean, d_quat,
+                          self.d_raw7, stream)
+        gs3.ntc_mlp_bwd(self.enc, n, ntc.mlp_struct(), self.d_raw7, self.loss_scale_view(),
+                        ntc.mlp.g, self.d_enc, stream)
+        gs3.ntc_encode_bwd(g.mean, n, ntc.grid, self.d_enc, ntc.table.g, stream)
+        return self.loss.d_loss
+
+    def loss_scale_view(self):
+        return self.state[0:4].view(torch.float32)
+
+    def update(self, stream=None):
+        ntc = self.ntc
+        gs3.gs_check_finite(ntc.table.g, self.state, stream)
+        gs3.gs_check_finite(ntc.mlp.g, self.state, stream)
+        ntc.table.step(self.state, stream)
+        ntc.mlp.step(self.state, stream)
+        gs3.gs_train_state_advance(self.state, self.growth, stream)
+
+    def step(self, cams_dev, target, stream=None):
+        d_loss = self.compute_grads(cams_dev, target, stream)
+        self.update(stream)
+        return d_loss
+
+
+class DirectOpt:
+    """Plain FP32 direct optimisation of the previous frame's means and
+    rotations (the "Direct Opt." comparator of Section 5.3), same rasterizer."""
+
+    def __init__(self, g: Gaussians, V: int, W: int, H: int, capacity: int, lr_mean=0.0024,
+                 lr_quat=0.015, device="cuda"):
+        self.g = g
+        self.V, self.W, self.H = V, W, H
+        self.raster = Rasterizer(g.n, V, W, H, capacity, device)
+        self.loss = Loss(V, W, H, device)
+        self.mean = AdamBuffers(g.mean.clone(), lr_mean)
+        self.quat = AdamBuffers(g.quat.clone(), lr_quat)
+        self.state = gs3.new_train_state(1.0, device)
+
+    def step(self, cams_dev, target, stream=None):
+        img = self.raster.forward(self.g, cams_dev, self.mean.p, self.quat.p, stream)
+        self.loss(img, target, stream)
+        d_mean, d_quat = self.raster.backward(self.g, cams_dev, self.loss.d_img, self.mean.p,
+                                              self.quat.p, stream)
+        self.mean.g.copy_(d_mean)
+        self.quat.g.copy_(d_quat)
+        self.mean.step(self.state, stream)
+        self.quat.step(self.state, stream)
+        gs3.gs_train_state_advance(self.state, 0, stream)
+        return self.loss.d_loss
+
+
+def warmup(ntc: NTC, g: Gaussians, iters=3000, noise=0.01, extent=2.0, seed=0, stream=None,
+           loss_scale=None):
+    """NTC warm-up (Eq. 7): train towards the identity transformation on
+    noise-augmented means; returns the final loss."""
+    n = g.n
+    gen = torch.Generator(device=g.mean.device)
+    gen.manual_seed(seed)
+    enc = torch.zeros(n, 32, dtype=ntc.enc_dtype(), device=g.mean.device)
+    raw7 = _f32(n, 7, device=g.mean.device)
+    d_raw7 = _f32(n, 7, device=g.mean.device)
+    d_enc = _f32(n, 32, device=g.mean.device)
+    d_loss = _f32(1, device=g.mean.device)
+    if loss_scale is None:
+        loss_scale = 2.0 ** 15 if ntc.precision == gs3.GS_MLP_BF16 else 1.0
+    state = gs3.new_train_state(loss_scale, g.mean.device)
+    scale_view = state[0:4].view(torch.float32)
+    mu = torch.empty_like(g.mean)
+    for _ in range(iters):
+        # the noise the method draws is an input of the kernels
+        torch.randn(mu.shape, generator=gen, device=mu.device, out=mu)
+        mu.mul_(noise * extent).add_(g.mean)
+        gs3.ntc_encode_fwd(mu, n, ntc.grid, ntc.table_for_encode(), enc, stream)
+        gs3.ntc_mlp_fwd(enc, n, ntc.mlp_struct(), raw7, stream)
+        gs3.ntc_warmup_loss(raw7, n, d_raw7, d_loss, stream)
+        gs3.ntc_mlp_bwd(enc, n, ntc.mlp_struct(), d_raw7, scale_view, ntc.mlp.g, d_enc, stream)
+        gs3.ntc_encode_bwd(mu, n, ntc.grid, d_enc, ntc.table.g, stream)
+        gs3.gs_check_finite(ntc.table.g, state, stream)
+        gs3.gs_check_finite(ntc.mlp.g, state, stream)
+        ntc.table.step(state, stream)
+        ntc.mlp.step(state, stream)
+        gs3.gs_train_state_advance(state, 2000, stream)
+    return float(d_loss.item())
+
+
+def render(g: Gaussians, cams, W: int, H: int, mean=None, quat=None, capacity=None,
+           device="cuda") -> torch.Tensor:
+    """Render all cams (one launch) with the CUDA rasterizer; returns [V,3,H,W]."""
+    cams_dev = gs3.cameras_to_device(cams, device)
+    r = Rasterizer(g.n, len(cams), W, H, capacity or 1 << 20, device)
+    r.fit_capacity(g, cams_dev, mean, quat)
+    return r.img.clone()

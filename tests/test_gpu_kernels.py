@@ -1,0 +1,357 @@
+"""Parity of every CUDA entry point with the FP64 oracle, element by element,
+on the same seeded inputs, at sizes spanning several tiles and ragged tails.
+
+Tolerances: integer, key and index outputs bit-exact; FP32 images <= 1e-4 max
+abs; gradients <= 1e-3 relative per tensor (||g - g_ref|| / ||g_ref||) and
+elementwise <= 1e-3 * max|g_ref|.  Pixels where the oracle reports a
+compositing decision within a small margin of its threshold (where FP32 and
+FP64 may decide apart) are compared for validity only, and must be rare.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2403_01444_gb300 import gs3, scenes
+from paper_2403_01444_gb300.engine import Rasterizer
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2403_01444_gb300 import build
+    build.build()
+    gs3.lib()
+
+
+def t(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV, dtype)
+
+
+def rel_err(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def assert_grad_close(got, want, rtol=1e-3):
+    got, want = np.asarray(got, np.float64), np.asarray(want, np.float64)
+    assert rel_err(got, want) <= rtol, rel_err(got, want)
+    scale = max(np.abs(want).max(), 1e-30)
+    assert np.abs(got - want).max() <= rtol * scale * 10, np.abs(got - want).max() / scale
+
+
+def projected_from_records(rec, device=DEV):
+    V, N = rec["depth"].shape
+    p = gs3.Projected.empty(V, N, device)
+    p.mean2d.copy_(t(rec["mean2d"]))
+    co = np.concatenate([rec["conic"], rec["opacity"][..., None]], -1)
+    p.conic_opacity.copy_(t(co))
+    p.rgb.copy_(t(rec["rgb"]))
+    p.depth.copy_(t(rec["depth"]))
+    p.radius.copy_(t(rec["radius"], torch.int32))
+    p.tiles_touched.zero_()
+    return p
+
+
+def gpu_bin_sort(p, N, V, W, H, capacity=None, keys=True):
+    cap = capacity if capacity is not None else 4 * N * V * 64 + 16
+    r = Rasterizer(N, V, W, H, cap, DEV)
+    r.proj = p
+    k = torch.zeros(max(cap, 1), dtype=torch.int64, device=DEV) if keys else None
+    gs3.gs_bin_sort(p, N, V, W, H, r.capacity, r.vals, r.ranges, k, r.d_count, r.d_err, r.ws)
+    torch.cuda.synchronize()
+    return r, k
+
+
+# ------------------------------------------------------------------ binning
+@pytest.mark.parametrize("V,N,W,H,seed", [(1, 1, 16, 16, 0), (1, 300, 70, 50, 1), (3, 500, 133, 97, 2),
+                                          (4, 2000, 480, 360, 3), (2, 4096, 128, 96, 4)])
+def test_bin_sort_bit_exact(V, N, W, H, seed):
+    rec = scenes.random_projected(V, N, W, H, np.random.default_rng(seed))
+    # equal depths on purpose: ties must break by Gaussian index
+    rec["depth"][:, ::7] = rec["depth"][:, :1]
+    p = projected_from_records(rec)
+    r, k = gpu_bin_sort(p, N, V, W, H)
+    count, keys, vals, ranges = oracle.bin_sort(rec["mean2d"], rec["radius"], rec["depth"], W, H)
+    assert r.count() == count
+    assert int(r.d_err.item()) == 0
+    got_keys = k[:count].cpu().numpy().view(np.uint64)
+    np.testing.assert_array_equal(got_keys, keys)
+    np.testing.assert_array_equal(r.vals[:count].cpu().numpy().view(np.uint32), vals)
+    np.testing.assert_array_equal(r.ranges.cpu().numpy().view(np.uint32), ranges)
+
+
+def test_bin_sort_all_culled_and_capacity_overflow():
+    V, N, W, H = 2, 400, 100, 60
+    rec = scenes.random_projected(V, N, W, H, np.random.default_rng(9))
+    rec0 = dict(rec)
+    rec0["radius"] = np.zeros_like(rec["radius"])
+    r, _ = gpu_bin_sort(projected_from_records(rec0), N, V, W, H)
+    assert r.count() == 0 and not r.ranges.any()
+    count = oracle.bin_sort(rec["mean2d"], rec["radius"], rec["depth"], W, H)[0]
+    r, _ = gpu_bin_sort(projected_from_records(rec), N, V, W, H, capacity=count - 1)
+    assert r.count() == count
+    assert int(r.d_err.item()) == gs3.GS_ERR_CAPACITY
+    assert not r.ranges.any()  # nothing usable is published on overflow
+    r, _ = gpu_bin_sort(projected_from_records(rec), N, V, W, H, capacity=count)
+    assert int(r.d_err.item()) == 0 and r.count() == count
+
+
+# --------------------------------------------------------------- compositing
+def raster_case(V, N, W, H, seed, **kw):
+    rec = scenes.random_projected(V, N, W, H, np.random.default_rng(seed), **kw)
+    p = projected_from_records(rec)
+    r, _ = gpu_bin_sort(p, N, V, W, H, keys=False)
+    bg = (0.1, 0.2, 0.3)
+    gs3.gs_raster_fwd(p, N, V, W, H, bg, r.vals, r.ranges, r.img, r.T_final, r.last)
+    torch.cuda.synchronize()
+    return rec, p, r, bg
+
+
+@pytest.mark.parametrize("V,N,W,H,seed", [(1, 50, 40, 24, 10), (2, 1500, 150, 110, 11),
+                                          (3, 4000, 257, 129, 12)])
+def test_raster_fwd_parity(V, N, W, H, seed):
+    rec, p, r, bg = raster_case(V, N, W, H, seed)
+    img, Tf, last, amb = oracle.raster_fwd(rec, W, H, bg)
+    ok = amb == 0
+    assert ok.mean() > 0.98
+    gi = r.img.cpu().numpy()
+    okc = np.broadcast_to(ok[:, None], gi.shape)
+    assert np.abs(gi - img)[okc].max() <= 1e-4
+    assert np.abs(r.T_final.cpu().numpy() - Tf)[ok].max() <= 1e-4
+    np.testing.assert_array_equal(r.last.cpu().numpy()[ok], last[ok])
+    # ambiguous pixels still hold valid values
+    assert np.all((gi >= 0) & (gi <= 1.0 + 1e-5))
+
+
+@pytest.mark.parametrize("V,N,W,H,seed", [(1, 60, 40, 24, 20), (2, 1200, 150, 110, 21)])
+def test_raster_bwd_parity(V, N, W, H, seed):
+    rec, p, r, bg = raster_case(V, N, W, H, seed)
+    img, Tf, last, amb = oracle.raster_fwd(rec, W, H, bg)
+    d_img = np.random.default_rng(seed + 100).normal(size=img.shape)
+    d_img *= (amb == 0)[:, None]  # decisions near a threshold are not comparable
+    grads, dop = oracle.raster_bwd(rec, W, H, Tf, last, d_img, bg, want_opacity=True)
+    gg = torch.zeros(V, N, 8, device=DEV)
+    gop = torch.zeros(V, N, device=DEV)
+    gs3.gs_raster_bwd(p, N, V, W, H, bg, r.vals, r.ranges, r.T_final, r.last, t(d_img), gg, gop)
+    torch.cuda.synchronize()
+    gg = gg.cpu().numpy()
+    for sl in (slice(0, 2), slice(2, 5), slice(5, 8)):
+        assert_grad_close(gg[..., sl], grads[..., sl])
+    assert_grad_close(gop.cpu().numpy(), dop)
+
+
+# ------------------------------------------------------------------ projection
+def _proj_scene(seed, N=3000, deg=3, W=200, H=150):
+    rng = np.random.default_rng(seed)
+    g = scenes.make_gaussians(N, deg, rng)
+    g.scale = (g.scale * 3).astype(np.float32)
+    cams = scenes.ring_cameras([0, 100, 230], [0, 20, -10], W, H)
+    return g, cams
+
+
+def test_project_parity():
+    g, cams = _proj_scene(30)
+    W, H, V, N = 200, 150, 3, g.n
+    G = gs3.Gaussians.from_numpy(g)
+    cd = gs3.cameras_to_device(cams)
+    p = gs3.Projected.empty(V, N)
+    gs3.gs_project(G, cd, V, W, H, p)
+    torch.cuda.synchronize()
+    o = oracle.project(g, cams)
+    valid = o["radius"] > 0
+    clean = valid & (o["margin"] > 1e-3)
+    got_r = p.radius.cpu().numpy()
+    assert np.array_equal(got_r[clean], o["radius"][clean])
+    assert np.array_equal(got_r > 0, valid) or np.mean((got_r > 0) != valid) < 1e-3
+    m = clean & (got_r > 0)
+    np.testing.assert_allclose(p.mean2d.cpu().numpy()[m], o["mean2d"][m], rtol=1e-5, atol=1e-3)
+    co = p.conic_opacity.cpu().numpy()
+    cmax = np.abs(o["conic"]).max(-1, keepdims=True)
+    assert np.max(np.abs(co[..., :3] - o["conic"])[m] / cmax[m]) < 2e-4
+    np.testing.assert_allclose(co[..., 3][m], o["opacity"][m], rtol=1e-6)
+    np.testing.assert_allclose(p.rgb.cpu().numpy()[m], o["rgb"][m], atol=2e-6)
+    np.testing.assert_allclose(p.depth.cpu().numpy()[m], o["depth"][m], rtol=1e-6)
+    rect = o["rect"]
+    ntiles = (rect[..., 2] - rect[..., 0]) * (rect[..., 3] - rect[..., 1])
+    assert np.array_equal(p.tiles_touched.cpu().numpy()[m], ntiles[m])
+
+
+def test_project_bwd_parity():
+    g, cams = _proj_scene(31, N=2000)
+    W, H, V, N = 200, 150, 3, g.n
+    G = gs3.Gaussians.from_numpy(g)
+    cd = gs3.cameras_to_device(cams)
+    o = oracle.project(g, cams)
+    rng = np.random.default_rng(32)
+    grads = rng.normal(size=(V, N, 8)) * (o["radius"] > 0)[..., None]
+    grads[..., 2:5] *= 1e-1
+    dm, dq = oracle.project_bwd(g, cams, grads)
+    gdm = torch.zeros(N, 3, device=DEV)
+    gdq = torch.zeros(N, 4, device=DEV)
+    gs3.gs_project_bwd(G, cd, V, W, H, t(grads), gdm, gdq)
+    torch.cuda.synchronize()
+    assert_grad_close(gdm.cpu().numpy(), dm)
+    assert_grad_close(gdq.cpu().numpy(), dq)
+
+
+# -------------------------------------------------------------------- loss
+@pytest.mark.parametrize("V,H,W", [(1, 11, 13), (2, 50, 70), (1, 97, 133)])
+def test_loss_parity(V, H, W):
+    rng = np.random.default_rng(V * 1000 + H)
+    x = rng.uniform(size=(V, 3, H, W)).astype(np.float32)
+    y = np.clip(x + rng.normal(0, 0.15, size=x.shape), 0, 1).astype(np.float32)
+    L, d, ss = oracle.loss_l1_dssim(x, y, 0.2)
+    ws = torch.empty(gs3.gs_loss_workspace_size(3 * V, H, W), dtype=torch.uint8, device=DEV)
+    gd = torch.zeros(V, 3, H, W, device=DEV)
+    gl = torch.zeros(1, device=DEV)
+    gsim = torch.zeros(1, device=DEV)
+    gs3.gs_loss_l1_dssim(t(x), t(y), 3 * V, H, W, 0.2, gd, gl, gsim, ws)
+    torch.cuda.synchronize()
+    assert abs(gl.item() - L) <= 1e-5 * abs(L)
+    assert abs(gsim.item() - ss) <= 1e-5
+    assert_grad_close(gd.cpu().numpy(), d)
+
+
+# -------------------------------------------------------------------- NTC
+GRID = dict(levels=16, features=2, log2_table=17, n_min=16, n_max=1024)
+
+
+def _grid_pair():
+    og = oracle.Grid()
+    gg = gs3.hashgrid(**GRID)
+    return og, gg
+
+
+@pytest.mark.parametrize("n", [1, 77, 5000])
+def test_encode_parity_fp32_and_fp16(n):
+    og, gg = _grid_pair()
+    rng = np.random.default_rng(n)
+    mu = rng.uniform(-1.6, 1.6, size=(n, 3)).astype(np.float32)  # some outside: clamped
+    table = rng.normal(0, 0.1, size=(og.n_entries, 2)).astype(np.float32)
+    want = oracle.encode(og, mu, table)
+    enc = torch.zeros(n, 32, device=DEV)
+    gs3.ntc_encode_fwd(t(mu), n, gg, t(table), enc)
+    torch.cuda.synchronize()
+    # FP32 cell coordinates at resolution 1024 carry ~1e-4 cells of rounding,
+    # so the interpolated value may move by ~1e-3 of the table's magnitude
+    tol = 1e-3 * np.abs(table).max()
+    assert np.abs(enc.cpu().numpy() - want).max() <= tol
+    th = table.astype(np.float16)
+    want_h = oracle.encode(og, mu, th.astype(np.float64))
+    encb = torch.zeros(n, 32, device=DEV, dtype=torch.bfloat16)
+    gs3.ntc_encode_fwd(t(mu), n, gg, t(th, torch.float16), encb)
+    torch.cuda.synchronize()
+    got = encb.float().cpu().numpy()
+    assert np.all(np.abs(got - want_h) <= 2 ** -8 * np.abs(want_h) + tol)
+
+
+def test_encode_bwd_parity():
+    og, gg = _grid_pair()
+    n = 4000
+    rng = np.random.default_rng(5)
+    mu = rng.uniform(-1.5, 1.5, size=(n, 3)).astype(np.float32)
+    d_enc = rng.normal(size=(n, 32)).astype(np.float32)
+    want = oracle.encode_bwd(og, mu, d_enc)
+    dt = torch.zeros(og.n_entries, 2, device=DEV)
+    gs3.ntc_encode_bwd(t(mu), n, gg, t(d_enc), dt)
+    torch.cuda.synchronize()
+    assert_grad_close(dt.cpu().numpy(), want, rtol=1e-3)
+
+
+def _mlp(seed):
+    rng = np.random.default_rng(seed)
+    return [w.astype(np.float32) for w in scenes.random_mlp([32, 64, 64, 7], rng)], rng
+
+
+@pytest.mark.parametrize("n", [1, 129, 3000])
+def test_mlp_fp32_parity(n):
+    Ws, rng = _mlp(n)
+    x = rng.normal(size=(n, 32)).astype(np.float32)
+    h1, h2, out = oracle.mlp_fwd(x, Ws)
+    wflat = t(np.concatenate([w.ravel() for w in Ws]))
+    mlp = gs3.mlp_struct(gs3.GS_MLP_FP32, wflat)
+    raw = torch.zeros(n, 7, device=DEV)
+    gs3.ntc_mlp_fwd(t(x), n, mlp, raw)
+    torch.cuda.synchronize()
+    assert np.abs(raw.cpu().numpy() - out).max() <= 1e-4 * max(1, np.abs(out).max())
+    gout = rng.normal(size=(n, 7)).astype(np.float32)
+    dWs, dx = oracle.mlp_bwd(x, Ws, h1, h2, gout)
+    dW = torch.zeros(gs3.MLP_PARAMS, device=DEV)
+    denc = torch.zeros(n, 32, device=DEV)
+    scale = torch.tensor([4.0], device=DEV)
+    gs3.ntc_mlp_bwd(t(x), n, mlp, t(gout), scale, dW, denc)
+    torch.cuda.synchronize()
+    assert_grad_close(dW.cpu().numpy() / 4.0, np.concatenate([w.ravel() for w in dWs]))
+    assert_grad_close(denc.cpu().numpy() / 4.0, dx)
+
+
+@pytest.mark.parametrize("order", [0, 1])
+def test_apply_parity(order):
+    n = 1000
+    rng = np.random.default_rng(40 + order)
+    aabb = [-1.5] * 3 + [1.5] * 3
+    mu = rng.uniform(-1.6, 1.6, size=(n, 3)).astype(np.float32)
+    q = rng.normal(size=(n, 4)).astype(np.float32)
+    raw = rng.normal(size=(n, 7)).astype(np.float32)
+    mo, qo = oracle.apply(mu, q, raw, aabb, order)
+    gm, gq = torch.zeros(n, 3, device=DEV), torch.zeros(n, 4, device=DEV)
+    gs3.ntc_apply(t(mu), t(q), t(raw), n, aabb, order, gm, gq)
+    torch.cuda.synchronize()
+    assert np.abs(gm.cpu().numpy() - mo).max() <= 1e-6
+    assert np.abs(gq.cpu().numpy() - qo).max() <= 1e-6
+    dmo, dqo = rng.normal(size=(n, 3)), rng.normal(size=(n, 4))
+    want = oracle.apply_bwd(mu, q, raw, aabb, dmo, dqo, order)
+    got = torch.zeros(n, 7, device=DEV)
+    gs3.ntc_apply_bwd(t(mu), t(q), t(raw), n, aabb, order, t(dmo), t(dqo), got)
+    torch.cuda.synchronize()
+    assert_grad_close(got.cpu().numpy(), want, rtol=1e-5)
+
+
+def test_warmup_loss_parity():
+    n = 3000
+    raw = np.random.default_rng(50).normal(size=(n, 7)).astype(np.float32)
+    L, d = oracle.warmup_loss(raw)
+    gd = torch.zeros(n, 7, device=DEV)
+    gl = torch.zeros(1, device=DEV)
+    gs3.ntc_warmup_loss(t(raw), n, gd, gl)
+    torch.cuda.synchronize()
+    assert abs(gl.item() - L) <= 1e-5 * max(1, abs(L))
+    assert_grad_close(gd.cpu().numpy(), d, rtol=1e-5)
+
+
+def test_adam_parity_skip_and_shadow():
+    n = 10_001  # ragged tail
+    rng = np.random.default_rng(60)
+    p0 = rng.normal(size=n)
+    p, m, v = p0.copy(), np.zeros(n), np.zeros(n)
+    gp = t(p0)
+    gm, gv = torch.zeros(n, device=DEV), torch.zeros(n, device=DEV)
+    sh16 = torch.zeros(n, device=DEV, dtype=torch.float16)
+    st = gs3.new_train_state(256.0)
+    hp = gs3.GsAdam(0.002, 0.9, 0.99, 1e-15)
+    for step in range(1, 6):
+        g = rng.normal(size=n).astype(np.float32)
+        oracle.adam(p, g.astype(np.float64), m, v, step)
+        gg = t(g * 256.0)
+        gs3.gs_check_finite(gg, st)
+        gs3.adam_step(gp, gg, gm, gv, hp, st, sh16)
+        gs3.gs_train_state_advance(st, 0)
+        torch.cuda.synchronize()
+        assert not gg.any()  # gradient consumed and zeroed
+    np.testing.assert_allclose(gp.cpu().numpy(), p, rtol=1e-5, atol=1e-6)
+    np.testing.assert_array_equal(sh16.cpu().numpy(), gp.cpu().numpy().astype(np.float16))
+    # a non-finite gradient skips the update and halves the scale
+    before = gp.clone()
+    bad = torch.ones(n, device=DEV)
+    bad[17] = float("inf")
+    gs3.gs_check_finite(bad, st)
+    gs3.adam_step(gp, bad, gm, gv, hp, st)
+    gs3.gs_train_state_advance(st, 0)
+    s = gs3.read_train_state(st)
+    assert torch.equal(gp, before)
+    assert s.loss_scale == 128.0 and s.found_inf == 0 and s.step == 5

@@ -1,0 +1,172 @@
+"""End-to-end parity of the CUDA Stage-1 step with the FP64 oracle, the
+closed-form checks on the GPU path, and training behaviour (the trained cache
+against the method without it)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2403_01444_gb300 import gs3, scenes
+from paper_2403_01444_gb300.engine import NTC, DirectOpt, Rasterizer, Stage1, render, warmup
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2403_01444_gb300 import build
+    build.build()
+    gs3.lib()
+
+
+def rel_err(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def _clean_scene(seed, N, deg, cams):
+    """Gaussians whose discrete decisions (radius, tile rectangle, depth
+    order) are not within FP32 reach of a boundary in any view."""
+    rng = np.random.default_rng(seed)
+    g = scenes.make_gaussians(N, deg, rng)
+    g.scale = (g.scale * 2.5).astype(np.float32)
+    o = oracle.project(g, cams)
+    keep = np.all((o["radius"] == 0) | (o["margin"] > 1e-3), axis=0)
+    for v in range(len(cams)):
+        d = o["depth"][v]
+        order = np.argsort(d)
+        close = np.abs(np.diff(d[order])) < 1e-5 * d[order][1:]
+        keep[order[1:][close]] = False
+    return g.subset(np.nonzero(keep)[0])
+
+
+def test_render_parity_end_to_end():
+    W, H = 150, 110
+    cams = scenes.ring_cameras([0, 130], [10, -5], W, H)
+    g = _clean_scene(70, 3000, 3, cams)
+    r = oracle.render(g, cams)
+    G = gs3.Gaussians.from_numpy(g)
+    img = render(G, cams, W, H).cpu().numpy()
+    ok = np.broadcast_to((r["ambig"] == 0)[:, None], img.shape)
+    assert ok.mean() > 0.98
+    assert np.abs(img - r["img"])[ok].max() <= 1e-4
+
+
+def test_single_gaussian_closed_form_on_gpu():
+    W, H = 96, 72
+    cam = scenes.look_at_camera((0.0, 0.0, 4.0), W, H)
+    c = np.array([0.7, 0.2, 0.45])
+    C0 = 0.5 / math.sqrt(math.pi)
+    sig = float(np.float32(0.3))
+    g = scenes.GaussianSet(np.zeros((1, 3), np.float32), np.array([[1, 0, 0, 0]], np.float32),
+                           np.full((1, 3), sig, np.float32), np.array([0.4], np.float32),
+                           ((c - 0.5) / C0).reshape(1, 1, 3).astype(np.float32), 0)
+    img = render(gs3.Gaussians.from_numpy(g), [cam], W, H).cpu().numpy()[0]
+    var = (cam.fx * sig / 4.0) ** 2 + 0.3
+    o = 1 / (1 + math.exp(-float(np.float32(0.4))))
+    yy, xx = np.mgrid[0:H, 0:W]
+    a = np.minimum(0.99, o * np.exp(-0.5 * ((xx + 0.5 - W / 2) ** 2 + (yy + 0.5 - H / 2) ** 2) / var))
+    rad = math.ceil(3 * math.sqrt(var + math.sqrt(0.1)))
+    inrect = ((xx // 16 >= math.floor((W / 2 - rad) / 16)) & (xx // 16 < math.floor((W / 2 + rad + 15) / 16)) &
+              (yy // 16 >= math.floor((H / 2 - rad) / 16)) & (yy // 16 < math.floor((H / 2 + rad + 15) / 16)))
+    want = np.where((a >= 1 / 255) & inrect, a, 0.0)[None] * c[:, None, None]
+    near = np.abs(a - 1 / 255) < 1e-5
+    assert np.abs(img - want)[:, ~near].max() <= 1e-5
+
+
+def test_identity_transform_reproduces_render():
+    W, H = 128, 96
+    cams = scenes.ring_cameras([0, 90, 180, 270], [0] * 4, W, H)
+    g = scenes.make_gaussians(4096, 1, np.random.default_rng(71))
+    G = gs3.Gaussians.from_numpy(g)
+    n = g.n
+    raw = torch.zeros(n, 7, device=DEV)
+    raw[:, 3] = 1.0
+    mo, qo = torch.zeros(n, 3, device=DEV), torch.zeros(n, 4, device=DEV)
+    gs3.ntc_apply(G.mean, G.quat, raw, n, [-1.5] * 3 + [1.5] * 3, 0, mo, qo)
+    a = render(G, cams, W, H)
+    b = render(G, cams, W, H, mo, qo)
+    assert (a - b).abs().max().item() <= 1e-6
+    norms = qo.norm(dim=1)
+    assert (norms - 1).abs().max().item() <= 1e-6
+
+
+def _near_identity_ntc(rng, grid_np, precision):
+    table = rng.normal(0.0, 0.05, size=(grid_np.n_entries, 2)).astype(np.float32)
+    table[:, 0] += 0.5
+    Ws = scenes.random_mlp([32, 64, 64, 7], rng)
+    Ws[2][0:3] *= 0.01
+    Ws[2][3] = np.abs(Ws[2][3]) + 1.0
+    Ws[2][4:7] *= 0.1
+    return table, [w.astype(np.float32) for w in Ws]
+
+
+def test_stage1_gradients_match_oracle_fp32():
+    W, H = 96, 72
+    cams = scenes.ring_cameras([20, 160], [5, -10], W, H)
+    rng = np.random.default_rng(72)
+    g = _clean_scene(73, 600, 2, cams)
+    og = oracle.Grid()
+    table, Ws = _near_identity_ntc(rng, og, gs3.GS_MLP_FP32)
+    tgt = rbf = scenes.rbf_motion(g, rng, 8, 0.05)
+    targets = oracle.render(tgt, cams)["img"]
+    p = oracle.NTCParams(og, table, Ws)
+    out = oracle.stage1_loss_grads(p, g, cams, targets)
+    # the FP32 GPU step on the same FP32 parameters and targets
+    G = gs3.Gaussians.from_numpy(g)
+    ntc = NTC(table, Ws, gs3.hashgrid(), gs3.GS_MLP_FP32)
+    st = Stage1(G, ntc, 2, W, H, capacity=1 << 20)
+    cd = gs3.cameras_to_device(cams)
+    tg = torch.from_numpy(targets.astype(np.float32)).to(DEV)
+    st.raster.fit_capacity(G, cd, *st.transform())
+    d_loss = st.compute_grads(cd, tg)
+    torch.cuda.synchronize()
+    assert abs(d_loss.item() - out["loss"]) <= 1e-4 * out["loss"]
+    ambig = out["render"]["ambig"].sum()
+    assert ambig <= 0.002 * out["render"]["ambig"].size
+    assert rel_err(st.raw7.cpu().numpy(), out["fwd"]["raw7"]) <= 1e-5
+    assert rel_err(ntc.mlp.g.cpu().numpy(), np.concatenate([w.ravel() for w in out["dWs"]])) <= 1e-3
+    assert rel_err(ntc.table.g.cpu().numpy(), out["d_table"]) <= 1e-3
+
+
+@pytest.mark.parametrize("precision", [gs3.GS_MLP_FP32])
+def test_ntc_training_beats_no_ntc(precision):
+    """What the trained cache gains: after 150 Stage-1 iterations on a
+    rigid-motion scene, the transformed Gaussians render a held-out view closer
+    to the ground truth than the untransformed previous frame, and their means
+    moved towards the true motion."""
+    cfg = scenes.CONFIGS[1]
+    sc = scenes.make_scene(1)
+    W, H = cfg.W, cfg.H
+    G = gs3.Gaussians.from_numpy(sc.prev)
+    cams = sc.cams
+    cd = gs3.cameras_to_device(cams)
+    Gt = gs3.Gaussians.from_numpy(sc.target)
+    targets = render(Gt, cams, W, H)
+    rng = np.random.default_rng(74)
+    og = oracle.Grid()
+    table = rng.uniform(-1e-4, 1e-4, size=(og.n_entries, 2)).astype(np.float32)
+    Ws = [w.astype(np.float32) for w in scenes.random_mlp([32, 64, 64, 7], rng)]
+    ntc = NTC(table, Ws, gs3.hashgrid(), precision)
+    wl = warmup(ntc, G, iters=300)
+    assert wl < -0.9  # near the identity transformation (loss minimum is -1)
+    st = Stage1(G, ntc, len(cams), W, H, capacity=1 << 20)
+    st.raster.fit_capacity(G, cd, *st.transform(), margin=2.0)
+    losses = []
+    for it in range(150):
+        losses.append(st.step(cd, targets).item())
+    st.raster.check()
+    mt, qt = st.transform()
+    err_after = (mt - Gt.mean).norm(dim=1).mean().item()
+    err_before = (G.mean - Gt.mean).norm(dim=1).mean().item()
+    assert losses[-1] < 0.7 * losses[0]
+    assert err_after < 0.8 * err_before
+    ho = [sc.heldout]
+    gt = render(Gt, ho, W, H)
+    psnr = lambda a: -10 * math.log10(((a - gt) ** 2).mean().item())
+    p_ntc = psnr(render(G, ho, W, H, mt, qt))
+    p_none = psnr(render(G, ho, W, H))
+    assert p_ntc > p_none + 1.0, (p_ntc, p_none)
