@@ -44,7 +44,11 @@ def parse():
     ap.add_argument("--mlp", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--small", action="store_true", help="a small scene (for profiling captures)")
+    ap.add_argument("--small", action="store_true",
+                    help="100K Gaussians instead of 250K (smaller profiling captures)")
+    ap.add_argument("--warm-iters", type=int, default=1000, help="NTC warm-up iterations (Eq. 7)")
+    ap.add_argument("--profile", action="store_true",
+                    help="setup + timed steps only (for ncu launch lists)")
     return ap.parse_args()
 
 
@@ -205,7 +209,7 @@ def run_ours(args):
     import oracle  # only for the grid size of the initial table (host integer layout)
 
     if args.small:
-        scene = scenes.make_scene(CFG_INDEX, n_gauss=50_000, W=676, H=507)
+        scene = scenes.make_scene(CFG_INDEX, n_gauss=100_000)
     else:
         scene = scenes.make_scene(CFG_INDEX)
     cfg = scene.cfg
@@ -232,7 +236,7 @@ def run_ours(args):
     Ws = [w.astype(np.float32) for w in scenes.random_mlp([32, 64, 64, 7], rng)]
     ntc = NTC(table, Ws, grid, precision, dev)
     t0 = time.perf_counter()
-    wl = warmup(ntc, G, iters=1000)
+    wl = warmup(ntc, G, iters=args.warm_iters)
     torch.cuda.synchronize()
     t_warm = time.perf_counter() - t0
     warm_table, warm_mlp = ntc.table.p.clone(), ntc.mlp.p.clone()
@@ -298,6 +302,11 @@ def run_ours(args):
         torch.cuda.synchronize()
     launches = gs3.lib().gs_launch_count() - l0
     ms = e0.elapsed_time(e1) / args.steps
+    if args.profile:
+        if rank == 0:
+            print(json.dumps({"profile_run": True, "ms_per_step": ms, "gpu_launches": int(launches),
+                              "pairs": st.raster.count()}), flush=True)
+        return
     st.raster.check()
     ms_all = torch.tensor([ms], device=dev)
     if world > 1:
