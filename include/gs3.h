@@ -187,6 +187,24 @@ GS_API gs_status gs_bin_sort(const gs_projected *proj, int64_t n, int V, int W, 
                       uint32_t *vals, uint32_t *ranges, uint64_t *keys, int64_t *d_count,
                       int32_t *d_err, void *ws, size_t ws_bytes, gs_stream stream);
 
+/* gs_bin_sort without a caller workspace, for callers that cannot allocate
+ * device memory when they bin (allocators that forbid new device allocations
+ * after start-up, render loops that must not stall or fail on an allocation,
+ * plug-ins handed only pre-sized buffers).  The paper has no counterpart: it
+ * is a deployment variant of gs_bin_sort, with the same arguments, outputs,
+ * capacity protocol and bit-exact results, minus ws / ws_bytes.
+ * Scratch is a 20 MiB static device array inside the library, held by every
+ * GPU that loads it until exit.  Limits: n * V <= 131072, capacity <= 1048576,
+ * and gs_bin_sort_workspace_size() of the call <= 20 MiB; larger calls return
+ * GS_ERR_INVALID_ARG without launching.  All calls share the array: calls that
+ * overlap on the GPU race and must be serialised.  The first call on a device
+ * looks up the array's address; make it before any stream capture.
+ * Allocates nothing (no cudaMalloc / cudaFree, no allocating library call). */
+GS_API gs_status gs_bin_sort_noalloc(const gs_projected *proj, int64_t n, int V, int W, int H,
+                                     int64_t capacity, uint32_t *vals, uint32_t *ranges,
+                                     uint64_t *keys, int64_t *d_count, int32_t *d_err,
+                                     gs_stream stream);
+
 /* ------------------------------------------------------------ compositing */
 
 /* Front-to-back alpha compositing (Section 3.2, Eq. 4), one 16x16 tile per

@@ -213,6 +213,17 @@ def gs_bin_sort(proj: Projected, n, V, W, H, capacity, vals, ranges, keys, d_cou
         _stream(stream)))
 
 
+def gs_bin_sort_noalloc(proj: Projected, n, V, W, H, capacity, vals, ranges, keys, d_count, d_err,
+                        stream=None):
+    """gs_bin_sort with the library's built-in scratch (no workspace argument):
+    for callers that cannot allocate device memory.  Limits and sharing rules
+    are those of the C entry point."""
+    po = proj.struct()
+    _check("gs_bin_sort_noalloc", lib().gs_bin_sort_noalloc(
+        ctypes.byref(po), c_int64(n), c_int(V), c_int(W), c_int(H), c_int64(capacity), _ptr(vals),
+        _ptr(ranges), _ptr(keys), _ptr(d_count), _ptr(d_err), _stream(stream)))
+
+
 def _bg(bg):
     a = (c_float * 3)(*[float(x) for x in (bg if bg is not None else (0.0, 0.0, 0.0))])
     return a
