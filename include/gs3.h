@@ -140,6 +140,9 @@ GS_API const char *gs_last_error(void);
 GS_API int gs_version(void);
 /* Number of CUDA kernels this library has launched since it was loaded. */
 GS_API uint64_t gs_launch_count(void);
+/* Number of tensor-core MLP blocks that gave up a bounded wait on their MMA
+ * completion barrier (0 in normal operation; reads device memory, syncs). */
+GS_API int gs_tc_timeouts(void);
 
 /* ------------------------------------------------------------ projection */
 

@@ -22,8 +22,8 @@ namespace gs3 {
 constexpr int RADIX = 256;
 constexpr int SORT_THREADS = 256;
 constexpr int SORT_WARPS = SORT_THREADS / 32;
-constexpr int SORT_ITEMS = 16;
-constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;  // 4096 keys per block step
+constexpr int SORT_ITEMS = 8;
+constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;  // 2048 keys per block step
 constexpr int SORT_BLOCKS = kNumSMs * 4;              // fixed grid: n may live on the device
 constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_ITEMS = 4;
@@ -70,31 +70,38 @@ __global__ void __launch_bounds__(SORT_THREADS) radix_hist_kernel(SortPass s)
     s.hist[threadIdx.x * s.G + blockIdx.x] = h[threadIdx.x];
 }
 
-// Exclusive scan, in place, of M u32 counters with one block.
-__global__ void __launch_bounds__(SCAN_THREADS) scan_u32_kernel(uint32_t *a, int M)
+// Per digit d (one block each): exclusive scan, in place, of the G block
+// counts hist[d][0..G), and the digit's total in hist[RADIX * G + d].
+__global__ void __launch_bounds__(SORT_THREADS) scan_digit_rows_kernel(uint32_t *hist, int G)
 {
-    __shared__ uint32_t s[SCAN_THREADS];
-    int per = (M + SCAN_THREADS - 1) / SCAN_THREADS;
-    int beg = threadIdx.x * per, end = min(M, beg + per);
-    uint32_t sum = 0;
-    for (int i = beg; i < end; ++i) sum += a[i];
-    s[threadIdx.x] = sum;
+    __shared__ uint32_t s_w[SORT_WARPS];
+    __shared__ uint32_t s_carry;
+    const int d = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *row = hist + (int64_t)d * G;
+    if (threadIdx.x == 0) s_carry = 0;
     __syncthreads();
-    for (int o = 1; o < SCAN_THREADS; o <<= 1) {
-        uint32_t x = threadIdx.x >= o ? s[threadIdx.x - o] : 0u;
+    for (int base = 0; base < G; base += SORT_THREADS) {
+        int i = base + threadIdx.x;
+        uint32_t x = i < G ? row[i] : 0u;
+        uint32_t inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) s_w[warp] = inc;
         __syncthreads();
-        s[threadIdx.x] += x;
+        uint32_t before = s_carry;
+        for (int w = 0; w < warp; ++w) before += s_w[w];
+        if (i < G) row[i] = before + inc - x;
+        __syncthreads();
+        if (threadIdx.x == SORT_THREADS - 1) s_carry = before + inc;
         __syncthreads();
     }
-    uint32_t run = s[threadIdx.x] - sum;
-    for (int i = beg; i < end; ++i) {
-        uint32_t x = a[i];
-        a[i] = run;
-        run += x;
-    }
+    if (threadIdx.x == 0) hist[(int64_t)RADIX * G + d] = s_carry;
 }
 
-__global__ void __launch_bounds__(SORT_THREADS) radix_scatter_kernel(SortPass s)
+__global__ void __launch_bounds__(SORT_THREADS, 4) radix_scatter_kernel(SortPass s)
 {
     __shared__ uint32_t s_off[RADIX];
     __shared__ uint32_t s_tot[RADIX];
@@ -103,7 +110,22 @@ __global__ void __launch_bounds__(SORT_THREADS) radix_scatter_kernel(SortPass s)
     const unsigned lt = (1u << lane) - 1u;
     int64_t beg, end;
     block_range(pass_n(s), s.G, blockIdx.x, beg, end);
-    s_off[tid] = s.hist[tid * s.G + blockIdx.x];
+    {
+        // digit base = exclusive scan of the digit totals (RADIX == threads)
+        uint32_t tot = s.hist[(int64_t)RADIX * s.G + tid];
+        uint32_t inc = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) s_tot[warp] = inc;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int w = 0; w < warp; ++w) before += s_tot[w];
+        s_off[tid] = before + inc - tot + s.hist[tid * s.G + blockIdx.x];
+        __syncthreads();
+    }
     for (int64_t t0 = beg; t0 < end; t0 += SORT_TILE) {
         for (int k = tid; k < SORT_WARPS * RADIX; k += SORT_THREADS) (&s_wh[0][0])[k] = 0u;
         __syncthreads();
@@ -390,7 +412,7 @@ static BinWs carve(void *base, int64_t NV, int64_t cap)
     w.offsets = reinterpret_cast<int64_t *>(take(8 * (NV + 1)));
     w.cnt = reinterpret_cast<int32_t *>(take(4 * NV));
     w.bsum = reinterpret_cast<int64_t *>(take(8 * (ceil_div(NV, SCAN_TILE) + 1)));
-    w.hist = reinterpret_cast<uint32_t *>(take(4 * RADIX * SORT_BLOCKS));
+    w.hist = reinterpret_cast<uint32_t *>(take(4 * (RADIX * SORT_BLOCKS + RADIX)));
     w.n_eff = reinterpret_cast<int64_t *>(take(64));
     for (int k = 0; k < 2; ++k) w.tk[k] = reinterpret_cast<uint32_t *>(take(4 * cap));
     w.tv = reinterpret_cast<uint32_t *>(take(4 * cap));
@@ -404,7 +426,7 @@ static gs_status run_pass(SortPass s, int64_t grid_items_hint, cudaStream_t st)
     note_launch();
     radix_hist_kernel<<<s.G, SORT_THREADS, 0, st>>>(s);
     note_launch();
-    scan_u32_kernel<<<1, SCAN_THREADS, 0, st>>>(s.hist, RADIX * s.G);
+    scan_digit_rows_kernel<<<RADIX, SORT_THREADS, 0, st>>>(s.hist, s.G);
     note_launch();
     radix_scatter_kernel<<<s.G, SORT_THREADS, 0, st>>>(s);
     return launch_status("radix pass");

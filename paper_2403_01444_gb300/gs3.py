@@ -181,7 +181,9 @@ def hashgrid(levels=16, features=2, log2_table=17, n_min=16, n_max=1024,
 
 
 def mlp_struct(precision: int, w_f32: torch.Tensor, w_bf16: Optional[torch.Tensor] = None) -> GsMlp:
-    return GsMlp(precision, _ptr(w_f32), _ptr(w_bf16))
+    s = GsMlp(precision, _ptr(w_f32), _ptr(w_bf16))
+    s._keep = (w_f32, w_bf16)  # the struct holds raw pointers: keep the tensors alive with it
+    return s
 
 
 # ------------------------------------------------------------------ calls
