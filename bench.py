@@ -266,13 +266,13 @@ def run_ours(args):
         gs3.gs_project(G, cd, Vb, W, H, st.raster.proj, st.mean_t, st.quat_t)
         E("t2")
         r = st.raster
-        gs3.gs_bin_sort(r.proj, G.n, Vb, W, H, r.capacity, r.vals, r.ranges, None, r.d_count, r.d_err, r.ws)
+        gs3.gs_bin_sort(r.proj, G.n, Vb, W, H, r.bin, r.capacity, r.vals, r.ranges, None, r.d_count, r.d_err, r.ws)
         E("t3")
-        gs3.gs_raster_fwd(r.proj, G.n, Vb, W, H, r.bg, r.vals, r.ranges, r.img, r.T_final, r.last)
+        gs3.gs_raster_fwd(r.proj, G.n, Vb, W, H, r.bin, r.bg, r.vals, r.ranges, r.img, r.T_final, r.last)
         E("t4")
         st.loss(r.img, tg)
         E("t5")
-        gs3.gs_raster_bwd(r.proj, G.n, Vb, W, H, r.bg, r.vals, r.ranges, r.T_final, r.last,
+        gs3.gs_raster_bwd(r.proj, G.n, Vb, W, H, r.bin, r.bg, r.vals, r.ranges, r.T_final, r.last,
                           st.loss.d_img, r.grads, None)
         E("t6")
         gs3.gs_project_bwd(G, cd, Vb, W, H, r.grads, r.d_mean, r.d_quat, st.mean_t, st.quat_t)

@@ -177,16 +177,22 @@ GS_API gs_status gs_project_bwd(const gs_gaussians *g, const gs_camera *d_cams, 
  * for `capacity` (Gaussian, tile) pairs. */
 GS_API size_t gs_bin_sort_workspace_size(int64_t n, int V, int W, int H, int64_t capacity);
 
-/* Tile binning and key sort (the tile pipeline of Section 3.2).  Every
- * (view, Gaussian, tile of its rect) pair gets key = (view * tiles + tile) << 32
- * | IEEE bits of its FP32 depth and value = Gaussian index; pairs are ordered by
- * (key, value).  Writes vals[count] (sorted values), ranges[V * tiles][2]
- * ([first, last+1) per tile, zeros when empty), *d_count (device int64) and,
- * when keys != NULL, keys[count] (for checking).  Bit-exact and deterministic.
+/* Tile binning and key sort (the tile pipeline of Section 3.2).  Tiles are
+ * grouped in bins of bin x bin tiles (bin = 1: one tile per bin).  Every
+ * (view, Gaussian, bin touched by its tile rect) pair gets key =
+ * (view * bins + bin_id) << 32 | IEEE bits of its FP32 depth and value =
+ * Gaussian index, bin_id = (tile_y / bin) * bins_x + tile_x / bin; pairs are
+ * ordered by (key, value).  Writes vals[count] (sorted values),
+ * ranges[V * bins][2] ([first, last+1) per bin, zeros when empty), *d_count
+ * (device int64) and, when keys != NULL, keys[count] (for checking).
+ * Bit-exact and deterministic.  With bin > 1 each tile's list is the ordered
+ * subsequence of its bin's list whose tile rectangles hold the tile, which the
+ * compositing kernels select on the fly (same records, same order).
  * If count > capacity, *d_err is set to GS_ERR_CAPACITY, nothing is written
  * past capacity, and every range is empty; the caller regrows and reruns.
  * ws: scratch of gs_bin_sort_workspace_size bytes, 256-byte aligned. */
-GS_API gs_status gs_bin_sort(const gs_projected *proj, int64_t n, int V, int W, int H, int64_t capacity,
+GS_API gs_status gs_bin_sort(const gs_projected *proj, int64_t n, int V, int W, int H, int bin,
+                      int64_t capacity,
                       uint32_t *vals, uint32_t *ranges, uint64_t *keys, int64_t *d_count,
                       int32_t *d_err, void *ws, size_t ws_bytes, gs_stream stream);
 
@@ -204,7 +210,7 @@ GS_API gs_status gs_bin_sort(const gs_projected *proj, int64_t n, int V, int W, 
  * looks up the array's address; make it before any stream capture.
  * Allocates nothing (no cudaMalloc / cudaFree, no allocating library call). */
 GS_API gs_status gs_bin_sort_noalloc(const gs_projected *proj, int64_t n, int V, int W, int H,
-                                     int64_t capacity, uint32_t *vals, uint32_t *ranges,
+                                     int bin, int64_t capacity, uint32_t *vals, uint32_t *ranges,
                                      uint64_t *keys, int64_t *d_count, int32_t *d_err,
                                      gs_stream stream);
 
@@ -216,10 +222,11 @@ GS_API gs_status gs_bin_sort_noalloc(const gs_projected *proj, int64_t n, int V,
  * alpha = min(0.99, opacity exp(power)); skip if alpha < 1/255; stop before a
  * Gaussian that would take T below 1e-4; C += rgb alpha T; T *= 1 - alpha.
  * Writes img[V][3][H][W] = C + T bg, T_final[V][H][W] and last[V][H][W] (1 +
- * list position of the last Gaussian added, 0 if none). */
-GS_API gs_status gs_raster_fwd(const gs_projected *proj, int64_t n, int V, int W, int H, const float *bg,
-                        const uint32_t *vals, const uint32_t *ranges, float *img, float *T_final,
-                        int32_t *last, gs_stream stream);
+ * position in the bin's list of the last Gaussian added, 0 if none).  vals /
+ * ranges are gs_bin_sort's output for the same bin. */
+GS_API gs_status gs_raster_fwd(const gs_projected *proj, int64_t n, int V, int W, int H, int bin,
+                        const float *bg, const uint32_t *vals, const uint32_t *ranges, float *img,
+                        float *T_final, int32_t *last, gs_stream stream);
 
 /* Reverse of gs_raster_fwd: walks each pixel's list back to front from
  * `last`, recomputing T_i = T_{i+1} / (1 - alpha_i) from T_final (no per-pair
@@ -227,10 +234,10 @@ GS_API gs_status gs_raster_fwd(const gs_projected *proj, int64_t n, int V, int W
  * warp and each tile before one vector atomic per (Gaussian, tile).
  * Overwrites grads[V][N][8] = dL/d(u, v, A, B, C, r, g, b) and, when non-NULL,
  * d_opacity[V][N].  bg is a host array of 3 floats. */
-GS_API gs_status gs_raster_bwd(const gs_projected *proj, int64_t n, int V, int W, int H, const float *bg,
-                        const uint32_t *vals, const uint32_t *ranges, const float *T_final,
-                        const int32_t *last, const float *d_img, float *grads, float *d_opacity,
-                        gs_stream stream);
+GS_API gs_status gs_raster_bwd(const gs_projected *proj, int64_t n, int V, int W, int H, int bin,
+                        const float *bg, const uint32_t *vals, const uint32_t *ranges,
+                        const float *T_final, const int32_t *last, const float *d_img,
+                        float *grads, float *d_opacity, gs_stream stream);
 
 /* ------------------------------------------------------------------- loss */
 

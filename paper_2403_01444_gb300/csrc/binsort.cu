@@ -5,9 +5,14 @@
 // (Gaussian, tile) pair, the sort is split in two stable stages:
 //   1. the V*N (view, Gaussian) entries are sorted by (view, depth bits) --
 //      4 byte-digit passes on the FP32 depth bits plus one pass on the view;
-//   2. pairs are emitted in that order (each entry's tiles row-major) and
-//      stably sorted on the (view * tiles + tile) key alone, which needs
-//      ceil(log2(V * tiles) / 8) passes (2 for 4 views of 1352x1014).
+//   2. pairs are emitted in that order (each entry's bins row-major) and
+//      stably sorted on the (view * bins + bin) key alone, which needs
+//      ceil(log2(V * bins) / 8) passes (2 for 4 views of 1352x1014).
+// A bin is bin x bin tiles.  With bin = 1 the lists are the per-tile lists;
+// with larger bins every tile of a bin shares the bin's depth-ordered list and
+// the compositing kernels keep, on the fly, the entries whose footprint
+// rectangle holds their tile -- the same records in the same order as the
+// per-tile list, for far fewer pairs to sort.
 // Stage 2 keeps the depth order inside every tile, so the result equals the
 // full-key sort while moving 8 bytes per pair per pass over 2 passes instead
 // of 12 bytes over 6.  All passes are stable LSD byte passes of
@@ -183,10 +188,10 @@ __global__ void depth_keys_kernel(const float *depth, const int32_t *radius, int
     v[i] = (uint32_t)i;
 }
 
-// Number of tiles of every entry, in the sorted order (same rectangle rule as
+// Number of bins of every entry, in the sorted order (same rectangle rule as
 // the emission below and as gs_project's tiles_touched).
 __global__ void sorted_counts_kernel(const uint32_t *svals, const float2 *mean2d,
-                                     const int32_t *radius, int64_t NV, int tx, int ty,
+                                     const int32_t *radius, int64_t NV, int tx, int ty, int bin,
                                      int32_t *cnt)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -197,7 +202,7 @@ __global__ void sorted_counts_kernel(const uint32_t *svals, const float2 *mean2d
     if (r > 0) {
         float2 m = mean2d[sv];
         int x0, y0, x1, y1;
-        tile_rect(m.x, m.y, r, tx, ty, x0, y0, x1, y1);
+        bin_rect(m.x, m.y, r, tx, ty, bin, x0, y0, x1, y1);
         c = (x1 - x0) * (y1 - y0);
     }
     cnt[i] = c;
@@ -300,7 +305,7 @@ struct EmitParams {
     const float2 *mean2d;
     const int32_t *radius;
     int64_t NV, n;
-    int tx, ty, tiles;
+    int tx, ty, bin, bins_x, bins;
     uint32_t *tkeys, *tvals;
 };
 
@@ -319,7 +324,7 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitParams e)
         int r = e.radius[sv];
         if (r > 0) {
             float2 m = e.mean2d[sv];
-            tile_rect(m.x, m.y, r, e.tx, e.ty, x0, y0, x1, y1);
+            bin_rect(m.x, m.y, r, e.tx, e.ty, e.bin, x0, y0, x1, y1);
         }
     }
     int w = x1 - x0;
@@ -333,7 +338,7 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitParams e)
     int64_t wbeg = __shfl_sync(0xffffffffu, off, 0);
     uint32_t view = sv / (uint32_t)e.n;
     uint32_t g = sv - view * (uint32_t)e.n;
-    uint32_t kbase = view * (uint32_t)e.tiles;
+    uint32_t kbase = view * (uint32_t)e.bins;
     int64_t span = wend - wbeg;
     for (int64_t k0 = 0; k0 < span; k0 += 32) {
         int64_t o = wbeg + k0 + lane;
@@ -354,7 +359,7 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitParams e)
             int local = (int)(o - so);
             int ty = sy + local / sw;
             int tx = sx + local - (local / sw) * sw;
-            e.tkeys[o] = sk + (uint32_t)(ty * e.tx + tx);
+            e.tkeys[o] = sk + (uint32_t)(ty * e.bins_x + tx);
             e.tvals[o] = sg;
         }
     }
@@ -444,11 +449,12 @@ extern "C" size_t gs_bin_sort_workspace_size(int64_t n, int V, int W, int H, int
     return carve(nullptr, n * V, capacity).bytes;
 }
 
-extern "C" gs_status gs_bin_sort(const gs_projected *proj, int64_t n, int V, int W, int H,
+extern "C" gs_status gs_bin_sort(const gs_projected *proj, int64_t n, int V, int W, int H, int bin,
                                  int64_t capacity, uint32_t *vals, uint32_t *ranges, uint64_t *keys,
                                  int64_t *d_count, int32_t *d_err, void *ws, size_t ws_bytes,
                                  gs_stream stream)
 {
+    GS_REQUIRE(bin >= 1 && bin <= 64, "gs_bin_sort: bin must be 1..64 tiles");
     GS_REQUIRE(proj && vals && ranges && d_count && ws, "gs_bin_sort: null argument");
     GS_REQUIRE(n >= 0 && V >= 1 && V <= GS_MAX_VIEWS, "gs_bin_sort: bad n or V");
     GS_REQUIRE(W > 0 && H > 0 && W <= 16384 && H <= 16384, "gs_bin_sort: bad image size");
@@ -462,8 +468,9 @@ extern "C" gs_status gs_bin_sort(const gs_projected *proj, int64_t n, int V, int
                w.bytes);
     cudaStream_t st = as_stream(stream);
     const int tx = tiles_x_of(W), ty = tiles_y_of(H);
-    const int tiles = tx * ty;
-    const int64_t nkeys = (int64_t)V * tiles;
+    const int bins_x = bins_x_of(W, bin);
+    const int bins = bins_x * bins_y_of(H, bin);
+    const int64_t nkeys = (int64_t)V * bins;
     cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * nkeys, st);
     if (NV == 0) {
         cudaMemsetAsync(d_count, 0, sizeof(int64_t), st);
@@ -496,7 +503,7 @@ extern "C" gs_status gs_bin_sort(const gs_projected *proj, int64_t n, int V, int
     int nb = (int)ceil_div(NV, SCAN_TILE);
     note_launch();
     sorted_counts_kernel<<<(int)ceil_div(NV, 256), 256, 0, st>>>(
-        svals, reinterpret_cast<const float2 *>(proj->mean2d), proj->radius, NV, tx, ty, w.cnt);
+        svals, reinterpret_cast<const float2 *>(proj->mean2d), proj->radius, NV, tx, ty, bin, w.cnt);
     note_launch();
     count_reduce_kernel<<<nb, SCAN_THREADS, 0, st>>>(w.cnt, NV, w.bsum);
     note_launch();
@@ -517,7 +524,9 @@ extern "C" gs_status gs_bin_sort(const gs_projected *proj, int64_t n, int V, int
     ep.n = n;
     ep.tx = tx;
     ep.ty = ty;
-    ep.tiles = tiles;
+    ep.bin = bin;
+    ep.bins_x = bins_x;
+    ep.bins = bins;
     ep.tkeys = w.tk[0];
     ep.tvals = (passes % 2 == 0) ? vals : w.tv;
     note_launch();
@@ -547,7 +556,7 @@ extern "C" gs_status gs_bin_sort(const gs_projected *proj, int64_t n, int V, int
     ranges_kernel<<<kNumSMs * 8, 256, 0, st>>>(w.tk[kc], w.n_eff, ranges);
     if (keys) {
         note_launch();
-        keys64_kernel<<<kNumSMs * 8, 256, 0, st>>>(w.tk[kc], vals, w.n_eff, proj->depth, n, tiles,
+        keys64_kernel<<<kNumSMs * 8, 256, 0, st>>>(w.tk[kc], vals, w.n_eff, proj->depth, n, bins,
                                                    keys);
     }
     return launch_status("gs_bin_sort");

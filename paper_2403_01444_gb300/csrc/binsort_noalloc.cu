@@ -72,7 +72,7 @@ static void *scratch_address(int dev, gs_status &st)
 using namespace gs3;
 
 extern "C" gs_status gs_bin_sort_noalloc(const gs_projected *proj, int64_t n, int V, int W, int H,
-                                         int64_t capacity, uint32_t *vals, uint32_t *ranges,
+                                         int bin, int64_t capacity, uint32_t *vals, uint32_t *ranges,
                                          uint64_t *keys, int64_t *d_count, int32_t *d_err,
                                          gs_stream stream)
 {
@@ -96,6 +96,6 @@ extern "C" gs_status gs_bin_sort_noalloc(const gs_projected *proj, int64_t n, in
     gs_status st = GS_OK;
     void *ws = scratch_address(dev, st);
     if (st != GS_OK) return st;
-    return gs_bin_sort(proj, n, V, W, H, capacity, vals, ranges, keys, d_count, d_err, ws,
+    return gs_bin_sort(proj, n, V, W, H, bin, capacity, vals, ranges, keys, d_count, d_err, ws,
                        kNoAllocScratchBytes, stream);
 }

@@ -50,6 +50,8 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 inline int tiles_x_of(int W) { return (W + GS_TILE - 1) / GS_TILE; }
 inline int tiles_y_of(int H) { return (H + GS_TILE - 1) / GS_TILE; }
+inline int bins_x_of(int W, int bin) { return (tiles_x_of(W) + bin - 1) / bin; }
+inline int bins_y_of(int H, int bin) { return (tiles_y_of(H) + bin - 1) / bin; }
 
 constexpr int kNumSMs = 152;  // GB300: 2 dies x 76 SMs
 
@@ -73,6 +75,23 @@ __device__ __forceinline__ void tile_rect(float u, float v, int r, int tx, int t
     x1 = min(tx, max(0, floor_div16_of_sum(u, (float)(r + GS_TILE - 1))));
     y0 = min(ty, max(0, floor_div16_of_sum(v, -(float)r)));
     y1 = min(ty, max(0, floor_div16_of_sum(v, (float)(r + GS_TILE - 1))));
+}
+
+// Bins of bin x bin tiles: the bin rectangle holding a footprint's tile
+// rectangle (empty when the tile rectangle is empty).
+__device__ __forceinline__ void bin_rect(float u, float v, int r, int tx, int ty, int bin, int &bx0,
+                                         int &by0, int &bx1, int &by1)
+{
+    int x0, y0, x1, y1;
+    tile_rect(u, v, r, tx, ty, x0, y0, x1, y1);
+    if (x1 <= x0 || y1 <= y0) {
+        bx0 = by0 = bx1 = by1 = 0;
+        return;
+    }
+    bx0 = x0 / bin;
+    by0 = y0 / bin;
+    bx1 = (x1 - 1) / bin + 1;
+    by1 = (y1 - 1) / bin + 1;
 }
 
 __device__ __forceinline__ float warp_sum(float x)

@@ -5,19 +5,20 @@
 
 namespace gs3 {
 
-constexpr int RT = 128;         // threads per 16x16 tile: two pixels each, rows y and y + 8
-constexpr int FWD_BATCH = 256;  // records staged per forward batch
-constexpr int BWD_BATCH = 32;   // records per backward batch (one per lane)
+constexpr int FT = 256;         // forward: threads per 16x16 tile, one pixel each
+constexpr int RT = 128;         // backward: threads per tile, two pixels each (rows y, y + 8)
+constexpr int BWD_CHUNK = 32;   // records per backward reduction chunk
 constexpr int RWARPS = RT / 32;
 
 struct RasterParams {
     const float2 *mean2d;
     const float4 *conic_op;
     const float *rgb;
+    const int32_t *radius;
     const uint32_t *vals;
     const uint2 *ranges;
     int64_t n;
-    int V, W, H, tx, tiles;
+    int V, W, H, tx, ty, bin, bins_x, bins;
     float bg0, bg1, bg2;
     float *img;
     float *T_final;
@@ -48,93 +49,111 @@ constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaCap = 0.99f;
 constexpr float kTEps = 1e-4f;
 
-// Front-to-back compositing state of one pixel.
-struct PixFwd {
-    float T, C0, C1, C2;
-    int last;
-    bool done;
-};
-
-__device__ __forceinline__ void blend_one(PixFwd &P, float2 xy, float4 co, const float *c, float pxf,
-                                          float pyf, int pos)
+// Does the footprint of record o cover tile (tx_t, ty_t)?  (Bins of one tile
+// hold only covering records.)
+template <bool BINNED>
+__device__ __forceinline__ bool covers(const RasterParams &p, int64_t o, int tx_t, int ty_t)
 {
-    float dx, dy;
-    float power = pair_power(xy, co, pxf, pyf, dx, dy);
-    if (power > 0.f) return;
-    float alpha = fminf(kAlphaCap, pair_alpha_raw(co, power));
-    if (alpha < kAlphaMin) return;
-    float test_T = P.T * (1.f - alpha);
-    if (test_T < kTEps) {
-        P.done = true;
-        return;
-    }
-    float w = alpha * P.T;
-    P.C0 = fmaf(c[0], w, P.C0);
-    P.C1 = fmaf(c[1], w, P.C1);
-    P.C2 = fmaf(c[2], w, P.C2);
-    P.T = test_T;
-    P.last = pos + 1;
+    if (!BINNED) return true;
+    int r = p.radius[o];
+    if (r <= 0) return false;
+    float2 m = p.mean2d[o];
+    int x0, y0, x1, y1;
+    tile_rect(m.x, m.y, r, p.tx, p.ty, x0, y0, x1, y1);
+    return tx_t >= x0 && tx_t < x1 && ty_t >= y0 && ty_t < y1;
 }
 
-__global__ void __launch_bounds__(RT) raster_fwd_kernel(RasterParams p)
+// Block-wide stream compaction, order preserving: returns this thread's slot
+// (or -1) and the number kept.
+template <int THREADS>
+__device__ __forceinline__ int compact_slot(bool keep, int *s_wcnt, int &count)
 {
-    __shared__ float2 s_xy[FWD_BATCH];
-    __shared__ float4 s_co[FWD_BATCH];
-    __shared__ float s_rgb[FWD_BATCH][3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned b = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) s_wcnt[warp] = __popc(b);
+    __syncthreads();
+    int off = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < THREADS / 32; ++w) {
+        int c = s_wcnt[w];
+        off += w < warp ? c : 0;
+        tot += c;
+    }
+    count = tot;
+    return keep ? off + __popc(b & ((1u << lane) - 1u)) : -1;
+}
+
+template <bool BINNED>
+__global__ void __launch_bounds__(FT) raster_fwd_kernel(RasterParams p)
+{
+    __shared__ float2 s_xy[FT];
+    __shared__ float4 s_co[FT];
+    __shared__ float s_rgb[FT][3];
+    __shared__ int s_pos[FT];
+    __shared__ int s_wcnt[FT / 32];
     const int tile = blockIdx.x, view = blockIdx.y;
     const int tid = threadIdx.x;
-    const int px = (tile % p.tx) * 16 + (tid & 15);
-    const int py0 = (tile / p.tx) * 16 + (tid >> 4);
-    const int py1 = py0 + 8;
-    const float pxf = (float)px + 0.5f, pyf0 = (float)py0 + 0.5f, pyf1 = (float)py1 + 0.5f;
-    const uint2 range = p.ranges[(int64_t)view * p.tiles + tile];
+    const int tx_t = tile % p.tx, ty_t = tile / p.tx;
+    const int px = tx_t * 16 + (tid & 15);
+    const int py = ty_t * 16 + (tid >> 4);
+    const bool inside = px < p.W && py < p.H;
+    const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
+    const int binid = (ty_t / p.bin) * p.bins_x + tx_t / p.bin;
+    const uint2 range = p.ranges[(int64_t)view * p.bins + binid];
     const int total = (int)(range.y - range.x);
     const int64_t vb = (int64_t)view * p.n;
-    PixFwd A{1.f, 0.f, 0.f, 0.f, 0, !(px < p.W && py0 < p.H)};
-    PixFwd B{1.f, 0.f, 0.f, 0.f, 0, !(px < p.W && py1 < p.H)};
-    for (int base = 0; base < total; base += FWD_BATCH) {
-        if (__syncthreads_count(A.done && B.done) == RT) break;
-#pragma unroll
-        for (int h = 0; h < FWD_BATCH / RT; ++h) {
-            int k = base + tid + h * RT;
-            if (k < total) {
-                int64_t o = vb + p.vals[range.x + k];
-                int slot = tid + h * RT;
-                s_xy[slot] = p.mean2d[o];
-                s_co[slot] = p.conic_op[o];
-                s_rgb[slot][0] = p.rgb[3 * o];
-                s_rgb[slot][1] = p.rgb[3 * o + 1];
-                s_rgb[slot][2] = p.rgb[3 * o + 2];
-            }
+    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+    int last = 0;
+    bool done = !inside;
+    for (int base = 0; base < total; base += FT) {
+        if (__syncthreads_count(done) == FT) break;
+        const int k = base + tid;
+        int64_t o = 0;
+        bool keep = false;
+        if (k < total) {
+            o = vb + p.vals[range.x + k];
+            keep = covers<BINNED>(p, o, tx_t, ty_t);
+        }
+        int cnt;
+        const int slot = compact_slot<FT>(keep, s_wcnt, cnt);
+        if (slot >= 0) {
+            s_xy[slot] = p.mean2d[o];
+            s_co[slot] = p.conic_op[o];
+            s_rgb[slot][0] = p.rgb[3 * o];
+            s_rgb[slot][1] = p.rgb[3 * o + 1];
+            s_rgb[slot][2] = p.rgb[3 * o + 2];
+            s_pos[slot] = k;
         }
         __syncthreads();
-        const int cnt = min(FWD_BATCH, total - base);
-        for (int j = 0; j < cnt && !(A.done && B.done); ++j) {
-            float2 xy = s_xy[j];
+        for (int j = 0; !done && j < cnt; ++j) {
+            float dx, dy;
             float4 co = s_co[j];
-            const float *c = s_rgb[j];
-            if (!A.done) blend_one(A, xy, co, c, pxf, pyf0, base + j);
-            if (!B.done) blend_one(B, xy, co, c, pxf, pyf1, base + j);
+            float power = pair_power(s_xy[j], co, pxf, pyf, dx, dy);
+            if (power > 0.f) continue;
+            float alpha = fminf(kAlphaCap, pair_alpha_raw(co, power));
+            if (alpha < kAlphaMin) continue;
+            float test_T = T * (1.f - alpha);
+            if (test_T < kTEps) {
+                done = true;
+                break;
+            }
+            float w = alpha * T;
+            C0 = fmaf(s_rgb[j][0], w, C0);
+            C1 = fmaf(s_rgb[j][1], w, C1);
+            C2 = fmaf(s_rgb[j][2], w, C2);
+            T = test_T;
+            last = s_pos[j] + 1;
         }
     }
-    const int64_t HW = (int64_t)p.H * p.W;
-    if (px < p.W && py0 < p.H) {
-        int64_t pix = (int64_t)py0 * p.W + px;
+    if (inside) {
+        int64_t HW = (int64_t)p.H * p.W;
+        int64_t pix = (int64_t)py * p.W + px;
         float *im = p.img + (int64_t)view * 3 * HW + pix;
-        im[0] = fmaf(A.T, p.bg0, A.C0);
-        im[HW] = fmaf(A.T, p.bg1, A.C1);
-        im[2 * HW] = fmaf(A.T, p.bg2, A.C2);
-        p.T_final[(int64_t)view * HW + pix] = A.T;
-        p.last[(int64_t)view * HW + pix] = A.last;
-    }
-    if (px < p.W && py1 < p.H) {
-        int64_t pix = (int64_t)py1 * p.W + px;
-        float *im = p.img + (int64_t)view * 3 * HW + pix;
-        im[0] = fmaf(B.T, p.bg0, B.C0);
-        im[HW] = fmaf(B.T, p.bg1, B.C1);
-        im[2 * HW] = fmaf(B.T, p.bg2, B.C2);
-        p.T_final[(int64_t)view * HW + pix] = B.T;
-        p.last[(int64_t)view * HW + pix] = B.last;
+        im[0] = fmaf(T, p.bg0, C0);
+        im[HW] = fmaf(T, p.bg1, C1);
+        im[2 * HW] = fmaf(T, p.bg2, C2);
+        p.T_final[(int64_t)view * HW + pix] = T;
+        p.last[(int64_t)view * HW + pix] = last;
     }
 }
 
@@ -176,23 +195,27 @@ __device__ __forceinline__ bool unblend_one(PixBwd &P, float2 xy, float4 co, con
     return true;
 }
 
-template <bool WANT_OP>
+template <bool WANT_OP, bool BINNED>
 __global__ void __launch_bounds__(RT) raster_bwd_kernel(RasterParams p)
 {
     constexpr int NV = WANT_OP ? 9 : 8;
-    __shared__ float2 s_xy[BWD_BATCH];
-    __shared__ float4 s_co[BWD_BATCH];
-    __shared__ float s_rgb[BWD_BATCH][3];
-    __shared__ uint32_t s_g[BWD_BATCH];
-    __shared__ float s_part[RWARPS][BWD_BATCH][NV];
+    __shared__ float2 s_xy[RT];
+    __shared__ float4 s_co[RT];
+    __shared__ float s_rgb[RT][3];
+    __shared__ uint32_t s_g[RT];
+    __shared__ int s_pos[RT];
+    __shared__ int s_wcnt[RWARPS];
+    __shared__ float s_part[RWARPS][BWD_CHUNK][NV];
     __shared__ int s_max;
     const int tile = blockIdx.x, view = blockIdx.y;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int px = (tile % p.tx) * 16 + (tid & 15);
-    const int py0 = (tile / p.tx) * 16 + (tid >> 4);
+    const int tx_t = tile % p.tx, ty_t = tile / p.tx;
+    const int px = tx_t * 16 + (tid & 15);
+    const int py0 = ty_t * 16 + (tid >> 4);
     const int py1 = py0 + 8;
     const float pxf = (float)px + 0.5f, pyf0 = (float)py0 + 0.5f, pyf1 = (float)py1 + 0.5f;
-    const uint2 range = p.ranges[(int64_t)view * p.tiles + tile];
+    const int binid = (ty_t / p.bin) * p.bins_x + tx_t / p.bin;
+    const uint2 range = p.ranges[(int64_t)view * p.bins + binid];
     const int64_t vb = (int64_t)view * p.n;
     const int64_t HW = (int64_t)p.H * p.W;
     PixBwd A{0, 1.f, 0.f, 0.f, 0.f, p.bg0, p.bg1, p.bg2};
@@ -221,69 +244,84 @@ __global__ void __launch_bounds__(RT) raster_bwd_kernel(RasterParams p)
     if (mylast > 0) atomicMax(&s_max, mylast);
     __syncthreads();
     const int maxlast = s_max;
-    for (int hi = maxlast; hi > 0; hi -= BWD_BATCH) {
-        const int lo = max(0, hi - BWD_BATCH);
-        const int cnt = hi - lo;
-        if (tid < cnt) {
-            uint32_t g = p.vals[range.x + lo + tid];
-            int64_t o = vb + g;
-            s_g[tid] = g;
-            s_xy[tid] = p.mean2d[o];
-            s_co[tid] = p.conic_op[o];
-            s_rgb[tid][0] = p.rgb[3 * o];
-            s_rgb[tid][1] = p.rgb[3 * o + 1];
-            s_rgb[tid][2] = p.rgb[3 * o + 2];
+    for (int hi = maxlast; hi > 0; hi -= RT) {
+        // candidates [lo, hi) of the bin list, compacted to this tile's records
+        const int lo = max(0, hi - RT);
+        const int k = lo + tid;
+        int64_t o = 0;
+        uint32_t g = 0;
+        bool keep = false;
+        if (k < hi) {
+            g = p.vals[range.x + k];
+            o = vb + g;
+            keep = covers<BINNED>(p, o, tx_t, ty_t);
+        }
+        int cnt;
+        const int slot = compact_slot<RT>(keep, s_wcnt, cnt);
+        if (slot >= 0) {
+            s_g[slot] = g;
+            s_xy[slot] = p.mean2d[o];
+            s_co[slot] = p.conic_op[o];
+            s_rgb[slot][0] = p.rgb[3 * o];
+            s_rgb[slot][1] = p.rgb[3 * o + 1];
+            s_rgb[slot][2] = p.rgb[3 * o + 2];
+            s_pos[slot] = k;
         }
         __syncthreads();
-        for (int j = cnt - 1; j >= 0; --j) {
-            float v[NV];
+        for (int chi = cnt; chi > 0; chi -= BWD_CHUNK) {
+            const int clo = max(0, chi - BWD_CHUNK);
+            for (int j = chi - 1; j >= clo; --j) {
+                float v[NV];
 #pragma unroll
-            for (int k = 0; k < NV; ++k) v[k] = 0.f;
-            const int pos = lo + j;
-            bool contrib = false;
-            if (pos < mylast) {
-                float2 xy = s_xy[j];
-                float4 co = s_co[j];
-                const float *c = s_rgb[j];
-                if (pos < A.last) contrib |= unblend_one<WANT_OP>(A, xy, co, c, pxf, pyf0, v);
-                if (pos < B.last) contrib |= unblend_one<WANT_OP>(B, xy, co, c, pxf, pyf1, v);
-            }
-            if (__any_sync(0xffffffffu, contrib)) {
+                for (int q = 0; q < NV; ++q) v[q] = 0.f;
+                const int pos = s_pos[j];
+                bool contrib = false;
+                if (pos < mylast) {
+                    float2 xy = s_xy[j];
+                    float4 co = s_co[j];
+                    const float *c = s_rgb[j];
+                    if (pos < A.last) contrib |= unblend_one<WANT_OP>(A, xy, co, c, pxf, pyf0, v);
+                    if (pos < B.last) contrib |= unblend_one<WANT_OP>(B, xy, co, c, pxf, pyf1, v);
+                }
+                if (__any_sync(0xffffffffu, contrib)) {
 #pragma unroll
-                for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
-            }
-            if (lane == 0) {
+                    for (int q = 0; q < NV; ++q) v[q] = warp_sum(v[q]);
+                }
+                if (lane == 0) {
 #pragma unroll
-                for (int k = 0; k < NV; ++k) s_part[warp][j][k] = v[k];
+                    for (int q = 0; q < NV; ++q) s_part[warp][j - clo][q] = v[q];
+                }
             }
+            __syncthreads();
+            const int ccnt = chi - clo;
+            // tile-wide sums: thread t -> (record t/2, half t%2), one float4 atomic
+            if (tid < 2 * ccnt) {
+                int j = tid >> 1, h = (tid & 1) * 4;
+                float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int w = 0; w < RWARPS; ++w) {
+                    sum.x += s_part[w][j][h];
+                    sum.y += s_part[w][j][h + 1];
+                    sum.z += s_part[w][j][h + 2];
+                    sum.w += s_part[w][j][h + 3];
+                }
+                if (sum.x != 0.f || sum.y != 0.f || sum.z != 0.f || sum.w != 0.f)
+                    atomicAdd(reinterpret_cast<float4 *>(p.grads + 8 * (vb + s_g[clo + j]) + h), sum);
+            } else if (WANT_OP && tid >= 64 && tid < 64 + ccnt) {
+                int j = tid - 64;
+                float sum = 0.f;
+#pragma unroll
+                for (int w = 0; w < RWARPS; ++w) sum += s_part[w][j][NV - 1];
+                if (sum != 0.f) atomicAdd(p.d_opacity + vb + s_g[clo + j], sum);
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        // tile-wide sums: thread t -> (record t/2, half t%2), one float4 atomic
-        if (tid < 2 * cnt) {
-            int j = tid >> 1, h = (tid & 1) * 4;
-            float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-            for (int w = 0; w < RWARPS; ++w) {
-                s.x += s_part[w][j][h];
-                s.y += s_part[w][j][h + 1];
-                s.z += s_part[w][j][h + 2];
-                s.w += s_part[w][j][h + 3];
-            }
-            if (s.x != 0.f || s.y != 0.f || s.z != 0.f || s.w != 0.f)
-                atomicAdd(reinterpret_cast<float4 *>(p.grads + 8 * (vb + s_g[j]) + h), s);
-        } else if (WANT_OP && tid >= 64 && tid < 64 + cnt) {
-            int j = tid - 64;
-            float s = 0.f;
-#pragma unroll
-            for (int w = 0; w < RWARPS; ++w) s += s_part[w][j][NV - 1];
-            if (s != 0.f) atomicAdd(p.d_opacity + vb + s_g[j], s);
-        }
-        __syncthreads();
     }
 }
 
-static gs_status fill(const gs_projected *proj, int64_t n, int V, int W, int H, const float *bg,
-                      const uint32_t *vals, const uint32_t *ranges, RasterParams &p)
+static gs_status fill(const gs_projected *proj, int64_t n, int V, int W, int H, int bin,
+                      const float *bg, const uint32_t *vals, const uint32_t *ranges,
+                      RasterParams &p)
 {
     GS_REQUIRE(proj && vals && ranges, "raster: null argument");
     GS_REQUIRE(n >= 0 && V >= 1 && V <= GS_MAX_VIEWS, "raster: bad n or V");
@@ -293,6 +331,9 @@ static gs_status fill(const gs_projected *proj, int64_t n, int V, int W, int H, 
     p.mean2d = reinterpret_cast<const float2 *>(proj->mean2d);
     p.conic_op = reinterpret_cast<const float4 *>(proj->conic_opacity);
     p.rgb = proj->rgb;
+    p.radius = proj->radius;
+    GS_REQUIRE(bin >= 1 && bin <= 64, "raster: bin must be 1..64 tiles");
+    GS_REQUIRE(bin == 1 || proj->radius, "raster: binned lists need the radius array");
     p.vals = vals;
     p.ranges = reinterpret_cast<const uint2 *>(ranges);
     p.n = n;
@@ -300,7 +341,10 @@ static gs_status fill(const gs_projected *proj, int64_t n, int V, int W, int H, 
     p.W = W;
     p.H = H;
     p.tx = tiles_x_of(W);
-    p.tiles = p.tx * tiles_y_of(H);
+    p.ty = tiles_y_of(H);
+    p.bin = bin;
+    p.bins_x = bins_x_of(W, bin);
+    p.bins = p.bins_x * bins_y_of(H, bin);
     p.bg0 = bg ? bg[0] : 0.f;
     p.bg1 = bg ? bg[1] : 0.f;
     p.bg2 = bg ? bg[2] : 0.f;
@@ -312,29 +356,34 @@ static gs_status fill(const gs_projected *proj, int64_t n, int V, int W, int H, 
 using namespace gs3;
 
 extern "C" gs_status gs_raster_fwd(const gs_projected *proj, int64_t n, int V, int W, int H,
-                                   const float *bg, const uint32_t *vals, const uint32_t *ranges,
-                                   float *img, float *T_final, int32_t *last, gs_stream stream)
+                                   int bin, const float *bg, const uint32_t *vals,
+                                   const uint32_t *ranges, float *img, float *T_final,
+                                   int32_t *last, gs_stream stream)
 {
     RasterParams p{};
-    gs_status st = fill(proj, n, V, W, H, bg, vals, ranges, p);
+    gs_status st = fill(proj, n, V, W, H, bin, bg, vals, ranges, p);
     if (st != GS_OK) return st;
     GS_REQUIRE(img && T_final && last, "gs_raster_fwd: null output");
     p.img = img;
     p.T_final = T_final;
     p.last = last;
-    dim3 grid(p.tiles, V);
+    dim3 grid(p.tx * p.ty, V);
     note_launch();
-    raster_fwd_kernel<<<grid, RT, 0, as_stream(stream)>>>(p);
+    if (bin > 1)
+        raster_fwd_kernel<true><<<grid, FT, 0, as_stream(stream)>>>(p);
+    else
+        raster_fwd_kernel<false><<<grid, FT, 0, as_stream(stream)>>>(p);
     return launch_status("gs_raster_fwd");
 }
 
 extern "C" gs_status gs_raster_bwd(const gs_projected *proj, int64_t n, int V, int W, int H,
-                                   const float *bg, const uint32_t *vals, const uint32_t *ranges,
-                                   const float *T_final, const int32_t *last, const float *d_img,
-                                   float *grads, float *d_opacity, gs_stream stream)
+                                   int bin, const float *bg, const uint32_t *vals,
+                                   const uint32_t *ranges, const float *T_final,
+                                   const int32_t *last, const float *d_img, float *grads,
+                                   float *d_opacity, gs_stream stream)
 {
     RasterParams p{};
-    gs_status st = fill(proj, n, V, W, H, bg, vals, ranges, p);
+    gs_status st = fill(proj, n, V, W, H, bin, bg, vals, ranges, p);
     if (st != GS_OK) return st;
     GS_REQUIRE(T_final && last && d_img && grads, "gs_raster_bwd: null argument");
     GS_REQUIRE(aligned(grads, 16), "gs_raster_bwd: grads must be 16-byte aligned");
@@ -346,11 +395,15 @@ extern "C" gs_status gs_raster_bwd(const gs_projected *proj, int64_t n, int V, i
     p.d_img = d_img;
     p.grads = grads;
     p.d_opacity = d_opacity;
-    dim3 grid(p.tiles, V);
+    dim3 grid(p.tx * p.ty, V);
     note_launch();
-    if (d_opacity)
-        raster_bwd_kernel<true><<<grid, RT, 0, s>>>(p);
+    if (d_opacity && bin > 1)
+        raster_bwd_kernel<true, true><<<grid, RT, 0, s>>>(p);
+    else if (d_opacity)
+        raster_bwd_kernel<true, false><<<grid, RT, 0, s>>>(p);
+    else if (bin > 1)
+        raster_bwd_kernel<false, true><<<grid, RT, 0, s>>>(p);
     else
-        raster_bwd_kernel<false><<<grid, RT, 0, s>>>(p);
+        raster_bwd_kernel<false, false><<<grid, RT, 0, s>>>(p);
     return launch_status("gs_raster_bwd");
 }

@@ -19,6 +19,7 @@ LAMBDA_DSSIM = 0.2          # Eq. 6
 NTC_LR = 0.002              # Suppl. A
 ADAM_BETAS = (0.9, 0.99)    # I-NGP's Adam constants (the paper's NTC follows I-NGP)
 ADAM_EPS = 1e-15
+DEFAULT_BIN = 8             # tiles per bin side for the binned pair lists
 
 
 def _i32(*shape, device="cuda"):
@@ -33,13 +34,14 @@ class Rasterizer:
     """Projection + binning + compositing (+ reverse) for V views of W x H."""
 
     def __init__(self, n: int, V: int, W: int, H: int, capacity: int, device="cuda",
-                 bg=(0.0, 0.0, 0.0)):
+                 bg=(0.0, 0.0, 0.0), bin: int = DEFAULT_BIN):
         self.n, self.V, self.W, self.H = n, V, W, H
         self.device = device
         self.bg = tuple(float(x) for x in bg)
-        self.tiles = math.ceil(W / gs3.TILE) * math.ceil(H / gs3.TILE)
+        self.bin = int(bin)
+        self.bins = gs3.bins_of(W, H, self.bin)
         self.proj = Projected.empty(V, n, device)
-        self.ranges = _i32(V * self.tiles, 2, device=device)
+        self.ranges = _i32(V * self.bins, 2, device=device)
         self.d_count = torch.zeros(1, dtype=torch.int64, device=device)
         self.d_err = _i32(1, device=device)
         self.img = _f32(V, 3, H, W, device=device)
@@ -59,16 +61,16 @@ class Rasterizer:
     def forward(self, g: Gaussians, cams_dev, mean=None, quat=None, stream=None, keys=None):
         V, W, H, n = self.V, self.W, self.H, self.n
         gs3.gs_project(g, cams_dev, V, W, H, self.proj, mean, quat, stream)
-        gs3.gs_bin_sort(self.proj, n, V, W, H, self.capacity, self.vals, self.ranges, keys,
+        gs3.gs_bin_sort(self.proj, n, V, W, H, self.bin, self.capacity, self.vals, self.ranges, keys,
                         self.d_count, self.d_err, self.ws, stream)
-        gs3.gs_raster_fwd(self.proj, n, V, W, H, self.bg, self.vals, self.ranges, self.img,
+        gs3.gs_raster_fwd(self.proj, n, V, W, H, self.bin, self.bg, self.vals, self.ranges, self.img,
                           self.T_final, self.last, stream)
         return self.img
 
     def backward(self, g: Gaussians, cams_dev, d_img, mean=None, quat=None, stream=None):
         V, W, H, n = self.V, self.W, self.H, self.n
-        gs3.gs_raster_bwd(self.proj, n, V, W, H, self.bg, self.vals, self.ranges, self.T_final,
-                          self.last, d_img, self.grads, None, stream)
+        gs3.gs_raster_bwd(self.proj, n, V, W, H, self.bin, self.bg, self.vals, self.ranges,
+                          self.T_final, self.last, d_img, self.grads, None, stream)
         gs3.gs_project_bwd(g, cams_dev, V, W, H, self.grads, self.d_mean, self.d_quat, mean, quat,
                            stream)
         return self.d_mean, self.d_quat
@@ -177,10 +179,10 @@ class Stage1:
 
     def __init__(self, g: Gaussians, ntc: NTC, V: int, W: int, H: int, capacity: int,
                  order: int = 0, loss_scale: Optional[float] = None, growth_interval=2000,
-                 device="cuda"):
+                 device="cuda", bin: int = DEFAULT_BIN):
         n = g.n
         self.g, self.ntc, self.V, self.W, self.H, self.order = g, ntc, V, W, H, order
-        self.raster = Rasterizer(n, V, W, H, capacity, device)
+        self.raster = Rasterizer(n, V, W, H, capacity, device, bin=bin)
         self.loss = Loss(V, W, H, device)
         self.enc = torch.zeros(n, 32, dtype=ntc.enc_dtype(), device=device)
         self.raw7 = _f32(n, 7, device=device)
@@ -245,10 +247,10 @@ class DirectOpt:
     rotations (the "Direct Opt." comparator of Section 5.3), same rasterizer."""
 
     def __init__(self, g: Gaussians, V: int, W: int, H: int, capacity: int, lr_mean=0.0024,
-                 lr_quat=0.015, device="cuda"):
+                 lr_quat=0.015, device="cuda", bin: int = DEFAULT_BIN):
         self.g = g
         self.V, self.W, self.H = V, W, H
-        self.raster = Rasterizer(g.n, V, W, H, capacity, device)
+        self.raster = Rasterizer(g.n, V, W, H, capacity, device, bin=bin)
         self.loss = Loss(V, W, H, device)
         self.mean = AdamBuffers(g.mean.clone(), lr_mean)
         self.quat = AdamBuffers(g.quat.clone(), lr_quat)
@@ -302,9 +304,9 @@ def warmup(ntc: NTC, g: Gaussians, iters=3000, noise=0.01, extent=2.0, seed=0, s
 
 
 def render(g: Gaussians, cams, W: int, H: int, mean=None, quat=None, capacity=None,
-           device="cuda") -> torch.Tensor:
+           device="cuda", bin: int = DEFAULT_BIN) -> torch.Tensor:
     """Render all cams (one launch) with the CUDA rasterizer; returns [V,3,H,W]."""
     cams_dev = gs3.cameras_to_device(cams, device)
-    r = Rasterizer(g.n, len(cams), W, H, capacity or 1 << 20, device)
+    r = Rasterizer(g.n, len(cams), W, H, capacity or 1 << 20, device, bin=bin)
     r.fit_capacity(g, cams_dev, mean, quat)
     return r.img.clone()

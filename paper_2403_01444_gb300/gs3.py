@@ -25,6 +25,12 @@ GS_MLP_FP32, GS_MLP_BF16 = 0, 1
 MLP_PARAMS = 64 * 32 + 64 * 64 + 7 * 64
 TILE = 16
 
+
+def bins_of(W, H, bin):
+    """Number of bins (of bin x bin tiles) of a W x H view."""
+    tx, ty = (W + TILE - 1) // TILE, (H + TILE - 1) // TILE
+    return ((tx + bin - 1) // bin) * ((ty + bin - 1) // bin)
+
 c_void_p, c_int, c_int32, c_int64, c_float, c_size_t = (
     ctypes.c_void_p, ctypes.c_int, ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_size_t)
 
@@ -206,23 +212,23 @@ def gs_bin_sort_workspace_size(n, V, W, H, capacity) -> int:
     return int(lib().gs_bin_sort_workspace_size(n, V, W, H, capacity))
 
 
-def gs_bin_sort(proj: Projected, n, V, W, H, capacity, vals, ranges, keys, d_count, d_err, ws,
+def gs_bin_sort(proj: Projected, n, V, W, H, bin, capacity, vals, ranges, keys, d_count, d_err, ws,
                 stream=None):
     po = proj.struct()
     _check("gs_bin_sort", lib().gs_bin_sort(
-        ctypes.byref(po), c_int64(n), c_int(V), c_int(W), c_int(H), c_int64(capacity), _ptr(vals),
+        ctypes.byref(po), c_int64(n), c_int(V), c_int(W), c_int(H), c_int(bin), c_int64(capacity), _ptr(vals),
         _ptr(ranges), _ptr(keys), _ptr(d_count), _ptr(d_err), _ptr(ws), c_size_t(ws.numel()),
         _stream(stream)))
 
 
-def gs_bin_sort_noalloc(proj: Projected, n, V, W, H, capacity, vals, ranges, keys, d_count, d_err,
-                        stream=None):
+def gs_bin_sort_noalloc(proj: Projected, n, V, W, H, bin, capacity, vals, ranges, keys, d_count,
+                        d_err, stream=None):
     """gs_bin_sort with the library's built-in scratch (no workspace argument):
     for callers that cannot allocate device memory.  Limits and sharing rules
     are those of the C entry point."""
     po = proj.struct()
     _check("gs_bin_sort_noalloc", lib().gs_bin_sort_noalloc(
-        ctypes.byref(po), c_int64(n), c_int(V), c_int(W), c_int(H), c_int64(capacity), _ptr(vals),
+        ctypes.byref(po), c_int64(n), c_int(V), c_int(W), c_int(H), c_int(bin), c_int64(capacity), _ptr(vals),
         _ptr(ranges), _ptr(keys), _ptr(d_count), _ptr(d_err), _stream(stream)))
 
 
@@ -231,18 +237,18 @@ def _bg(bg):
     return a
 
 
-def gs_raster_fwd(proj: Projected, n, V, W, H, bg, vals, ranges, img, T_final, last, stream=None):
+def gs_raster_fwd(proj: Projected, n, V, W, H, bin, bg, vals, ranges, img, T_final, last, stream=None):
     po = proj.struct()
     _check("gs_raster_fwd", lib().gs_raster_fwd(
-        ctypes.byref(po), c_int64(n), c_int(V), c_int(W), c_int(H), _bg(bg), _ptr(vals), _ptr(ranges),
+        ctypes.byref(po), c_int64(n), c_int(V), c_int(W), c_int(H), c_int(bin), _bg(bg), _ptr(vals), _ptr(ranges),
         _ptr(img), _ptr(T_final), _ptr(last), _stream(stream)))
 
 
-def gs_raster_bwd(proj: Projected, n, V, W, H, bg, vals, ranges, T_final, last, d_img, grads,
+def gs_raster_bwd(proj: Projected, n, V, W, H, bin, bg, vals, ranges, T_final, last, d_img, grads,
                   d_opacity=None, stream=None):
     po = proj.struct()
     _check("gs_raster_bwd", lib().gs_raster_bwd(
-        ctypes.byref(po), c_int64(n), c_int(V), c_int(W), c_int(H), _bg(bg), _ptr(vals), _ptr(ranges),
+        ctypes.byref(po), c_int64(n), c_int(V), c_int(W), c_int(H), c_int(bin), _bg(bg), _ptr(vals), _ptr(ranges),
         _ptr(T_final), _ptr(last), _ptr(d_img), _ptr(grads), _ptr(d_opacity), _stream(stream)))
 
 

@@ -57,12 +57,12 @@ def projected_from_records(rec, device=DEV):
     return p
 
 
-def gpu_bin_sort(p, N, V, W, H, capacity=None, keys=True):
+def gpu_bin_sort(p, N, V, W, H, capacity=None, keys=True, bin=1):
     cap = capacity if capacity is not None else 4 * N * V * 64 + 16
-    r = Rasterizer(N, V, W, H, cap, DEV)
+    r = Rasterizer(N, V, W, H, cap, DEV, bin=bin)
     r.proj = p
     k = torch.zeros(max(cap, 1), dtype=torch.int64, device=DEV) if keys else None
-    gs3.gs_bin_sort(p, N, V, W, H, r.capacity, r.vals, r.ranges, k, r.d_count, r.d_err, r.ws)
+    gs3.gs_bin_sort(p, N, V, W, H, bin, r.capacity, r.vals, r.ranges, k, r.d_count, r.d_err, r.ws)
     torch.cuda.synchronize()
     return r, k
 
@@ -102,12 +102,12 @@ def test_bin_sort_all_culled_and_capacity_overflow():
 
 
 # --------------------------------------------------------------- compositing
-def raster_case(V, N, W, H, seed, **kw):
+def raster_case(V, N, W, H, seed, bin=1, **kw):
     rec = scenes.random_projected(V, N, W, H, np.random.default_rng(seed), **kw)
     p = projected_from_records(rec)
-    r, _ = gpu_bin_sort(p, N, V, W, H, keys=False)
+    r, _ = gpu_bin_sort(p, N, V, W, H, keys=False, bin=bin)
     bg = (0.1, 0.2, 0.3)
-    gs3.gs_raster_fwd(p, N, V, W, H, bg, r.vals, r.ranges, r.img, r.T_final, r.last)
+    gs3.gs_raster_fwd(p, N, V, W, H, bin, bg, r.vals, r.ranges, r.img, r.T_final, r.last)
     torch.cuda.synchronize()
     return rec, p, r, bg
 
@@ -137,12 +137,68 @@ def test_raster_bwd_parity(V, N, W, H, seed):
     grads, dop = oracle.raster_bwd(rec, W, H, Tf, last, d_img, bg, want_opacity=True)
     gg = torch.zeros(V, N, 8, device=DEV)
     gop = torch.zeros(V, N, device=DEV)
-    gs3.gs_raster_bwd(p, N, V, W, H, bg, r.vals, r.ranges, r.T_final, r.last, t(d_img), gg, gop)
+    gs3.gs_raster_bwd(p, N, V, W, H, 1, bg, r.vals, r.ranges, r.T_final, r.last, t(d_img), gg, gop)
     torch.cuda.synchronize()
     gg = gg.cpu().numpy()
     for sl in (slice(0, 2), slice(2, 5), slice(5, 8)):
         assert_grad_close(gg[..., sl], grads[..., sl])
     assert_grad_close(gop.cpu().numpy(), dop)
+
+
+@pytest.mark.parametrize("bin", [2, 3, 8])
+def test_binned_keys_brute_force(bin):
+    """Bins of bin x bin tiles: keys (view * bins + bin_id) << 32 | depth bits,
+    values and ranges against a brute-force enumeration of (entry, bin) pairs."""
+    V, N, W, H = 2, 700, 200, 130
+    rec = scenes.random_projected(V, N, W, H, np.random.default_rng(40 + bin))
+    rec["depth"][:, ::5] = rec["depth"][:, :1]
+    p = projected_from_records(rec)
+    r, k = gpu_bin_sort(p, N, V, W, H, bin=bin)
+    tx, ty = math.ceil(W / 16), math.ceil(H / 16)
+    bx, by = math.ceil(tx / bin), math.ceil(ty / bin)
+    pairs = []
+    for v in range(V):
+        for i in range(N):
+            rr = int(rec["radius"][v, i])
+            if rr <= 0:
+                continue
+            u, w = (float(x) for x in rec["mean2d"][v, i])
+            x0 = min(tx, max(0, math.floor((u - rr) / 16)))
+            x1 = min(tx, max(0, math.floor((u + rr + 15) / 16)))
+            y0 = min(ty, max(0, math.floor((w - rr) / 16)))
+            y1 = min(ty, max(0, math.floor((w + rr + 15) / 16)))
+            if x1 <= x0 or y1 <= y0:
+                continue
+            db = int(np.float32(rec["depth"][v, i]).view(np.uint32))
+            for yb in range(y0 // bin, (y1 - 1) // bin + 1):
+                for xb in range(x0 // bin, (x1 - 1) // bin + 1):
+                    pairs.append((((v * bx * by + yb * bx + xb) << 32) | db, i))
+    pairs.sort()
+    n = r.count()
+    assert n == len(pairs)
+    assert [int(x) for x in k[:n].cpu().numpy().view(np.uint64)] == [q[0] for q in pairs]
+    assert [int(x) for x in r.vals[:n].cpu().numpy().view(np.uint32)] == [q[1] for q in pairs]
+
+
+@pytest.mark.parametrize("bin", [2, 4, 8])
+def test_binned_raster_equals_per_tile(bin):
+    """A tile's records, taken on the fly from its bin's list, are the per-tile
+    list: identical images and transmittance, and equal gradients."""
+    V, N, W, H = 2, 3000, 300, 170
+    rec, p, r1, bg = raster_case(V, N, W, H, 50, bin=1)
+    _, p2, r2, _ = raster_case(V, N, W, H, 50, bin=bin)
+    assert torch.equal(r1.img, r2.img)
+    assert torch.equal(r1.T_final, r2.T_final)
+    d_img = t(np.random.default_rng(51).normal(size=(V, 3, H, W)))
+    g1 = torch.zeros(V, N, 8, device=DEV)
+    g2 = torch.zeros(V, N, 8, device=DEV)
+    o1 = torch.zeros(V, N, device=DEV)
+    o2 = torch.zeros(V, N, device=DEV)
+    gs3.gs_raster_bwd(p, N, V, W, H, 1, bg, r1.vals, r1.ranges, r1.T_final, r1.last, d_img, g1, o1)
+    gs3.gs_raster_bwd(p2, N, V, W, H, bin, bg, r2.vals, r2.ranges, r2.T_final, r2.last, d_img, g2, o2)
+    torch.cuda.synchronize()
+    assert rel_err(g2.cpu().numpy(), g1.cpu().numpy()) <= 1e-5
+    assert rel_err(o2.cpu().numpy(), o1.cpu().numpy()) <= 1e-5
 
 
 # ------------------------------------------------------------------ projection

@@ -53,12 +53,12 @@ def _run_both(V, N, W, H, seed):
     cap = 200_000
     ref = _outputs(V, N, W, H, cap)
     ws = torch.empty(gs3.gs_bin_sort_workspace_size(N, V, W, H, cap), dtype=torch.uint8, device=DEV)
-    gs3.gs_bin_sort(p, N, V, W, H, cap, ref["vals"], ref["ranges"], ref["keys"], ref["count"],
+    gs3.gs_bin_sort(p, N, V, W, H, 1, cap, ref["vals"], ref["ranges"], ref["keys"], ref["count"],
                     ref["err"], ws)
     got = _outputs(V, N, W, H, cap)
     got["vals"].fill_(-1)
     got["keys"].fill_(-1)
-    gs3.gs_bin_sort_noalloc(p, N, V, W, H, cap, got["vals"], got["ranges"], got["keys"],
+    gs3.gs_bin_sort_noalloc(p, N, V, W, H, 1, cap, got["vals"], got["ranges"], got["keys"],
                             got["count"], got["err"])
     torch.cuda.synchronize()
     n = int(ref["count"].item())
@@ -80,10 +80,10 @@ def test_noalloc_rejects_oversized_problems():
     o = _outputs(V, 8, W, H, 16)
     with pytest.raises(gs3.GsError) as e:
         # n * V above the 131072-entry limit: refused before any launch
-        gs3.gs_bin_sort_noalloc(p, 200_000, V, W, H, 16, o["vals"], o["ranges"], o["keys"],
+        gs3.gs_bin_sort_noalloc(p, 200_000, V, W, H, 1, 16, o["vals"], o["ranges"], o["keys"],
                                 o["count"], o["err"])
     assert e.value.status == gs3.GS_ERR_INVALID_ARG
     with pytest.raises(gs3.GsError) as e:
-        gs3.gs_bin_sort_noalloc(p, 8, V, W, H, 1 << 21, o["vals"], o["ranges"], o["keys"],
+        gs3.gs_bin_sort_noalloc(p, 8, V, W, H, 1, 1 << 21, o["vals"], o["ranges"], o["keys"],
                                 o["count"], o["err"])
     assert e.value.status == gs3.GS_ERR_INVALID_ARG
