@@ -250,6 +250,8 @@ def run_ours(args):
 
     stream = torch.cuda.current_stream()
     ev = {}
+    stats = torch.zeros(4, dtype=torch.int64, device=dev)
+    count_pairs = False
 
     def step(i, record=False):
         if i % ITERS_PER_FRAME == 0:
@@ -268,12 +270,13 @@ def run_ours(args):
         r = st.raster
         gs3.gs_bin_sort(r.proj, G.n, Vb, W, H, r.bin, r.capacity, r.vals, r.ranges, None, r.d_count, r.d_err, r.ws)
         E("t3")
-        gs3.gs_raster_fwd(r.proj, G.n, Vb, W, H, r.bin, r.bg, r.vals, r.ranges, r.img, r.T_final, r.last)
+        gs3.gs_raster_fwd(r.proj, G.n, Vb, W, H, r.bin, r.bg, r.vals, r.ranges, r.img, r.T_final, r.last,
+                          stats[0:2] if count_pairs else None)
         E("t4")
         st.loss(r.img, tg)
         E("t5")
         gs3.gs_raster_bwd(r.proj, G.n, Vb, W, H, r.bin, r.bg, r.vals, r.ranges, r.T_final, r.last,
-                          st.loss.d_img, r.grads, None)
+                          st.loss.d_img, r.grads, None, stats[2:4] if count_pairs else None)
         E("t6")
         gs3.gs_project_bwd(G, cd, Vb, W, H, r.grads, r.d_mean, r.d_quat, st.mean_t, st.quat_t)
         E("t7")
@@ -319,6 +322,15 @@ def run_ours(args):
     for i in range(args.warmup + args.steps, args.warmup + args.steps + 10):
         step(i, record=True)
     torch.cuda.synchronize()
+    # (pixel, Gaussian) pairs the compositing kernels evaluate in one step
+    ev_keep = {k: list(v) for k, v in ev.items()}
+    stats.zero_()
+    count_pairs = True
+    step(args.warmup + args.steps + 10, record=True)
+    count_pairs = False
+    torch.cuda.synchronize()
+    ev = ev_keep
+    pair_counts = [int(x) for x in stats.cpu().tolist()]
     names = ["ntc_fwd", "project", "bin_sort", "raster_fwd", "loss", "raster_bwd", "project_bwd",
              "ntc_bwd", "adam"]
     stages = {}
@@ -333,7 +345,8 @@ def run_ours(args):
     # roofline of the dominant kernel group
     hbm, bf16, src = load_peaks()
     dom = max(stages, key=stages.get)
-    roof = roofline_for(dom, stages[dom], pairs, G.n, Vb, W, H, cfg, hbm, src)
+    sm_mhz = clk.summary().get("sm_mhz") or 2070.0
+    roof = roofline_for(dom, stages[dom], pairs, pair_counts, G.n, Vb, W, H, cfg, hbm, src, sm_mhz)
 
     # plain FP32 direct optimisation on the same inputs and rasterizer
     plain = None
@@ -396,7 +409,8 @@ def run_ours(args):
                 "plain_fp32_direct_opt": plain,
                 "speedup_vs_plain_per_iter": (plain["ms_per_iter"] / ms_max) if plain else None,
                 "stages_ms": {k: round(v, 4) for k, v in stages.items()},
-                "pairs_per_step": pairs, "warmup_loss": wl, "warmup_s": t_warm,
+                "bin_pairs_per_step": pairs, "composited_pairs": pair_counts,
+                "warmup_loss": wl, "warmup_s": t_warm,
                 "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_ms * ITERS_PER_FRAME / 1e3, "unit": "s/frame",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4},
@@ -412,16 +426,34 @@ def ctypes_u64():
     return ctypes.c_uint64
 
 
-def roofline_for(stage, ms, pairs, n, V, W, H, cfg, hbm_gbs, src):
-    """Algorithmic bytes of one launch of the stage's kernels (each logically
-    required read or write counted once) over its measured time."""
+# FP32 operations per (pixel, Gaussian) pair, counted from the compositing
+# formulas: the power and alpha of a pair (12), the front-to-back update of
+# an added pair (9), and the reverse of an added pair (47: T recovery, colour,
+# alpha and conic/mean gradients, behind-colour update).
+FLOPS_TESTED, FLOPS_FWD_ADDED, FLOPS_BWD_ADDED = 12, 9, 47
+
+
+def roofline_for(stage, ms, pairs, pair_counts, n, V, W, H, cfg, hbm_gbs, src, sm_mhz):
+    """Roofline of one launch of the stage's kernels: compositing is bound by
+    FP32 arithmetic (FLOPs of the evaluated pairs over the FP32 FMA peak of
+    152 SMs x 128 lanes x 2 FLOPs x SM clock); the other stages by HBM
+    (each logically required read or write counted once)."""
+    if stage in ("raster_fwd", "raster_bwd"):
+        tested, added = (pair_counts[0], pair_counts[1]) if stage == "raster_fwd" else \
+            (pair_counts[2], pair_counts[3])
+        per_added = FLOPS_FWD_ADDED if stage == "raster_fwd" else FLOPS_BWD_ADDED
+        flops = tested * FLOPS_TESTED + added * per_added
+        achieved = flops / (ms * 1e-3) / 1e12
+        peak = kNumSMs * 128 * 2 * sm_mhz * 1e6 / 1e12
+        return {"bound": "alu", "kernel": stage, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "algorithmic_flops": flops, "pairs_evaluated": tested, "pairs_added": added,
+                "ms": ms, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_mhz}
     K = (cfg.sh_deg + 1) ** 2
     px = V * W * H
     per_gauss_params = 12 + 16 + 12 + 4 + 12 * K
     bytes_ = {
-        "bin_sort": pairs * (12 + 24 + 8),              # key/val write, one sort r+w, range scan
-        "raster_fwd": pairs * 40 + px * 20,             # records + index per pair, outputs
-        "raster_bwd": pairs * 40 + px * 32 + n * V * 32,
+        "bin_sort": pairs * (12 + 24 + 8),
         "project": n * per_gauss_params + n * V * 44,
         "project_bwd": n * per_gauss_params + n * V * 32 + n * 28,
         "loss": px * 3 * 4 * 3,
@@ -433,6 +465,9 @@ def roofline_for(stage, ms, pairs, n, V, W, H, cfg, hbm_gbs, src):
     return {"bound": "hbm", "kernel": stage, "achieved": achieved, "peak": hbm_gbs,
             "unit": "GB/s", "frac": achieved / hbm_gbs, "traffic": None,
             "algorithmic_bytes": bytes_, "ms": ms, "peak_source": src}
+
+
+kNumSMs = 152
 
 
 def main():

@@ -223,21 +223,27 @@ GS_API gs_status gs_bin_sort_noalloc(const gs_projected *proj, int64_t n, int V,
  * Gaussian that would take T below 1e-4; C += rgb alpha T; T *= 1 - alpha.
  * Writes img[V][3][H][W] = C + T bg, T_final[V][H][W] and last[V][H][W] (1 +
  * position in the bin's list of the last Gaussian added, 0 if none).  vals /
- * ranges are gs_bin_sort's output for the same bin. */
+ * ranges are gs_bin_sort's output for the same bin.  A record whose
+ * alpha-ellipse cannot reach 1/255 at any pixel centre of a tile (a margin
+ * of 0.01 in the quadratic form) is not staged for that tile: every pixel
+ * would skip it, so results are unchanged.  d_stats (device uint64[2], or
+ * NULL) accumulates the (pixel, Gaussian) pairs evaluated and added. */
 GS_API gs_status gs_raster_fwd(const gs_projected *proj, int64_t n, int V, int W, int H, int bin,
                         const float *bg, const uint32_t *vals, const uint32_t *ranges, float *img,
-                        float *T_final, int32_t *last, gs_stream stream);
+                        float *T_final, int32_t *last, uint64_t *d_stats, gs_stream stream);
 
 /* Reverse of gs_raster_fwd: walks each pixel's list back to front from
  * `last`, recomputing T_i = T_{i+1} / (1 - alpha_i) from T_final (no per-pair
  * state is stored).  Per-(view, Gaussian) gradients are reduced across each
  * warp and each tile before one vector atomic per (Gaussian, tile).
  * Overwrites grads[V][N][8] = dL/d(u, v, A, B, C, r, g, b) and, when non-NULL,
- * d_opacity[V][N].  bg is a host array of 3 floats. */
+ * d_opacity[V][N].  bg is a host array of 3 floats.  d_stats (device
+ * uint64[2], or NULL) accumulates the pairs walked and the pairs that had
+ * contributed. */
 GS_API gs_status gs_raster_bwd(const gs_projected *proj, int64_t n, int V, int W, int H, int bin,
                         const float *bg, const uint32_t *vals, const uint32_t *ranges,
                         const float *T_final, const int32_t *last, const float *d_img,
-                        float *grads, float *d_opacity, gs_stream stream);
+                        float *grads, float *d_opacity, uint64_t *d_stats, gs_stream stream);
 
 /* ------------------------------------------------------------------- loss */
 

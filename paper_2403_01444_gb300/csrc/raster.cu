@@ -27,7 +27,25 @@ struct RasterParams {
     const float *d_img;
     float *grads;
     float *d_opacity;
+    unsigned long long *stats;  // optional: [tested, contributing] (pixel, Gaussian) pairs
 };
+
+// Add this thread's pair counts to the optional statistics words.
+__device__ __forceinline__ void flush_stats(unsigned long long *stats, uint32_t tested,
+                                            uint32_t contrib)
+{
+    if (!stats) return;
+    unsigned long long a = tested, b = contrib;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(stats, a);
+        atomicAdd(stats + 1, b);
+    }
+}
 
 // power and alpha of one (pixel, Gaussian) pair.  Written with explicit
 // roundings so the forward and the reverse pass take bit-identical decisions.
@@ -49,18 +67,50 @@ constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaCap = 0.99f;
 constexpr float kTEps = 1e-4f;
 
-// Does the footprint of record o cover tile (tx_t, ty_t)?  (Bins of one tile
-// hold only covering records.)
-template <bool BINNED>
-__device__ __forceinline__ bool covers(const RasterParams &p, int64_t o, int tx_t, int ty_t)
+// Can record (m, co) reach alpha >= 1/255 at some pixel centre of tile
+// (tx_t, ty_t)?  alpha = o exp(-q/2) with q = A dx^2 + 2B dx dy + C dy^2, so
+// it needs q <= 2 ln(255 o) somewhere in the tile.  The minimum of the convex
+// q over the tile's rectangle of pixel centres is 0 when the mean lies inside,
+// else it is on an edge, where q is a 1-D quadratic minimised in closed form.
+// A margin of 0.01 in q (far above FP32 rounding) keeps the test
+// conservative: a dropped record is one every pixel of the tile would skip,
+// so images, gradients and list positions are unchanged.
+__device__ __forceinline__ bool ellipse_hits_tile(float2 m, float4 co, int tx_t, int ty_t)
 {
-    if (!BINNED) return true;
-    int r = p.radius[o];
-    if (r <= 0) return false;
-    float2 m = p.mean2d[o];
-    int x0, y0, x1, y1;
-    tile_rect(m.x, m.y, r, p.tx, p.ty, x0, y0, x1, y1);
-    return tx_t >= x0 && tx_t < x1 && ty_t >= y0 && ty_t < y1;
+    if (!(co.w * 255.f >= 1.f)) return false;
+    const float tau = 2.f * __logf(255.f * co.w) + 0.01f;
+    const float xa = (float)(tx_t * 16) + 0.5f - m.x, xb = xa + 15.f;
+    const float ya = (float)(ty_t * 16) + 0.5f - m.y, yb = ya + 15.f;
+    if (xa <= 0.f && xb >= 0.f && ya <= 0.f && yb >= 0.f) return true;
+    const float A = co.x, B = co.y, C = co.z;
+    auto qx = [&](float dx) {  // min over dy in [ya, yb] at fixed dx
+        float dy = fminf(fmaxf(-B * dx / C, ya), yb);
+        return A * dx * dx + 2.f * B * dx * dy + C * dy * dy;
+    };
+    auto qy = [&](float dy) {  // min over dx in [xa, xb] at fixed dy
+        float dx = fminf(fmaxf(-B * dy / A, xa), xb);
+        return A * dx * dx + 2.f * B * dx * dy + C * dy * dy;
+    };
+    float q = fminf(fminf(qx(xa), qx(xb)), fminf(qy(ya), qy(yb)));
+    return q <= tau;
+}
+
+// Does record o belong to tile (tx_t, ty_t)'s list (its tile rectangle holds
+// the tile; implied when bins are single tiles) and can it contribute there?
+template <bool BINNED>
+__device__ __forceinline__ bool keep_record(const RasterParams &p, int64_t o, int tx_t, int ty_t,
+                                            float2 &m, float4 &co)
+{
+    m = p.mean2d[o];
+    co = p.conic_op[o];
+    if (BINNED) {
+        int r = p.radius[o];
+        if (r <= 0) return false;
+        int x0, y0, x1, y1;
+        tile_rect(m.x, m.y, r, p.tx, p.ty, x0, y0, x1, y1);
+        if (!(tx_t >= x0 && tx_t < x1 && ty_t >= y0 && ty_t < y1)) return false;
+    }
+    return ellipse_hits_tile(m, co, tx_t, ty_t);
 }
 
 // Block-wide stream compaction, order preserving: returns this thread's slot
@@ -105,20 +155,23 @@ __global__ void __launch_bounds__(FT) raster_fwd_kernel(RasterParams p)
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
     int last = 0;
     bool done = !inside;
+    uint32_t n_tested = 0, n_contrib = 0;
     for (int base = 0; base < total; base += FT) {
         if (__syncthreads_count(done) == FT) break;
         const int k = base + tid;
         int64_t o = 0;
         bool keep = false;
+        float2 m;
+        float4 co;
         if (k < total) {
             o = vb + p.vals[range.x + k];
-            keep = covers<BINNED>(p, o, tx_t, ty_t);
+            keep = keep_record<BINNED>(p, o, tx_t, ty_t, m, co);
         }
         int cnt;
         const int slot = compact_slot<FT>(keep, s_wcnt, cnt);
         if (slot >= 0) {
-            s_xy[slot] = p.mean2d[o];
-            s_co[slot] = p.conic_op[o];
+            s_xy[slot] = m;
+            s_co[slot] = co;
             s_rgb[slot][0] = p.rgb[3 * o];
             s_rgb[slot][1] = p.rgb[3 * o + 1];
             s_rgb[slot][2] = p.rgb[3 * o + 2];
@@ -128,6 +181,7 @@ __global__ void __launch_bounds__(FT) raster_fwd_kernel(RasterParams p)
         for (int j = 0; !done && j < cnt; ++j) {
             float dx, dy;
             float4 co = s_co[j];
+            ++n_tested;
             float power = pair_power(s_xy[j], co, pxf, pyf, dx, dy);
             if (power > 0.f) continue;
             float alpha = fminf(kAlphaCap, pair_alpha_raw(co, power));
@@ -143,8 +197,10 @@ __global__ void __launch_bounds__(FT) raster_fwd_kernel(RasterParams p)
             C2 = fmaf(s_rgb[j][2], w, C2);
             T = test_T;
             last = s_pos[j] + 1;
+            ++n_contrib;
         }
     }
+    flush_stats(p.stats, n_tested, n_contrib);
     if (inside) {
         int64_t HW = (int64_t)p.H * p.W;
         int64_t pix = (int64_t)py * p.W + px;
@@ -155,6 +211,33 @@ __global__ void __launch_bounds__(FT) raster_fwd_kernel(RasterParams p)
         p.T_final[(int64_t)view * HW + pix] = T;
         p.last[(int64_t)view * HW + pix] = last;
     }
+}
+
+// Sum 8 per-lane values over the warp with 9 shuffles: each butterfly stage
+// hands half of the remaining values to the partner lane.  Lane l returns the
+// warp total of value index 4*bit4(l) + 2*bit3(l) + bit2(l).
+__device__ __forceinline__ float warp_reduce8(const float *v)
+{
+    const int lane = threadIdx.x & 31;
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    float a[4], b[2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float send = b4 ? v[i] : v[i + 4];
+        float keep = b4 ? v[i + 4] : v[i];
+        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        float send = b3 ? a[i] : a[i + 2];
+        float keep = b3 ? a[i + 2] : a[i];
+        b[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    float send = b2 ? b[0] : b[1];
+    float c = (b2 ? b[1] : b[0]) + __shfl_xor_sync(0xffffffffu, send, 4);
+    c += __shfl_xor_sync(0xffffffffu, c, 2);
+    c += __shfl_xor_sync(0xffffffffu, c, 1);
+    return c;
 }
 
 // Back-to-front state of one pixel.
@@ -174,7 +257,7 @@ __device__ __forceinline__ bool unblend_one(PixBwd &P, float2 xy, float4 co, con
     float araw = __fmul_rn(co.w, G);
     float alpha = fminf(kAlphaCap, araw);
     if (alpha < kAlphaMin) return false;
-    P.T = P.T / (1.f - alpha);
+    P.T = __fdividef(P.T, 1.f - alpha);
     float w = alpha * P.T;
     v[5] = fmaf(P.dC0, w, v[5]);
     v[6] = fmaf(P.dC1, w, v[6]);
@@ -244,6 +327,7 @@ __global__ void __launch_bounds__(RT) raster_bwd_kernel(RasterParams p)
     if (mylast > 0) atomicMax(&s_max, mylast);
     __syncthreads();
     const int maxlast = s_max;
+    uint32_t n_tested = 0, n_contrib = 0;
     for (int hi = maxlast; hi > 0; hi -= RT) {
         // candidates [lo, hi) of the bin list, compacted to this tile's records
         const int lo = max(0, hi - RT);
@@ -251,17 +335,19 @@ __global__ void __launch_bounds__(RT) raster_bwd_kernel(RasterParams p)
         int64_t o = 0;
         uint32_t g = 0;
         bool keep = false;
+        float2 m;
+        float4 co;
         if (k < hi) {
             g = p.vals[range.x + k];
             o = vb + g;
-            keep = covers<BINNED>(p, o, tx_t, ty_t);
+            keep = keep_record<BINNED>(p, o, tx_t, ty_t, m, co);
         }
         int cnt;
         const int slot = compact_slot<RT>(keep, s_wcnt, cnt);
         if (slot >= 0) {
             s_g[slot] = g;
-            s_xy[slot] = p.mean2d[o];
-            s_co[slot] = p.conic_op[o];
+            s_xy[slot] = m;
+            s_co[slot] = co;
             s_rgb[slot][0] = p.rgb[3 * o];
             s_rgb[slot][1] = p.rgb[3 * o + 1];
             s_rgb[slot][2] = p.rgb[3 * o + 2];
@@ -280,16 +366,29 @@ __global__ void __launch_bounds__(RT) raster_bwd_kernel(RasterParams p)
                     float2 xy = s_xy[j];
                     float4 co = s_co[j];
                     const float *c = s_rgb[j];
-                    if (pos < A.last) contrib |= unblend_one<WANT_OP>(A, xy, co, c, pxf, pyf0, v);
-                    if (pos < B.last) contrib |= unblend_one<WANT_OP>(B, xy, co, c, pxf, pyf1, v);
+                    if (pos < A.last) {
+                        ++n_tested;
+                        bool h = unblend_one<WANT_OP>(A, xy, co, c, pxf, pyf0, v);
+                        n_contrib += h;
+                        contrib |= h;
+                    }
+                    if (pos < B.last) {
+                        ++n_tested;
+                        bool h = unblend_one<WANT_OP>(B, xy, co, c, pxf, pyf1, v);
+                        n_contrib += h;
+                        contrib |= h;
+                    }
                 }
                 if (__any_sync(0xffffffffu, contrib)) {
-#pragma unroll
-                    for (int q = 0; q < NV; ++q) v[q] = warp_sum(v[q]);
-                }
-                if (lane == 0) {
-#pragma unroll
-                    for (int q = 0; q < NV; ++q) s_part[warp][j - clo][q] = v[q];
+                    float r = warp_reduce8(v);
+                    if ((lane & 3) == 0) s_part[warp][j - clo][lane >> 2] = r;
+                    if (WANT_OP) {
+                        float ro = warp_sum(v[NV - 1]);
+                        if (lane == 0) s_part[warp][j - clo][NV - 1] = ro;
+                    }
+                } else if ((lane & 3) == 0) {
+                    s_part[warp][j - clo][lane >> 2] = 0.f;
+                    if (WANT_OP && lane == 0) s_part[warp][j - clo][NV - 1] = 0.f;
                 }
             }
             __syncthreads();
@@ -317,6 +416,7 @@ __global__ void __launch_bounds__(RT) raster_bwd_kernel(RasterParams p)
             __syncthreads();
         }
     }
+    flush_stats(p.stats, n_tested, n_contrib);
 }
 
 static gs_status fill(const gs_projected *proj, int64_t n, int V, int W, int H, int bin,
@@ -358,7 +458,7 @@ using namespace gs3;
 extern "C" gs_status gs_raster_fwd(const gs_projected *proj, int64_t n, int V, int W, int H,
                                    int bin, const float *bg, const uint32_t *vals,
                                    const uint32_t *ranges, float *img, float *T_final,
-                                   int32_t *last, gs_stream stream)
+                                   int32_t *last, uint64_t *d_stats, gs_stream stream)
 {
     RasterParams p{};
     gs_status st = fill(proj, n, V, W, H, bin, bg, vals, ranges, p);
@@ -367,6 +467,7 @@ extern "C" gs_status gs_raster_fwd(const gs_projected *proj, int64_t n, int V, i
     p.img = img;
     p.T_final = T_final;
     p.last = last;
+    p.stats = reinterpret_cast<unsigned long long *>(d_stats);
     dim3 grid(p.tx * p.ty, V);
     note_launch();
     if (bin > 1)
@@ -380,7 +481,7 @@ extern "C" gs_status gs_raster_bwd(const gs_projected *proj, int64_t n, int V, i
                                    int bin, const float *bg, const uint32_t *vals,
                                    const uint32_t *ranges, const float *T_final,
                                    const int32_t *last, const float *d_img, float *grads,
-                                   float *d_opacity, gs_stream stream)
+                                   float *d_opacity, uint64_t *d_stats, gs_stream stream)
 {
     RasterParams p{};
     gs_status st = fill(proj, n, V, W, H, bin, bg, vals, ranges, p);
@@ -395,6 +496,7 @@ extern "C" gs_status gs_raster_bwd(const gs_projected *proj, int64_t n, int V, i
     p.d_img = d_img;
     p.grads = grads;
     p.d_opacity = d_opacity;
+    p.stats = reinterpret_cast<unsigned long long *>(d_stats);
     dim3 grid(p.tx * p.ty, V);
     note_launch();
     if (d_opacity && bin > 1)

@@ -64,13 +64,13 @@ class Rasterizer:
         gs3.gs_bin_sort(self.proj, n, V, W, H, self.bin, self.capacity, self.vals, self.ranges, keys,
                         self.d_count, self.d_err, self.ws, stream)
         gs3.gs_raster_fwd(self.proj, n, V, W, H, self.bin, self.bg, self.vals, self.ranges, self.img,
-                          self.T_final, self.last, stream)
+                          self.T_final, self.last, None, stream)
         return self.img
 
     def backward(self, g: Gaussians, cams_dev, d_img, mean=None, quat=None, stream=None):
         V, W, H, n = self.V, self.W, self.H, self.n
         gs3.gs_raster_bwd(self.proj, n, V, W, H, self.bin, self.bg, self.vals, self.ranges,
-                          self.T_final, self.last, d_img, self.grads, None, stream)
+                          self.T_final, self.last, d_img, self.grads, None, None, stream)
         gs3.gs_project_bwd(g, cams_dev, V, W, H, self.grads, self.d_mean, self.d_quat, mean, quat,
                            stream)
         return self.d_mean, self.d_quat

@@ -237,19 +237,21 @@ def _bg(bg):
     return a
 
 
-def gs_raster_fwd(proj: Projected, n, V, W, H, bin, bg, vals, ranges, img, T_final, last, stream=None):
+def gs_raster_fwd(proj: Projected, n, V, W, H, bin, bg, vals, ranges, img, T_final, last,
+                  stats=None, stream=None):
     po = proj.struct()
     _check("gs_raster_fwd", lib().gs_raster_fwd(
         ctypes.byref(po), c_int64(n), c_int(V), c_int(W), c_int(H), c_int(bin), _bg(bg), _ptr(vals), _ptr(ranges),
-        _ptr(img), _ptr(T_final), _ptr(last), _stream(stream)))
+        _ptr(img), _ptr(T_final), _ptr(last), _ptr(stats), _stream(stream)))
 
 
 def gs_raster_bwd(proj: Projected, n, V, W, H, bin, bg, vals, ranges, T_final, last, d_img, grads,
-                  d_opacity=None, stream=None):
+                  d_opacity=None, stats=None, stream=None):
     po = proj.struct()
     _check("gs_raster_bwd", lib().gs_raster_bwd(
         ctypes.byref(po), c_int64(n), c_int(V), c_int(W), c_int(H), c_int(bin), _bg(bg), _ptr(vals), _ptr(ranges),
-        _ptr(T_final), _ptr(last), _ptr(d_img), _ptr(grads), _ptr(d_opacity), _stream(stream)))
+        _ptr(T_final), _ptr(last), _ptr(d_img), _ptr(grads), _ptr(d_opacity), _ptr(stats),
+        _stream(stream)))
 
 
 def gs_loss_workspace_size(planes, H, W) -> int:
