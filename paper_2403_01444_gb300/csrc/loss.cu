@@ -38,6 +38,14 @@ struct LossParams {
     int nblocks;
 };
 
+// Horizontal pass work split: a thread filters HSEG consecutive outputs of
+// one staged row, keeping the HSEG + 10 inputs in registers; the vertical
+// pass gives a thread VSEG consecutive rows of one column.
+constexpr int HSEG = 8;
+constexpr int VSEG = 4;
+static_assert(LT % HSEG == 0 && LT % VSEG == 0, "tile split");
+static_assert((LT / VSEG) * LT == LTHREADS, "vertical pass: one item per thread");
+
 __global__ void __launch_bounds__(LTHREADS) ssim_fwd_kernel(LossParams p)
 {
     __shared__ float sx[LS][LS + 1], sy[LS][LS + 1];
@@ -58,54 +66,75 @@ __global__ void __launch_bounds__(LTHREADS) ssim_fwd_kernel(LossParams p)
         sy[r][c] = in ? Y[o] : 0.f;
     }
     __syncthreads();
-    for (int i = tid; i < LS * LT; i += LTHREADS) {
-        int r = i / LT, c = i % LT;
-        float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, m4 = 0.f;
+    float w[11];
 #pragma unroll
-        for (int k = 0; k < 11; ++k) {
-            float a = sx[r][c + k], b = sy[r][c + k], w = c_win[k];
-            m0 = fmaf(w, a, m0);
-            m1 = fmaf(w, b, m1);
-            m2 = fmaf(w, a * a, m2);
-            m3 = fmaf(w, b * b, m3);
-            m4 = fmaf(w, a * b, m4);
+    for (int k = 0; k < 11; ++k) w[k] = c_win[k];
+    // horizontal: (x, y, x^2, y^2, xy) filtered along rows
+    for (int item = tid; item < LS * (LT / HSEG); item += LTHREADS) {
+        const int r = item / (LT / HSEG), c0 = (item % (LT / HSEG)) * HSEG;
+        float xv[HSEG + 10], yv[HSEG + 10];
+#pragma unroll
+        for (int k = 0; k < HSEG + 10; ++k) {
+            xv[k] = sx[r][c0 + k];
+            yv[k] = sy[r][c0 + k];
         }
-        hs[0][r][c] = m0;
-        hs[1][r][c] = m1;
-        hs[2][r][c] = m2;
-        hs[3][r][c] = m3;
-        hs[4][r][c] = m4;
+#pragma unroll
+        for (int o = 0; o < HSEG; ++o) {
+            float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, m4 = 0.f;
+#pragma unroll
+            for (int k = 0; k < 11; ++k) {
+                float a = xv[o + k], b = yv[o + k];
+                m0 = fmaf(w[k], a, m0);
+                m1 = fmaf(w[k], b, m1);
+                m2 = fmaf(w[k], a * a, m2);
+                m3 = fmaf(w[k], b * b, m3);
+                m4 = fmaf(w[k], a * b, m4);
+            }
+            hs[0][r][c0 + o] = m0;
+            hs[1][r][c0 + o] = m1;
+            hs[2][r][c0 + o] = m2;
+            hs[3][r][c0 + o] = m3;
+            hs[4][r][c0 + o] = m4;
+        }
     }
     __syncthreads();
+    // vertical: thread -> column c, rows r0 .. r0 + VSEG - 1
     const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
-    double ssum = 0.0, lsum = 0.0;
-    const int c = tid % LT;
-    for (int r = tid / LT; r < LT; r += LTHREADS / LT) {
-        int gy = y0 + r, gx = x0 + c;
-        if (gy >= p.H || gx >= p.W) continue;
-        float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
+    const int c = tid % LT, r0 = (tid / LT) * VSEG;
+    float f[5][VSEG];
 #pragma unroll
-        for (int k = 0; k < 11; ++k) {
-            float w = c_win[k];
-            mx = fmaf(w, hs[0][r + k][c], mx);
-            my = fmaf(w, hs[1][r + k][c], my);
-            exx = fmaf(w, hs[2][r + k][c], exx);
-            eyy = fmaf(w, hs[3][r + k][c], eyy);
-            exy = fmaf(w, hs[4][r + k][c], exy);
+    for (int m = 0; m < 5; ++m) {
+        float col[VSEG + 10];
+#pragma unroll
+        for (int k = 0; k < VSEG + 10; ++k) col[k] = hs[m][r0 + k][c];
+#pragma unroll
+        for (int o = 0; o < VSEG; ++o) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < 11; ++k) acc = fmaf(w[k], col[o + k], acc);
+            f[m][o] = acc;
         }
+    }
+    double ssum = 0.0, lsum = 0.0;
+    const int gx = x0 + c;
+#pragma unroll
+    for (int o = 0; o < VSEG; ++o) {
+        const int r = r0 + o, gy = y0 + r;
+        if (gy >= p.H || gx >= p.W) continue;
+        float mx = f[0][o], my = f[1][o], exx = f[2][o], eyy = f[3][o], exy = f[4][o];
         float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
         float n1 = 2.f * mx * my + C1, n2 = 2.f * sxy + C2;
         float d1 = mx * mx + my * my + C1, d2 = sxx + syy + C2;
         float idd = 1.f / (d1 * d2);
-        float s = n1 * n2 * idd;
-        float ds_dmx = 2.f * my * n2 * idd - s * 2.f * mx / d1;
-        float ds_dsxx = -s / d2;
+        float sv = n1 * n2 * idd;
+        float ds_dmx = 2.f * my * n2 * idd - sv * 2.f * mx / d1;
+        float ds_dsxx = -sv / d2;
         float ds_dsxy = 2.f * n1 * idd;
-        int64_t o = pl * HW + (int64_t)gy * p.W + gx;
-        p.ca[o] = ds_dmx - 2.f * mx * ds_dsxx - my * ds_dsxy;
-        p.cb[o] = ds_dsxx;
-        p.cc[o] = ds_dsxy;
-        ssum += (double)s;
+        int64_t oo = pl * HW + (int64_t)gy * p.W + gx;
+        p.ca[oo] = ds_dmx - 2.f * mx * ds_dsxx - my * ds_dsxy;
+        p.cb[oo] = ds_dsxx;
+        p.cc[oo] = ds_dsxy;
+        ssum += (double)sv;
         lsum += (double)fabsf(sx[r + LH][c + LH] - sy[r + LH][c + LH]);
     }
 #pragma unroll
@@ -120,9 +149,9 @@ __global__ void __launch_bounds__(LTHREADS) ssim_fwd_kernel(LossParams p)
     __syncthreads();
     if (tid == 0) {
         double a = 0.0, b = 0.0;
-        for (int w = 0; w < LTHREADS / 32; ++w) {
-            a += red[0][w];
-            b += red[1][w];
+        for (int ww = 0; ww < LTHREADS / 32; ++ww) {
+            a += red[0][ww];
+            b += red[1][ww];
         }
         int64_t bid = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
         p.partial[2 * bid] = a;
@@ -149,40 +178,60 @@ __global__ void __launch_bounds__(LTHREADS) ssim_bwd_kernel(LossParams p)
         sc[r][c] = in ? p.cc[o] : 0.f;
     }
     __syncthreads();
-    for (int i = tid; i < LS * LT; i += LTHREADS) {
-        int r = i / LT, c = i % LT;
-        float m0 = 0.f, m1 = 0.f, m2 = 0.f;
+    float w[11];
 #pragma unroll
-        for (int k = 0; k < 11; ++k) {
-            float w = c_win[k];
-            m0 = fmaf(w, sa[r][c + k], m0);
-            m1 = fmaf(w, sb[r][c + k], m1);
-            m2 = fmaf(w, sc[r][c + k], m2);
+    for (int k = 0; k < 11; ++k) w[k] = c_win[k];
+    for (int item = tid; item < LS * (LT / HSEG); item += LTHREADS) {
+        const int r = item / (LT / HSEG), c0 = (item % (LT / HSEG)) * HSEG;
+        float av[HSEG + 10], bv[HSEG + 10], cv[HSEG + 10];
+#pragma unroll
+        for (int k = 0; k < HSEG + 10; ++k) {
+            av[k] = sa[r][c0 + k];
+            bv[k] = sb[r][c0 + k];
+            cv[k] = sc[r][c0 + k];
         }
-        hs[0][r][c] = m0;
-        hs[1][r][c] = m1;
-        hs[2][r][c] = m2;
+#pragma unroll
+        for (int o = 0; o < HSEG; ++o) {
+            float m0 = 0.f, m1 = 0.f, m2 = 0.f;
+#pragma unroll
+            for (int k = 0; k < 11; ++k) {
+                m0 = fmaf(w[k], av[o + k], m0);
+                m1 = fmaf(w[k], bv[o + k], m1);
+                m2 = fmaf(w[k], cv[o + k], m2);
+            }
+            hs[0][r][c0 + o] = m0;
+            hs[1][r][c0 + o] = m1;
+            hs[2][r][c0 + o] = m2;
+        }
     }
     __syncthreads();
     const float invM = 1.f / (float)((double)p.P * (double)HW);
-    const int c = tid % LT;
-    for (int r = tid / LT; r < LT; r += LTHREADS / LT) {
-        int gy = y0 + r, gx = x0 + c;
-        if (gy >= p.H || gx >= p.W) continue;
-        float fa = 0.f, fb = 0.f, fc = 0.f;
+    const int c = tid % LT, r0 = (tid / LT) * VSEG;
+    float f[3][VSEG];
 #pragma unroll
-        for (int k = 0; k < 11; ++k) {
-            float w = c_win[k];
-            fa = fmaf(w, hs[0][r + k][c], fa);
-            fb = fmaf(w, hs[1][r + k][c], fb);
-            fc = fmaf(w, hs[2][r + k][c], fc);
+    for (int m = 0; m < 3; ++m) {
+        float col[VSEG + 10];
+#pragma unroll
+        for (int k = 0; k < VSEG + 10; ++k) col[k] = hs[m][r0 + k][c];
+#pragma unroll
+        for (int o = 0; o < VSEG; ++o) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < 11; ++k) acc = fmaf(w[k], col[o + k], acc);
+            f[m][o] = acc;
         }
-        int64_t o = pl * HW + (int64_t)gy * p.W + gx;
-        float xv = p.x[o], yv = p.y[o];
+    }
+    const int gx = x0 + c;
+#pragma unroll
+    for (int o = 0; o < VSEG; ++o) {
+        const int gy = y0 + r0 + o;
+        if (gy >= p.H || gx >= p.W) continue;
+        int64_t oo = pl * HW + (int64_t)gy * p.W + gx;
+        float xv = p.x[oo], yv = p.y[oo];
         float diff = xv - yv;
         float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
-        float dssim = fa + 2.f * xv * fb + yv * fc;
-        p.d_img[o] = ((1.f - p.lam) * sgn - p.lam * dssim) * invM;
+        float dssim = f[0][o] + 2.f * xv * f[1][o] + yv * f[2][o];
+        p.d_img[oo] = ((1.f - p.lam) * sgn - p.lam * dssim) * invM;
     }
 }
 
