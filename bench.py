@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--small", action="store_true",
                     help="100K Gaussians instead of 250K (smaller profiling captures)")
     ap.add_argument("--warm-iters", type=int, default=1000, help="NTC warm-up iterations (Eq. 7)")
+    ap.add_argument("--eager", action="store_true", help="launch kernels one by one (no CUDA graph)")
+    ap.add_argument("--no-converge", action="store_true", help="skip the equal-PSNR comparison")
     ap.add_argument("--profile", action="store_true",
                     help="setup + timed steps only (for ncu launch lists)")
     return ap.parse_args()
@@ -248,6 +250,11 @@ def run_ours(args):
     ntc.reset_to(warm_table, warm_mlp)
     st.reset_state()
 
+    # one CUDA graph of the whole iteration per view batch
+    batches = [(batch_cams[b], targets[b * Vb:(b + 1) * Vb]) for b in range(nb)]
+    graphs = st.capture(batches) if not args.eager else None
+    ntc.reset_to(warm_table, warm_mlp)
+    st.reset_state()
     stream = torch.cuda.current_stream()
     ev = {}
     stats = torch.zeros(4, dtype=torch.int64, device=dev)
@@ -259,7 +266,10 @@ def run_ours(args):
         b = i % nb
         cd, tg = batch_cams[b], targets[b * Vb:(b + 1) * Vb]
         if not record:
-            st.step(cd, tg)
+            if graphs is not None:
+                graphs[b].replay()
+            else:
+                st.step(cd, tg)
             return
         E = lambda k: ev.setdefault(k, []).append(torch.cuda.Event(enable_timing=True)) or ev[k][-1].record(stream)
         E("t0")
@@ -304,6 +314,12 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
     launches = gs3.lib().gs_launch_count() - l0
+    if graphs is not None:
+        # replays do not pass through the library: count one eager iteration
+        c0 = gs3.lib().gs_launch_count()
+        st.step(*batches[0])
+        torch.cuda.synchronize()
+        launches = (gs3.lib().gs_launch_count() - c0) * args.steps
     ms = e0.elapsed_time(e1) / args.steps
     if args.profile:
         if rank == 0:
@@ -354,17 +370,26 @@ def run_ours(args):
         do = DirectOpt(G, Vb, W, H, st.raster.capacity, device=dev)
         for i in range(3):
             do.step(batch_cams[i % nb], targets[(i % nb) * Vb:(i % nb + 1) * Vb])
+        dgraphs = do.capture(batches) if not args.eager else None
         torch.cuda.synchronize()
         e0.record(stream)
         kp = max(10, args.steps // 2)
         for i in range(kp):
             b = i % nb
-            do.step(batch_cams[b], targets[b * Vb:(b + 1) * Vb])
+            if dgraphs is not None:
+                dgraphs[b].replay()
+            else:
+                do.step(batch_cams[b], targets[b * Vb:(b + 1) * Vb])
         e1.record(stream)
         torch.cuda.synchronize()
         pms = e0.elapsed_time(e1) / kp
         plain = {"s_per_frame": pms * ITERS_PER_FRAME / 1e3, "ms_per_iter": pms, "iters": kp}
-        del do
+        del do, dgraphs
+
+    converge = None
+    if not args.no_converge and plain is not None:
+        converge = equal_psnr(scene, G, Gt, ntc, warm_table, warm_mlp, st, batches, nb, Vb, W, H,
+                              ms_max, plain["ms_per_iter"], dev)
 
     # end to end through the public API with host buffers: per step the batch's
     # target views go host->device from pinned memory and the loss comes back
@@ -382,8 +407,12 @@ def run_ours(args):
         if i % ITERS_PER_FRAME == 0:
             ntc.reset_to(warm_table, warm_mlp)
         b = i % nb
-        dev_tg.copy_(host_targets[b * Vb:(b + 1) * Vb], non_blocking=True)
-        st.step(batch_cams[b], dev_tg)
+        if graphs is not None:
+            targets[b * Vb:(b + 1) * Vb].copy_(host_targets[b * Vb:(b + 1) * Vb], non_blocking=True)
+            graphs[b].replay()
+        else:
+            dev_tg.copy_(host_targets[b * Vb:(b + 1) * Vb], non_blocking=True)
+            st.step(batch_cams[b], dev_tg)
         host_loss.copy_(st.loss.d_loss, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -391,6 +420,11 @@ def run_ours(args):
     h2d = Vb * 3 * H * W * 4
 
     cpu = None
+    if converge is not None:
+        # the paths' own final held-out PSNRs: does the plain path ever reach the cache's?
+        n_fin = converge["ntc"]["final_psnr"]
+        reach = [it for it, p in converge["direct"]["curve"] if p >= n_fin - 0.05]
+        converge["direct_reaches_ntc_final_psnr_within_frame"] = bool(reach)
     if rank == 0 and world == 1 and not args.no_cpu:
         per_iter, desc, cores = oracle_sample(scene)
         cpu = {"value": per_iter * ITERS_PER_FRAME, "unit": "s/frame", "cores": cores,
@@ -408,6 +442,8 @@ def run_ours(args):
                 "raster_fwd_bwd_ms": raster_ms,
                 "plain_fp32_direct_opt": plain,
                 "speedup_vs_plain_per_iter": (plain["ms_per_iter"] / ms_max) if plain else None,
+                "equal_psnr": converge,
+                "graphs": graphs is not None,
                 "stages_ms": {k: round(v, 4) for k, v in stages.items()},
                 "bin_pairs_per_step": pairs, "composited_pairs": pair_counts,
                 "warmup_loss": wl, "warmup_s": t_warm,
@@ -419,6 +455,56 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
+
+
+def equal_psnr(scene, G, Gt, ntc, warm_table, warm_mlp, st, batches, nb, Vb, W, H, ms_ntc, ms_plain,
+               dev, iters=ITERS_PER_FRAME, every=10):
+    """One frame of each path from the same previous-frame Gaussians: PSNR of
+    the held-out view (and of the training views at the end) every `every`
+    iterations.  Target = the lower of the two final held-out PSNRs; each
+    path's time to reach it (within 0.05 dB) = first checkpoint reaching it x
+    its measured time per iteration."""
+    import torch
+    from paper_2403_01444_gb300.engine import DirectOpt, render
+    ho = [scene.heldout]
+    gt_ho = render(Gt, ho, W, H)
+    psnr = lambda a, b: float(-10.0 * math.log10(max(((a - b) ** 2).mean().item(), 1e-20)))
+    gt_train = torch.cat([render(Gt, scene.cams[b * Vb:(b + 1) * Vb], W, H) for b in range(nb)])
+
+    def train_psnr(m, q):
+        img = torch.cat([render(G, scene.cams[b * Vb:(b + 1) * Vb], W, H, m, q) for b in range(nb)])
+        return psnr(img, gt_train)
+
+    start = psnr(render(G, ho, W, H), gt_ho)
+    ntc.reset_to(warm_table, warm_mlp)
+    st.reset_state()
+    curve_n = []
+    for i in range(iters):
+        st.step(*batches[i % nb])
+        if (i + 1) % every == 0:
+            m, q = st.transform()
+            curve_n.append((i + 1, psnr(render(G, ho, W, H, m, q), gt_ho)))
+    m, q = st.transform()
+    tr_n = train_psnr(m, q)
+    do = DirectOpt(G, Vb, W, H, st.raster.capacity, device=dev)
+    curve_d = []
+    for i in range(iters):
+        do.step(*batches[i % nb])
+        if (i + 1) % every == 0:
+            curve_d.append((i + 1, psnr(render(G, ho, W, H, do.mean.p, do.quat.p), gt_ho)))
+    tr_d = train_psnr(do.mean.p, do.quat.p)
+    target = min(curve_n[-1][1], curve_d[-1][1])
+    first = lambda c: next(it for it, p in c if p >= target - 0.05)
+    it_n, it_d = first(curve_n), first(curve_d)
+    t_n, t_d = it_n * ms_ntc / 1e3, it_d * ms_plain / 1e3
+    return {"view": "held-out camera (azimuth 7.5, elevation 5)", "psnr_previous_frame": start,
+            "target_psnr": target, "ntc": {"final_psnr": curve_n[-1][1], "train_views_psnr": tr_n,
+                                          "iters_to_target": it_n, "s_to_target": t_n,
+                                          "curve": [(a, round(b, 2)) for a, b in curve_n]},
+            "direct": {"final_psnr": curve_d[-1][1], "train_views_psnr": tr_d,
+                       "iters_to_target": it_d, "s_to_target": t_d,
+                       "curve": [(a, round(b, 2)) for a, b in curve_d]},
+            "speedup_at_equal_psnr": t_d / t_n}
 
 
 def ctypes_u64():

@@ -44,6 +44,19 @@ inline gs_status launch_status(const char *what)
 
 inline cudaStream_t as_stream(gs_stream s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Raise a kernel's dynamic shared-memory limit, except while the stream is
+// being captured into a graph (the first, eager call has already done it).
+inline void set_smem_limit(const void *kernel, int bytes, cudaStream_t s)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    if (cs == cudaStreamCaptureStatusNone)
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
 inline bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

@@ -443,10 +443,10 @@ gs_status mlp_tc_fwd(const void *enc, int enc_dtype, int64_t n, const gs_mlp *w,
     const bf16 *wb = reinterpret_cast<const bf16 *>(w->w_bf16);
     note_launch();
     if (enc_dtype == GS_BF16) {
-        cudaFuncSetAttribute(mlp_tc_fwd_kernel<bf16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        set_smem_limit((const void *)mlp_tc_fwd_kernel<bf16>, (int)smem, s);
         mlp_tc_fwd_kernel<bf16><<<grid, TM, smem, s>>>((const bf16 *)enc, n, wb, raw7);
     } else {
-        cudaFuncSetAttribute(mlp_tc_fwd_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        set_smem_limit((const void *)mlp_tc_fwd_kernel<float>, (int)smem, s);
         mlp_tc_fwd_kernel<float><<<grid, TM, smem, s>>>((const float *)enc, n, wb, raw7);
     }
     return launch_status("ntc_mlp_fwd (tcgen05)");
@@ -465,10 +465,10 @@ gs_status mlp_tc_bwd(const void *enc, int enc_dtype, int64_t n, const gs_mlp *w,
     const bf16 *wb = reinterpret_cast<const bf16 *>(w->w_bf16);
     note_launch();
     if (enc_dtype == GS_BF16) {
-        cudaFuncSetAttribute(mlp_tc_bwd_kernel<bf16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        set_smem_limit((const void *)mlp_tc_bwd_kernel<bf16>, (int)smem, s);
         mlp_tc_bwd_kernel<bf16><<<grid, TM, smem, s>>>((const bf16 *)enc, n, wb, d_raw7, d_scale, dW, d_enc);
     } else {
-        cudaFuncSetAttribute(mlp_tc_bwd_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        set_smem_limit((const void *)mlp_tc_bwd_kernel<float>, (int)smem, s);
         mlp_tc_bwd_kernel<float><<<grid, TM, smem, s>>>((const float *)enc, n, wb, d_raw7, d_scale, dW, d_enc);
     }
     return launch_status("ntc_mlp_bwd (tcgen05)");

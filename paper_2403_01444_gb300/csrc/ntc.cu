@@ -468,14 +468,12 @@ extern "C" gs_status ntc_mlp_bwd(const void *enc, int enc_dtype, int64_t n, cons
     cudaStream_t s = as_stream(stream);
     int blocks = (int)std::min<int64_t>(ceil_div(n, MB_ROWS), 2 * kNumSMs);
     if (enc_dtype == GS_F32) {
-        cudaFuncSetAttribute(mlp_bwd_simt_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)MB_SMEM);
+        set_smem_limit((const void *)mlp_bwd_simt_kernel<float>, (int)MB_SMEM, s);
         note_launch();
         mlp_bwd_simt_kernel<float><<<blocks, MB_ROWS, MB_SMEM, s>>>((const float *)enc, n, w->w_f32,
                                                                     d_raw7, d_scale, dW, d_enc);
     } else {
-        cudaFuncSetAttribute(mlp_bwd_simt_kernel<__nv_bfloat16>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MB_SMEM);
+        set_smem_limit((const void *)mlp_bwd_simt_kernel<__nv_bfloat16>, (int)MB_SMEM, s);
         note_launch();
         mlp_bwd_simt_kernel<__nv_bfloat16><<<blocks, MB_ROWS, MB_SMEM, s>>>(
             (const __nv_bfloat16 *)enc, n, w->w_f32, d_raw7, d_scale, dW, d_enc);

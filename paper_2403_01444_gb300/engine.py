@@ -241,6 +241,13 @@ class Stage1:
         self.update(stream)
         return d_loss
 
+    def capture(self, batches):
+        """One CUDA graph of step() per (cams_dev, target) batch; a replay runs
+        the whole iteration with no host work.  Captured after one eager step
+        per batch (side stream), which also advances the training state: reset
+        the cache and the state before timing or training."""
+        return capture_graphs(self.step, batches)
+
 
 class DirectOpt:
     """Plain FP32 direct optimisation of the previous frame's means and
@@ -267,6 +274,26 @@ class DirectOpt:
         self.quat.step(self.state, stream)
         gs3.gs_train_state_advance(self.state, 0, stream)
         return self.loss.d_loss
+
+    def capture(self, batches):
+        return capture_graphs(self.step, batches)
+
+
+def capture_graphs(step_fn, batches):
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for cd, tg in batches:
+            step_fn(cd, tg)
+    torch.cuda.current_stream().wait_stream(side)
+    graphs = []
+    for cd, tg in batches:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            step_fn(cd, tg)
+        graphs.append(g)
+    torch.cuda.synchronize()
+    return graphs
 
 
 def warmup(ntc: NTC, g: Gaussians, iters=3000, noise=0.01, extent=2.0, seed=0, stream=None,

@@ -170,3 +170,39 @@ def test_ntc_training_beats_no_ntc(precision):
     p_ntc = psnr(render(G, ho, W, H, mt, qt))
     p_none = psnr(render(G, ho, W, H))
     assert p_ntc > p_none + 1.0, (p_ntc, p_none)
+
+
+def test_graph_replay_matches_eager_steps():
+    """The iteration captured in CUDA graphs (one per view batch) computes what
+    the eager calls compute."""
+    sc = scenes.make_scene(2, n_gauss=20_000, W=240, H=180)
+    W, H, Vb = 240, 180, 4
+    G = gs3.Gaussians.from_numpy(sc.prev)
+    Gt = gs3.Gaussians.from_numpy(sc.target)
+    cd = gs3.cameras_to_device(sc.cams)
+    bc = [gs3.camera_slice(cd, 0, Vb), gs3.camera_slice(cd, Vb, Vb)]
+    tg = torch.cat([render(Gt, sc.cams[:Vb], W, H), render(Gt, sc.cams[Vb:2 * Vb], W, H)])
+    rng = np.random.default_rng(75)
+    og = oracle.Grid()
+    table, Ws = _near_identity_ntc(rng, og, gs3.GS_MLP_BF16)
+    results = []
+    for use_graph in (False, True):
+        ntc = NTC(table, Ws, gs3.hashgrid(), gs3.GS_MLP_BF16)
+        st = Stage1(G, ntc, Vb, W, H, capacity=1 << 20)
+        batches = [(bc[0], tg[:Vb]), (bc[1], tg[Vb:])]
+        graphs = st.capture(batches) if use_graph else None
+        ntc.reset_to(ntc.init_table, ntc.init_mlp)
+        st.reset_state()
+        losses = []
+        for i in range(6):
+            if use_graph:
+                graphs[i % 2].replay()
+            else:
+                st.step(*batches[i % 2])
+            losses.append(st.loss.d_loss.item())
+        st.raster.check()
+        results.append((losses, ntc.mlp.p.clone(), ntc.table.p.clone()))
+    (l0, w0, t0), (l1, w1, t1) = results
+    np.testing.assert_allclose(l1, l0, rtol=1e-4)
+    assert rel_err(w1.cpu().numpy(), w0.cpu().numpy()) < 1e-4
+    assert rel_err(t1.cpu().numpy(), t0.cpu().numpy()) < 1e-4
