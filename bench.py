@@ -290,9 +290,13 @@ def run_ours(args):
         E("t6")
         gs3.gs_project_bwd(G, cd, Vb, W, H, r.grads, r.d_mean, r.d_quat, st.mean_t, st.quat_t)
         E("t7")
-        gs3.ntc_apply_bwd(G.mean, G.quat, st.raw7, G.n, st.aabb, st.order, r.d_mean, r.d_quat, st.d_raw7)
-        gs3.ntc_mlp_bwd(st.enc, G.n, ntc.mlp_struct(), st.d_raw7, st.loss_scale_view(), ntc.mlp.g, st.d_enc)
-        gs3.ntc_encode_bwd(G.mean, G.n, ntc.grid, st.d_enc, ntc.table.g)
+        if st.fused:
+            gs3.ntc_fused_bwd(G.mean, G.quat, st.raw7, st.enc, G.n, ntc.grid, ntc.mlp_struct(), st.order,
+                              r.d_mean, r.d_quat, st.loss_scale_view(), ntc.mlp.g, ntc.table.g)
+        else:
+            gs3.ntc_apply_bwd(G.mean, G.quat, st.raw7, G.n, st.aabb, st.order, r.d_mean, r.d_quat, st.d_raw7)
+            gs3.ntc_mlp_bwd(st.enc, G.n, ntc.mlp_struct(), st.d_raw7, st.loss_scale_view(), ntc.mlp.g, st.d_enc)
+            gs3.ntc_encode_bwd(G.mean, G.n, ntc.grid, st.d_enc, ntc.table.g)
         E("t8")
         st.update()
         E("t9")

@@ -300,6 +300,27 @@ GS_API gs_status ntc_apply_bwd(const float *mean, const float *quat, const float
                         const float *aabb, int order, const float *d_mean_out,
                         const float *d_quat_out, float *d_raw7, gs_stream stream);
 
+/* Fused cache forward (Section 4.1, Eq. 5): hash encoding of every mean from
+ * the FP16 table, the BF16 tcgen05 MLP and the transformation in one kernel.
+ * Same arithmetic as ntc_encode_fwd (FP16 table, BF16 encoding) +
+ * ntc_mlp_fwd (GS_MLP_BF16) + ntc_apply.  Writes mean_out[n][3],
+ * quat_out[n][4], raw7[n][7] and enc_save (BF16 [n][32], the encodings the
+ * backward reads).  w->precision must be GS_MLP_BF16. */
+GS_API gs_status ntc_fused_fwd(const float *mean, const float *quat, int64_t n,
+                               const gs_hashgrid *grid, const void *table_f16, const gs_mlp *w,
+                               int order, float *mean_out, float *quat_out, float *raw7,
+                               void *enc_save, gs_stream stream);
+
+/* Fused cache backward: ntc_apply_bwd + ntc_mlp_bwd + ntc_encode_bwd in one
+ * kernel, from the gradients wrt the transformed means and rotations.
+ * d_raw7 is scaled by *d_scale (device float; NULL = 1) as in ntc_mlp_bwd;
+ * dW[6592] and d_table[entries][2] are accumulated (scaled). */
+GS_API gs_status ntc_fused_bwd(const float *mean, const float *quat, const float *raw7,
+                               const void *enc_save, int64_t n, const gs_hashgrid *grid,
+                               const gs_mlp *w, int order, const float *d_mean_out,
+                               const float *d_quat_out, const float *d_scale, float *dW,
+                               float *d_table, gs_stream stream);
+
 /* Warm-up loss (Section 4.1 Eq. 7): mean over rows of |dmu|_1 - cos^2(norm(dq), (1,0,0,0)).
  * Writes *d_loss (device float) and d_raw7[n][7] = dL/d raw7. */
 GS_API gs_status ntc_warmup_loss(const float *raw7, int64_t n, float *d_raw7, float *d_loss,

@@ -50,6 +50,30 @@ struct BwdSmem {
     uint32_t tmem;
 };
 
+// Arguments of the MLP kernels.  The standalone MLP reads encodings and
+// writes raw outputs; the fused cache kernels (FUSED = true) also encode the
+// means from the FP16 hash table and apply the transformation (forward), or
+// take the transformation's backward and scatter into the table (backward).
+struct TcParams {
+    const void *enc;
+    int64_t n;
+    const bf16 *w;
+    float *raw7;
+    const float *d_raw7, *d_scale;
+    float *dW, *d_enc;
+    // fused cache path
+    const float *mean, *quat;
+    GridParams grid;
+    const __half *table;
+    bf16 *enc_save;
+    const float *raw7_in;
+    float *mean_out, *quat_out;
+    const float *d_mean_out, *d_quat_out;
+    float *d_table;
+    Box box;
+    int order;
+};
+
 template <typename T>
 __device__ __forceinline__ T *aligned_smem(unsigned char *raw)
 {
@@ -96,6 +120,96 @@ __device__ __forceinline__ void load_row32(const bf16 *enc, int64_t row, int64_t
     }
 }
 
+// Hash encoding of one mean (Section 4.1), FP16 features, FP32 sums: the
+// arithmetic of encode_fwd_kernel, so the values are the same.
+__device__ __forceinline__ void encode_row(const TcParams &p, int64_t row, float *v)
+{
+    if (row >= p.n) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k] = 0.f;
+        return;
+    }
+    float3 m = make_float3(p.mean[3 * row], p.mean[3 * row + 1], p.mean[3 * row + 2]);
+    const __half2 *tab = reinterpret_cast<const __half2 *>(p.table);
+#pragma unroll
+    for (int l = 0; l < 16; ++l) {
+        float f0 = 0.f, f1 = 0.f;
+        if (l < p.grid.L) {
+            uint32_t idx[8];
+            float w8[8];
+            level_corners(p.grid, l, m, idx, w8);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                float2 t = __half22float2(tab[idx[c]]);
+                f0 = fmaf(w8[c], t.x, f0);
+                f1 = fmaf(w8[c], t.y, f1);
+            }
+        }
+        v[2 * l] = f0;
+        v[2 * l + 1] = f1;
+    }
+}
+
+// Trilinear-weighted scatter of one row's encoding gradient into the table.
+__device__ __forceinline__ void scatter_row(const TcParams &p, int64_t row, const float *g)
+{
+    float3 m = make_float3(p.mean[3 * row], p.mean[3 * row + 1], p.mean[3 * row + 2]);
+    float2 *dt = reinterpret_cast<float2 *>(p.d_table);
+#pragma unroll
+    for (int l = 0; l < 16; ++l) {
+        if (l >= p.grid.L) break;
+        float gx = g[2 * l], gy = g[2 * l + 1];
+        if (gx == 0.f && gy == 0.f) continue;
+        uint32_t idx[8];
+        float w8[8];
+        level_corners(p.grid, l, m, idx, w8);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) atomicAdd(dt + idx[c], make_float2(w8[c] * gx, w8[c] * gy));
+    }
+}
+
+// Transformation of one Gaussian (Section 4.1): the arithmetic of apply_kernel.
+__device__ __forceinline__ void apply_row(const TcParams &p, int64_t row, const float *r)
+{
+    float3 m = make_float3(p.mean[3 * row], p.mean[3 * row + 1], p.mean[3 * row + 2]);
+    float4 qn = qnormalize(reinterpret_cast<const float4 *>(p.quat)[row]);
+    if (!p.box.inside(m)) {
+        p.mean_out[3 * row] = m.x;
+        p.mean_out[3 * row + 1] = m.y;
+        p.mean_out[3 * row + 2] = m.z;
+        reinterpret_cast<float4 *>(p.quat_out)[row] = qn;
+        return;
+    }
+    float4 dq = qnormalize(make_float4(r[3], r[4], r[5], r[6]));
+    p.mean_out[3 * row] = m.x + r[0];
+    p.mean_out[3 * row + 1] = m.y + r[1];
+    p.mean_out[3 * row + 2] = m.z + r[2];
+    reinterpret_cast<float4 *>(p.quat_out)[row] = p.order == 0 ? qmul(qn, dq) : qmul(dq, qn);
+}
+
+// Reverse of apply_row wrt the raw outputs (the arithmetic of apply_bwd_kernel).
+__device__ __forceinline__ void apply_bwd_row(const TcParams &p, int64_t row, float *g)
+{
+    float3 m = make_float3(p.mean[3 * row], p.mean[3 * row + 1], p.mean[3 * row + 2]);
+    if (!p.box.inside(m)) {
+#pragma unroll
+        for (int k = 0; k < 7; ++k) g[k] = 0.f;
+        return;
+    }
+    g[0] = p.d_mean_out[3 * row];
+    g[1] = p.d_mean_out[3 * row + 1];
+    g[2] = p.d_mean_out[3 * row + 2];
+    float4 qn = qnormalize(reinterpret_cast<const float4 *>(p.quat)[row]);
+    const float *r = p.raw7_in + 7 * row;
+    float4 gq = reinterpret_cast<const float4 *>(p.d_quat_out)[row];
+    float4 gd = p.order == 0 ? qmul_left_T(qn, gq) : qmul_right_T(qn, gq);
+    float4 d = qnormalize_bwd(make_float4(r[3], r[4], r[5], r[6]), gd);
+    g[3] = d.x;
+    g[4] = d.y;
+    g[5] = d.z;
+    g[6] = d.w;
+}
+
 // W1 | W2 | W3 (bf16, [out][in] row-major) into K-major B operands.
 __device__ __forceinline__ void load_weights_fwd(const bf16 *w, bf16 *w1, bf16 *w2, bf16 *w3)
 {
@@ -126,12 +240,15 @@ __device__ __forceinline__ void publish_smem()
     __syncthreads();
 }
 
-template <typename ET>
-__global__ void __launch_bounds__(TM) mlp_tc_fwd_kernel(const ET *enc, int64_t n, const bf16 *w,
-                                                        float *raw7)
+template <typename ET, bool FUSED>
+__global__ void __launch_bounds__(TM) mlp_tc_fwd_kernel(TcParams p)
 {
     extern __shared__ unsigned char smem_raw[];
     FwdSmem &S = *aligned_smem<FwdSmem>(smem_raw);
+    const ET *enc = reinterpret_cast<const ET *>(p.enc);
+    const int64_t n = p.n;
+    const bf16 *w = p.w;
+    float *raw7 = p.raw7;
     const int t = threadIdx.x, warp = t >> 5;
     load_weights_fwd(w, S.w1, S.w2, S.w3);
     const uint32_t mbar = smem_u32(&S.mbar);
@@ -154,7 +271,18 @@ __global__ void __launch_bounds__(TM) mlp_tc_fwd_kernel(const ET *enc, int64_t n
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const int64_t row = tile * TM + t;
         float v[64];
-        load_row32(enc, row, n, v);
+        if (FUSED) {
+            encode_row(p, row, v);
+            if (row < n) {
+                uint4 *dst = reinterpret_cast<uint4 *>(p.enc_save + row * 32);
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    dst[c] = make_uint4(pack_bf16x2(v[8 * c], v[8 * c + 1]), pack_bf16x2(v[8 * c + 2], v[8 * c + 3]),
+                                        pack_bf16x2(v[8 * c + 4], v[8 * c + 5]), pack_bf16x2(v[8 * c + 6], v[8 * c + 7]));
+            }
+        } else {
+            load_row32(enc, row, n, v);
+        }
 #pragma unroll
         for (int c = 0; c < 4; ++c) st_chunk8(S.a1, t, 8 * c, 32, v + 8 * c);
         publish_smem();
@@ -203,6 +331,7 @@ __global__ void __launch_bounds__(TM) mlp_tc_fwd_kernel(const ET *enc, int64_t n
         if (row < n) {
 #pragma unroll
             for (int q = 0; q < 7; ++q) raw7[row * 7 + q] = v[q];
+            if (FUSED) apply_row(p, row, v);
         }
         fence_before_sync();
         __syncthreads();
@@ -214,13 +343,16 @@ __global__ void __launch_bounds__(TM) mlp_tc_fwd_kernel(const ET *enc, int64_t n
     if (warp == 0) tmem_dealloc(tm, 64);
 }
 
-template <typename ET>
-__global__ void __launch_bounds__(TM) mlp_tc_bwd_kernel(const ET *enc, int64_t n, const bf16 *w,
-                                                        const float *d_raw7, const float *d_scale,
-                                                        float *dW, float *d_enc)
+template <typename ET, bool FUSED>
+__global__ void __launch_bounds__(TM) mlp_tc_bwd_kernel(TcParams p)
 {
     extern __shared__ unsigned char smem_raw[];
     BwdSmem &S = *aligned_smem<BwdSmem>(smem_raw);
+    const ET *enc = reinterpret_cast<const ET *>(p.enc);
+    const int64_t n = p.n;
+    const bf16 *w = p.w;
+    const float *d_raw7 = p.d_raw7, *d_scale = p.d_scale;
+    float *dW = p.dW, *d_enc = p.d_enc;
     const int t = threadIdx.x, warp = t >> 5;
     load_weights_fwd(w, S.w1, S.w2, S.w3t);  // w3t slot reused below; rewritten transposed
     __syncthreads();
@@ -271,7 +403,17 @@ __global__ void __launch_bounds__(TM) mlp_tc_bwd_kernel(const ET *enc, int64_t n
         for (int i = 0; i < 32; ++i) S.BT[kmajor_off(64 + i, t, TM)] = __float2bfloat16_rn(v[i]);
         float g[16];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) g[q] = (q < 7 && row < n) ? d_raw7[row * 7 + q] * scale : 0.f;
+        for (int q = 0; q < 16; ++q) g[q] = 0.f;
+        if (row < n) {
+            if (FUSED) {
+                apply_bwd_row(p, row, g);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 7; ++q) g[q] = d_raw7[row * 7 + q];
+            }
+#pragma unroll
+            for (int q = 0; q < 7; ++q) g[q] *= scale;
+        }
         st_chunk8(S.ga, t, 0, 16, g);
         st_chunk8(S.ga, t, 8, 16, g + 8);
 #pragma unroll
@@ -380,7 +522,11 @@ __global__ void __launch_bounds__(TM) mlp_tc_bwd_kernel(const ET *enc, int64_t n
             mma_commit(mbar);
         }
         if (!(ok = wait_mma(mbar, phase))) break;
-        if (d_enc) {
+        if (FUSED) {
+            tmem_ld16(D0 + lane, v);
+            tmem_ld16(D0 + lane + 16, v + 16);
+            if (row < n) scatter_row(p, row, v);
+        } else if (d_enc) {
             tmem_ld16(D0 + lane, v);
             tmem_ld16(D0 + lane + 16, v + 16);
             if (row < n) {
@@ -432,24 +578,39 @@ static gs_status check_common(const void *enc, int enc_dtype, const gs_mlp *w)
     return GS_OK;
 }
 
+template <typename ET, bool FUSED>
+static gs_status launch_fwd(const TcParams &p, cudaStream_t s)
+{
+    const size_t smem = sizeof(FwdSmem) + 1024;
+    const int grid = (int)std::min<int64_t>(ceil_div(p.n, TM), kNumSMs * 4);
+    set_smem_limit((const void *)mlp_tc_fwd_kernel<ET, FUSED>, (int)smem, s);
+    note_launch();
+    mlp_tc_fwd_kernel<ET, FUSED><<<grid, TM, smem, s>>>(p);
+    return launch_status(FUSED ? "ntc_fused_fwd" : "ntc_mlp_fwd (tcgen05)");
+}
+
+template <typename ET, bool FUSED>
+static gs_status launch_bwd(const TcParams &p, cudaStream_t s)
+{
+    const size_t smem = sizeof(BwdSmem) + 1024;
+    const int grid = (int)std::min<int64_t>(ceil_div(p.n, TM), kNumSMs);
+    set_smem_limit((const void *)mlp_tc_bwd_kernel<ET, FUSED>, (int)smem, s);
+    note_launch();
+    mlp_tc_bwd_kernel<ET, FUSED><<<grid, TM, smem, s>>>(p);
+    return launch_status(FUSED ? "ntc_fused_bwd" : "ntc_mlp_bwd (tcgen05)");
+}
+
 gs_status mlp_tc_fwd(const void *enc, int enc_dtype, int64_t n, const gs_mlp *w, float *raw7,
                      cudaStream_t s)
 {
     gs_status st = check_common(enc, enc_dtype, w);
     if (st != GS_OK) return st;
-    const size_t smem = sizeof(FwdSmem) + 1024;
-    const int64_t ntiles = ceil_div(n, TM);
-    const int grid = (int)std::min<int64_t>(ntiles, kNumSMs * 4);
-    const bf16 *wb = reinterpret_cast<const bf16 *>(w->w_bf16);
-    note_launch();
-    if (enc_dtype == GS_BF16) {
-        set_smem_limit((const void *)mlp_tc_fwd_kernel<bf16>, (int)smem, s);
-        mlp_tc_fwd_kernel<bf16><<<grid, TM, smem, s>>>((const bf16 *)enc, n, wb, raw7);
-    } else {
-        set_smem_limit((const void *)mlp_tc_fwd_kernel<float>, (int)smem, s);
-        mlp_tc_fwd_kernel<float><<<grid, TM, smem, s>>>((const float *)enc, n, wb, raw7);
-    }
-    return launch_status("ntc_mlp_fwd (tcgen05)");
+    TcParams p{};
+    p.enc = enc;
+    p.n = n;
+    p.w = reinterpret_cast<const bf16 *>(w->w_bf16);
+    p.raw7 = raw7;
+    return enc_dtype == GS_BF16 ? launch_fwd<bf16, false>(p, s) : launch_fwd<float, false>(p, s);
 }
 
 gs_status mlp_tc_bwd(const void *enc, int enc_dtype, int64_t n, const gs_mlp *w,
@@ -459,22 +620,85 @@ gs_status mlp_tc_bwd(const void *enc, int enc_dtype, int64_t n, const gs_mlp *w,
     gs_status st = check_common(enc, enc_dtype, w);
     if (st != GS_OK) return st;
     GS_REQUIRE(d_enc == nullptr || aligned(d_enc, 16), "BF16 MLP: d_enc misaligned");
-    const size_t smem = sizeof(BwdSmem) + 1024;
-    const int64_t ntiles = ceil_div(n, TM);
-    const int grid = (int)std::min<int64_t>(ntiles, kNumSMs);
-    const bf16 *wb = reinterpret_cast<const bf16 *>(w->w_bf16);
-    note_launch();
-    if (enc_dtype == GS_BF16) {
-        set_smem_limit((const void *)mlp_tc_bwd_kernel<bf16>, (int)smem, s);
-        mlp_tc_bwd_kernel<bf16><<<grid, TM, smem, s>>>((const bf16 *)enc, n, wb, d_raw7, d_scale, dW, d_enc);
-    } else {
-        set_smem_limit((const void *)mlp_tc_bwd_kernel<float>, (int)smem, s);
-        mlp_tc_bwd_kernel<float><<<grid, TM, smem, s>>>((const float *)enc, n, wb, d_raw7, d_scale, dW, d_enc);
-    }
-    return launch_status("ntc_mlp_bwd (tcgen05)");
+    TcParams p{};
+    p.enc = enc;
+    p.n = n;
+    p.w = reinterpret_cast<const bf16 *>(w->w_bf16);
+    p.d_raw7 = d_raw7;
+    p.d_scale = d_scale;
+    p.dW = dW;
+    p.d_enc = d_enc;
+    return enc_dtype == GS_BF16 ? launch_bwd<bf16, false>(p, s) : launch_bwd<float, false>(p, s);
 }
 
 }  // namespace gs3
+
+using namespace gs3;
+
+extern "C" gs_status ntc_fused_fwd(const float *mean, const float *quat, int64_t n,
+                                   const gs_hashgrid *grid, const void *table_f16, const gs_mlp *w,
+                                   int order, float *mean_out, float *quat_out, float *raw7,
+                                   void *enc_save, gs_stream stream)
+{
+    GS_REQUIRE(mean && quat && grid && table_f16 && w && mean_out && quat_out && raw7 && enc_save &&
+                   n >= 0,
+               "ntc_fused_fwd: null argument");
+    GS_REQUIRE(w->precision == GS_MLP_BF16 && w->w_bf16, "ntc_fused_fwd: needs BF16 MLP weights");
+    GS_REQUIRE(order == 0 || order == 1, "ntc_fused_fwd: order must be 0 or 1");
+    GS_REQUIRE(aligned(quat, 16) && aligned(quat_out, 16) && aligned(enc_save, 16) &&
+                   aligned(w->w_bf16, 16) && aligned(table_f16, 4),
+               "ntc_fused_fwd: misaligned argument");
+    TcParams p{};
+    int64_t total;
+    GS_REQUIRE(grid_params(grid, p.grid, total), "ntc_fused_fwd: invalid hash grid");
+    if (n == 0) return GS_OK;
+    p.n = n;
+    p.w = reinterpret_cast<const bf16 *>(w->w_bf16);
+    p.raw7 = raw7;
+    p.mean = mean;
+    p.quat = quat;
+    p.table = reinterpret_cast<const __half *>(table_f16);
+    p.enc_save = reinterpret_cast<bf16 *>(enc_save);
+    p.mean_out = mean_out;
+    p.quat_out = quat_out;
+    p.box = Box::from(grid->aabb);
+    p.order = order;
+    return launch_fwd<bf16, true>(p, as_stream(stream));
+}
+
+extern "C" gs_status ntc_fused_bwd(const float *mean, const float *quat, const float *raw7,
+                                   const void *enc_save, int64_t n, const gs_hashgrid *grid,
+                                   const gs_mlp *w, int order, const float *d_mean_out,
+                                   const float *d_quat_out, const float *d_scale, float *dW,
+                                   float *d_table, gs_stream stream)
+{
+    GS_REQUIRE(mean && quat && raw7 && enc_save && grid && w && d_mean_out && d_quat_out && dW &&
+                   d_table && n >= 0,
+               "ntc_fused_bwd: null argument");
+    GS_REQUIRE(w->precision == GS_MLP_BF16 && w->w_bf16, "ntc_fused_bwd: needs BF16 MLP weights");
+    GS_REQUIRE(order == 0 || order == 1, "ntc_fused_bwd: order must be 0 or 1");
+    GS_REQUIRE(aligned(quat, 16) && aligned(d_quat_out, 16) && aligned(enc_save, 16) &&
+                   aligned(w->w_bf16, 16) && aligned(d_table, 8),
+               "ntc_fused_bwd: misaligned argument");
+    TcParams p{};
+    int64_t total;
+    GS_REQUIRE(grid_params(grid, p.grid, total), "ntc_fused_bwd: invalid hash grid");
+    if (n == 0) return GS_OK;
+    p.enc = enc_save;
+    p.n = n;
+    p.w = reinterpret_cast<const bf16 *>(w->w_bf16);
+    p.d_scale = d_scale;
+    p.dW = dW;
+    p.mean = mean;
+    p.quat = quat;
+    p.raw7_in = raw7;
+    p.d_mean_out = d_mean_out;
+    p.d_quat_out = d_quat_out;
+    p.d_table = d_table;
+    p.box = Box::from(grid->aabb);
+    p.order = order;
+    return launch_bwd<bf16, true>(p, as_stream(stream));
+}
 
 extern "C" int gs_tc_timeouts(void)
 {

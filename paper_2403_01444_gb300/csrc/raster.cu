@@ -6,9 +6,10 @@
 namespace gs3 {
 
 constexpr int FT = 256;         // forward: threads per 16x16 tile, one pixel each
-constexpr int RT = 128;         // backward: threads per tile, two pixels each (rows y, y + 8)
-constexpr int BWD_CHUNK = 32;   // records per backward reduction chunk
-constexpr int RWARPS = RT / 32;
+#ifndef BWD_PIXELS_PER_THREAD
+#define BWD_PIXELS_PER_THREAD 2  // backward: pixels per thread (256 / this threads per tile)
+#endif
+constexpr int BWD_CHUNK = 32;    // records per backward reduction chunk
 
 struct RasterParams {
     const float2 *mean2d;
@@ -278,59 +279,59 @@ __device__ __forceinline__ bool unblend_one(PixBwd &P, float2 xy, float4 co, con
     return true;
 }
 
-template <bool WANT_OP, bool BINNED>
-__global__ void __launch_bounds__(RT) raster_bwd_kernel(RasterParams p)
+template <bool WANT_OP, bool BINNED, int PPT>
+__global__ void __launch_bounds__(256 / PPT) raster_bwd_kernel(RasterParams p)
 {
+    constexpr int NT = 256 / PPT;        // threads per tile
+    constexpr int NW = NT / 32;          // warps per tile
+    constexpr int ROWSTEP = 16 / PPT;    // a thread's pixels: rows r0, r0 + ROWSTEP, ...
     constexpr int NV = WANT_OP ? 9 : 8;
-    __shared__ float2 s_xy[RT];
-    __shared__ float4 s_co[RT];
-    __shared__ float s_rgb[RT][3];
-    __shared__ uint32_t s_g[RT];
-    __shared__ int s_pos[RT];
-    __shared__ int s_wcnt[RWARPS];
-    __shared__ float s_part[RWARPS][BWD_CHUNK][NV];
+    __shared__ float2 s_xy[NT];
+    __shared__ float4 s_co[NT];
+    __shared__ float s_rgb[NT][3];
+    __shared__ uint32_t s_g[NT];
+    __shared__ int s_pos[NT];
+    __shared__ int s_wcnt[NW];
+    __shared__ float s_part[NW][BWD_CHUNK][NV];
     __shared__ int s_max;
     const int tile = blockIdx.x, view = blockIdx.y;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tx_t = tile % p.tx, ty_t = tile / p.tx;
     const int px = tx_t * 16 + (tid & 15);
-    const int py0 = ty_t * 16 + (tid >> 4);
-    const int py1 = py0 + 8;
-    const float pxf = (float)px + 0.5f, pyf0 = (float)py0 + 0.5f, pyf1 = (float)py1 + 0.5f;
+    const int r0 = tid >> 4;
+    const float pxf = (float)px + 0.5f;
     const int binid = (ty_t / p.bin) * p.bins_x + tx_t / p.bin;
     const uint2 range = p.ranges[(int64_t)view * p.bins + binid];
     const int64_t vb = (int64_t)view * p.n;
     const int64_t HW = (int64_t)p.H * p.W;
-    PixBwd A{0, 1.f, 0.f, 0.f, 0.f, p.bg0, p.bg1, p.bg2};
-    PixBwd B{0, 1.f, 0.f, 0.f, 0.f, p.bg0, p.bg1, p.bg2};
-    if (px < p.W && py0 < p.H) {
-        int64_t pix = (int64_t)view * HW + (int64_t)py0 * p.W + px;
-        A.last = p.last[pix];
-        A.T = p.T_final[pix];
-        const float *di = p.d_img + (int64_t)view * 3 * HW + (int64_t)py0 * p.W + px;
-        A.dC0 = di[0];
-        A.dC1 = di[HW];
-        A.dC2 = di[2 * HW];
-    }
-    if (px < p.W && py1 < p.H) {
-        int64_t pix = (int64_t)view * HW + (int64_t)py1 * p.W + px;
-        B.last = p.last[pix];
-        B.T = p.T_final[pix];
-        const float *di = p.d_img + (int64_t)view * 3 * HW + (int64_t)py1 * p.W + px;
-        B.dC0 = di[0];
-        B.dC1 = di[HW];
-        B.dC2 = di[2 * HW];
+    PixBwd P[PPT];
+    float pyf[PPT];
+    int mylast = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int py = ty_t * 16 + r0 + k * ROWSTEP;
+        pyf[k] = (float)py + 0.5f;
+        P[k] = PixBwd{0, 1.f, 0.f, 0.f, 0.f, p.bg0, p.bg1, p.bg2};
+        if (px < p.W && py < p.H) {
+            int64_t pix = (int64_t)view * HW + (int64_t)py * p.W + px;
+            P[k].last = p.last[pix];
+            P[k].T = p.T_final[pix];
+            const float *di = p.d_img + (int64_t)view * 3 * HW + (int64_t)py * p.W + px;
+            P[k].dC0 = di[0];
+            P[k].dC1 = di[HW];
+            P[k].dC2 = di[2 * HW];
+        }
+        mylast = max(mylast, P[k].last);
     }
     if (tid == 0) s_max = 0;
     __syncthreads();
-    const int mylast = max(A.last, B.last);
     if (mylast > 0) atomicMax(&s_max, mylast);
     __syncthreads();
     const int maxlast = s_max;
     uint32_t n_tested = 0, n_contrib = 0;
-    for (int hi = maxlast; hi > 0; hi -= RT) {
+    for (int hi = maxlast; hi > 0; hi -= NT) {
         // candidates [lo, hi) of the bin list, compacted to this tile's records
-        const int lo = max(0, hi - RT);
+        const int lo = max(0, hi - NT);
         const int k = lo + tid;
         int64_t o = 0;
         uint32_t g = 0;
@@ -343,7 +344,7 @@ __global__ void __launch_bounds__(RT) raster_bwd_kernel(RasterParams p)
             keep = keep_record<BINNED>(p, o, tx_t, ty_t, m, co);
         }
         int cnt;
-        const int slot = compact_slot<RT>(keep, s_wcnt, cnt);
+        const int slot = compact_slot<NT>(keep, s_wcnt, cnt);
         if (slot >= 0) {
             s_g[slot] = g;
             s_xy[slot] = m;
@@ -364,19 +365,16 @@ __global__ void __launch_bounds__(RT) raster_bwd_kernel(RasterParams p)
                 bool contrib = false;
                 if (pos < mylast) {
                     float2 xy = s_xy[j];
-                    float4 co = s_co[j];
+                    float4 cc = s_co[j];
                     const float *c = s_rgb[j];
-                    if (pos < A.last) {
-                        ++n_tested;
-                        bool h = unblend_one<WANT_OP>(A, xy, co, c, pxf, pyf0, v);
-                        n_contrib += h;
-                        contrib |= h;
-                    }
-                    if (pos < B.last) {
-                        ++n_tested;
-                        bool h = unblend_one<WANT_OP>(B, xy, co, c, pxf, pyf1, v);
-                        n_contrib += h;
-                        contrib |= h;
+#pragma unroll
+                    for (int q = 0; q < PPT; ++q) {
+                        if (pos < P[q].last) {
+                            ++n_tested;
+                            bool h = unblend_one<WANT_OP>(P[q], xy, cc, c, pxf, pyf[q], v);
+                            n_contrib += h;
+                            contrib |= h;
+                        }
                     }
                 }
                 if (__any_sync(0xffffffffu, contrib)) {
@@ -398,7 +396,7 @@ __global__ void __launch_bounds__(RT) raster_bwd_kernel(RasterParams p)
                 int j = tid >> 1, h = (tid & 1) * 4;
                 float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-                for (int w = 0; w < RWARPS; ++w) {
+                for (int w = 0; w < NW; ++w) {
                     sum.x += s_part[w][j][h];
                     sum.y += s_part[w][j][h + 1];
                     sum.z += s_part[w][j][h + 2];
@@ -406,12 +404,14 @@ __global__ void __launch_bounds__(RT) raster_bwd_kernel(RasterParams p)
                 }
                 if (sum.x != 0.f || sum.y != 0.f || sum.z != 0.f || sum.w != 0.f)
                     atomicAdd(reinterpret_cast<float4 *>(p.grads + 8 * (vb + s_g[clo + j]) + h), sum);
-            } else if (WANT_OP && tid >= 64 && tid < 64 + ccnt) {
-                int j = tid - 64;
-                float sum = 0.f;
+            }
+            if (WANT_OP) {
+                for (int j = tid; j < ccnt; j += NT) {
+                    float sum = 0.f;
 #pragma unroll
-                for (int w = 0; w < RWARPS; ++w) sum += s_part[w][j][NV - 1];
-                if (sum != 0.f) atomicAdd(p.d_opacity + vb + s_g[clo + j], sum);
+                    for (int w = 0; w < NW; ++w) sum += s_part[w][j][NV - 1];
+                    if (sum != 0.f) atomicAdd(p.d_opacity + vb + s_g[clo + j], sum);
+                }
             }
             __syncthreads();
         }
@@ -499,13 +499,15 @@ extern "C" gs_status gs_raster_bwd(const gs_projected *proj, int64_t n, int V, i
     p.stats = reinterpret_cast<unsigned long long *>(d_stats);
     dim3 grid(p.tx * p.ty, V);
     note_launch();
+    constexpr int PPT = BWD_PIXELS_PER_THREAD;
+    constexpr int NT = 256 / PPT;
     if (d_opacity && bin > 1)
-        raster_bwd_kernel<true, true><<<grid, RT, 0, s>>>(p);
+        raster_bwd_kernel<true, true, PPT><<<grid, NT, 0, s>>>(p);
     else if (d_opacity)
-        raster_bwd_kernel<true, false><<<grid, RT, 0, s>>>(p);
+        raster_bwd_kernel<true, false, PPT><<<grid, NT, 0, s>>>(p);
     else if (bin > 1)
-        raster_bwd_kernel<false, true><<<grid, RT, 0, s>>>(p);
+        raster_bwd_kernel<false, true, PPT><<<grid, NT, 0, s>>>(p);
     else
-        raster_bwd_kernel<false, false><<<grid, RT, 0, s>>>(p);
+        raster_bwd_kernel<false, false, PPT><<<grid, NT, 0, s>>>(p);
     return launch_status("gs_raster_bwd");
 }

@@ -179,8 +179,10 @@ class Stage1:
 
     def __init__(self, g: Gaussians, ntc: NTC, V: int, W: int, H: int, capacity: int,
                  order: int = 0, loss_scale: Optional[float] = None, growth_interval=2000,
-                 device="cuda", bin: int = DEFAULT_BIN):
+                 device="cuda", bin: int = DEFAULT_BIN, fused: bool = True):
         n = g.n
+        # the fused cache kernels exist for the BF16 tensor-core MLP
+        self.fused = fused and ntc.precision == gs3.GS_MLP_BF16
         self.g, self.ntc, self.V, self.W, self.H, self.order = g, ntc, V, W, H, order
         self.raster = Rasterizer(n, V, W, H, capacity, device, bin=bin)
         self.loss = Loss(V, W, H, device)
@@ -203,6 +205,10 @@ class Stage1:
     def transform(self, stream=None):
         """NTC query + transformation: writes mean_t, quat_t."""
         g, ntc, n = self.g, self.ntc, self.g.n
+        if self.fused:
+            gs3.ntc_fused_fwd(g.mean, g.quat, n, ntc.grid, ntc.table.shadow, ntc.mlp_struct(), self.order,
+                              self.mean_t, self.quat_t, self.raw7, self.enc, stream)
+            return self.mean_t, self.quat_t
         gs3.ntc_encode_fwd(g.mean, n, ntc.grid, ntc.table_for_encode(), self.enc, stream)
         gs3.ntc_mlp_fwd(self.enc, n, ntc.mlp_struct(), self.raw7, stream)
         gs3.ntc_apply(g.mean, g.quat, self.raw7, n, self.aabb, self.order, self.mean_t, self.quat_t,
@@ -218,6 +224,10 @@ class Stage1:
         self.loss(img, target, stream)
         d_mean, d_quat = self.raster.backward(g, cams_dev, self.loss.d_img, self.mean_t, self.quat_t,
                                               stream)
+        if self.fused:
+            gs3.ntc_fused_bwd(g.mean, g.quat, self.raw7, self.enc, n, ntc.grid, ntc.mlp_struct(), self.order,
+                              d_mean, d_quat, self.loss_scale_view(), ntc.mlp.g, ntc.table.g, stream)
+            return self.loss.d_loss
         gs3.ntc_apply_bwd(g.mean, g.quat, self.raw7, n, self.aabb, self.order, d_mean, d_quat,
                           self.d_raw7, stream)
         gs3.ntc_mlp_bwd(self.enc, n, ntc.mlp_struct(), self.d_raw7, self.loss_scale_view(),

@@ -308,6 +308,21 @@ def ntc_apply_bwd(mean, quat, raw7, n, aabb, order, d_mean_out, d_quat_out, d_ra
         _ptr(d_quat_out), _ptr(d_raw7), _stream(stream)))
 
 
+def ntc_fused_fwd(mean, quat, n, grid: GsHashgrid, table_f16, mlp: GsMlp, order, mean_out, quat_out,
+                  raw7, enc_save, stream=None):
+    _check("ntc_fused_fwd", lib().ntc_fused_fwd(
+        _ptr(mean), _ptr(quat), c_int64(n), ctypes.byref(grid), _ptr(table_f16), ctypes.byref(mlp),
+        c_int(order), _ptr(mean_out), _ptr(quat_out), _ptr(raw7), _ptr(enc_save), _stream(stream)))
+
+
+def ntc_fused_bwd(mean, quat, raw7, enc_save, n, grid: GsHashgrid, mlp: GsMlp, order, d_mean_out,
+                  d_quat_out, d_scale, dW, d_table, stream=None):
+    _check("ntc_fused_bwd", lib().ntc_fused_bwd(
+        _ptr(mean), _ptr(quat), _ptr(raw7), _ptr(enc_save), c_int64(n), ctypes.byref(grid),
+        ctypes.byref(mlp), c_int(order), _ptr(d_mean_out), _ptr(d_quat_out), _ptr(d_scale), _ptr(dW),
+        _ptr(d_table), _stream(stream)))
+
+
 def ntc_warmup_loss(raw7, n, d_raw7, d_loss, stream=None):
     _check("ntc_warmup_loss", lib().ntc_warmup_loss(_ptr(raw7), c_int64(n), _ptr(d_raw7), _ptr(d_loss),
                                                     _stream(stream)))

@@ -477,3 +477,54 @@ def test_mlp_bf16_tensor_core_parity(n):
     for sl in (slice(0, 2048), slice(2048, 6144), slice(6144, 6592)):
         assert rel_err(gW[sl], wantW[sl]) <= 5e-2, sl
     assert rel_err(gd, dx) <= 5e-2
+
+
+@pytest.mark.parametrize("n", [1, 300, 20_001])
+def test_fused_cache_kernels_match_separate_kernels(n):
+    """ntc_fused_fwd = encode (FP16 table) + BF16 MLP + apply, bit for bit;
+    ntc_fused_bwd = apply_bwd + MLP bwd + encode_bwd up to the order of the
+    FP32 atomic additions."""
+    og, gg = _grid_pair()
+    rng = np.random.default_rng(3000 + n)
+    aabb = [-1.5] * 3 + [1.5] * 3
+    mu = t(rng.uniform(-1.6, 1.6, size=(n, 3)))   # a few outside the box
+    q = t(rng.normal(size=(n, 4)))
+    table = t(rng.normal(0, 0.3, size=(og.n_entries, 2))).to(torch.float16)
+    Ws, _ = _mlp(3100 + n)
+    w32 = t(np.concatenate([w.ravel() for w in Ws]))
+    wbf = w32.to(torch.bfloat16)
+    mlp = gs3.mlp_struct(gs3.GS_MLP_BF16, w32, wbf)
+    # separate kernels
+    enc = torch.zeros(n, 32, device=DEV, dtype=torch.bfloat16)
+    raw = torch.zeros(n, 7, device=DEV)
+    mo, qo = torch.zeros(n, 3, device=DEV), torch.zeros(n, 4, device=DEV)
+    gs3.ntc_encode_fwd(mu, n, gg, table, enc)
+    gs3.ntc_mlp_fwd(enc, n, mlp, raw)
+    gs3.ntc_apply(mu, q, raw, n, aabb, 0, mo, qo)
+    # fused
+    enc2 = torch.zeros_like(enc)
+    raw2, mo2, qo2 = torch.zeros_like(raw), torch.zeros_like(mo), torch.zeros_like(qo)
+    gs3.ntc_fused_fwd(mu, q, n, gg, table, mlp, 0, mo2, qo2, raw2, enc2)
+    torch.cuda.synchronize()
+    assert torch.equal(enc2, enc) and torch.equal(raw2, raw)
+    assert torch.equal(mo2, mo) and torch.equal(qo2, qo)
+    dmo, dqo = t(rng.normal(size=(n, 3))), t(rng.normal(size=(n, 4)))
+    scale = torch.tensor([64.0], device=DEV)
+    d_raw = torch.zeros(n, 7, device=DEV)
+    dW, d_enc = torch.zeros(gs3.MLP_PARAMS, device=DEV), torch.zeros(n, 32, device=DEV)
+    dT = torch.zeros(og.n_entries, 2, device=DEV)
+    gs3.ntc_apply_bwd(mu, q, raw, n, aabb, 0, dmo, dqo, d_raw)
+    gs3.ntc_mlp_bwd(enc, n, mlp, d_raw, scale, dW, d_enc)
+    gs3.ntc_encode_bwd(mu, n, gg, d_enc, dT)
+    dW2, dT2 = torch.zeros_like(dW), torch.zeros_like(dT)
+    gs3.ntc_fused_bwd(mu, q, raw2, enc2, n, gg, mlp, 0, dmo, dqo, scale, dW2, dT2)
+    torch.cuda.synchronize()
+    assert rel_err(dW2.cpu().numpy(), dW.cpu().numpy()) <= 1e-5
+    assert rel_err(dT2.cpu().numpy(), dT.cpu().numpy()) <= 1e-5
+    # and the fused forward against the FP64 oracle on the same FP16 / BF16 values
+    want_enc = oracle.encode(og, mu.cpu().numpy(), table.float().cpu().numpy())
+    got_enc = enc2.float().cpu().numpy()
+    assert np.all(np.abs(got_enc - want_enc) <= 2 ** -8 * np.abs(want_enc) + 1e-3 * 0.3 * 5)
+    Wb = [_bf16(w) for w in Ws]
+    _, _, want_raw = oracle.mlp_fwd(got_enc, Wb)
+    assert rel_err(raw2.cpu().numpy(), want_raw) <= 1e-2
