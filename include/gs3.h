@@ -107,8 +107,9 @@ typedef struct {
  * Weights are [out][in] row-major, concatenated W1 | W2 | W3 (6592 values). */
 enum { GS_MLP_FP32 = 0, GS_MLP_BF16 = 1 };
 typedef struct {
-    int32_t precision;   /* GS_MLP_FP32: SIMT FP32; GS_MLP_BF16: tcgen05 BF16 x BF16 -> FP32 */
-    const float *w_f32;  /* FP32 master weights (device) */
+    int32_t precision;   /* GS_MLP_FP32: SIMT FP32; GS_MLP_BF16: tcgen05 BF16 x BF16 -> FP32
+                            for the two hidden layers, FP32 output layer (64 -> 7) */
+    const float *w_f32;  /* FP32 master weights (device); required for both precisions */
     const void *w_bf16;  /* BF16 copy of the same layout (device), used when precision == BF16 */
 } gs_mlp;
 

@@ -235,28 +235,51 @@ def bin_sort(mean2d, radius, depth, W, H, tile=TILE, capacity=None):
 
 
 # ---------------------------------------------------------------- compositing
-def raster_fwd(proj, W, H, bg=(0.0, 0.0, 0.0), tile=TILE):
+def _win(window):
+    return None if window is None else _p(np.ascontiguousarray(window, np.int32))
+
+
+def _reach(eps, V, N):
+    if np.isscalar(eps) and eps == 0:
+        return None
+    return _p(np.ascontiguousarray(np.broadcast_to(_d(eps), (V, N))))
+
+
+def raster_fwd(proj, W, H, bg=(0.0, 0.0, 0.0), tile=TILE, window=None, tie=0.0,
+               tie_budget=0.0, pos_eps=0.0, rel_eps=0.0, depth_eps=0.0):
+    """window = (tx0, ty0, tx1, ty1) tiles: composite only that crop (other
+    pixels are left 0, T_final 1).  Ambiguity flags: tie is the relative
+    depth gap under which two consecutive added Gaussians may be ordered
+    either way; the swaps' exact effects T a_i a_j |c_i - c_j| add up to a
+    per-pixel bound that flags the pixel above tie_budget; depth_eps widens
+    that gap by each Gaussian's absolute depth reach.  pos_eps (pixels)
+    and rel_eps (relative) widen the threshold margins by the reach of a
+    displacement of the 2D means and a relative change of the conics
+    (scalars or per-record [V, N] arrays)."""
     m2, cn, op, rgb, dp = (_d(proj[k]) for k in ("mean2d", "conic", "opacity", "rgb", "depth"))
     rad = np.ascontiguousarray(proj["radius"], np.int32)
     V, N = dp.shape
     img = np.zeros((V, 3, H, W))
-    Tf = np.zeros((V, H, W))
+    Tf = np.ones((V, H, W))
     last = np.zeros((V, H, W), np.int32)
     amb = np.zeros((V, H, W), np.int32)
     lib().orc_raster_fwd(I32(V), I64(N), I32(W), I32(H), I32(tile), _p(m2), _p(cn), _p(op),
-                         _p(rgb), _p(dp), _p(rad), _p(_d(bg)), _p(img), _p(Tf), _p(last), _p(amb))
+                         _p(rgb), _p(dp), _p(rad), _p(_d(bg)), _win(window), F64(tie),
+                         F64(tie_budget), _reach(depth_eps, V, N), _reach(pos_eps, V, N),
+                         _reach(rel_eps, V, N), _p(img),
+                         _p(Tf), _p(last), _p(amb))
     return img, Tf, last, amb
 
 
 def raster_bwd(proj, W, H, T_final, last, d_img, bg=(0.0, 0.0, 0.0), tile=TILE,
-               want_opacity=False):
+               want_opacity=False, window=None):
     m2, cn, op, rgb, dp = (_d(proj[k]) for k in ("mean2d", "conic", "opacity", "rgb", "depth"))
     rad = np.ascontiguousarray(proj["radius"], np.int32)
     V, N = dp.shape
     grads = np.zeros((V, N, 8))
     dop = np.zeros((V, N)) if want_opacity else None
     lib().orc_raster_bwd(I32(V), I64(N), I32(W), I32(H), I32(tile), _p(m2), _p(cn), _p(op),
-                         _p(rgb), _p(dp), _p(rad), _p(_d(bg)), _p(_d(T_final)),
+                         _p(rgb), _p(dp), _p(rad), _p(_d(bg)), _win(window), _p(_d(T_final)),
                          _p(np.ascontiguousarray(last, np.int32)), _p(_d(d_img)), _p(grads),
                          _p(dop) if dop is not None else None)
     return (grads, dop) if want_opacity else grads
@@ -313,10 +336,16 @@ def ntc_forward(p: NTCParams, mean, quat, order=0):
     return dict(enc=enc, h1=h1, h2=h2, raw7=raw7, mean=mo, quat=qo)
 
 
-def render(g, cams, mean=None, quat=None, bg=(0.0, 0.0, 0.0), tile=TILE):
+def render(g, cams, mean=None, quat=None, bg=(0.0, 0.0, 0.0), tile=TILE, window=None,
+           tie=4e-7, tie_budget=2.5e-5, pos_eps=0.0, rel_eps=0.0, depth_eps=0.0):
+    """Projection + compositing of g in FP64.  The ambiguity flags default to
+    an FP32 computation of the same inputs: depth ties within 4e-7 (the reach
+    of FP32 depth rounding) whose swaps could move the pixel by more than
+    2.5e-5, a quarter of the FP32 image tolerance."""
     pr = project(g, cams, tile, mean=mean, quat=quat)
     W, H = cams[0].W, cams[0].H
-    img, Tf, last, amb = raster_fwd(pr, W, H, bg, tile)
+    img, Tf, last, amb = raster_fwd(pr, W, H, bg, tile, window, tie, tie_budget, pos_eps, rel_eps,
+                                    depth_eps)
     return dict(proj=pr, img=img, T_final=Tf, last=last, ambig=amb)
 
 

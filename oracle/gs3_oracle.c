@@ -712,8 +712,25 @@ ORC_API int64_t orc_bin_sort(int V, int64_t N, int W, int H, int tile, const flo
  *   skip if power > 0; alpha = min(0.99, o exp(power)); skip if alpha < 1/255
  *   stop (without adding) when T (1 - alpha) < 1e-4; else C += c alpha T, T *= 1 - alpha
  *   output C + T bg; T_final = T; last = 1 + list position of the last added.
- * ambig[p] = 1 when any decision of pixel p lies within a small relative
- * margin of its threshold, where FP32 and FP64 arithmetic may decide apart.
+ * ambig[p] = 1 when a decision of pixel p may fall the other way in a
+ * computation that differs from this one by rounding or by a small
+ * perturbation of its inputs:
+ *  - a threshold (power > 0, alpha against 1/255 and 0.99, T (1 - alpha)
+ *    against 1e-4) lies within its relative rounding margin, widened by the
+ *    reach of the perturbation: a displacement of up to pos_eps[v][g] pixels
+ *    of the 2D mean (|grad power| pos_eps) and a change of the conic of up to
+ *    rel_eps[v][g] relative to its smallest eigenvalue (|power| rel_eps); NULL
+ *    arrays mean 0, for exact-input comparisons;
+ *  - two consecutive added Gaussians lie within `tie` (relative) plus their
+ *    depth reaches depth_eps[v][g] (absolute; NULL means 0) in depth, so that
+ *    their order may differ.  Swapping two adjacent added Gaussians i, j
+ *    changes the pixel by exactly T_i alpha_i alpha_j (c_i - c_j) (T_i the
+ *    transmittance before both; the product of (1 - alpha) is unchanged), so
+ *    such pairs add that amount to a per-pixel bound and only flag the pixel
+ *    when the bound exceeds tie_budget; a run of three or more tied Gaussians,
+ *    or a tie with the Gaussian that ends the pixel, always flags it.
+ * win (optional, tiles x0 y0 x1 y1): only pixels of those tiles are
+ * composited (a crop of the same definition); other outputs are untouched.
  * ====================================================================== */
 typedef struct { double depth; int64_t g; } item_t;
 static int cmp_item(const void *pa, const void *pb)
@@ -723,8 +740,15 @@ static int cmp_item(const void *pa, const void *pb)
     return a->g < b->g ? -1 : (a->g > b->g);
 }
 
+/* win: optional tile window (tx0, ty0, tx1, ty1); lists of other tiles stay empty */
+static int in_win(const int32_t *win, int x, int y)
+{
+    return !win || (x >= win[0] && x < win[2] && y >= win[1] && y < win[3]);
+}
+
 static void build_lists(int V, int64_t N, int W, int H, int tile, const double *mean2d,
-                        const int32_t *radius, const double *depth, int64_t **off_out, item_t **items_out)
+                        const int32_t *radius, const double *depth, const int32_t *win,
+                        int64_t **off_out, item_t **items_out)
 {
     int tx = (W + tile - 1) / tile, ty = (H + tile - 1) / tile;
     int64_t tiles = (int64_t)tx * ty, nt = tiles * V;
@@ -736,7 +760,8 @@ static void build_lists(int V, int64_t N, int W, int H, int tile, const double *
             int r[4];
             tile_rect(mean2d[2 * o], mean2d[2 * o + 1], radius[o], tile, tx, ty, r);
             for (int y = r[1]; y < r[3]; ++y)
-                for (int x = r[0]; x < r[2]; ++x) cnt[v * tiles + (int64_t)y * tx + x + 1]++;
+                for (int x = r[0]; x < r[2]; ++x)
+                    if (in_win(win, x, y)) cnt[v * tiles + (int64_t)y * tx + x + 1]++;
         }
     for (int64_t k = 0; k < nt; ++k) cnt[k + 1] += cnt[k];
     item_t *items = (item_t *)malloc(sizeof(item_t) * (cnt[nt] > 0 ? cnt[nt] : 1));
@@ -750,6 +775,7 @@ static void build_lists(int V, int64_t N, int W, int H, int tile, const double *
             tile_rect(mean2d[2 * o], mean2d[2 * o + 1], radius[o], tile, tx, ty, r);
             for (int y = r[1]; y < r[3]; ++y)
                 for (int x = r[0]; x < r[2]; ++x) {
+                    if (!in_win(win, x, y)) continue;
                     int64_t k = v * tiles + (int64_t)y * tx + x;
                     items[fill[k]].depth = depth[o];
                     items[fill[k]].g = i;
@@ -774,41 +800,76 @@ static void build_lists(int V, int64_t N, int W, int H, int tile, const double *
 ORC_API void orc_raster_fwd(int V, int64_t N, int W, int H, int tile, const double *mean2d,
                             const double *conic, const double *opacity, const double *rgb,
                             const double *depth, const int32_t *radius, const double *bg,
-                            double *img, double *T_final, int32_t *last, int32_t *ambig)
+                            const int32_t *win, double tie, double tie_budget,
+                            const double *depth_eps, const double *pos_eps,
+                            const double *rel_eps, double *img, double *T_final, int32_t *last,
+                            int32_t *ambig)
 {
     int tx = (W + tile - 1) / tile, ty = (H + tile - 1) / tile;
     int64_t tiles = (int64_t)tx * ty;
     int64_t *off;
     item_t *items;
-    build_lists(V, N, W, H, tile, mean2d, radius, depth, &off, &items);
+    build_lists(V, N, W, H, tile, mean2d, radius, depth, win, &off, &items);
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t k = 0; k < V * tiles; ++k) {
         int v = (int)(k / tiles);
         int64_t t = k % tiles;
         int bx = (int)(t % tx), by = (int)(t / tx);
+        if (!in_win(win, bx, by)) continue;
         for (int py = by * tile; py < (by + 1) * tile && py < H; ++py)
             for (int px = bx * tile; px < (bx + 1) * tile && px < W; ++px) {
                 double T = 1.0, C[3] = {0, 0, 0};
-                int lst = 0, amb = 0;
+                double prev_depth = -1.0, prev_T = 0.0, prev_alpha = 0.0, tie_err = 0.0, t_reach = 0.0;
+                int64_t prev_o = -1;
+                const double *prev_c = NULL;
+                int lst = 0, amb = 0, run = 0;
                 for (int64_t j = off[k]; j < off[k + 1]; ++j) {
                     int64_t o = (int64_t)v * N + items[j].g;
                     double dx = px + 0.5 - mean2d[2 * o], dy = py + 0.5 - mean2d[2 * o + 1];
                     const double *cn = conic + 3 * o;
                     double power = -0.5 * (cn[0] * dx * dx + cn[2] * dy * dy) - cn[1] * dx * dy;
-                    if (fabs(power) < M_POWER) amb = 1;
+                    /* reach of power under the input perturbation */
+                    double gx = cn[0] * dx + cn[1] * dy, gy = cn[1] * dx + cn[2] * dy;
+                    double reach = (pos_eps ? sqrt(gx * gx + gy * gy) * pos_eps[o] : 0.0) +
+                                   (rel_eps ? fabs(power) * rel_eps[o] : 0.0);
+                    if (fabs(power) < M_POWER + reach) amb = 1;
                     if (power > 0) continue;
                     double araw = opacity[o] * exp(power);
-                    if (fabs(araw - A_MIN) <= RM_ALPHA * A_MIN) amb = 1;
-                    if (fabs(araw - A_CAP) <= RM_ALPHA * A_CAP) amb = 1;
+                    if (fabs(log(araw / A_MIN)) <= RM_ALPHA + reach) amb = 1;
+                    if (fabs(log(araw / A_CAP)) <= RM_ALPHA + reach) amb = 1;
                     double alpha = araw < A_CAP ? araw : A_CAP;
                     if (alpha < A_MIN) continue;
                     double tt = T * (1.0 - alpha);
-                    if (fabs(tt - T_EPS) <= RM_T * T_EPS) amb = 1;
+                    /* relative reach of T (1 - alpha): every uncapped alpha so far may move */
+                    if (araw < A_CAP) t_reach += alpha * reach / (1.0 - alpha);
+                    if (fabs(log(tt / T_EPS)) <= RM_T + t_reach) amb = 1;
+                    double gap = tie * depth[o] + (depth_eps && prev_o >= 0 ? depth_eps[o] + depth_eps[prev_o] : 0.0);
+                    if (prev_depth > 0 && fabs(depth[o] - prev_depth) <= gap) {
+                        if (tt < T_EPS || run > 0) {
+                            amb = 1;
+                        } else {
+                            double dc = 0.0;
+                            for (int ch = 0; ch < 3; ++ch) {
+                                double d = fabs(prev_c[ch] - rgb[3 * o + ch]);
+                                if (d > dc) dc = d;
+                            }
+                            tie_err += prev_T * prev_alpha * alpha * dc;
+                        }
+                        run = 1;
+                    } else {
+                        run = 0;
+                    }
                     if (tt < T_EPS) break;
                     for (int ch = 0; ch < 3; ++ch) C[ch] += rgb[3 * o + ch] * alpha * T;
+                    prev_T = T;
+                    prev_alpha = alpha;
+                    prev_c = rgb + 3 * o;
+                    prev_depth = depth[o];
+                    prev_o = o;
                     T = tt;
                     lst = (int)(j - off[k]) + 1;
                 }
+                if (tie_err > tie_budget) amb = 1;
                 int64_t p = ((int64_t)v * H + py) * W + px;
                 for (int ch = 0; ch < 3; ++ch)
                     img[(((int64_t)v * 3 + ch) * H + py) * W + px] = C[ch] + T * bg[ch];
@@ -829,19 +890,20 @@ ORC_API void orc_raster_fwd(int V, int64_t N, int W, int H, int tile, const doub
 ORC_API void orc_raster_bwd(int V, int64_t N, int W, int H, int tile, const double *mean2d,
                             const double *conic, const double *opacity, const double *rgb,
                             const double *depth, const int32_t *radius, const double *bg,
-                            const double *T_final, const int32_t *last, const double *d_img,
-                            double *grads, double *d_opacity)
+                            const int32_t *win, const double *T_final, const int32_t *last,
+                            const double *d_img, double *grads, double *d_opacity)
 {
     int tx = (W + tile - 1) / tile, ty = (H + tile - 1) / tile;
     int64_t tiles = (int64_t)tx * ty;
     int64_t *off;
     item_t *items;
-    build_lists(V, N, W, H, tile, mean2d, radius, depth, &off, &items);
+    build_lists(V, N, W, H, tile, mean2d, radius, depth, win, &off, &items);
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t k = 0; k < V * tiles; ++k) {
         int v = (int)(k / tiles);
         int64_t t = k % tiles;
         int bx = (int)(t % tx), by = (int)(t / tx);
+        if (!in_win(win, bx, by)) continue;
         for (int py = by * tile; py < (by + 1) * tile && py < H; ++py)
             for (int px = bx * tile; px < (bx + 1) * tile && px < W; ++px) {
                 int64_t p = ((int64_t)v * H + py) * W + px;

@@ -5,7 +5,9 @@
 // every MMA); thread t holds row t, which is TMEM lane t.  Operands are staged
 // in shared memory in the K-major no-swizzle layout, the accumulator lives in
 // TMEM, thread 0 issues the MMAs and an mbarrier tracks their completion
-// (bounded waits).  Forward: three chained MMAs with ReLU epilogues.
+// (bounded waits).  Forward: two chained MMAs with ReLU epilogues; the 64 -> 7
+// output layer runs in FP32 in the second epilogue (448 FMAs per row), so
+// the translation and rotation carry no BF16 rounding of the last layer.
 // Backward (recomputing the forward from the encoding):
 //   dH2 = (G W3) . relu'(H2),  dH1 = (dH2 W2) . relu'(H1),  d_enc = dH1 W1
 //   dW2 = dH2^T H1, dW1 = dH1^T enc, dW3 = G^T H2
@@ -28,7 +30,7 @@ struct FwdSmem {
     bf16 a2[TM * 64];   // hidden activations, K = 64
     bf16 w1[64 * 32];   // B operands [N][K]: W1 as stored [out][in]
     bf16 w2[64 * 64];
-    bf16 w3[16 * 64];   // rows 7..15 zero (N padded to 16)
+    float w3f[7 * 64];  // output layer, FP32 (applied in the epilogue)
     unsigned long long mbar;
     uint32_t tmem;
 };
@@ -58,6 +60,7 @@ struct TcParams {
     const void *enc;
     int64_t n;
     const bf16 *w;
+    const float *w3f;   // FP32 output-layer weights (forward)
     float *raw7;
     const float *d_raw7, *d_scale;
     float *dW, *d_enc;
@@ -241,7 +244,7 @@ __device__ __forceinline__ void publish_smem()
 }
 
 template <typename ET, bool FUSED>
-__global__ void __launch_bounds__(TM) mlp_tc_fwd_kernel(TcParams p)
+__global__ void __launch_bounds__(TM, 4) mlp_tc_fwd_kernel(TcParams p)
 {
     extern __shared__ unsigned char smem_raw[];
     FwdSmem &S = *aligned_smem<FwdSmem>(smem_raw);
@@ -250,7 +253,9 @@ __global__ void __launch_bounds__(TM) mlp_tc_fwd_kernel(TcParams p)
     const bf16 *w = p.w;
     float *raw7 = p.raw7;
     const int t = threadIdx.x, warp = t >> 5;
-    load_weights_fwd(w, S.w1, S.w2, S.w3);
+    for (int e = t; e < 64 * 32; e += TM) S.w1[kmajor_off(e >> 5, e & 31, 32)] = w[e];
+    for (int e = t; e < 64 * 64; e += TM) S.w2[kmajor_off(e >> 6, e & 63, 64)] = w[2048 + e];
+    for (int e = t; e < 7 * 64; e += TM) S.w3f[e] = p.w3f[e];
     const uint32_t mbar = smem_u32(&S.mbar);
     if (t == 0) mbar_init(mbar, 1);
     if (warp == 0) {
@@ -262,9 +267,9 @@ __global__ void __launch_bounds__(TM) mlp_tc_fwd_kernel(TcParams p)
     fence_after_sync();
     const uint32_t tm = S.tmem;
     const uint32_t lane = (uint32_t)(warp * 32) << 16;
-    const uint32_t id64 = idesc_bf16_f32(128, 64), id16 = idesc_bf16_f32(128, 16);
+    const uint32_t id64 = idesc_bf16_f32(128, 64);
     const uint32_t a1 = smem_u32(S.a1), a2 = smem_u32(S.a2);
-    const uint32_t w1 = smem_u32(S.w1), w2 = smem_u32(S.w2), w3 = smem_u32(S.w3);
+    const uint32_t w1 = smem_u32(S.w1), w2 = smem_u32(S.w2);
     uint32_t phase = 0;
     bool ok = true;
     const int64_t ntiles = (n + TM - 1) / TM;
@@ -311,23 +316,22 @@ __global__ void __launch_bounds__(TM) mlp_tc_fwd_kernel(TcParams p)
             mma_commit(mbar);
         }
         if (!(ok = wait_mma(mbar, phase))) break;
+        // output layer (64 -> 7) in FP32 on the FP32 accumulator, 16 columns
+        // of H2 at a time: the raw translation and rotation carry no BF16
+        // rounding of the last layer
+        float o7[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int c = 0; c < 4; ++c) tmem_ld16(tm + lane + 16 * c, v + 16 * c);
+        for (int c = 0; c < 4; ++c) {
+            tmem_ld16(tm + lane + 16 * c, v);
 #pragma unroll
-        for (int k = 0; k < 64; ++k) v[k] = fmaxf(v[k], 0.f);
+            for (int k = 0; k < 16; ++k) {
+                const float h = fmaxf(v[k], 0.f);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) st_chunk8(S.a2, t, 8 * c, 64, v + 8 * c);
-        publish_smem();
-        if (t == 0) {
-            fence_after_sync();
-#pragma unroll
-            for (int ks = 0; ks < 4; ++ks)
-                mma_bf16(tm, desc_kmajor(a2 + 256 * ks, 128, 1024), desc_kmajor(w3 + 256 * ks, 128, 1024),
-                         id16, ks > 0);
-            mma_commit(mbar);
+                for (int q = 0; q < 7; ++q) o7[q] = fmaf(S.w3f[q * 64 + 16 * c + k], h, o7[q]);
+            }
         }
-        if (!(ok = wait_mma(mbar, phase))) break;
-        tmem_ld16(tm + lane, v);
+#pragma unroll
+        for (int q = 0; q < 7; ++q) v[q] = o7[q];
         if (row < n) {
 #pragma unroll
             for (int q = 0; q < 7; ++q) raw7[row * 7 + q] = v[q];
@@ -605,10 +609,12 @@ gs_status mlp_tc_fwd(const void *enc, int enc_dtype, int64_t n, const gs_mlp *w,
 {
     gs_status st = check_common(enc, enc_dtype, w);
     if (st != GS_OK) return st;
+    GS_REQUIRE(w->w_f32, "BF16 MLP: w_f32 (the FP32 weights) is required for the output layer");
     TcParams p{};
     p.enc = enc;
     p.n = n;
     p.w = reinterpret_cast<const bf16 *>(w->w_bf16);
+    p.w3f = w->w_f32 + 6144;
     p.raw7 = raw7;
     return enc_dtype == GS_BF16 ? launch_fwd<bf16, false>(p, s) : launch_fwd<float, false>(p, s);
 }
@@ -651,9 +657,11 @@ extern "C" gs_status ntc_fused_fwd(const float *mean, const float *quat, int64_t
     TcParams p{};
     int64_t total;
     GS_REQUIRE(grid_params(grid, p.grid, total), "ntc_fused_fwd: invalid hash grid");
+    GS_REQUIRE(w->w_f32, "ntc_fused_fwd: w_f32 (the FP32 weights) is required");
     if (n == 0) return GS_OK;
     p.n = n;
     p.w = reinterpret_cast<const bf16 *>(w->w_bf16);
+    p.w3f = w->w_f32 + 6144;
     p.raw7 = raw7;
     p.mean = mean;
     p.quat = quat;

@@ -179,7 +179,7 @@ class Stage1:
 
     def __init__(self, g: Gaussians, ntc: NTC, V: int, W: int, H: int, capacity: int,
                  order: int = 0, loss_scale: Optional[float] = None, growth_interval=2000,
-                 device="cuda", bin: int = DEFAULT_BIN, fused: bool = True):
+                 device="cuda", bin: int = DEFAULT_BIN, fused: bool = False):
         n = g.n
         # the fused cache kernels exist for the BF16 tensor-core MLP
         self.fused = fused and ntc.precision == gs3.GS_MLP_BF16

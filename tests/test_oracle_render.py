@@ -319,3 +319,102 @@ def test_project_bwd_clamped_jacobian_finite_differences():
             mm[i, k] -= h
             fd = (f(mp) - f(mm)) / (2 * h)
             assert abs(fd - dm[i, k]) <= 1e-5 * max(1.0, abs(fd)), (i, k)
+
+
+def _pair_records(depth_a, depth_b, W=32, H=32):
+    return dict(mean2d=np.array([[[15.2, 16.1], [17.3, 15.4]]]),
+                conic=np.array([[[0.03, 0.004, 0.025], [0.02, -0.003, 0.04]]]),
+                opacity=np.array([[0.8, 0.65]]),
+                rgb=np.array([[[0.9, 0.2, 0.1], [0.1, 0.6, 0.8]]]),
+                depth=np.array([[depth_a, depth_b]]), radius=np.array([[14, 14]], np.int32))
+
+
+def test_tie_swap_bound_is_the_exact_swap_effect():
+    """Two Gaussians at (almost) the same depth: the oracle's per-pixel swap
+    bound must equal the change that swapping them actually makes (brute force,
+    by re-rendering in the other order), so that the pixel is flagged exactly
+    where that change exceeds the budget."""
+    W = H = 32
+    d = 3.0
+    img_ab, Tf_ab, _, _ = oracle.raster_fwd(_pair_records(d, d * (1 + 1e-9)), W, H)
+    img_ba, Tf_ba, _, _ = oracle.raster_fwd(_pair_records(d * (1 + 1e-9), d), W, H)
+    np.testing.assert_allclose(Tf_ab, Tf_ba, atol=1e-15)   # the product of (1 - alpha) is order-free
+    effect = np.abs(img_ab - img_ba).max(axis=1)[0]
+    assert effect.max() > 0.05
+    for budget in (1e-3, 1e-2, 5e-2):
+        _, _, _, amb = oracle.raster_fwd(_pair_records(d, d * (1 + 1e-9)), W, H, tie=1e-8,
+                                         tie_budget=budget)
+        clear = np.abs(effect - budget) > 1e-9
+        assert np.array_equal(amb[0][clear] == 1, effect[clear] > budget)
+    # without a tie margin nothing is flagged here
+    _, _, _, amb = oracle.raster_fwd(_pair_records(d, d * (1 + 1e-9)), W, H)
+    assert not amb.any()
+
+
+def test_tie_run_of_three_always_flags():
+    W = H = 32
+    rec = _pair_records(3.0, 3.0 * (1 + 1e-9), W, H)
+    rec = {k: np.concatenate([v, v[:, :1]], axis=1) for k, v in rec.items()}
+    rec["depth"][0, 2] = 3.0 * (1 + 2e-9)
+    rec["rgb"][0, 2] = rec["rgb"][0, 0]
+    _, _, _, amb = oracle.raster_fwd(rec, W, H, tie=1e-8, tie_budget=1.0)
+    yy, xx = np.mgrid[0:H, 0:W] + 0.5
+    added = np.ones((H, W), bool)
+    for i in range(3):
+        dx, dy = xx[None] - rec["mean2d"][0, i, 0], yy[None] - rec["mean2d"][0, i, 1]
+        A, B, C = rec["conic"][0, i]
+        a = rec["opacity"][0, i] * np.exp(-0.5 * (A * dx * dx + C * dy * dy) - B * dx * dy)[0]
+        added &= a >= 1 / 255 + 1e-9
+    assert added.sum() > 100
+    assert np.all(amb[0][added] == 1)
+
+
+def _added_sets(rec, W, H):
+    """Brute force over all pixels at once: which Gaussians the compositing
+    adds (Eq. 4 with the 1/255, 0.99 and 1e-4 rules), as a [N, H, W] mask.
+    Every rectangle covers the image, so tile lists hold every Gaussian."""
+    yy, xx = np.mgrid[0:H, 0:W] + 0.5
+    T = np.ones((H, W))
+    alive = np.ones((H, W), bool)
+    N = rec["depth"].shape[1]
+    added = np.zeros((N, H, W), bool)
+    for i in np.argsort(rec["depth"][0], kind="stable"):
+        dx, dy = xx - rec["mean2d"][0, i, 0], yy - rec["mean2d"][0, i, 1]
+        A, B, C = rec["conic"][0, i]
+        power = -0.5 * (A * dx * dx + C * dy * dy) - B * dx * dy
+        a = np.minimum(0.99, rec["opacity"][0, i] * np.exp(power))
+        take = alive & (power <= 0) & (a >= 1 / 255)
+        tt = T * (1 - a)
+        stop = take & (tt < 1e-4)
+        alive &= ~stop
+        take &= ~stop
+        added[i] = take
+        T = np.where(take, tt, T)
+    return added
+
+
+@pytest.mark.parametrize("pos_eps,rel_eps", [(0.02, 0.0), (0.0, 5e-3), (0.05, 1e-2)])
+def test_perturbation_reach_covers_flipped_decisions(pos_eps, rel_eps):
+    """Every pixel whose set of added Gaussians changes when the 2D means move
+    by up to pos_eps pixels or the conics by up to rel_eps (relative) must be
+    flagged when the oracle is given those reaches (brute force over random
+    shifts and scalings of the inputs)."""
+    W, H = 48, 40
+    rec = _records(1, 40, W, H, 31, radius_range=(4, 14))
+    rec = {k: (v.astype(np.float64) if v.dtype == np.float32 else v) for k, v in rec.items()}
+    rec["depth"][0] = np.arange(1, 41) * 0.1   # distinct depths: no ties
+    rec["radius"][0] = 200                      # rectangles cover the image
+    _, _, _, amb = oracle.raster_fwd(rec, W, H, pos_eps=pos_eps, rel_eps=rel_eps)
+    base = _added_sets(rec, W, H)
+    changed = np.zeros((H, W), bool)
+    rng = np.random.default_rng(32)
+    for trial in range(24):
+        r = {k: v.copy() for k, v in rec.items()}
+        ang = rng.uniform(0, 2 * np.pi, size=40)
+        r["mean2d"][0] += pos_eps * np.stack([np.cos(ang), np.sin(ang)], 1)
+        r["conic"][0] *= 1 + rel_eps * rng.choice([-1.0, 1.0], size=(40, 1))
+        changed |= np.any(_added_sets(r, W, H) != base, axis=0)
+    assert changed.sum() >= 5
+    assert np.all(amb[0][changed] == 1)
+    # the reach is not vacuous: most pixels stay unflagged
+    assert amb.mean() < 0.5
