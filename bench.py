@@ -38,7 +38,7 @@ CFG_INDEX = 3
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--steps", type=int, default=ITERS_PER_FRAME)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mlp", default="bf16", choices=["bf16", "fp32"])
@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--warm-iters", type=int, default=1000, help="NTC warm-up iterations (Eq. 7)")
     ap.add_argument("--eager", action="store_true", help="launch kernels one by one (no CUDA graph)")
     ap.add_argument("--no-converge", action="store_true", help="skip the equal-PSNR comparison")
+    ap.add_argument("--no-render", action="store_true", help="skip the render-only measurement")
+    ap.add_argument("--bin", type=int, default=0,
+                    help="bin side in tiles (0: autotune over 1, 2, 4, 8, 16)")
     ap.add_argument("--profile", action="store_true",
                     help="setup + timed steps only (for ncu launch lists)")
     return ap.parse_args()
@@ -77,7 +80,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -207,7 +210,8 @@ def run_ours(args):
     from paper_2403_01444_gb300 import build as _b
     _b.build()
     from paper_2403_01444_gb300 import gs3, scenes
-    from paper_2403_01444_gb300.engine import NTC, DirectOpt, Rasterizer, Stage1, warmup
+    from paper_2403_01444_gb300.engine import (NTC, DirectOpt, Rasterizer, Renderer, Stage1,
+                                               autotune_bin, warmup)
     import oracle  # only for the grid size of the initial table (host integer layout)
 
     if args.small:
@@ -242,7 +246,19 @@ def run_ours(args):
     torch.cuda.synchronize()
     t_warm = time.perf_counter() - t0
     warm_table, warm_mlp = ntc.table.p.clone(), ntc.mlp.p.clone()
-    st = Stage1(G, ntc, Vb, W, H, capacity=1 << 20)
+    # bin size: autotuned on the first batch's fwd + bwd of compositing
+    tune = None
+    if args.bin > 0:
+        bin_side = args.bin
+    else:
+        tmp = Stage1(G, ntc, Vb, W, H, capacity=1 << 20)
+        mt, qt = tmp.transform()
+        tune_ms, bin_side = autotune_bin(G, batch_cams[0], Vb, W, H, mt.clone(), qt.clone())
+        tune = {"bin_tiles": {str(k): round(v, 4) for k, v in tune_ms.items()}, "best": bin_side,
+                "timed": "project + bin/sort + raster fwd + raster bwd + project bwd, one 4-view batch"}
+        del tmp, mt, qt
+        torch.cuda.empty_cache()
+    st = Stage1(G, ntc, Vb, W, H, capacity=1 << 20, bin=bin_side)
     counts = []
     for b in range(nb):
         counts.append(st.raster.fit_capacity(G, batch_cams[b], *st.transform(), margin=1.0))
@@ -368,10 +384,52 @@ def run_ours(args):
     sm_mhz = clk.summary().get("sm_mhz") or 2070.0
     roof = roofline_for(dom, stages[dom], pairs, pair_counts, G.n, Vb, W, H, cfg, hbm, src, sm_mhz)
 
+    # the rasterizer fwd+bwd against HBM: algorithmic bytes of projection,
+    # binning/sort, compositing fwd/bwd and projection bwd, counted per
+    # Gaussian, per (view, Gaussian, 16x16 tile) intersection and per pixel
+    inter = int(st.raster.proj.tiles_touched.sum().item())
+    K = (cfg.sh_deg + 1) ** 2
+    per_g = (44 + 12 * K) * 2 + 28 + Vb * (44 + 32)   # params read twice (a4, a9), records, grads
+    raster_bytes = G.n * per_g + inter * 124 + Vb * W * H * (20 + 32)
+    raster_roof = {"bound": "hbm", "achieved": raster_bytes / (raster_ms * 1e-3) / 1e9, "peak": hbm,
+                   "unit": "GB/s", "frac": raster_bytes / (raster_ms * 1e-3) / 1e9 / hbm,
+                   "algorithmic_bytes": raster_bytes, "intersections": inter,
+                   "bytes_per": {"gaussian": per_g, "intersection": 124, "pixel": 52},
+                   "ms": raster_ms, "peak_source": src}
+
+    # render-only: NTC query + transformation + projection + binning +
+    # compositing of one 1352x1014 view, one CUDA graph per frame
+    render_only = None
+    if not args.no_render:
+        ro_ms, ro_bin = autotune_bin(G, gs3.camera_slice(cams_dev, 0, 1),
+                                     1, W, H, st.mean_t.clone(), st.quat_t.clone(), backward=False)
+        rr = Renderer(G, ntc, 1, W, H, 1 << 20, bin=ro_bin)
+        rr.raster.fit_capacity(G, gs3.camera_slice(cams_dev, 0, 1), *st.transform(), margin=1.3)
+        views = [gs3.camera_slice(cams_dev, v, 1) for v in range(cfg.n_cams)]
+        rgraphs = [rr.capture(v) for v in views] if not args.eager else None
+        kr = 100
+        for i in range(5):
+            rgraphs[i % len(views)].replay() if rgraphs else rr.frame(views[i % len(views)])
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for i in range(kr):
+            rgraphs[i % len(views)].replay() if rgraphs else rr.frame(views[i % len(views)])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rr.raster.check()
+        rms = e0.elapsed_time(e1) / kr
+        render_only = {"ms_per_frame": rms, "fps": 1e3 / rms, "width": W, "height": H, "views": 1,
+                       "gaussians": G.n, "bin_tiles": ro_bin,
+                       "autotune_ms": {str(k): round(v, 4) for k, v in ro_ms.items()},
+                       "includes": "NTC query (encode, BF16 MLP), transformation, projection, "
+                                   "binning/sort, compositing; CUDA graph per frame"}
+        del rr, rgraphs
+        torch.cuda.empty_cache()
+
     # plain FP32 direct optimisation on the same inputs and rasterizer
     plain = None
     if not args.no_plain:
-        do = DirectOpt(G, Vb, W, H, st.raster.capacity, device=dev)
+        do = DirectOpt(G, Vb, W, H, st.raster.capacity, device=dev, bin=bin_side)
         for i in range(3):
             do.step(batch_cams[i % nb], targets[(i % nb) * Vb:(i % nb + 1) * Vb])
         dgraphs = do.capture(batches) if not args.eager else None
@@ -451,7 +509,12 @@ def run_ours(args):
                 "stages_ms": {k: round(v, 4) for k, v in stages.items()},
                 "bin_pairs_per_step": pairs, "composited_pairs": pair_counts,
                 "warmup_loss": wl, "warmup_s": t_warm,
-                "roofline": roof, "cpu_baseline": cpu,
+                "roofline": roof, "raster_fwd_bwd_roofline": raster_roof,
+                "render_only": render_only, "bin_autotune": tune, "bin_tiles": bin_side,
+                "paper_context": {"s_per_frame": 12.0, "fps_render": 200,
+                                  "hardware": "one RTX 3090", "workload": "N3DV, real video",
+                                  "note": "context only: other hardware, data and precision"},
+                "cpu_baseline": cpu,
                 "e2e": {"value": e2e_ms * ITERS_PER_FRAME / 1e3, "unit": "s/frame",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4},
                 "gpu_launches": int(launches), "clocks": clocks}

@@ -340,6 +340,77 @@ def warmup(ntc: NTC, g: Gaussians, iters=3000, noise=0.01, extent=2.0, seed=0, s
     return float(d_loss.item())
 
 
+class Renderer:
+    """Render-only path (Section 5.4's rendering of a streamed frame): NTC
+    query of the frozen means, transformation, projection, binning and
+    compositing of V views into a device buffer, with no backward.  capture()
+    records one frame as a CUDA graph, the headless analogue of the viewer's
+    per-frame work."""
+
+    def __init__(self, g: Gaussians, ntc: NTC, V: int, W: int, H: int, capacity: int,
+                 order: int = 0, device="cuda", bin: int = DEFAULT_BIN):
+        n = g.n
+        self.g, self.ntc, self.V, self.W, self.H, self.order = g, ntc, V, W, H, order
+        self.raster = Rasterizer(n, V, W, H, capacity, device, bin=bin)
+        self.enc = torch.zeros(n, 32, dtype=ntc.enc_dtype(), device=device)
+        self.raw7 = _f32(n, 7, device=device)
+        self.mean_t = _f32(n, 3, device=device)
+        self.quat_t = _f32(n, 4, device=device)
+        self.aabb = list(ntc.grid.aabb)
+
+    def frame(self, cams_dev, stream=None):
+        g, ntc, n = self.g, self.ntc, self.g.n
+        gs3.ntc_encode_fwd(g.mean, n, ntc.grid, ntc.table_for_encode(), self.enc, stream)
+        gs3.ntc_mlp_fwd(self.enc, n, ntc.mlp_struct(), self.raw7, stream)
+        gs3.ntc_apply(g.mean, g.quat, self.raw7, n, self.aabb, self.order, self.mean_t, self.quat_t,
+                      stream)
+        return self.raster.forward(g, cams_dev, self.mean_t, self.quat_t, stream)
+
+    def capture(self, cams_dev):
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self.frame(cams_dev)
+        torch.cuda.current_stream().wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            self.frame(cams_dev)
+        torch.cuda.synchronize()
+        return graph
+
+
+def autotune_bin(g: Gaussians, cams_dev, V: int, W: int, H: int, mean=None, quat=None,
+                 candidates=(1, 2, 4, 8, 16), backward=True, iters=5, device="cuda"):
+    """Time projection + binning + compositing (and, with backward=True, the
+    reverse of compositing and projection under a constant image gradient) at
+    each bin size (bins of S x S 16-pixel tiles); returns ({S: ms}, best S).
+    Every bin size composites the same records in the same order, so the
+    choice changes the time only."""
+    times = {}
+    stream = torch.cuda.current_stream()
+    for S in candidates:
+        r = Rasterizer(g.n, V, W, H, 1 << 20, device, bin=S)
+        r.fit_capacity(g, cams_dev, mean, quat, margin=1.2)
+        d_img = torch.full_like(r.img, 1e-3)
+
+        def once():
+            r.forward(g, cams_dev, mean, quat)
+            if backward:
+                r.backward(g, cams_dev, d_img, mean, quat)
+
+        once()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(iters):
+            once()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        r.check()
+        times[S] = e0.elapsed_time(e1) / iters
+        del r, d_img
+    return times, min(times, key=times.get)
+
+
 def render(g: Gaussians, cams, W: int, H: int, mean=None, quat=None, capacity=None,
            device="cuda", bin: int = DEFAULT_BIN) -> torch.Tensor:
     """Render all cams (one launch) with the CUDA rasterizer; returns [V,3,H,W]."""
