@@ -134,13 +134,12 @@ __device__ __forceinline__ int compact_slot(bool keep, int *s_wcnt, int &count)
     return keep ? off + __popc(b & ((1u << lane) - 1u)) : -1;
 }
 
-template <bool BINNED>
+template <bool BINNED, bool STATS>
 __global__ void __launch_bounds__(FT) raster_fwd_kernel(RasterParams p)
 {
     __shared__ float2 s_xy[FT];
     __shared__ float4 s_co[FT];
-    __shared__ float s_rgb[FT][3];
-    __shared__ int s_pos[FT];
+    __shared__ float4 s_rgbk[FT];  // colour and (bit pattern of) the list position
     __shared__ int s_wcnt[FT / 32];
     const int tile = blockIdx.x, view = blockIdx.y;
     const int tid = threadIdx.x;
@@ -173,16 +172,14 @@ __global__ void __launch_bounds__(FT) raster_fwd_kernel(RasterParams p)
         if (slot >= 0) {
             s_xy[slot] = m;
             s_co[slot] = co;
-            s_rgb[slot][0] = p.rgb[3 * o];
-            s_rgb[slot][1] = p.rgb[3 * o + 1];
-            s_rgb[slot][2] = p.rgb[3 * o + 2];
-            s_pos[slot] = k;
+            s_rgbk[slot] = make_float4(p.rgb[3 * o], p.rgb[3 * o + 1], p.rgb[3 * o + 2],
+                                       __int_as_float(k));
         }
         __syncthreads();
         for (int j = 0; !done && j < cnt; ++j) {
             float dx, dy;
             float4 co = s_co[j];
-            ++n_tested;
+            if (STATS) ++n_tested;
             float power = pair_power(s_xy[j], co, pxf, pyf, dx, dy);
             if (power > 0.f) continue;
             float alpha = fminf(kAlphaCap, pair_alpha_raw(co, power));
@@ -193,15 +190,16 @@ __global__ void __launch_bounds__(FT) raster_fwd_kernel(RasterParams p)
                 break;
             }
             float w = alpha * T;
-            C0 = fmaf(s_rgb[j][0], w, C0);
-            C1 = fmaf(s_rgb[j][1], w, C1);
-            C2 = fmaf(s_rgb[j][2], w, C2);
+            const float4 ck = s_rgbk[j];
+            C0 = fmaf(ck.x, w, C0);
+            C1 = fmaf(ck.y, w, C1);
+            C2 = fmaf(ck.z, w, C2);
             T = test_T;
-            last = s_pos[j] + 1;
-            ++n_contrib;
+            last = __float_as_int(ck.w) + 1;
+            if (STATS) ++n_contrib;
         }
     }
-    flush_stats(p.stats, n_tested, n_contrib);
+    if (STATS) flush_stats(p.stats, n_tested, n_contrib);
     if (inside) {
         int64_t HW = (int64_t)p.H * p.W;
         int64_t pix = (int64_t)py * p.W + px;
@@ -248,7 +246,7 @@ struct PixBwd {
 };
 
 template <bool WANT_OP>
-__device__ __forceinline__ bool unblend_one(PixBwd &P, float2 xy, float4 co, const float *c,
+__device__ __forceinline__ bool unblend_one(PixBwd &P, float2 xy, float4 co, float4 c,
                                             float pxf, float pyf, float *v)
 {
     float dx, dy;
@@ -263,10 +261,10 @@ __device__ __forceinline__ bool unblend_one(PixBwd &P, float2 xy, float4 co, con
     v[5] = fmaf(P.dC0, w, v[5]);
     v[6] = fmaf(P.dC1, w, v[6]);
     v[7] = fmaf(P.dC2, w, v[7]);
-    float dalpha = P.T * (P.dC0 * (c[0] - P.B0) + P.dC1 * (c[1] - P.B1) + P.dC2 * (c[2] - P.B2));
-    P.B0 = fmaf(alpha, c[0] - P.B0, P.B0);
-    P.B1 = fmaf(alpha, c[1] - P.B1, P.B1);
-    P.B2 = fmaf(alpha, c[2] - P.B2, P.B2);
+    float dalpha = P.T * (P.dC0 * (c.x - P.B0) + P.dC1 * (c.y - P.B1) + P.dC2 * (c.z - P.B2));
+    P.B0 = fmaf(alpha, c.x - P.B0, P.B0);
+    P.B1 = fmaf(alpha, c.y - P.B1, P.B1);
+    P.B2 = fmaf(alpha, c.z - P.B2, P.B2);
     if (araw < kAlphaCap) {
         float dpow = dalpha * alpha;
         v[0] = fmaf(dpow, co.x * dx + co.y * dy, v[0]);
@@ -279,7 +277,7 @@ __device__ __forceinline__ bool unblend_one(PixBwd &P, float2 xy, float4 co, con
     return true;
 }
 
-template <bool WANT_OP, bool BINNED, int PPT>
+template <bool WANT_OP, bool BINNED, int PPT, bool STATS>
 __global__ void __launch_bounds__(256 / PPT) raster_bwd_kernel(RasterParams p)
 {
     constexpr int NT = 256 / PPT;        // threads per tile
@@ -288,9 +286,8 @@ __global__ void __launch_bounds__(256 / PPT) raster_bwd_kernel(RasterParams p)
     constexpr int NV = WANT_OP ? 9 : 8;
     __shared__ float2 s_xy[NT];
     __shared__ float4 s_co[NT];
-    __shared__ float s_rgb[NT][3];
+    __shared__ float4 s_rgbk[NT];  // colour and (bit pattern of) the list position
     __shared__ uint32_t s_g[NT];
-    __shared__ int s_pos[NT];
     __shared__ int s_wcnt[NW];
     __shared__ float s_part[NW][BWD_CHUNK][NV];
     __shared__ int s_max;
@@ -349,10 +346,8 @@ __global__ void __launch_bounds__(256 / PPT) raster_bwd_kernel(RasterParams p)
             s_g[slot] = g;
             s_xy[slot] = m;
             s_co[slot] = co;
-            s_rgb[slot][0] = p.rgb[3 * o];
-            s_rgb[slot][1] = p.rgb[3 * o + 1];
-            s_rgb[slot][2] = p.rgb[3 * o + 2];
-            s_pos[slot] = k;
+            s_rgbk[slot] = make_float4(p.rgb[3 * o], p.rgb[3 * o + 1], p.rgb[3 * o + 2],
+                                       __int_as_float(k));
         }
         __syncthreads();
         for (int chi = cnt; chi > 0; chi -= BWD_CHUNK) {
@@ -361,18 +356,18 @@ __global__ void __launch_bounds__(256 / PPT) raster_bwd_kernel(RasterParams p)
                 float v[NV];
 #pragma unroll
                 for (int q = 0; q < NV; ++q) v[q] = 0.f;
-                const int pos = s_pos[j];
+                const float4 c = s_rgbk[j];
+                const int pos = __float_as_int(c.w);
                 bool contrib = false;
                 if (pos < mylast) {
                     float2 xy = s_xy[j];
                     float4 cc = s_co[j];
-                    const float *c = s_rgb[j];
 #pragma unroll
                     for (int q = 0; q < PPT; ++q) {
                         if (pos < P[q].last) {
-                            ++n_tested;
+                            if (STATS) ++n_tested;
                             bool h = unblend_one<WANT_OP>(P[q], xy, cc, c, pxf, pyf[q], v);
-                            n_contrib += h;
+                            if (STATS) n_contrib += h;
                             contrib |= h;
                         }
                     }
@@ -416,7 +411,7 @@ __global__ void __launch_bounds__(256 / PPT) raster_bwd_kernel(RasterParams p)
             __syncthreads();
         }
     }
-    flush_stats(p.stats, n_tested, n_contrib);
+    if (STATS) flush_stats(p.stats, n_tested, n_contrib);
 }
 
 static gs_status fill(const gs_projected *proj, int64_t n, int V, int W, int H, int bin,
@@ -451,6 +446,17 @@ static gs_status fill(const gs_projected *proj, int64_t n, int V, int W, int H, 
     return GS_OK;
 }
 
+template <bool WANT_OP, bool BINNED>
+static void launch_bwd(const RasterParams &p, dim3 grid, cudaStream_t s)
+{
+    constexpr int PPT = BWD_PIXELS_PER_THREAD;
+    constexpr int NT = 256 / PPT;
+    if (p.stats)
+        raster_bwd_kernel<WANT_OP, BINNED, PPT, true><<<grid, NT, 0, s>>>(p);
+    else
+        raster_bwd_kernel<WANT_OP, BINNED, PPT, false><<<grid, NT, 0, s>>>(p);
+}
+
 }  // namespace gs3
 
 using namespace gs3;
@@ -470,10 +476,15 @@ extern "C" gs_status gs_raster_fwd(const gs_projected *proj, int64_t n, int V, i
     p.stats = reinterpret_cast<unsigned long long *>(d_stats);
     dim3 grid(p.tx * p.ty, V);
     note_launch();
-    if (bin > 1)
-        raster_fwd_kernel<true><<<grid, FT, 0, as_stream(stream)>>>(p);
+    cudaStream_t s = as_stream(stream);
+    if (bin > 1 && p.stats)
+        raster_fwd_kernel<true, true><<<grid, FT, 0, s>>>(p);
+    else if (bin > 1)
+        raster_fwd_kernel<true, false><<<grid, FT, 0, s>>>(p);
+    else if (p.stats)
+        raster_fwd_kernel<false, true><<<grid, FT, 0, s>>>(p);
     else
-        raster_fwd_kernel<false><<<grid, FT, 0, as_stream(stream)>>>(p);
+        raster_fwd_kernel<false, false><<<grid, FT, 0, s>>>(p);
     return launch_status("gs_raster_fwd");
 }
 
@@ -499,15 +510,13 @@ extern "C" gs_status gs_raster_bwd(const gs_projected *proj, int64_t n, int V, i
     p.stats = reinterpret_cast<unsigned long long *>(d_stats);
     dim3 grid(p.tx * p.ty, V);
     note_launch();
-    constexpr int PPT = BWD_PIXELS_PER_THREAD;
-    constexpr int NT = 256 / PPT;
     if (d_opacity && bin > 1)
-        raster_bwd_kernel<true, true, PPT><<<grid, NT, 0, s>>>(p);
+        launch_bwd<true, true>(p, grid, s);
     else if (d_opacity)
-        raster_bwd_kernel<true, false, PPT><<<grid, NT, 0, s>>>(p);
+        launch_bwd<true, false>(p, grid, s);
     else if (bin > 1)
-        raster_bwd_kernel<false, true, PPT><<<grid, NT, 0, s>>>(p);
+        launch_bwd<false, true>(p, grid, s);
     else
-        raster_bwd_kernel<false, false, PPT><<<grid, NT, 0, s>>>(p);
+        launch_bwd<false, false>(p, grid, s);
     return launch_status("gs_raster_bwd");
 }
