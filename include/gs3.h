@@ -172,6 +172,21 @@ GS_API gs_status gs_project(const gs_gaussians *g, const gs_camera *d_cams, int 
 GS_API gs_status gs_project_bwd(const gs_gaussians *g, const gs_camera *d_cams, int V, int W, int H,
                          const float *grads, float *d_mean, float *d_quat, gs_stream stream);
 
+/* Reverse of gs_project wrt every parameter, for the Gaussians
+ * [first, first + count) of g (Stage 2 of Section 4.2 trains every attribute
+ * of the added Gaussians while the transformed ones stay fixed).  grads is
+ * gs_raster_bwd's [V][g->n][8] array and d_opacity its [V][g->n] opacity
+ * gradient (NULL = 0).  Overwrites, for j < count, d_mean[j][3],
+ * d_quat[j][4] (wrt the un-normalised quaternion), d_scale[j][3] (wrt the
+ * scales s, not log s), d_opacity_logit[j] (opacity = sigmoid(logit)) and
+ * d_sh[j][K][3], summed over the V views.  GS_ERR_INVALID_ARG if the range
+ * leaves [0, g->n). */
+GS_API gs_status gs_project_bwd_full(const gs_gaussians *g, const gs_camera *d_cams, int V, int W,
+                                     int H, const float *grads, const float *d_opacity,
+                                     int64_t first, int64_t count, float *d_mean, float *d_quat,
+                                     float *d_scale, float *d_opacity_logit, float *d_sh,
+                                     gs_stream stream);
+
 /* --------------------------------------------------------- binning + sort */
 
 /* Scratch bytes gs_bin_sort needs for n Gaussians, V views of W x H and room
@@ -345,6 +360,81 @@ GS_API gs_status adam_step(float *p, float *g, float *m, float *v, int64_t n, co
  * flag; else count the step and double the scale after growth_interval clean
  * steps (growth_interval <= 0 keeps the scale fixed). */
 GS_API gs_status gs_train_state_advance(gs_train_state *d_state, int growth_interval, gs_stream stream);
+
+/* ----------------------------------------- Stage 2: adaptive 3DG addition */
+
+/* The added, frame-specific Gaussians of Stage 2 (Section 4.2) as rows of
+ * their trainable parameters, row = [mean 3 | quat 4 | log scale 3 |
+ * opacity logit 1 | SH K x 3] (GS_ADDED_COLS(K) floats, K = (sh_deg + 1)^2),
+ * with their Adam moments in the same layout.  All device arrays of
+ * capacity rows, owned by the caller. */
+#define GS_ADDED_COLS(K) (11 + 3 * (K))
+typedef struct {
+    float *rows;
+    float *m, *v;
+    int64_t capacity;
+    int32_t sh_deg;
+} gs_added;
+
+/* View-space positional gradient statistics (Section 4.2, after 3DG-S): for
+ * j < count and each view v where record (v, first + j) is visible
+ * (radius > 0), accum[j] += grad_scale * |(dL/du * W / 2, dL/dv * H / 2)|
+ * (the gradient wrt the normalised device coordinates of the 2D mean) and
+ * denom[j] += 1.  grads [V][n][8] and radius [V][n] as written by
+ * gs_raster_bwd / gs_project for n Gaussians. */
+GS_API gs_status gs_viewspace_grad_accum(const float *grads, const int32_t *radius, int V, int64_t n,
+                                         int64_t first, int64_t count, int W, int H,
+                                         float grad_scale, float *accum, int32_t *denom,
+                                         gs_stream stream);
+
+/* idx[0 .. *d_nsel) = the j < count, in increasing order, with denom[j] > 0
+ * and accum[j] / denom[j] > tau (FP32).  One block; no workspace. */
+GS_API gs_status gs_select_above(const float *accum, const int32_t *denom, int64_t count, float tau,
+                                 int32_t *idx, int64_t *d_nsel, gs_stream stream);
+
+/* Spawn (Section 4.2): for k < *d_nsel, source Gaussian i = idx[k] of src
+ * gives the added row *d_nadd + k: mean = mu_i + sqrt(2) R_i diag(s_i) z[k]
+ * (a draw from N(mu_i, 2 Sigma_i); z [*d_nsel][3] standard normal draws
+ * supplied by the caller), rotation (1, 0, 0, 0), log scale = log s_i,
+ * opacity logit = log(opacity_init / (1 - opacity_init)), SH copied.  Rows
+ * beyond dst->capacity are dropped and *d_err set to GS_ERR_CAPACITY;
+ * *d_nadd becomes min(capacity, *d_nadd + *d_nsel).  Moments of new rows
+ * are zeroed. */
+GS_API gs_status gs_added_spawn(const gs_gaussians *src, const int32_t *idx, const int64_t *d_nsel,
+                                const float *z, float opacity_init, gs_added *dst,
+                                int64_t *d_nadd, int32_t *d_err, gs_stream stream);
+
+/* Quantity control at the end of a Stage-2 epoch (Section 4.2): of the n_src
+ * rows of src, those with sigmoid(opacity logit) >= tau_opacity are kept, in
+ * order (with their moments); then every kept row j with denom[j] > 0 and
+ * accum[j] / denom[j] > tau_grad adds, in order, a row with mean =
+ * mu_j + R_j diag(s_j) z[j] (a draw from N(mu_j, Sigma_j); z [n_src][3]),
+ * log scale + log(split_scale), rotation, opacity and SH of row j, moments
+ * zero.  Writes dst (a different buffer) and *d_ndst; rows beyond
+ * dst->capacity are dropped with *d_err = GS_ERR_CAPACITY.  One block. */
+GS_API gs_status gs_added_densify_prune(const gs_added *src, int64_t n_src, const float *accum,
+                                        const int32_t *denom, float tau_grad, float tau_opacity,
+                                        float split_scale, const float *z, gs_added *dst,
+                                        int64_t *d_ndst, int32_t *d_err, gs_stream stream);
+
+/* Bias-corrected Adam on the n rows of a: gradients from
+ * gs_project_bwd_full's arrays (d_scale wrt s is turned into the gradient wrt
+ * log s), per-group learning rates lr[6] = {mean, rotation, log scale,
+ * opacity logit, SH band 0, SH bands >= 1}, step d_state->step + 1 (loss
+ * scale 1; skipped when d_state->found_inf is set); then writes the rendered
+ * attributes of each row into out's arrays (mean, quat, scale =
+ * exp(log scale), opacity_logit, sh; written through out's pointers) at
+ * Gaussian index out_first + row. */
+GS_API gs_status gs_added_adam(gs_added *a, int64_t n, const float *d_mean, const float *d_quat,
+                               const float *d_scale, const float *d_opacity_logit,
+                               const float *d_sh, const float *lr, float beta1, float beta2,
+                               float eps, const gs_train_state *d_state, const gs_gaussians *out,
+                               int64_t out_first, gs_stream stream);
+
+/* Writes the rendered attributes of rows [0, n) of a into out at Gaussian
+ * index out_first + row (as the tail of gs_added_adam). */
+GS_API gs_status gs_added_to_render(const gs_added *a, int64_t n, const gs_gaussians *out,
+                                    int64_t out_first, gs_stream stream);
 
 #ifdef __cplusplus
 }

@@ -214,6 +214,27 @@ def project_bwd(g, cams, grads, tile=TILE, mean=None, quat=None):
     return dm, dq
 
 
+def project_bwd_full(g, cams, grads, d_opacity=None, tile=TILE):
+    """Reverse of the projection wrt every parameter of g: returns a dict of
+    d_mean [N,3], d_quat [N,4], d_scale [N,3] (wrt s), d_ologit [N] and
+    d_sh [N,K,3], from grads [V,N,8] and d_opacity [V,N]."""
+    mean, quat, scale = _d(g.mean), _d(g.quat), _d(g.scale)
+    op, sh = _d(g.opacity_logit), _d(g.sh)
+    grads = _d(grads)
+    N, V = mean.shape[0], len(cams)
+    K = (g.sh_deg + 1) ** 2
+    ca = cam_array(cams)
+    out = dict(d_mean=np.zeros((N, 3)), d_quat=np.zeros((N, 4)), d_scale=np.zeros((N, 3)),
+               d_ologit=np.zeros(N), d_sh=np.zeros((N, K, 3)))
+    dop = None if d_opacity is None else _d(d_opacity)
+    lib().orc_project_bwd_full(I64(N), I32(V), _p(mean), _p(quat), _p(scale), _p(op), _p(sh),
+                               I32(g.sh_deg), _p(ca), I32(tile), _p(grads),
+                               _p(dop) if dop is not None else None, _p(out["d_mean"]),
+                               _p(out["d_quat"]), _p(out["d_scale"]), _p(out["d_ologit"]),
+                               _p(out["d_sh"]))
+    return out
+
+
 # ---------------------------------------------------------------- binning
 def bin_sort(mean2d, radius, depth, W, H, tile=TILE, capacity=None):
     """Integer binning of FP32 projected records -> (count, keys, vals, ranges)."""

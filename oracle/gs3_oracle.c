@@ -530,7 +530,8 @@ ORC_API void orc_project(int64_t N, int V, const double *mean, const double *qua
 /* Reverse of the projection for one (Gaussian, view); g = (du, dv, dA, dB, dC,
  * dr, dg, db).  Adds into dmu[3] and dq[4] (gradient wrt the raw quaternion). */
 static void project_one_bwd(const pstate *P, const double *s, const double *sh, int deg,
-                            const double *cam, const double *g, double *dmu, double *dq)
+                            const double *cam, const double *g, double *dmu, double *dq,
+                            double *ds, double *dsh)
 {
     const double *Wm = cam;
     double fx = cam[12], fy = cam[13];
@@ -547,6 +548,10 @@ static void project_one_bwd(const pstate *P, const double *s, const double *sh, 
     }
     double dd = P->dir[0] * ddir[0] + P->dir[1] * ddir[1] + P->dir[2] * ddir[2];
     for (int a = 0; a < 3; ++a) dmu[a] += (ddir[a] - P->dir[a] * dd) / P->dlen;
+    /* SH coefficients: d rgb_raw / d sh_k = Y_k (per channel) */
+    if (dsh)
+        for (int k = 0; k < K; ++k)
+            for (int ch = 0; ch < 3; ++ch) dsh[3 * k + ch] += Y[k] * drr[ch];
 
     /* 2D mean: u = fx tx/tz + cx, v = fy ty/tz + cy */
     double tz = P->t[2];
@@ -608,6 +613,8 @@ static void project_one_bwd(const pstate *P, const double *s, const double *sh, 
             double acc = 0;
             for (int k = 0; k < 3; ++k) acc += dSig[3 * i + k] * P->M[3 * k + j];
             dR[3 * i + j] = 2.0 * acc * s[j];
+            /* M = R diag(s): dL/ds_j = sum_i dM_ij R_ij */
+            if (ds) ds[j] += 2.0 * acc * P->R[3 * i + j];
         }
     double w = P->qn[0], x = P->qn[1], y = P->qn[2], z = P->qn[3];
     double dqn[4];
@@ -634,7 +641,7 @@ ORC_API void orc_project_bwd(int64_t N, int V, const double *mean, const double 
                         sh_deg, cams + 21 * v, tile, &P);
             if (!P.valid) continue;
             project_one_bwd(&P, scale + 3 * i, sh + 3 * K * i, sh_deg, cams + 21 * v,
-                            grads + 8 * ((int64_t)v * N + i), dmu, dq);
+                            grads + 8 * ((int64_t)v * N + i), dmu, dq, NULL, NULL);
         }
         for (int k = 0; k < 3; ++k) d_mean[3 * i + k] = dmu[k];
         for (int k = 0; k < 4; ++k) d_quat[4 * i + k] = dq[k];
@@ -649,6 +656,40 @@ ORC_API void orc_project_bwd(int64_t N, int V, const double *mean, const double 
  * [first, last+1) of tile-key k (zeros when empty).  Returns the pair count;
  * writes at most `capacity` pairs.
  * ====================================================================== */
+/* Reverse of the projection wrt every Gaussian parameter (Stage 2 trains all
+ * attributes of the added Gaussians, Section 4.2): from grads[V][N][8] and
+ * d_opacity[V][N] (dL/d opacity of each record, NULL = 0), writes d_mean[N][3],
+ * d_quat[N][4], d_scale[N][3] (wrt s), d_ologit[N] (opacity = sigmoid(ologit))
+ * and d_sh[N][K][3], summed over the views. */
+ORC_API void orc_project_bwd_full(int64_t N, int V, const double *mean, const double *quat,
+                                  const double *scale, const double *opac_logit, const double *sh,
+                                  int sh_deg, const double *cams, int tile, const double *grads,
+                                  const double *d_opacity, double *d_mean, double *d_quat,
+                                  double *d_scale, double *d_ologit, double *d_sh)
+{
+    int K = (sh_deg + 1) * (sh_deg + 1);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; ++i) {
+        double dmu[3] = {0, 0, 0}, dq[4] = {0, 0, 0, 0}, ds[3] = {0, 0, 0}, dop = 0.0;
+        double *dsh = d_sh + 3 * K * i;
+        for (int k = 0; k < 3 * K; ++k) dsh[k] = 0.0;
+        double o = 1.0 / (1.0 + exp(-opac_logit[i]));
+        for (int v = 0; v < V; ++v) {
+            pstate P;
+            project_one(mean + 3 * i, quat + 4 * i, scale + 3 * i, opac_logit[i], sh + 3 * K * i,
+                        sh_deg, cams + 21 * v, tile, &P);
+            if (!P.valid) continue;
+            project_one_bwd(&P, scale + 3 * i, sh + 3 * K * i, sh_deg, cams + 21 * v,
+                            grads + 8 * ((int64_t)v * N + i), dmu, dq, ds, dsh);
+            if (d_opacity) dop += d_opacity[(int64_t)v * N + i];
+        }
+        for (int k = 0; k < 3; ++k) d_mean[3 * i + k] = dmu[k];
+        for (int k = 0; k < 4; ++k) d_quat[4 * i + k] = dq[k];
+        for (int k = 0; k < 3; ++k) d_scale[3 * i + k] = ds[k];
+        d_ologit[i] = dop * o * (1.0 - o);
+    }
+}
+
 typedef struct { uint64_t key; uint32_t val; } kv_t;
 static int cmp_kv(const void *pa, const void *pb)
 {

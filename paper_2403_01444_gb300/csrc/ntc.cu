@@ -343,9 +343,10 @@ __global__ void __launch_bounds__(256) adam_kernel(float *p, float *g, float *m,
                                                    void *shadow)
 {
     const bool skip = st->found_inf != 0;
+    // bias corrections 1 - b^t as -expm1(t log b): no cancellation when b is close to 1
     const int t = st->step + 1;
-    const float bc1 = 1.f - powf(hp.beta1, (float)t);
-    const float bc2 = 1.f - powf(hp.beta2, (float)t);
+    const float bc1 = -expm1f((float)t * logf(hp.beta1));
+    const float bc2 = -expm1f((float)t * logf(hp.beta2));
     const float inv = 1.f / st->loss_scale;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {

@@ -21,6 +21,10 @@ struct ProjectParams {
     // backward
     const float *grads;
     float *d_mean, *d_quat;
+    // full backward (every parameter of Gaussians [first, first + count))
+    const float *d_opacity;
+    int64_t first, count;
+    float *d_scale, *d_ologit, *d_sh;
 };
 
 // Real SH basis to degree 3 (Condon-Shortley signs, as the 3DG-S renderer),
@@ -286,18 +290,27 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ProjectParams p)
     }
 }
 
+// FULL = false: gradients wrt mean and rotation of every Gaussian (Stage 1).
+// FULL = true: gradients wrt every parameter of Gaussians [first, first + count)
+// (Stage 2), written at row j = i - first.
+template <bool FULL>
 __global__ void __launch_bounds__(128) project_bwd_kernel(ProjectParams p)
 {
     extern __shared__ gs_camera s_cams[];
     for (int k = threadIdx.x; k < p.V; k += blockDim.x) s_cams[k] = p.cams[k];
     __syncthreads();
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= p.n) return;
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= (FULL ? p.count : p.n)) return;
+    const int64_t i = FULL ? p.first + j : j;
     GaussLocal G;
     load_gauss(p, i, G);
     const float *sh = p.sh + (int64_t)3 * p.K * i;
+    float *dsh = FULL ? p.d_sh + (int64_t)3 * p.K * j : nullptr;
+    if (FULL)
+        for (int k = 0; k < 3 * p.K; ++k) dsh[k] = 0.f;
     float dmu[3] = {0.f, 0.f, 0.f};
     float dS[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma, symmetric (00 01 02 11 12 22)
+    float dop = 0.f;
     for (int v = 0; v < p.V; ++v) {
         const gs_camera &c = s_cams[v];
         ViewLocal L;
@@ -307,6 +320,16 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(ProjectParams p)
         float4 g0 = gp[0], g1 = gp[1];
         float du = g0.x, dv = g0.y, dA = g0.z, dB = g0.w, dC = g1.x;
         float drgb[3] = {g1.y, g1.z, g1.w};
+        if (FULL) {
+            // SH coefficients: d rgb_raw / d sh_k = Y_k where the colour is not clamped
+            float Y[16];
+            sh_basis(p.deg, L.dir.x, L.dir.y, L.dir.z, Y);
+            for (int k = 0; k < p.K; ++k)
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch)
+                    if (L.rgb_raw[ch] > 0.f) dsh[3 * k + ch] = fmaf(Y[k], drgb[ch], dsh[3 * k + ch]);
+            if (p.d_opacity) dop += p.d_opacity[(int64_t)v * p.n + i];
+        }
         // colour -> direction -> mean
         float wk[16];
         for (int k = 0; k < p.K; ++k) {
@@ -391,13 +414,16 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(ProjectParams p)
     for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int c = 0; c < 3; ++c) M[3 * r + c] = G.R[3 * r + c] * G.s[c];
-    float dR[9];
+    float dR[9], ds[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-            dR[3 * r + c] = 2.f * G.s[c] *
-                            (dSf[3 * r] * M[c] + dSf[3 * r + 1] * M[3 + c] + dSf[3 * r + 2] * M[6 + c]);
+        for (int c = 0; c < 3; ++c) {
+            // dM = 2 dSigma M; M = R diag(s): dR = dM diag(s), ds_c = sum_r dM_rc R_rc
+            const float dM = 2.f * (dSf[3 * r] * M[c] + dSf[3 * r + 1] * M[3 + c] + dSf[3 * r + 2] * M[6 + c]);
+            dR[3 * r + c] = dM * G.s[c];
+            ds[c] = fmaf(dM, G.R[3 * r + c], ds[c]);
+        }
     float w = G.qn[0], x = G.qn[1], y = G.qn[2], z = G.qn[3];
     float dqn[4];
     dqn[0] = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
@@ -409,12 +435,18 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(ProjectParams p)
                     y * dR[5] + x * dR[6] + y * dR[7]);
     float dot = w * dqn[0] + x * dqn[1] + y * dqn[2] + z * dqn[3];
     float iq = 1.f / G.qlen;
-    p.d_mean[3 * i] = dmu[0];
-    p.d_mean[3 * i + 1] = dmu[1];
-    p.d_mean[3 * i + 2] = dmu[2];
-    reinterpret_cast<float4 *>(p.d_quat)[i] =
+    p.d_mean[3 * j] = dmu[0];
+    p.d_mean[3 * j + 1] = dmu[1];
+    p.d_mean[3 * j + 2] = dmu[2];
+    reinterpret_cast<float4 *>(p.d_quat)[j] =
         make_float4((dqn[0] - w * dot) * iq, (dqn[1] - x * dot) * iq, (dqn[2] - y * dot) * iq,
                     (dqn[3] - z * dot) * iq);
+    if (FULL) {
+        p.d_scale[3 * j] = ds[0];
+        p.d_scale[3 * j + 1] = ds[1];
+        p.d_scale[3 * j + 2] = ds[2];
+        p.d_ologit[j] = dop * G.op * (1.f - G.op);  // opacity = sigmoid(logit)
+    }
 }
 
 static gs_status fill_params(const gs_gaussians *g, const gs_camera *d_cams, int V, int W, int H,
@@ -488,6 +520,37 @@ extern "C" gs_status gs_project_bwd(const gs_gaussians *g, const gs_camera *d_ca
     int threads = 128;
     int blocks = (int)ceil_div(p.n, threads);
     note_launch();
-    project_bwd_kernel<<<blocks, threads, sizeof(gs_camera) * V, as_stream(stream)>>>(p);
+    project_bwd_kernel<false><<<blocks, threads, sizeof(gs_camera) * V, as_stream(stream)>>>(p);
     return launch_status("gs_project_bwd");
+}
+
+extern "C" gs_status gs_project_bwd_full(const gs_gaussians *g, const gs_camera *d_cams, int V,
+                                         int W, int H, const float *grads, const float *d_opacity,
+                                         int64_t first, int64_t count, float *d_mean,
+                                         float *d_quat, float *d_scale, float *d_opacity_logit,
+                                         float *d_sh, gs_stream stream)
+{
+    ProjectParams p{};
+    gs_status st = fill_params(g, d_cams, V, W, H, p);
+    if (st != GS_OK) return st;
+    GS_REQUIRE(grads && d_mean && d_quat && d_scale && d_opacity_logit && d_sh,
+               "gs_project_bwd_full: null argument");
+    GS_REQUIRE(first >= 0 && count >= 0 && first + count <= g->n,
+               "gs_project_bwd_full: range [first, first + count) outside the Gaussians");
+    GS_REQUIRE(aligned(grads, 16) && aligned(d_quat, 16), "gs_project_bwd_full: misaligned arrays");
+    if (count == 0) return GS_OK;
+    p.grads = grads;
+    p.d_opacity = d_opacity;
+    p.first = first;
+    p.count = count;
+    p.d_mean = d_mean;
+    p.d_quat = d_quat;
+    p.d_scale = d_scale;
+    p.d_ologit = d_opacity_logit;
+    p.d_sh = d_sh;
+    int threads = 128;
+    int blocks = (int)ceil_div(count, threads);
+    note_launch();
+    project_bwd_kernel<true><<<blocks, threads, sizeof(gs_camera) * V, as_stream(stream)>>>(p);
+    return launch_status("gs_project_bwd_full");
 }

@@ -34,28 +34,46 @@ class Rasterizer:
     """Projection + binning + compositing (+ reverse) for V views of W x H."""
 
     def __init__(self, n: int, V: int, W: int, H: int, capacity: int, device="cuda",
-                 bg=(0.0, 0.0, 0.0), bin: int = DEFAULT_BIN):
-        self.n, self.V, self.W, self.H = n, V, W, H
+                 bg=(0.0, 0.0, 0.0), bin: int = DEFAULT_BIN, n_max: Optional[int] = None):
+        self.V, self.W, self.H = V, W, H
         self.device = device
         self.bg = tuple(float(x) for x in bg)
         self.bin = int(bin)
         self.bins = gs3.bins_of(W, H, self.bin)
-        self.proj = Projected.empty(V, n, device)
+        self.n_max = max(n, n_max or n)
+        nm = self.n_max
+        # flat storage for up to n_max Gaussians; the [V][n] views follow n
+        self._proj = Projected.empty(V, nm, device)
+        self._grads = _f32(V * nm * 8, device=device)
+        self._d_mean = _f32(nm * 3, device=device)
+        self._d_quat = _f32(nm * 4, device=device)
         self.ranges = _i32(V * self.bins, 2, device=device)
         self.d_count = torch.zeros(1, dtype=torch.int64, device=device)
         self.d_err = _i32(1, device=device)
         self.img = _f32(V, 3, H, W, device=device)
         self.T_final = _f32(V, H, W, device=device)
         self.last = _i32(V, H, W, device=device)
-        self.grads = _f32(V, n, 8, device=device)
-        self.d_mean = _f32(n, 3, device=device)
-        self.d_quat = _f32(n, 4, device=device)
+        self.set_n(n)
         self.set_capacity(capacity)
+
+    def set_n(self, n: int):
+        """Number of Gaussians of the next calls (<= n_max); the per-record
+        arrays are [V][n] views of the same storage."""
+        assert 0 <= n <= self.n_max
+        self.n = n
+        V = self.V
+        sub = lambda t, *tail: t.view(-1)[:V * n * int(np.prod(tail or (1,)))].view(V, n, *tail)
+        P = self._proj
+        self.proj = Projected(sub(P.mean2d, 2), sub(P.conic_opacity, 4), sub(P.rgb, 3),
+                              sub(P.depth), sub(P.radius), sub(P.tiles_touched))
+        self.grads = self._grads[:V * n * 8].view(V, n, 8)
+        self.d_mean = self._d_mean[:n * 3].view(n, 3)
+        self.d_quat = self._d_quat[:n * 4].view(n, 4)
 
     def set_capacity(self, capacity: int):
         self.capacity = int(capacity)
         self.vals = _i32(max(self.capacity, 1), device=self.device)
-        ws = gs3.gs_bin_sort_workspace_size(self.n, self.V, self.W, self.H, self.capacity)
+        ws = gs3.gs_bin_sort_workspace_size(self.n_max, self.V, self.W, self.H, self.capacity)
         self.ws = torch.empty(ws, dtype=torch.uint8, device=self.device)
 
     def forward(self, g: Gaussians, cams_dev, mean=None, quat=None, stream=None, keys=None):
@@ -197,6 +215,19 @@ class Stage1:
         self.growth = growth_interval if ntc.precision == gs3.GS_MLP_BF16 else 0
         self.state = gs3.new_train_state(loss_scale, device)
         self.aabb = list(ntc.grid.aabb)
+        self.track = None  # (accum [n], denom [n]) while tracking view-space gradients
+
+    def track_viewspace(self, on: bool = True):
+        """Start (zeroed) or stop accumulating the view-space positional
+        gradient statistics of the Gaussians (Section 4.2: during the final
+        epoch of Stage 1).  Graphs captured while tracking include it."""
+        if on:
+            n = self.g.n
+            dev = self.g.mean.device
+            self.track = (torch.zeros(n, device=dev), torch.zeros(n, dtype=torch.int32, device=dev))
+        else:
+            self.track = None
+        return self.track
 
     def reset_state(self, loss_scale=None):
         ls = gs3.read_train_state(self.state).loss_scale if loss_scale is None else loss_scale
@@ -224,6 +255,11 @@ class Stage1:
         self.loss(img, target, stream)
         d_mean, d_quat = self.raster.backward(g, cams_dev, self.loss.d_img, self.mean_t, self.quat_t,
                                               stream)
+        if self.track is not None:
+            # view-space positional gradients of the final epoch feed Stage 2's spawn
+            accum, denom = self.track
+            gs3.gs_viewspace_grad_accum(self.raster.grads, self.raster.proj.radius, self.V, n, 0, n,
+                                        self.W, self.H, float(self.V), accum, denom, stream)
         if self.fused:
             gs3.ntc_fused_bwd(g.mean, g.quat, self.raw7, self.enc, n, ntc.grid, ntc.mlp_struct(), self.order,
                               d_mean, d_quat, self.loss_scale_view(), ntc.mlp.g, ntc.table.g, stream)
@@ -257,6 +293,163 @@ class Stage1:
         per batch (side stream), which also advances the training state: reset
         the cache and the state before timing or training."""
         return capture_graphs(self.step, batches)
+
+
+STAGE2_LR = (0.0024, 0.015, 0.075, 0.75, 0.0375, 0.0375 / 20)  # Suppl. A; SH bands >= 1 at 1/20
+STAGE2_BETAS = (0.9, 0.999)   # 3DG-S's Adam for Gaussian attributes
+STAGE2_EPS = 1e-15
+TAU_GRAD = 0.00015            # Section 4.2
+TAU_ALPHA = 0.01
+SPAWN_OPACITY = 0.1
+SPLIT_SCALE = 0.8
+
+
+class Stage2:
+    """Stage 2, adaptive 3DG addition (Section 4.2): Gaussians added around
+    the transformed Gaussians with large view-space positional gradients are
+    trained (every attribute, Adam) while the transformed ones stay fixed;
+    at the end of each epoch (one pass over the view batches) the added ones
+    above the gradient threshold spawn one more nearby and those below the
+    opacity threshold are discarded.
+
+    The rasterizer draws one set: the n fixed Gaussians first, then the
+    added ones, from buffers of n + capacity rows."""
+
+    def __init__(self, g: Gaussians, V: int, W: int, H: int, capacity: int,
+                 pair_capacity: int = 1 << 22, device="cuda", bin: int = DEFAULT_BIN,
+                 lr=STAGE2_LR, tau_grad=TAU_GRAD, tau_alpha=TAU_ALPHA, seed: int = 0):
+        self.g, self.V, self.W, self.H = g, V, W, H
+        self.n_fixed, self.cap = g.n, int(capacity)
+        self.deg = g.sh_deg
+        K = (self.deg + 1) ** 2
+        P = gs3.added_cols(self.deg)
+        nm = self.n_fixed + self.cap
+        f = lambda *sh: _f32(*sh, device=device)
+        self.all = Gaussians(f(nm, 3), f(nm, 4), f(nm, 3), f(nm), f(nm, K, 3), self.deg)
+        self.rows = [f(self.cap, P) for _ in range(2)]
+        self.m = [f(self.cap, P) for _ in range(2)]
+        self.v = [f(self.cap, P) for _ in range(2)]
+        self.cur = 0
+        self.n_add = 0
+        self.d_n = torch.zeros(1, dtype=torch.int64, device=device)
+        self.d_nsel = torch.zeros(1, dtype=torch.int64, device=device)
+        self.d_err = _i32(1, device=device)
+        self.idx = _i32(max(self.n_fixed, self.cap), device=device)
+        self.d_mean, self.d_quat, self.d_scale = f(self.cap, 3), f(self.cap, 4), f(self.cap, 3)
+        self.d_ologit, self.d_sh = f(self.cap), f(self.cap, K, 3)
+        self.accum = f(self.cap)
+        self.denom = _i32(self.cap, device=device)
+        self.raster = Rasterizer(self.n_fixed, V, W, H, pair_capacity, device, bin=bin, n_max=nm)
+        self._d_op = f(V * nm)
+        self.loss = Loss(V, W, H, device)
+        self.lr = tuple(lr)
+        self.tau_grad, self.tau_alpha = tau_grad, tau_alpha
+        self.state = gs3.new_train_state(1.0, device)
+        self.gen = torch.Generator(device=device)
+        self.gen.manual_seed(seed)
+
+    def added(self, k=None) -> gs3.GsAdded:
+        k = self.cur if k is None else k
+        return gs3.added_struct(self.rows[k], self.m[k], self.v[k], self.deg)
+
+    def view(self) -> Gaussians:
+        """The drawn set: fixed Gaussians followed by the current added ones."""
+        n = self.n_fixed + self.n_add
+        a = self.all
+        return Gaussians(a.mean[:n], a.quat[:n], a.scale[:n], a.opacity_logit[:n], a.sh[:n], self.deg)
+
+    def begin(self, mean_t, quat_t, accum, denom, random_count: Optional[int] = None):
+        """Fixed set = the previous frame's Gaussians at the transformed means
+        and rotations; one added Gaussian around each with an average
+        view-space gradient above tau_grad (accum / denom from the final epoch
+        of Stage 1).  random_count = k instead spawns around k fixed
+        Gaussians drawn uniformly (the random-spawn ablation of Section 5.3).
+        Reads the number added back to the host."""
+        n, g, a = self.n_fixed, self.g, self.all
+        a.mean[:n].copy_(mean_t)
+        a.quat[:n].copy_(quat_t)
+        a.scale[:n].copy_(g.scale)
+        a.opacity_logit[:n].copy_(g.opacity_logit)
+        a.sh[:n].copy_(g.sh)
+        fixed = Gaussians(a.mean[:n], a.quat[:n], a.scale[:n], a.opacity_logit[:n], a.sh[:n], self.deg)
+        if random_count is None:
+            gs3.gs_select_above(accum, denom, n, self.tau_grad, self.idx, self.d_nsel)
+        else:
+            pick = torch.randperm(n, generator=self.gen, device=mean_t.device)[:random_count]
+            self.idx[:pick.numel()].copy_(pick.sort().values.to(torch.int32))
+            self.d_nsel.fill_(pick.numel())
+        z = torch.randn(n, 3, generator=self.gen, device=mean_t.device)
+        self.cur = 0
+        self.d_n.zero_()
+        self.d_err.zero_()
+        gs3.gs_added_spawn(fixed, self.idx, self.d_nsel, z, SPAWN_OPACITY, self.added(), self.d_n,
+                           self.d_err)
+        self.n_add = int(self.d_n.item())
+        self._after_resize()
+        self.state.copy_(gs3.new_train_state(1.0, self.state.device))
+        return self.n_add
+
+    def _after_resize(self):
+        self.accum.zero_()
+        self.denom.zero_()
+        self.raster.set_n(self.n_fixed + self.n_add)
+        gs3.gs_added_to_render(self.added(), self.n_add, self.view(), self.n_fixed)
+
+    def compute_grads(self, cams_dev, target, stream=None):
+        """Forward and backward of one iteration: gradients of the added rows
+        in d_mean .. d_sh, view-space statistics accumulated."""
+        g = self.view()
+        r, n, V, W, H = self.raster, g.n, self.V, self.W, self.H
+        r.forward(g, cams_dev, stream=stream)
+        self.loss(r.img, target, stream)
+        d_op = self._d_op[:V * n]
+        gs3.gs_raster_bwd(r.proj, n, V, W, H, r.bin, r.bg, r.vals, r.ranges, r.T_final, r.last,
+                          self.loss.d_img, r.grads, d_op, None, stream)
+        gs3.gs_project_bwd_full(g, cams_dev, V, W, H, r.grads, d_op, self.n_fixed, self.n_add,
+                                self.d_mean, self.d_quat, self.d_scale, self.d_ologit, self.d_sh,
+                                stream)
+        gs3.gs_viewspace_grad_accum(r.grads, r.proj.radius, V, n, self.n_fixed, self.n_add, W, H,
+                                    float(V), self.accum, self.denom, stream)
+        return self.loss.d_loss
+
+    def step(self, cams_dev, target, stream=None):
+        d_loss = self.compute_grads(cams_dev, target, stream)
+        gs3.gs_added_adam(self.added(), self.n_add, self.d_mean, self.d_quat, self.d_scale,
+                          self.d_ologit, self.d_sh, self.lr, STAGE2_BETAS[0], STAGE2_BETAS[1],
+                          STAGE2_EPS, self.state, self.view(), self.n_fixed, stream)
+        gs3.gs_train_state_advance(self.state, 0, stream)
+        return d_loss
+
+    def epoch_end(self):
+        """Split the added Gaussians above tau_grad (one more each, 80 % scale)
+        and discard those below tau_alpha; reads the new count back."""
+        z = torch.randn(max(self.n_add, 1), 3, generator=self.gen, device=self.accum.device)
+        gs3.gs_added_densify_prune(self.added(), self.n_add, self.accum, self.denom, self.tau_grad,
+                                   self.tau_alpha, SPLIT_SCALE, z, self.added(1 - self.cur), self.d_n,
+                                   self.d_err)
+        self.cur = 1 - self.cur
+        self.n_add = int(self.d_n.item())
+        self._after_resize()
+        return self.n_add
+
+    def fit_capacity(self, cams_dev, margin=1.5):
+        self.raster.fit_capacity(self.view(), cams_dev, margin=margin)
+
+    def run(self, batches, iters: int = 100):
+        """iters iterations over the view batches in turn, quantity control at
+        the end of every epoch (len(batches) iterations)."""
+        nb = len(batches)
+        for it in range(iters):
+            cd, tg = batches[it % nb]
+            if it % nb == 0:
+                self.fit_capacity(cd, margin=1.5)
+            self.step(cd, tg)
+            if (it + 1) % nb == 0 and it + 1 < iters:
+                self.epoch_end()
+        self.raster.check()
+        if int(self.d_err.item()) != 0:
+            raise gs3.GsError("Stage2", int(self.d_err.item()), "added-Gaussian capacity exceeded")
+        return self.n_add
 
 
 class DirectOpt:

@@ -69,6 +69,16 @@ class GsAdam(ctypes.Structure):
     _fields_ = [("lr", c_float), ("beta1", c_float), ("beta2", c_float), ("eps", c_float)]
 
 
+class GsAdded(ctypes.Structure):
+    _fields_ = [("rows", c_void_p), ("m", c_void_p), ("v", c_void_p), ("capacity", c_int64),
+                ("sh_deg", c_int32)]
+
+
+def added_cols(sh_deg: int) -> int:
+    """Floats per row of an added Gaussian: mean 3, quat 4, log scale 3, opacity logit 1, SH."""
+    return 11 + 3 * (sh_deg + 1) ** 2
+
+
 class GsTrainState(ctypes.Structure):
     _fields_ = [("loss_scale", c_float), ("found_inf", c_int32), ("step", c_int32),
                 ("clean_steps", c_int32)]
@@ -206,6 +216,15 @@ def gs_project_bwd(g: Gaussians, cams_dev, V, W, H, grads, d_mean, d_quat, mean=
     _check("gs_project_bwd", lib().gs_project_bwd(ctypes.byref(gg), _ptr(cams_dev), c_int(V), c_int(W),
                                                   c_int(H), _ptr(grads), _ptr(d_mean), _ptr(d_quat),
                                                   _stream(stream)))
+
+
+def gs_project_bwd_full(g: Gaussians, cams_dev, V, W, H, grads, d_opacity, first, count, d_mean,
+                        d_quat, d_scale, d_opacity_logit, d_sh, stream=None):
+    gg = g.struct()
+    _check("gs_project_bwd_full", lib().gs_project_bwd_full(
+        ctypes.byref(gg), _ptr(cams_dev), c_int(V), c_int(W), c_int(H), _ptr(grads), _ptr(d_opacity),
+        c_int64(first), c_int64(count), _ptr(d_mean), _ptr(d_quat), _ptr(d_scale),
+        _ptr(d_opacity_logit), _ptr(d_sh), _stream(stream)))
 
 
 def gs_bin_sort_workspace_size(n, V, W, H, capacity) -> int:
@@ -354,3 +373,56 @@ def new_train_state(loss_scale=2.0 ** 15, device="cuda") -> torch.Tensor:
 def read_train_state(d_state: torch.Tensor) -> GsTrainState:
     b = bytes(d_state.cpu().numpy().tobytes())
     return GsTrainState.from_buffer_copy(b)
+
+
+# ------------------------------------------------------------------ Stage 2
+def added_struct(rows, m, v, sh_deg) -> GsAdded:
+    s = GsAdded(_ptr(rows), _ptr(m), _ptr(v), int(rows.shape[0]), int(sh_deg))
+    s._keep = (rows, m, v)
+    return s
+
+
+def gs_viewspace_grad_accum(grads, radius, V, n, first, count, W, H, grad_scale, accum, denom,
+                            stream=None):
+    _check("gs_viewspace_grad_accum", lib().gs_viewspace_grad_accum(
+        _ptr(grads), _ptr(radius), c_int(V), c_int64(n), c_int64(first), c_int64(count), c_int(W),
+        c_int(H), c_float(grad_scale), _ptr(accum), _ptr(denom), _stream(stream)))
+
+
+def gs_select_above(accum, denom, count, tau, idx, d_nsel, stream=None):
+    _check("gs_select_above", lib().gs_select_above(
+        _ptr(accum), _ptr(denom), c_int64(count), c_float(tau), _ptr(idx), _ptr(d_nsel),
+        _stream(stream)))
+
+
+def gs_added_spawn(src: Gaussians, idx, d_nsel, z, opacity_init, dst: GsAdded, d_nadd, d_err,
+                   stream=None):
+    gg = src.struct()
+    _check("gs_added_spawn", lib().gs_added_spawn(
+        ctypes.byref(gg), _ptr(idx), _ptr(d_nsel), _ptr(z), c_float(opacity_init), ctypes.byref(dst),
+        _ptr(d_nadd), _ptr(d_err), _stream(stream)))
+
+
+def gs_added_densify_prune(src: GsAdded, n_src, accum, denom, tau_grad, tau_opacity, split_scale, z,
+                           dst: GsAdded, d_ndst, d_err, stream=None):
+    _check("gs_added_densify_prune", lib().gs_added_densify_prune(
+        ctypes.byref(src), c_int64(n_src), _ptr(accum), _ptr(denom), c_float(tau_grad),
+        c_float(tau_opacity), c_float(split_scale), _ptr(z), ctypes.byref(dst), _ptr(d_ndst),
+        _ptr(d_err), _stream(stream)))
+
+
+def gs_added_adam(a: GsAdded, n, d_mean, d_quat, d_scale, d_opacity_logit, d_sh, lr, beta1, beta2,
+                  eps, d_state, out: Gaussians, out_first, stream=None):
+    lr6 = (c_float * 6)(*[float(x) for x in lr])
+    gg = out.struct()
+    _check("gs_added_adam", lib().gs_added_adam(
+        ctypes.byref(a), c_int64(n), _ptr(d_mean), _ptr(d_quat), _ptr(d_scale), _ptr(d_opacity_logit),
+        _ptr(d_sh), lr6, c_float(beta1), c_float(beta2), c_float(eps), _ptr(d_state), ctypes.byref(gg),
+        c_int64(out_first), _stream(stream)))
+
+
+def gs_added_to_render(a: GsAdded, n, out: Gaussians, out_first, stream=None):
+    gg = out.struct()
+    _check("gs_added_to_render", lib().gs_added_to_render(
+        ctypes.byref(a), c_int64(n), ctypes.byref(gg), c_int64(out_first), _stream(stream)))
+

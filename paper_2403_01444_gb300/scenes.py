@@ -34,7 +34,7 @@ __all__ = [
     "GaussianSet", "Camera", "SceneConfig", "CONFIGS", "make_gaussians",
     "look_at_camera", "ring_cameras", "arc_cameras", "rigid_motion",
     "rbf_motion", "random_projected", "random_hashgrid_table", "random_mlp",
-    "make_scene",
+    "make_scene", "emerging_content", "union",
 ]
 
 
@@ -95,6 +95,42 @@ def make_gaussians(n: int, sh_deg: int, rng: np.random.Generator,
     f = np.float32
     return GaussianSet(mean.astype(f), q.astype(f), np.exp(log_s).astype(f),
                        op.astype(f), sh.astype(f), sh_deg)
+
+
+def emerging_content(rng: np.random.Generator, n_new: int, sh_deg: int, radius: float = 0.2,
+                     centre_extent: float = 0.5) -> GaussianSet:
+    """Gaussians of an object absent from the previous frame (the emerging
+    content of Section 4.2): centres uniform in a ball of `radius` around a
+    centre at x, y uniform in [-centre_extent, centre_extent] and z = 1 +
+    radius, just in front of the scene's +z face (the side the arc and ring
+    cameras at azimuth 0 look at, so the object is not hidden inside the
+    cloud), smaller and more
+    opaque than the scene's (log-scales N(-3.5, 0.3), opacity logits
+    N(2, 0.5)) and of one saturated hue (SH DC terms 3 (hue - 1/3) +
+    N(0, 0.1^2), hue a Dirichlet(0.3) draw; higher bands zero)."""
+    centre = np.array([rng.uniform(-centre_extent, centre_extent),
+                       rng.uniform(-centre_extent, centre_extent), 1.0 + radius])
+    d = rng.normal(size=(n_new, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    r = radius * rng.uniform(size=(n_new, 1)) ** (1.0 / 3.0)
+    mean = centre + d * r
+    log_s = rng.normal(-3.5, 0.3, size=(n_new, 3))
+    q = rng.normal(size=(n_new, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    op = rng.normal(2.0, 0.5, size=n_new)
+    hue = rng.dirichlet(np.ones(3) * 0.3)
+    k = (sh_deg + 1) ** 2
+    sh = np.zeros((n_new, k, 3))
+    sh[:, 0, :] = 3.0 * (hue - 1.0 / 3.0) + rng.normal(0.0, 0.1, size=(n_new, 3))
+    f = np.float32
+    return GaussianSet(mean.astype(f), q.astype(f), np.exp(log_s).astype(f), op.astype(f),
+                       sh.astype(f), sh_deg)
+
+
+def union(a: GaussianSet, b: GaussianSet) -> GaussianSet:
+    c = lambda x, y: np.concatenate([x, y]).astype(np.float32)
+    return GaussianSet(c(a.mean, b.mean), c(a.quat, b.quat), c(a.scale, b.scale),
+                       c(a.opacity_logit, b.opacity_logit), c(a.sh, b.sh), a.sh_deg)
 
 
 def look_at_camera(pos, W: int, H: int, fov_x_deg: float = 60.0,
@@ -229,6 +265,7 @@ class SceneConfig:
     iters: int
     motion: str            # "rigid", "rbf", "rigid+rbf"
     cam_layout: str        # "ring4", "ring8", "arc20", "arc12", "ring16"
+    emerging: bool = False  # the target holds an object absent from the previous frame
 
 
 CONFIGS = {
@@ -237,7 +274,7 @@ CONFIGS = {
     3: SceneConfig("ntc-250k-20v-1352x1014", 250_000, 3, 20, 1352, 1014, 4, 150,
                    "rigid+rbf", "arc20"),
     4: SceneConfig("stage2-500k-12v-1280x720", 500_000, 3, 12, 1280, 720, 4, 100,
-                   "rigid+rbf", "arc12"),
+                   "rigid+rbf", "arc12", emerging=True),
     5: SceneConfig("large-1m-16v-1920x1080", 1_000_000, 3, 16, 1920, 1080, 16, 150,
                    "rbf", "ring16"),
 }
@@ -292,6 +329,11 @@ def make_scene(cfg_index: int, n_gauss: Optional[int] = None, W: Optional[int] =
         tgt = rbf_motion(prev, rng, 8, 0.1)
     else:
         tgt = rbf_motion(rigid_motion(prev, rng, 1.0, 0.01), rng, 8, 0.02)
+    if cfg.emerging:
+        # an object absent from the previous frame appears (Section 4.2):
+        # 5 000 to 10 000 new Gaussians in a ball of radius 0.2, scaled with n
+        n_new = int(rng.integers(5000, 10001) * cfg.n_gauss / CONFIGS[cfg_index].n_gauss)
+        tgt = union(tgt, emerging_content(rng, max(n_new, 1), cfg.sh_deg))
     cams = cameras_for(cfg)
     if n_cams is not None:
         cams = cams[:n_cams]

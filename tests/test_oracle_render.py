@@ -293,6 +293,44 @@ def test_project_bwd_finite_differences():
             assert abs(fd - dq[i, k]) <= 1e-5 * max(1.0, abs(fd)), (i, k)
 
 
+def test_project_bwd_full_finite_differences():
+    """Every parameter (mean, rotation, scale, opacity logit, SH) against
+    central finite differences of the FP64 projection, with a gradient on the
+    opacity of every record as well."""
+    rng = np.random.default_rng(19)
+    cams = scenes.ring_cameras([0, 100], [5, -10], 200, 150)
+    g0 = scenes.make_gaussians(20, 2, rng)
+    g0.sh[:, 1:, :] *= 10
+    g = scenes.GaussianSet(g0.mean.astype(np.float64), g0.quat.astype(np.float64) * 1.3,
+                           g0.scale.astype(np.float64), g0.opacity_logit.astype(np.float64),
+                           g0.sh.astype(np.float64), g0.sh_deg)
+    pr = oracle.project(g, cams)
+    vis = (pr["radius"] > 0)
+    G = rng.normal(size=(2, 20, 8)) * vis[..., None]
+    D = rng.normal(size=(2, 20)) * vis
+
+    def f(gg):
+        p = oracle.project(gg, cams)
+        out = np.concatenate([p["mean2d"], p["conic"], p["rgb"]], -1)
+        return np.sum(out * G) + np.sum(p["opacity"] * D)
+
+    d = oracle.project_bwd_full(g, cams, G, D)
+    dm, dq = oracle.project_bwd(g, cams, G)
+    np.testing.assert_allclose(d["d_mean"], dm, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(d["d_quat"], dq, rtol=1e-12, atol=1e-12)
+    h = 1e-6
+    for name, key in (("scale", "d_scale"), ("opacity_logit", "d_ologit"), ("sh", "d_sh")):
+        base = getattr(g, name)
+        for idx in np.ndindex(*base.shape):
+            if rng.uniform() > (0.35 if name == "sh" else 1.0):
+                continue   # a sample of the SH coefficients keeps the test short
+            gp, gm = g.copy(), g.copy()
+            getattr(gp, name)[idx] += h
+            getattr(gm, name)[idx] -= h
+            fd = (f(gp) - f(gm)) / (2 * h)
+            assert abs(fd - d[key][idx]) <= 1e-5 * max(1.0, abs(fd)), (name, idx, fd, d[key][idx])
+
+
 def test_project_bwd_clamped_jacobian_finite_differences():
     """Gaussians outside 1.3x the half field of view (J evaluated at the clamp)."""
     cam = scenes.look_at_camera((0.0, 0.0, 4.0), 64, 48)
