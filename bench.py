@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--eager", action="store_true", help="launch kernels one by one (no CUDA graph)")
     ap.add_argument("--no-converge", action="store_true", help="skip the equal-PSNR comparison")
     ap.add_argument("--no-render", action="store_true", help="skip the render-only measurement")
+    ap.add_argument("--no-stage2", action="store_true", help="skip the Stage-2 measurement")
+    ap.add_argument("--stream-frames", type=int, default=3,
+                    help="frames of the streaming run (0: skip)")
     ap.add_argument("--bin", type=int, default=0,
                     help="bin side in tiles (0: autotune over 1, 2, 4, 8, 16)")
     ap.add_argument("--profile", action="store_true",
@@ -487,6 +490,17 @@ def run_ours(args):
         n_fin = converge["ntc"]["final_psnr"]
         reach = [it for it, p in converge["direct"]["curve"] if p >= n_fin - 0.05]
         converge["direct_reaches_ntc_final_psnr_within_frame"] = bool(reach)
+    stage2 = None
+    used_graphs = graphs is not None
+    if not args.no_stage2 and rank == 0:
+        graphs = None
+        torch.cuda.empty_cache()
+        stage2 = stage2_workload(dev)
+    stream_res = None
+    if args.stream_frames > 0 and rank == 0:
+        graphs = None
+        torch.cuda.empty_cache()
+        stream_res = stream_workload(dev, args.stream_frames, (warm_table, warm_mlp), ntc)
     if rank == 0 and world == 1 and not args.no_cpu:
         per_iter, desc, cores = oracle_sample(scene)
         cpu = {"value": per_iter * ITERS_PER_FRAME, "unit": "s/frame", "cores": cores,
@@ -505,12 +519,13 @@ def run_ours(args):
                 "plain_fp32_direct_opt": plain,
                 "speedup_vs_plain_per_iter": (plain["ms_per_iter"] / ms_max) if plain else None,
                 "equal_psnr": converge,
-                "graphs": graphs is not None,
+                "graphs": used_graphs,
                 "stages_ms": {k: round(v, 4) for k, v in stages.items()},
                 "bin_pairs_per_step": pairs, "composited_pairs": pair_counts,
                 "warmup_loss": wl, "warmup_s": t_warm,
                 "roofline": roof, "raster_fwd_bwd_roofline": raster_roof,
                 "render_only": render_only, "bin_autotune": tune, "bin_tiles": bin_side,
+                "stage2": stage2, "stream": stream_res,
                 "paper_context": {"s_per_frame": 12.0, "fps_render": 200,
                                   "hardware": "one RTX 3090", "workload": "N3DV, real video",
                                   "note": "context only: other hardware, data and precision"},
@@ -522,6 +537,128 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
+
+
+def stage2_workload(dev, warm_iters=300):
+    """Stage 2 (Section 4.2) on the 500K-Gaussian, 12-view 1280x720 workload
+    whose target frame holds an object absent from the previous frame:
+    Stage 1 (150 iterations, view-space statistics over its final epoch),
+    then 100 timed Stage-2 iterations (spawn, training of the added
+    Gaussians, split/prune at every epoch end, host reads of the count
+    included).  Returns timings and the PSNR of the training views."""
+    import torch
+    from paper_2403_01444_gb300 import gs3, scenes
+    from paper_2403_01444_gb300.engine import NTC, Rasterizer, Stage1, Stage2, warmup
+    scene = scenes.make_scene(4)
+    cfg = scene.cfg
+    W, H, Vb = cfg.W, cfg.H, cfg.views_per_batch
+    nb = cfg.n_cams // Vb
+    G = gs3.Gaussians.from_numpy(scene.prev)
+    Gt = gs3.Gaussians.from_numpy(scene.target)
+    cd = gs3.cameras_to_device(scene.cams)
+    bc = [gs3.camera_slice(cd, b * Vb, Vb) for b in range(nb)]
+    rt = Rasterizer(Gt.n, Vb, W, H, 1 << 24, dev)
+    tg = torch.empty(cfg.n_cams, 3, H, W, device=dev)
+    for b in range(nb):
+        rt.fit_capacity(Gt, bc[b], margin=1.2)
+        tg[b * Vb:(b + 1) * Vb].copy_(rt.img)
+    del rt
+    batches = [(bc[b], tg[b * Vb:(b + 1) * Vb]) for b in range(nb)]
+    rng = np.random.default_rng(11)
+    grid = gs3.hashgrid()
+    table = rng.uniform(-1e-4, 1e-4, size=(gs3.ntc_hashgrid_entries(grid), 2)).astype(np.float32)
+    Ws = [w.astype(np.float32) for w in scenes.random_mlp([32, 64, 64, 7], rng)]
+    ntc = NTC(table, Ws, grid, gs3.GS_MLP_BF16, dev)
+    warmup(ntc, G, iters=warm_iters)
+    st1 = Stage1(G, ntc, Vb, W, H, capacity=1 << 20)
+    st1.raster.fit_capacity(G, bc[0], *st1.transform(), margin=2.0)
+    track = None
+    for it in range(ITERS_PER_FRAME):
+        if it == ITERS_PER_FRAME - nb:
+            track = st1.track_viewspace(True)
+        st1.step(*batches[it % nb])
+    st1.track_viewspace(False)
+    st1.raster.check()
+    mt, qt = [x.clone() for x in st1.transform()]
+
+    def psnr_views(gs, mean=None, quat=None):
+        r = Rasterizer(gs.n, Vb, W, H, 1 << 22, dev)
+        se = 0.0
+        for b in range(nb):
+            r.fit_capacity(gs, bc[b], mean, quat, margin=1.2)
+            se += float(((r.img - tg[b * Vb:(b + 1) * Vb]) ** 2).sum())
+        return -10 * math.log10(se / tg.numel())
+
+    p1 = psnr_views(G, mt, qt)
+    st2 = Stage2(G, Vb, W, H, capacity=300_000, pair_capacity=1 << 24)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(stream)
+    spawned = st2.begin(mt, qt, *track)
+    st2.run(batches, iters=100)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ms = e0.elapsed_time(e1)
+    p2 = psnr_views(st2.view())
+    added_final = st2.n_add
+    del st2
+    torch.cuda.empty_cache()
+    # the random-spawn ablation (Section 5.3): as many added Gaussians, around
+    # fixed ones drawn at random, same training and quantity control
+    st_r = Stage2(G, Vb, W, H, capacity=300_000, pair_capacity=1 << 24, seed=5)
+    st_r.begin(mt, qt, *track, random_count=spawned)
+    st_r.run(batches, iters=100)
+    p_rand, n_rand = psnr_views(st_r.view()), st_r.n_add
+    return {"workload": "stage2 500K Gaussians SH3 + emerging object of %d, 12 cams 1280x720, "
+                        "4 views/launch, 100 it" % (scene.target.n - scene.prev.n),
+            "ms_total": ms, "ms_per_iter": ms / 100, "wall_s": wall, "spawned": spawned,
+            "added_final": added_final, "psnr_train_views_stage1": p1, "psnr_train_views_stage2": p2,
+            "random_spawn_ablation": {"psnr_train_views": p_rand, "added_final": n_rand}}
+
+
+def stream_workload(dev, n_frames, warm_table_mlp, ntc):
+    """The streaming driver on the 250K-Gaussian, 20-view 1352x1014 video:
+    n_frames consecutive frames of cumulative rigid+RBF motion, each Stage 1
+    (150 iterations, graphs) then Stage 2 (100 iterations) on a second stream
+    overlapped with the next frame's Stage 1; targets of each frame rendered
+    on the fly (inside the timed loop)."""
+    import torch
+    from paper_2403_01444_gb300 import gs3, scenes
+    from paper_2403_01444_gb300.engine import Rasterizer, Streamer
+    cfg, frames, cams, ho = scenes.make_sequence(CFG_INDEX, n_frames)
+    W, H, Vb = cfg.W, cfg.H, cfg.views_per_batch
+    nb = cfg.n_cams // Vb
+    cd = gs3.cameras_to_device(cams)
+    hod = gs3.cameras_to_device([ho])
+    rt = Rasterizer(frames[0].n, Vb, W, H, 1 << 24, dev)
+    rh = Rasterizer(frames[0].n, 1, W, H, 1 << 22, dev)
+    out = torch.empty(cfg.n_cams, 3, H, W, device=dev)
+
+    def views(t):
+        Gt = gs3.Gaussians.from_numpy(frames[t + 1])
+        for b in range(nb):
+            rt.fit_capacity(Gt, gs3.camera_slice(cd, b * Vb, Vb), margin=1.2)
+            out[b * Vb:(b + 1) * Vb].copy_(rt.img)
+        return out
+
+    ho_gt = []
+    for t in range(n_frames):
+        rh.fit_capacity(gs3.Gaussians.from_numpy(frames[t + 1]), hod, margin=1.2)
+        ho_gt.append(rh.img.clone())
+    G0 = gs3.Gaussians.from_numpy(frames[0])
+    s = Streamer(G0, ntc, *warm_table_mlp, cd, cfg.n_cams, Vb, W, H, heldout_dev=hod)
+    rec = s.run(views, ho_gt)
+    mean = lambda k: float(np.mean([r[k] for r in rec]))
+    return {"workload": "stream: 250K Gaussians SH3, 20 cams 1352x1014, %d frames of cumulative "
+                        "rigid+RBF motion; Stage 1 150 it + Stage 2 100 it per frame, Stage 2 "
+                        "overlapped with the next frame's Stage 1" % n_frames,
+            "frames": n_frames, "wall_s": s.wall_s, "s_per_frame": s.wall_s / n_frames,
+            "psnr_heldout_carried": mean("psnr_carried"), "psnr_heldout_stage1": mean("psnr_stage1"),
+            "psnr_heldout_stage2": mean("psnr_stage2"), "added_per_frame": mean("added"),
+            "storage_bytes_per_frame": mean("storage_bytes"), "per_frame": rec}
 
 
 def equal_psnr(scene, G, Gt, ntc, warm_table, warm_mlp, st, batches, nb, Vb, W, H, ms_ntc, ms_plain,

@@ -409,13 +409,15 @@ GS_API gs_status gs_added_spawn(const gs_gaussians *src, const int32_t *idx, con
  * order (with their moments); then every kept row j with denom[j] > 0 and
  * accum[j] / denom[j] > tau_grad adds, in order, a row with mean =
  * mu_j + R_j diag(s_j) z[j] (a draw from N(mu_j, Sigma_j); z [n_src][3]),
- * log scale + log(split_scale), rotation, opacity and SH of row j, moments
- * zero.  Writes dst (a different buffer) and *d_ndst; rows beyond
- * dst->capacity are dropped with *d_err = GS_ERR_CAPACITY.  One block. */
+ * log scale + log(split_scale), rotation and SH of row j, opacity
+ * opacity_init (as a spawned Gaussian), moments zero.  Writes dst (a
+ * different buffer) and *d_ndst; rows beyond dst->capacity are dropped with
+ * *d_err = GS_ERR_CAPACITY.  One block. */
 GS_API gs_status gs_added_densify_prune(const gs_added *src, int64_t n_src, const float *accum,
                                         const int32_t *denom, float tau_grad, float tau_opacity,
-                                        float split_scale, const float *z, gs_added *dst,
-                                        int64_t *d_ndst, int32_t *d_err, gs_stream stream);
+                                        float split_scale, float opacity_init, const float *z,
+                                        gs_added *dst, int64_t *d_ndst, int32_t *d_err,
+                                        gs_stream stream);
 
 /* Bias-corrected Adam on the n rows of a: gradients from
  * gs_project_bwd_full's arrays (d_scale wrt s is turned into the gradient wrt

@@ -10,8 +10,9 @@ gives the steps:
   each, at a draw from N(mu, 2 Sigma), SH and scale copied, rotation identity,
   opacity 0.1 -> optimisation of the added Gaussians only (same loss as
   Stage 1) -> at the end of each epoch: added Gaussians above tau_grad spawn
-  one more nearby (draw from N(mu, Sigma), scale x 0.8, rotation, opacity and
-  SH inherited), then those with opacity below tau_alpha are discarded.
+  one more nearby (draw from N(mu, Sigma), scale x 0.8, rotation and SH
+  inherited, opacity 0.1 as at a spawn), then those with opacity below
+  tau_alpha are discarded.
 
 An added Gaussian is a row [mean 3 | quat 4 | log scale 3 | opacity logit 1 |
 SH K x 3].  Random draws are inputs (z), so the CUDA path can be given the
@@ -83,10 +84,11 @@ def spawn(g, idx, z, opacity_init=0.1) -> np.ndarray:
     return rows
 
 
-def densify_prune(rows, accum, denom, tau_grad, tau_opacity, split_scale, z):
+def densify_prune(rows, accum, denom, tau_grad, tau_opacity, split_scale, z, opacity_init=0.1):
     """Quantity control at the end of an epoch: returns (new rows, kept mask,
     split mask).  Kept rows first, in order, then one new row per kept row
-    above tau_grad, in order."""
+    above tau_grad, in order (rotation and SH inherited, scale x split_scale,
+    opacity opacity_init as at a spawn)."""
     rows = np.asarray(rows, np.float64)
     opacity = 1.0 / (1.0 + np.exp(-rows[:, COL_OPL]))
     keep = opacity >= tau_opacity
@@ -98,6 +100,7 @@ def densify_prune(rows, accum, denom, tau_grad, tau_opacity, split_scale, z):
     new[:, COL_MEAN:COL_QUAT] = parents[:, COL_MEAN:COL_QUAT] + np.einsum(
         "nij,nj->ni", R, s * np.asarray(z, np.float64)[split])
     new[:, COL_LOGS:COL_OPL] += np.log(split_scale)
+    new[:, COL_OPL] = np.log(opacity_init / (1.0 - opacity_init))
     return np.concatenate([rows[keep], new]), keep, split
 
 

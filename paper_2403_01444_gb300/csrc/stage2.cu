@@ -160,7 +160,8 @@ __global__ void spawn_count_kernel(const int64_t *d_nsel, int64_t cap, int64_t *
 // ------------------------------------------------------- split and prune
 __global__ void __launch_bounds__(SEL_THREADS) densify_prune_kernel(
     gs_added src, int64_t n_src, const float *accum, const int32_t *denom, float tau_grad,
-    float opl_min, float log_split, const float *z, gs_added dst, int64_t *d_ndst, int32_t *d_err)
+    float opl_min, float log_split, float opl_child, const float *z, gs_added dst, int64_t *d_ndst,
+    int32_t *d_err)
 {
     const int K = (src.sh_deg + 1) * (src.sh_deg + 1), P = added_cols(K);
     const int64_t c = (n_src + SEL_THREADS - 1) / SEL_THREADS;
@@ -196,6 +197,7 @@ __global__ void __launch_bounds__(SEL_THREADS) densify_prune_kernel(
             sample_around(r + COL_MEAN, r + COL_QUAT, s, z + 3 * j, 1.f, w + COL_MEAN);
             for (int q = COL_QUAT; q < P; ++q) w[q] = r[q];
             for (int a = 0; a < 3; ++a) w[COL_LOGS + a] = r[COL_LOGS + a] + log_split;
+            w[COL_OPL] = opl_child;
             for (int q = 0; q < P; ++q) {
                 dst.m[os * P + q] = 0.f;
                 dst.v[os * P + q] = 0.f;
@@ -334,21 +336,22 @@ extern "C" gs_status gs_added_spawn(const gs_gaussians *src, const int32_t *idx,
 
 extern "C" gs_status gs_added_densify_prune(const gs_added *src, int64_t n_src, const float *accum,
                                             const int32_t *denom, float tau_grad,
-                                            float tau_opacity, float split_scale, const float *z,
-                                            gs_added *dst, int64_t *d_ndst, int32_t *d_err,
-                                            gs_stream stream)
+                                            float tau_opacity, float split_scale,
+                                            float opacity_init, const float *z, gs_added *dst,
+                                            int64_t *d_ndst, int32_t *d_err, gs_stream stream)
 {
     GS_REQUIRE(added_ok(src) && added_ok(dst) && accum && denom && z && d_ndst && d_err,
                "gs_added_densify_prune: null argument");
     GS_REQUIRE(src->sh_deg == dst->sh_deg && src->rows != dst->rows,
                "gs_added_densify_prune: dst must be another buffer of the same SH degree");
     GS_REQUIRE(n_src >= 0 && n_src <= src->capacity, "gs_added_densify_prune: bad n_src");
-    GS_REQUIRE(tau_opacity > 0.f && tau_opacity < 1.f && split_scale > 0.f,
+    GS_REQUIRE(tau_opacity > 0.f && tau_opacity < 1.f && split_scale > 0.f && opacity_init > 0.f &&
+                   opacity_init < 1.f,
                "gs_added_densify_prune: bad thresholds");
     note_launch();
     densify_prune_kernel<<<1, SEL_THREADS, 0, as_stream(stream)>>>(
         *src, n_src, accum, denom, tau_grad, logf(tau_opacity / (1.f - tau_opacity)),
-        logf(split_scale), z, *dst, d_ndst, d_err);
+        logf(split_scale), logf(opacity_init / (1.f - opacity_init)), z, *dst, d_ndst, d_err);
     return launch_status("gs_added_densify_prune");
 }
 

@@ -7,6 +7,7 @@ this module owns buffers, streams and the order of calls.
 from __future__ import annotations
 
 import math
+import time
 from typing import List, Optional
 
 import numpy as np
@@ -421,12 +422,13 @@ class Stage2:
         return d_loss
 
     def epoch_end(self):
-        """Split the added Gaussians above tau_grad (one more each, 80 % scale)
-        and discard those below tau_alpha; reads the new count back."""
+        """Split the added Gaussians above tau_grad (one more each: 80 % scale,
+        rotation and SH inherited, opacity as a spawned Gaussian's) and
+        discard those below tau_alpha; reads the new count back."""
         z = torch.randn(max(self.n_add, 1), 3, generator=self.gen, device=self.accum.device)
         gs3.gs_added_densify_prune(self.added(), self.n_add, self.accum, self.denom, self.tau_grad,
-                                   self.tau_alpha, SPLIT_SCALE, z, self.added(1 - self.cur), self.d_n,
-                                   self.d_err)
+                                   self.tau_alpha, SPLIT_SCALE, SPAWN_OPACITY, z,
+                                   self.added(1 - self.cur), self.d_n, self.d_err)
         self.cur = 1 - self.cur
         self.n_add = int(self.d_n.item())
         self._after_resize()
@@ -450,6 +452,140 @@ class Stage2:
         if int(self.d_err.item()) != 0:
             raise gs3.GsError("Stage2", int(self.d_err.item()), "added-Gaussian capacity exceeded")
         return self.n_add
+
+
+class Streamer:
+    """Per-frame reconstruction of a multi-view video (Section 3): every frame
+    restarts the transformation cache from its warm-up parameters, trains it
+    for iters1 Stage-1 iterations (view-space statistics over the final
+    epoch), carries the transformed Gaussians to the next frame, and runs
+    Stage 2 (frame-specific added Gaussians, not carried) on a second CUDA
+    stream, overlapped with the next frame's Stage 1.
+
+    Per frame it records the held-out-view PSNR of the carried Gaussians
+    before the frame's training and after each stage, the number of added
+    Gaussians and the frame's storage: the cache parameters (FP16 table, BF16
+    MLP) and the added Gaussians' rows (FP32)."""
+
+    def __init__(self, g0: Gaussians, ntc: NTC, warm_table, warm_mlp, cams_dev, n_cams: int,
+                 Vb: int, W: int, H: int, heldout_dev=None, stage2: bool = True,
+                 iters1: int = 150, iters2: int = 100, added_capacity: int = 300_000,
+                 device="cuda", bin: int = DEFAULT_BIN, graphs: bool = True):
+        clone = lambda t: t.clone()
+        self.g = Gaussians(clone(g0.mean), clone(g0.quat), g0.scale, g0.opacity_logit, g0.sh, g0.sh_deg)
+        self.ntc, self.warm = ntc, (warm_table, warm_mlp)
+        self.Vb, self.W, self.H = Vb, W, H
+        self.nb = n_cams // Vb
+        self.cams = [gs3.camera_slice(cams_dev, b * Vb, Vb) for b in range(self.nb)]
+        self.heldout = heldout_dev
+        self.iters1, self.iters2 = iters1, iters2
+        self.st1 = Stage1(self.g, ntc, Vb, W, H, capacity=1 << 20, device=device, bin=bin)
+        self.st2 = Stage2(self.g, Vb, W, H, added_capacity, pair_capacity=1 << 22, device=device,
+                          bin=bin) if stage2 else None
+        # frame t's views for Stage 1 (graphs read this buffer) and a copy for
+        # Stage 2, which still trains frame t while Stage 1 runs frame t + 1
+        self.targets = _f32(n_cams, 3, H, W, device=device)
+        self.targets2 = _f32(n_cams, 3, H, W, device=device) if stage2 else None
+        self.batches = [(self.cams[b], self.targets[b * Vb:(b + 1) * Vb]) for b in range(self.nb)]
+        self.batches2 = ([(self.cams[b], self.targets2[b * Vb:(b + 1) * Vb]) for b in range(self.nb)]
+                         if stage2 else None)
+        self.side = torch.cuda.Stream() if stage2 else None
+        self.use_graphs = graphs
+        self.graphs = None
+        self.graphs_track = None
+        self.track = None
+
+    def _stage1(self, targets):
+        """Issue one frame of Stage 1 on the current stream (no host wait)."""
+        st = self.st1
+        self.targets.copy_(targets)
+        self.ntc.reset_to(*self.warm)
+        st.reset_state()
+        if self.track is None:
+            self.track = st.track_viewspace(True)
+            st.track_viewspace(False)
+        accum, denom = self.track
+        if self.use_graphs and self.graphs is None:
+            st.raster.fit_capacity(self.g, self.cams[0], *st.transform(), margin=2.0)
+            self.graphs = st.capture(self.batches)
+            st.track = self.track
+            self.graphs_track = st.capture(self.batches)
+            st.track = None
+            self.ntc.reset_to(*self.warm)
+            st.reset_state()
+        elif not self.use_graphs and st.raster.count() == 0:
+            st.raster.fit_capacity(self.g, self.cams[0], *st.transform(), margin=2.0)
+        for it in range(self.iters1):
+            b = it % self.nb
+            final = it >= self.iters1 - self.nb
+            if final and it == self.iters1 - self.nb:
+                accum.zero_()
+                denom.zero_()
+            if self.use_graphs:
+                (self.graphs_track if final else self.graphs)[b].replay()
+            else:
+                st.track = self.track if final else None
+                st.step(*self.batches[b])
+                st.track = None
+        return st.transform()
+
+    def _psnr(self, gs: Gaussians, gt_img, mean=None, quat=None):
+        img = render_dev(gs, self.heldout, 1, self.W, self.H, mean, quat)
+        return -10 * math.log10(float(((img - gt_img) ** 2).mean().item()))
+
+    def run(self, frame_targets, heldout_gt=None):
+        """frame_targets(t) (or a list): the [n_cams, 3, H, W] device tensor of
+        frame t + 1's training views, t = 0 .. n_frames - 1; heldout_gt: per
+        frame the held-out view [1, 3, H, W] (or None).  Returns one record
+        per frame."""
+        get = frame_targets if callable(frame_targets) else (lambda t: frame_targets[t])
+        n_frames = len(heldout_gt) if heldout_gt is not None else len(frame_targets)
+        records = []
+        main = torch.cuda.current_stream()
+        K = (self.g.sh_deg + 1) ** 2
+        cache_bytes = self.ntc.entries * 2 * 2 + gs3.MLP_PARAMS * 2
+        t_all = time.perf_counter()
+        mt, qt = self._stage1(get(0))
+        for t in range(n_frames):
+            rec = {"frame": t + 1}
+            main.synchronize()  # frame t's Stage 1 is done
+            if heldout_gt is not None and self.heldout is not None:
+                # the previous frame's Gaussians unchanged, then after Stage 1
+                rec["psnr_carried"] = self._psnr(self.g, heldout_gt[t])
+                rec["psnr_stage1"] = self._psnr(self.g, heldout_gt[t], mt, qt)
+            mt_c, qt_c = mt.clone(), qt.clone()
+            acc, den = self.track
+            if self.st2 is not None:
+                self.targets2.copy_(self.targets)
+                self.side.wait_stream(main)
+                with torch.cuda.stream(self.side):
+                    self.st2.begin(mt_c, qt_c, acc, den)  # reads back the spawn count
+            # carry the transformed Gaussians; issue the next frame's Stage 1
+            self.g.mean.copy_(mt_c)
+            self.g.quat.copy_(qt_c)
+            if t + 1 < n_frames:
+                mt, qt = self._stage1(get(t + 1))
+            if self.st2 is not None:
+                # frame t's Stage 2 on the side stream, overlapped with the above
+                with torch.cuda.stream(self.side):
+                    self.st2.run(self.batches2, iters=self.iters2)
+                    if heldout_gt is not None and self.heldout is not None:
+                        rec["psnr_stage2"] = self._psnr(self.st2.view(), heldout_gt[t])
+                    rec["added"] = self.st2.n_add
+                self.side.synchronize()
+            rec["storage_bytes"] = cache_bytes + rec.get("added", 0) * 4 * (11 + 3 * K)
+            records.append(rec)
+        torch.cuda.synchronize()
+        self.wall_s = time.perf_counter() - t_all
+        return records
+
+
+def render_dev(g: Gaussians, cams_dev, V: int, W: int, H: int, mean=None, quat=None,
+               capacity=None, device="cuda", bin: int = DEFAULT_BIN) -> torch.Tensor:
+    """Render V device cameras (one launch); returns [V, 3, H, W]."""
+    r = Rasterizer(g.n, V, W, H, capacity or 1 << 20, device, bin=bin)
+    r.fit_capacity(g, cams_dev, mean, quat)
+    return r.img.clone()
 
 
 class DirectOpt:

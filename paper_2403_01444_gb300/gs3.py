@@ -403,12 +403,12 @@ def gs_added_spawn(src: Gaussians, idx, d_nsel, z, opacity_init, dst: GsAdded, d
         _ptr(d_nadd), _ptr(d_err), _stream(stream)))
 
 
-def gs_added_densify_prune(src: GsAdded, n_src, accum, denom, tau_grad, tau_opacity, split_scale, z,
-                           dst: GsAdded, d_ndst, d_err, stream=None):
+def gs_added_densify_prune(src: GsAdded, n_src, accum, denom, tau_grad, tau_opacity, split_scale,
+                           opacity_init, z, dst: GsAdded, d_ndst, d_err, stream=None):
     _check("gs_added_densify_prune", lib().gs_added_densify_prune(
         ctypes.byref(src), c_int64(n_src), _ptr(accum), _ptr(denom), c_float(tau_grad),
-        c_float(tau_opacity), c_float(split_scale), _ptr(z), ctypes.byref(dst), _ptr(d_ndst),
-        _ptr(d_err), _stream(stream)))
+        c_float(tau_opacity), c_float(split_scale), c_float(opacity_init), _ptr(z), ctypes.byref(dst),
+        _ptr(d_ndst), _ptr(d_err), _stream(stream)))
 
 
 def gs_added_adam(a: GsAdded, n, d_mean, d_quat, d_scale, d_opacity_logit, d_sh, lr, beta1, beta2,

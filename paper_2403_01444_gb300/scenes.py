@@ -34,7 +34,7 @@ __all__ = [
     "GaussianSet", "Camera", "SceneConfig", "CONFIGS", "make_gaussians",
     "look_at_camera", "ring_cameras", "arc_cameras", "rigid_motion",
     "rbf_motion", "random_projected", "random_hashgrid_table", "random_mlp",
-    "make_scene", "emerging_content", "union",
+    "make_scene", "make_sequence", "emerging_content", "union",
 ]
 
 
@@ -311,6 +311,35 @@ class Scene:
     heldout: Camera
 
 
+def _motion_step(g: GaussianSet, motion: str, rng: np.random.Generator) -> GaussianSet:
+    if motion == "rigid":
+        return rigid_motion(g, rng, 5.0, 0.05)
+    if motion == "rbf":
+        return rbf_motion(g, rng, 8, 0.1)
+    return rbf_motion(rigid_motion(g, rng, 1.0, 0.01), rng, 8, 0.02)
+
+
+def make_sequence(cfg_index: int, n_frames: int, n_gauss: Optional[int] = None,
+                  W: Optional[int] = None, H: Optional[int] = None):
+    """A multi-view video of n_frames + 1 frames: frame 0 is the config's
+    previous-frame Gaussians and frame t applies one more step of the config's
+    motion to frame t - 1 (cumulative), drawn from the same seeded stream as
+    make_scene, so frame 1 is make_scene's target.  Returns (config, frames,
+    cameras, held-out camera)."""
+    cfg = dataclasses.replace(CONFIGS[cfg_index])
+    if n_gauss is not None:
+        cfg.n_gauss = n_gauss
+    if W is not None:
+        cfg.W = W
+    if H is not None:
+        cfg.H = H
+    rng = np.random.default_rng(cfg_index)
+    frames = [make_gaussians(cfg.n_gauss, cfg.sh_deg, rng)]
+    for _ in range(n_frames):
+        frames.append(_motion_step(frames[-1], cfg.motion, rng))
+    return cfg, frames, cameras_for(cfg), heldout_camera(cfg)
+
+
 def make_scene(cfg_index: int, n_gauss: Optional[int] = None, W: Optional[int] = None,
                H: Optional[int] = None, n_cams: Optional[int] = None) -> Scene:
     """Scene of config cfg_index (seed = config index), optionally shrunk."""
@@ -323,12 +352,7 @@ def make_scene(cfg_index: int, n_gauss: Optional[int] = None, W: Optional[int] =
         cfg.H = H
     rng = np.random.default_rng(cfg_index)
     prev = make_gaussians(cfg.n_gauss, cfg.sh_deg, rng)
-    if cfg.motion == "rigid":
-        tgt = rigid_motion(prev, rng, 5.0, 0.05)
-    elif cfg.motion == "rbf":
-        tgt = rbf_motion(prev, rng, 8, 0.1)
-    else:
-        tgt = rbf_motion(rigid_motion(prev, rng, 1.0, 0.01), rng, 8, 0.02)
+    tgt = _motion_step(prev, cfg.motion, rng)
     if cfg.emerging:
         # an object absent from the previous frame appears (Section 4.2):
         # 5 000 to 10 000 new Gaussians in a ball of radius 0.2, scaled with n

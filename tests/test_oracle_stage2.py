@@ -96,7 +96,8 @@ def test_densify_prune_invariants():
     par = rows[split]
     new = out[k1:]
     np.testing.assert_array_equal(new[:, 3:7], par[:, 3:7])
-    np.testing.assert_array_equal(new[:, 10:], par[:, 10:])
+    np.testing.assert_array_equal(new[:, 11:], par[:, 11:])
+    np.testing.assert_allclose(new[:, 10], logit(0.1), rtol=1e-12)
     np.testing.assert_allclose(new[:, 7:10], par[:, 7:10] + math.log(0.8), rtol=0, atol=1e-12)
     # mean = parent + R diag(s) z, R from scipy (scipy quaternions are (x, y, z, w))
     Rm = Rotation.from_quat(par[:, [4, 5, 6, 3]]).as_matrix()
