@@ -361,6 +361,17 @@ GS_API gs_status adam_step(float *p, float *g, float *m, float *v, int64_t n, co
  * steps (growth_interval <= 0 keeps the scale fixed). */
 GS_API gs_status gs_train_state_advance(gs_train_state *d_state, int growth_interval, gs_stream stream);
 
+/* SH rotation (Suppl. B): rotates the SH coefficients of n Gaussians whose
+ * orientation changed from quat_from to quat_to (both [n][4], w x y z, not
+ * necessarily unit; 16-byte aligned), i.e. by the world rotation
+ * Rw = R(quat_to) R(quat_from)^T, so that the colour seen from direction d
+ * afterwards is the colour seen from Rw^T d before.  Each band l >= 1 is
+ * multiplied by M_l = [P_l(Rw N_k)]_k A_l^-1 over 2l + 1 fixed directions N_k
+ * (the coordinate axes for band 1); band 0 is copied.  sh_in, sh_out
+ * [n][K][3] (K = (sh_deg + 1)^2) may be the same array. */
+GS_API gs_status gs_sh_rotate(const float *quat_from, const float *quat_to, const float *sh_in,
+                              int64_t n, int sh_deg, float *sh_out, gs_stream stream);
+
 /* ----------------------------------------- Stage 2: adaptive 3DG addition */
 
 /* The added, frame-specific Gaussians of Stage 2 (Section 4.2) as rows of

@@ -183,6 +183,43 @@ def cam_array(cams) -> np.ndarray:
     return out
 
 
+def _fibonacci_sphere(n, off=0.5):
+    t = np.arange(n) + off
+    z = 1.0 - 2.0 * t / n
+    r = np.sqrt(1.0 - z * z)
+    phi = t * np.pi * (3.0 - np.sqrt(5.0))
+    return np.stack([r * np.cos(phi), r * np.sin(phi), z], 1)
+
+
+def _rotation(q):
+    q = _d(q)
+    q = q / np.linalg.norm(q, axis=-1, keepdims=True)
+    w, x, y, z = np.moveaxis(q, -1, 0)
+    return np.stack([np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)], -1),
+                     np.stack([2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)], -1),
+                     np.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], -1)],
+                    -2)
+
+
+def sh_rotate(sh, quat_from, quat_to, deg, n_dirs=64):
+    """SH rotation (Suppl. B) by its definition: after a Gaussian turns by
+    Rw = R(quat_to) R(quat_from)^T its colour seen from d is the colour seen
+    from Rw^T d before; the new coefficients are those of that function, found
+    by least squares over n_dirs sample directions (exact, the function being
+    band-limited to deg).  sh [n, K, 3] -> [n, K, 3]."""
+    sh = _d(sh)
+    n, K = sh.shape[0], (deg + 1) ** 2
+    D = _fibonacci_sphere(n_dirs)
+    Yd, _ = sh_basis(deg, D)
+    Rw = _rotation(quat_to) @ np.swapaxes(_rotation(quat_from), -1, -2)
+    out = np.empty_like(sh)
+    for i in range(n):
+        Yr, _ = sh_basis(deg, D @ Rw[i])        # rows: Rw^T d
+        f = Yr @ sh[i]                           # [n_dirs, 3]: colours at Rw^T d
+        out[i] = np.linalg.lstsq(Yd, f, rcond=None)[0]
+    return out
+
+
 def project(g, cams, tile=TILE, mean=None, quat=None) -> Dict[str, np.ndarray]:
     """Project GaussianSet g (optionally with replaced mean/quat) into cams."""
     mean = _d(g.mean if mean is None else mean)

@@ -2,6 +2,7 @@
 // One thread per Gaussian handles all V views of a launch, so each Gaussian's
 // parameters (up to 236 bytes with SH degree 3) are read from HBM once.
 #include "common.cuh"
+#include "sh.cuh"
 
 namespace gs3 {
 
@@ -27,41 +28,9 @@ struct ProjectParams {
     float *d_scale, *d_ologit, *d_sh;
 };
 
-// Real SH basis to degree 3 (Condon-Shortley signs, as the 3DG-S renderer),
-// numeric values of 1/(2 sqrt(pi)), sqrt(3)/(2 sqrt(pi)), ...
-#define SH_C0 0.28209479177387814f
-#define SH_C1 0.4886025119029199f
-#define SH_C2A 1.0925484305920792f
-#define SH_C2B 0.31539156525252005f
-#define SH_C2C 0.5462742152960396f
-#define SH_C3A 0.5900435899266435f
-#define SH_C3B 2.890611442640554f
-#define SH_C3C 0.4570457994644658f
-#define SH_C3D 0.3731763325901154f
-#define SH_C3E 1.445305721320277f
-
 __device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, float *Y)
 {
-    Y[0] = SH_C0;
-    if (deg < 1) return;
-    Y[1] = -SH_C1 * y;
-    Y[2] = SH_C1 * z;
-    Y[3] = -SH_C1 * x;
-    if (deg < 2) return;
-    float xx = x * x, yy = y * y, zz = z * z;
-    Y[4] = SH_C2A * x * y;
-    Y[5] = -SH_C2A * y * z;
-    Y[6] = SH_C2B * (2.f * zz - xx - yy);
-    Y[7] = -SH_C2A * x * z;
-    Y[8] = SH_C2C * (xx - yy);
-    if (deg < 3) return;
-    Y[9] = -SH_C3A * y * (3.f * xx - yy);
-    Y[10] = SH_C3B * x * y * z;
-    Y[11] = -SH_C3C * y * (4.f * zz - xx - yy);
-    Y[12] = SH_C3D * z * (2.f * zz - 3.f * xx - 3.f * yy);
-    Y[13] = -SH_C3C * x * (4.f * zz - xx - yy);
-    Y[14] = SH_C3E * z * (xx - yy);
-    Y[15] = -SH_C3A * x * (xx - 3.f * yy);
+    sh_basis_t<float>(deg, x, y, z, Y);
 }
 
 // sum_k w[k] * grad Y_k(x, y, z)
@@ -70,42 +39,42 @@ __device__ __forceinline__ float3 sh_basis_grad_dot(int deg, float x, float y, f
 {
     float3 g = make_float3(0.f, 0.f, 0.f);
     if (deg < 1) return g;
-    g.y += -SH_C1 * w[1];
-    g.z += SH_C1 * w[2];
-    g.x += -SH_C1 * w[3];
+    g.y += -float(SH_C1) * w[1];
+    g.z += float(SH_C1) * w[2];
+    g.x += -float(SH_C1) * w[3];
     if (deg < 2) return g;
     float xx = x * x, yy = y * y, zz = z * z;
-    g.x += SH_C2A * y * w[4];
-    g.y += SH_C2A * x * w[4];
-    g.y += -SH_C2A * z * w[5];
-    g.z += -SH_C2A * y * w[5];
-    g.x += -2.f * SH_C2B * x * w[6];
-    g.y += -2.f * SH_C2B * y * w[6];
-    g.z += 4.f * SH_C2B * z * w[6];
-    g.x += -SH_C2A * z * w[7];
-    g.z += -SH_C2A * x * w[7];
-    g.x += 2.f * SH_C2C * x * w[8];
-    g.y += -2.f * SH_C2C * y * w[8];
+    g.x += float(SH_C2A) * y * w[4];
+    g.y += float(SH_C2A) * x * w[4];
+    g.y += -float(SH_C2A) * z * w[5];
+    g.z += -float(SH_C2A) * y * w[5];
+    g.x += -2.f * float(SH_C2B) * x * w[6];
+    g.y += -2.f * float(SH_C2B) * y * w[6];
+    g.z += 4.f * float(SH_C2B) * z * w[6];
+    g.x += -float(SH_C2A) * z * w[7];
+    g.z += -float(SH_C2A) * x * w[7];
+    g.x += 2.f * float(SH_C2C) * x * w[8];
+    g.y += -2.f * float(SH_C2C) * y * w[8];
     if (deg < 3) return g;
-    g.x += -6.f * SH_C3A * x * y * w[9];
-    g.y += -SH_C3A * (3.f * xx - 3.f * yy) * w[9];
-    g.x += SH_C3B * y * z * w[10];
-    g.y += SH_C3B * x * z * w[10];
-    g.z += SH_C3B * x * y * w[10];
-    g.x += 2.f * SH_C3C * x * y * w[11];
-    g.y += -SH_C3C * (4.f * zz - xx - 3.f * yy) * w[11];
-    g.z += -8.f * SH_C3C * y * z * w[11];
-    g.x += -6.f * SH_C3D * x * z * w[12];
-    g.y += -6.f * SH_C3D * y * z * w[12];
-    g.z += SH_C3D * (6.f * zz - 3.f * xx - 3.f * yy) * w[12];
-    g.x += -SH_C3C * (4.f * zz - 3.f * xx - yy) * w[13];
-    g.y += 2.f * SH_C3C * x * y * w[13];
-    g.z += -8.f * SH_C3C * x * z * w[13];
-    g.x += 2.f * SH_C3E * x * z * w[14];
-    g.y += -2.f * SH_C3E * y * z * w[14];
-    g.z += SH_C3E * (xx - yy) * w[14];
-    g.x += -SH_C3A * (3.f * xx - 3.f * yy) * w[15];
-    g.y += 6.f * SH_C3A * x * y * w[15];
+    g.x += -6.f * float(SH_C3A) * x * y * w[9];
+    g.y += -float(SH_C3A) * (3.f * xx - 3.f * yy) * w[9];
+    g.x += float(SH_C3B) * y * z * w[10];
+    g.y += float(SH_C3B) * x * z * w[10];
+    g.z += float(SH_C3B) * x * y * w[10];
+    g.x += 2.f * float(SH_C3C) * x * y * w[11];
+    g.y += -float(SH_C3C) * (4.f * zz - xx - 3.f * yy) * w[11];
+    g.z += -8.f * float(SH_C3C) * y * z * w[11];
+    g.x += -6.f * float(SH_C3D) * x * z * w[12];
+    g.y += -6.f * float(SH_C3D) * y * z * w[12];
+    g.z += float(SH_C3D) * (6.f * zz - 3.f * xx - 3.f * yy) * w[12];
+    g.x += -float(SH_C3C) * (4.f * zz - 3.f * xx - yy) * w[13];
+    g.y += 2.f * float(SH_C3C) * x * y * w[13];
+    g.z += -8.f * float(SH_C3C) * x * z * w[13];
+    g.x += 2.f * float(SH_C3E) * x * z * w[14];
+    g.y += -2.f * float(SH_C3E) * y * z * w[14];
+    g.z += float(SH_C3E) * (xx - yy) * w[14];
+    g.x += -float(SH_C3A) * (3.f * xx - 3.f * yy) * w[15];
+    g.y += 6.f * float(SH_C3A) * x * y * w[15];
     return g;
 }
 

@@ -470,9 +470,12 @@ class Streamer:
     def __init__(self, g0: Gaussians, ntc: NTC, warm_table, warm_mlp, cams_dev, n_cams: int,
                  Vb: int, W: int, H: int, heldout_dev=None, stage2: bool = True,
                  iters1: int = 150, iters2: int = 100, added_capacity: int = 300_000,
-                 device="cuda", bin: int = DEFAULT_BIN, graphs: bool = True):
+                 device="cuda", bin: int = DEFAULT_BIN, graphs: bool = True,
+                 sh_rotation: bool = True):
         clone = lambda t: t.clone()
-        self.g = Gaussians(clone(g0.mean), clone(g0.quat), g0.scale, g0.opacity_logit, g0.sh, g0.sh_deg)
+        self.g = Gaussians(clone(g0.mean), clone(g0.quat), g0.scale, g0.opacity_logit, clone(g0.sh),
+                           g0.sh_deg)
+        self.sh_rotation = sh_rotation
         self.ntc, self.warm = ntc, (warm_table, warm_mlp)
         self.Vb, self.W, self.H = Vb, W, H
         self.nb = n_cams // Vb
@@ -550,10 +553,14 @@ class Streamer:
             rec = {"frame": t + 1}
             main.synchronize()  # frame t's Stage 1 is done
             if heldout_gt is not None and self.heldout is not None:
-                # the previous frame's Gaussians unchanged, then after Stage 1
+                # the previous frame's Gaussians unchanged
                 rec["psnr_carried"] = self._psnr(self.g, heldout_gt[t])
-                rec["psnr_stage1"] = self._psnr(self.g, heldout_gt[t], mt, qt)
             mt_c, qt_c = mt.clone(), qt.clone()
+            if self.sh_rotation:
+                # the frame's rotations turn the colours too (Suppl. B)
+                gs3.gs_sh_rotate(self.g.quat, qt_c, self.g.sh, self.g.n, self.g.sh_deg, self.g.sh)
+            if heldout_gt is not None and self.heldout is not None:
+                rec["psnr_stage1"] = self._psnr(self.g, heldout_gt[t], mt_c, qt_c)
             acc, den = self.track
             if self.st2 is not None:
                 self.targets2.copy_(self.targets)
@@ -677,10 +684,14 @@ class Renderer:
     per-frame work."""
 
     def __init__(self, g: Gaussians, ntc: NTC, V: int, W: int, H: int, capacity: int,
-                 order: int = 0, device="cuda", bin: int = DEFAULT_BIN):
+                 order: int = 0, device="cuda", bin: int = DEFAULT_BIN, sh_rotation: bool = True):
         n = g.n
         self.g, self.ntc, self.V, self.W, self.H, self.order = g, ntc, V, W, H, order
         self.raster = Rasterizer(n, V, W, H, capacity, device, bin=bin)
+        # SH rotation (Suppl. B): the colours turn with the Gaussians
+        self.sh_rot = torch.empty_like(g.sh) if sh_rotation else None
+        self.g_rot = (Gaussians(g.mean, g.quat, g.scale, g.opacity_logit, self.sh_rot, g.sh_deg)
+                      if sh_rotation else g)
         self.enc = torch.zeros(n, 32, dtype=ntc.enc_dtype(), device=device)
         self.raw7 = _f32(n, 7, device=device)
         self.mean_t = _f32(n, 3, device=device)
@@ -693,7 +704,9 @@ class Renderer:
         gs3.ntc_mlp_fwd(self.enc, n, ntc.mlp_struct(), self.raw7, stream)
         gs3.ntc_apply(g.mean, g.quat, self.raw7, n, self.aabb, self.order, self.mean_t, self.quat_t,
                       stream)
-        return self.raster.forward(g, cams_dev, self.mean_t, self.quat_t, stream)
+        if self.sh_rot is not None:
+            gs3.gs_sh_rotate(g.quat, self.quat_t, g.sh, n, g.sh_deg, self.sh_rot, stream)
+        return self.raster.forward(self.g_rot, cams_dev, self.mean_t, self.quat_t, stream)
 
     def capture(self, cams_dev):
         side = torch.cuda.Stream()

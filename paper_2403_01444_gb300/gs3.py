@@ -426,3 +426,8 @@ def gs_added_to_render(a: GsAdded, n, out: Gaussians, out_first, stream=None):
     _check("gs_added_to_render", lib().gs_added_to_render(
         ctypes.byref(a), c_int64(n), ctypes.byref(gg), c_int64(out_first), _stream(stream)))
 
+
+def gs_sh_rotate(quat_from, quat_to, sh_in, n, sh_deg, sh_out, stream=None):
+    _check("gs_sh_rotate", lib().gs_sh_rotate(_ptr(quat_from), _ptr(quat_to), _ptr(sh_in), c_int64(n),
+                                              c_int(sh_deg), _ptr(sh_out), _stream(stream)))
+

@@ -528,3 +528,30 @@ def test_fused_cache_kernels_match_separate_kernels(n):
     Wb = [_bf16(w) for w in Ws]
     _, _, want_raw = oracle.mlp_fwd(got_enc, Wb)
     assert rel_err(raw2.cpu().numpy(), want_raw) <= 1e-2
+
+
+@pytest.mark.parametrize("deg", [1, 2, 3])
+def test_sh_rotate_matches_oracle(deg):
+    """gs_sh_rotate (fixed directions, A^-1 in the kernel) against the
+    oracle's least-squares definition, in place and out of place."""
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(70 + deg)
+    n, K = 3000, (deg + 1) ** 2
+    sh = rng.normal(size=(n, K, 3)).astype(np.float32)
+    qa = rng.normal(size=(n, 4)).astype(np.float32)
+    qb = rng.normal(size=(n, 4)).astype(np.float32) * 2.0   # not unit on purpose
+    want = oracle.sh_rotate(sh[:400], qa[:400], qb[:400], deg)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+    out = torch.empty(n, K, 3, device=DEV)
+    gs3.gs_sh_rotate(t(qa), t(qb), t(sh), n, deg, out)
+    inplace = t(sh)
+    gs3.gs_sh_rotate(t(qa), t(qb), inplace, n, deg, inplace)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    np.testing.assert_allclose(got[:400], want, rtol=0, atol=2e-5 * np.abs(sh).max() * K)
+    assert torch.equal(out, inplace)
+    # band energies preserved over all n (orthonormal basis)
+    for lo, hi in ((1, 4), (4, 9), (9, 16))[:deg]:
+        np.testing.assert_allclose(np.linalg.norm(got[:, lo:hi], axis=1),
+                                   np.linalg.norm(sh[:, lo:hi], axis=1), rtol=1e-4, atol=1e-5)
+

@@ -456,3 +456,45 @@ def test_perturbation_reach_covers_flipped_decisions(pos_eps, rel_eps):
     assert np.all(amb[0][changed] == 1)
     # the reach is not vacuous: most pixels stay unflagged
     assert amb.mean() < 0.5
+
+
+def _quat_of(rot):
+    x, y, z, w = rot.as_quat().T if rot.as_quat().ndim == 2 else rot.as_quat()
+    return np.stack([w, x, y, z], -1)
+
+
+def test_sh_rotate_pins():
+    """SH rotation: identity, composition of two rotations, the defining
+    identity at directions outside the fit, energy per band (orthonormal
+    basis) and the degree-1 closed form (the band is a dot product with a
+    vector, which turns with the Gaussian)."""
+    rng = np.random.default_rng(60)
+    n, deg = 6, 3
+    sh = rng.normal(size=(n, 16, 3))
+    R1 = Rotation.random(n, random_state=61)
+    R2 = Rotation.random(n, random_state=62)
+    q0 = _quat_of(Rotation.identity(n))
+    q1, q21 = _quat_of(R1), _quat_of(R2 * R1)
+    np.testing.assert_allclose(oracle.sh_rotate(sh, q0, q0, deg), sh, atol=1e-12)
+    a = oracle.sh_rotate(sh, q0, q1, deg)
+    b = oracle.sh_rotate(a, q1, q21, deg)
+    np.testing.assert_allclose(b, oracle.sh_rotate(sh, q0, q21, deg), atol=1e-10)
+    # colour from d after == colour from R^T d before, d random
+    d = rng.normal(size=(50, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    Yd, _ = oracle.sh_basis(deg, d)
+    for i in range(n):
+        Rm = R1[i].as_matrix()
+        Yr, _ = oracle.sh_basis(deg, d @ Rm)
+        np.testing.assert_allclose(Yd @ a[i], Yr @ sh[i], atol=1e-10)
+    for lo, hi in ((0, 1), (1, 4), (4, 9), (9, 16)):
+        np.testing.assert_allclose(np.linalg.norm(a[:, lo:hi], axis=1),
+                                   np.linalg.norm(sh[:, lo:hi], axis=1), rtol=1e-10)
+    np.testing.assert_allclose(a[:, 0], sh[:, 0], atol=1e-12)   # band 0 is invariant
+    # degree 1: Y = C1 (-y, z, -x), so the band is C1 v.d with v = (-c3, -c1, c2);
+    # turning the Gaussian turns v: v' = R v
+    for i in range(n):
+        c = sh[i, 1:4]                                  # [3 coefficients, 3 channels]
+        v = np.stack([-c[2], -c[0], c[1]])              # [xyz, channel]
+        v2 = R1[i].as_matrix() @ v
+        np.testing.assert_allclose(a[i, 1:4], np.stack([-v2[1], v2[2], -v2[0]]), atol=1e-10)
