@@ -351,7 +351,8 @@ GS_API gs_status gs_check_finite(const float *g, int64_t n, gs_train_state *d_st
  * and step number d_state->step + 1, skipped when d_state->found_inf is set.
  * Zeroes g afterwards (ready for the next step's accumulation).  If shadow is
  * non-NULL, writes the updated parameters converted to shadow_dtype (GS_F16 or
- * GS_BF16).  All state (m, v) FP32, in place. */
+ * GS_BF16).  All state (m, v) FP32, in place.  p, g, m, v 16-byte aligned,
+ * shadow 8-byte aligned (GS_ERR_INVALID_ARG otherwise). */
 GS_API gs_status adam_step(float *p, float *g, float *m, float *v, int64_t n, const gs_adam *hp,
                     const gs_train_state *d_state, void *shadow, int shadow_dtype,
                     gs_stream stream);

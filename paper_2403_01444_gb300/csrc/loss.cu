@@ -69,33 +69,35 @@ __global__ void __launch_bounds__(LTHREADS) ssim_fwd_kernel(LossParams p)
     float w[11];
 #pragma unroll
     for (int k = 0; k < 11; ++k) w[k] = c_win[k];
-    // horizontal: (x, y, x^2, y^2, xy) filtered along rows
+    // horizontal: (x, y, x^2, y^2, xy) filtered along rows.  Each staged input
+    // is read and squared once and added into the HSEG outputs it reaches;
+    // every output still sums its taps in increasing order.
     for (int item = tid; item < LS * (LT / HSEG); item += LTHREADS) {
         const int r = item / (LT / HSEG), c0 = (item % (LT / HSEG)) * HSEG;
-        float xv[HSEG + 10], yv[HSEG + 10];
+        float acc[HSEG][5];
+#pragma unroll
+        for (int o = 0; o < HSEG; ++o)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) acc[o][q] = 0.f;
 #pragma unroll
         for (int k = 0; k < HSEG + 10; ++k) {
-            xv[k] = sx[r][c0 + k];
-            yv[k] = sy[r][c0 + k];
-        }
+            const float a = sx[r][c0 + k], b = sy[r][c0 + k];
+            const float aa = a * a, bb = b * b, ab = a * b;
 #pragma unroll
-        for (int o = 0; o < HSEG; ++o) {
-            float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, m4 = 0.f;
-#pragma unroll
-            for (int k = 0; k < 11; ++k) {
-                float a = xv[o + k], b = yv[o + k];
-                m0 = fmaf(w[k], a, m0);
-                m1 = fmaf(w[k], b, m1);
-                m2 = fmaf(w[k], a * a, m2);
-                m3 = fmaf(w[k], b * b, m3);
-                m4 = fmaf(w[k], a * b, m4);
+            for (int o = 0; o < HSEG; ++o) {
+                const int t = k - o;
+                if (t < 0 || t > 10) continue;
+                acc[o][0] = fmaf(w[t], a, acc[o][0]);
+                acc[o][1] = fmaf(w[t], b, acc[o][1]);
+                acc[o][2] = fmaf(w[t], aa, acc[o][2]);
+                acc[o][3] = fmaf(w[t], bb, acc[o][3]);
+                acc[o][4] = fmaf(w[t], ab, acc[o][4]);
             }
-            hs[0][r][c0 + o] = m0;
-            hs[1][r][c0 + o] = m1;
-            hs[2][r][c0 + o] = m2;
-            hs[3][r][c0 + o] = m3;
-            hs[4][r][c0 + o] = m4;
         }
+#pragma unroll
+        for (int o = 0; o < HSEG; ++o)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) hs[q][r][c0 + o] = acc[o][q];
     }
     __syncthreads();
     // vertical: thread -> column c, rows r0 .. r0 + VSEG - 1
@@ -183,26 +185,27 @@ __global__ void __launch_bounds__(LTHREADS) ssim_bwd_kernel(LossParams p)
     for (int k = 0; k < 11; ++k) w[k] = c_win[k];
     for (int item = tid; item < LS * (LT / HSEG); item += LTHREADS) {
         const int r = item / (LT / HSEG), c0 = (item % (LT / HSEG)) * HSEG;
-        float av[HSEG + 10], bv[HSEG + 10], cv[HSEG + 10];
+        float acc[HSEG][3];
+#pragma unroll
+        for (int o = 0; o < HSEG; ++o)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) acc[o][q] = 0.f;
 #pragma unroll
         for (int k = 0; k < HSEG + 10; ++k) {
-            av[k] = sa[r][c0 + k];
-            bv[k] = sb[r][c0 + k];
-            cv[k] = sc[r][c0 + k];
-        }
+            const float a = sa[r][c0 + k], b = sb[r][c0 + k], cc = sc[r][c0 + k];
 #pragma unroll
-        for (int o = 0; o < HSEG; ++o) {
-            float m0 = 0.f, m1 = 0.f, m2 = 0.f;
-#pragma unroll
-            for (int k = 0; k < 11; ++k) {
-                m0 = fmaf(w[k], av[o + k], m0);
-                m1 = fmaf(w[k], bv[o + k], m1);
-                m2 = fmaf(w[k], cv[o + k], m2);
+            for (int o = 0; o < HSEG; ++o) {
+                const int t = k - o;
+                if (t < 0 || t > 10) continue;
+                acc[o][0] = fmaf(w[t], a, acc[o][0]);
+                acc[o][1] = fmaf(w[t], b, acc[o][1]);
+                acc[o][2] = fmaf(w[t], cc, acc[o][2]);
             }
-            hs[0][r][c0 + o] = m0;
-            hs[1][r][c0 + o] = m1;
-            hs[2][r][c0 + o] = m2;
         }
+#pragma unroll
+        for (int o = 0; o < HSEG; ++o)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) hs[q][r][c0 + o] = acc[o][q];
     }
     __syncthreads();
     const float invM = 1.f / (float)((double)p.P * (double)HW);

@@ -338,9 +338,23 @@ __global__ void check_finite_kernel(const float *g, int64_t n, gs_train_state *s
 }
 
 template <int SHADOW>
-__global__ void __launch_bounds__(256) adam_kernel(float *p, float *g, float *m, float *v, int64_t n,
-                                                   gs_adam hp, const gs_train_state *st,
-                                                   void *shadow)
+__device__ __forceinline__ void adam_one(float &p, float g, float &m, float &v, const gs_adam &hp,
+                                         float bc1, float bc2, float inv)
+{
+    g *= inv;
+    m = fmaf(hp.beta1, m, (1.f - hp.beta1) * g);
+    v = fmaf(hp.beta2, v, (1.f - hp.beta2) * g * g);
+    p = p - hp.lr * (m / bc1) / (sqrtf(v / bc2) + hp.eps);
+}
+
+// Four parameters per thread and step (16-byte loads, all issued before any
+// store), then a scalar tail; the arithmetic per parameter is adam_one's.
+template <int SHADOW>
+__global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ p, float *__restrict__ g,
+                                                   float *__restrict__ m, float *__restrict__ v,
+                                                   int64_t n, gs_adam hp,
+                                                   const gs_train_state *__restrict__ st,
+                                                   void *__restrict__ shadow)
 {
     const bool skip = st->found_inf != 0;
     // bias corrections 1 - b^t as -expm1(t log b): no cancellation when b is close to 1
@@ -348,17 +362,39 @@ __global__ void __launch_bounds__(256) adam_kernel(float *p, float *g, float *m,
     const float bc1 = -expm1f((float)t * logf(hp.beta1));
     const float bc2 = -expm1f((float)t * logf(hp.beta2));
     const float inv = 1.f / st->loss_scale;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        float gi = g[i];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n4 = n / 4;
+    float4 *p4 = reinterpret_cast<float4 *>(p), *g4 = reinterpret_cast<float4 *>(g);
+    float4 *m4 = reinterpret_cast<float4 *>(m), *v4 = reinterpret_cast<float4 *>(v);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += stride) {
+        float4 gq = g4[q], mq = m4[q], vq = v4[q], pq = p4[q];
+        g4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (skip) continue;
+        adam_one<SHADOW>(pq.x, gq.x, mq.x, vq.x, hp, bc1, bc2, inv);
+        adam_one<SHADOW>(pq.y, gq.y, mq.y, vq.y, hp, bc1, bc2, inv);
+        adam_one<SHADOW>(pq.z, gq.z, mq.z, vq.z, hp, bc1, bc2, inv);
+        adam_one<SHADOW>(pq.w, gq.w, mq.w, vq.w, hp, bc1, bc2, inv);
+        m4[q] = mq;
+        v4[q] = vq;
+        p4[q] = pq;
+        if (SHADOW == GS_F16) {
+            __half2 *h = reinterpret_cast<__half2 *>(shadow) + 2 * q;
+            h[0] = __floats2half2_rn(pq.x, pq.y);
+            h[1] = __floats2half2_rn(pq.z, pq.w);
+        }
+        if (SHADOW == GS_BF16) {
+            __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(shadow) + 2 * q;
+            h[0] = __floats2bfloat162_rn(pq.x, pq.y);
+            h[1] = __floats2bfloat162_rn(pq.z, pq.w);
+        }
+    }
+    for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        float gi = g[i], mi = m[i], vi = v[i], pi = p[i];
         g[i] = 0.f;
         if (skip) continue;
-        gi *= inv;
-        float mi = fmaf(hp.beta1, m[i], (1.f - hp.beta1) * gi);
-        float vi = fmaf(hp.beta2, v[i], (1.f - hp.beta2) * gi * gi);
+        adam_one<SHADOW>(pi, gi, mi, vi, hp, bc1, bc2, inv);
         m[i] = mi;
         v[i] = vi;
-        float pi = p[i] - hp.lr * (mi / bc1) / (sqrtf(vi / bc2) + hp.eps);
         p[i] = pi;
         if (SHADOW == GS_F16) reinterpret_cast<__half *>(shadow)[i] = __float2half_rn(pi);
         if (SHADOW == GS_BF16) reinterpret_cast<__nv_bfloat16 *>(shadow)[i] = __float2bfloat16_rn(pi);
@@ -544,7 +580,11 @@ extern "C" gs_status adam_step(float *p, float *g, float *m, float *v, int64_t n
     GS_REQUIRE(shadow == nullptr || shadow_dtype == GS_F16 || shadow_dtype == GS_BF16,
                "adam_step: shadow dtype must be GS_F16 or GS_BF16");
     if (n == 0) return GS_OK;
-    int blocks = (int)std::min<int64_t>(ceil_div(n, 256), kNumSMs * 8);
+    GS_REQUIRE(aligned(p, 16) && aligned(g, 16) && aligned(m, 16) && aligned(v, 16) &&
+                   (shadow == nullptr || aligned(shadow, 8)),
+               "adam_step: arrays must be 16-byte aligned (shadow 8)");
+    int blocks = (int)std::min<int64_t>(ceil_div(n, 4 * 256), kNumSMs * 8);
+    blocks = std::max(blocks, 1);
     cudaStream_t s = as_stream(stream);
     note_launch();
     if (!shadow)

@@ -1,6 +1,8 @@
 // EWA projection + SH colour (Section 3.2, Eq. 2-3) and its reverse.
 // One thread per Gaussian handles all V views of a launch, so each Gaussian's
 // parameters (up to 236 bytes with SH degree 3) are read from HBM once.
+#include <type_traits>
+
 #include "common.cuh"
 #include "sh.cuh"
 
@@ -134,9 +136,11 @@ struct ViewLocal {
     float rgb_raw[3];
 };
 
+template <int DEG>
 __device__ __forceinline__ void project_view(const ProjectParams &p, const GaussLocal &G,
                                              const float *sh, const gs_camera &c, ViewLocal &L)
 {
+    constexpr int K = (DEG + 1) * (DEG + 1);
     L.valid = false;
     L.radius = 0;
     L.tiles = 0;
@@ -210,9 +214,10 @@ __device__ __forceinline__ void project_view(const ProjectParams &p, const Gauss
     float il = 1.f / L.dlen;
     L.dir = make_float3(d.x * il, d.y * il, d.z * il);
     float Y[16];
-    sh_basis(p.deg, L.dir.x, L.dir.y, L.dir.z, Y);
+    sh_basis(DEG, L.dir.x, L.dir.y, L.dir.z, Y);
     float r0 = 0.f, r1 = 0.f, r2 = 0.f;
-    for (int k = 0; k < p.K; ++k) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
         r0 = fmaf(Y[k], __ldg(sh + 3 * k), r0);
         r1 = fmaf(Y[k], __ldg(sh + 3 * k + 1), r1);
         r2 = fmaf(Y[k], __ldg(sh + 3 * k + 2), r2);
@@ -223,8 +228,10 @@ __device__ __forceinline__ void project_view(const ProjectParams &p, const Gauss
     L.valid = true;
 }
 
+template <int DEG>
 __global__ void __launch_bounds__(256) project_fwd_kernel(ProjectParams p)
 {
+    constexpr int K = (DEG + 1) * (DEG + 1);
     extern __shared__ gs_camera s_cams[];
     for (int k = threadIdx.x; k < p.V; k += blockDim.x) s_cams[k] = p.cams[k];
     __syncthreads();
@@ -232,10 +239,10 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ProjectParams p)
     if (i >= p.n) return;
     GaussLocal G;
     load_gauss(p, i, G);
-    const float *sh = p.sh + (int64_t)3 * p.K * i;
+    const float *sh = p.sh + (int64_t)3 * K * i;
     for (int v = 0; v < p.V; ++v) {
         ViewLocal L;
-        project_view(p, G, sh, s_cams[v], L);
+        project_view<DEG>(p, G, sh, s_cams[v], L);
         int64_t o = (int64_t)v * p.n + i;
         if (L.valid) {
             p.mean2d[o] = make_float2(L.u, L.v);
@@ -259,123 +266,100 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ProjectParams p)
     }
 }
 
-// FULL = false: gradients wrt mean and rotation of every Gaussian (Stage 1).
-// FULL = true: gradients wrt every parameter of Gaussians [first, first + count)
-// (Stage 2), written at row j = i - first.
-template <bool FULL>
-__global__ void __launch_bounds__(128) project_bwd_kernel(ProjectParams p)
+// One view's contribution to dL/dmu and dL/dSigma (everything but the
+// SH-coefficient and opacity terms) from that view's record gradient.
+template <int DEG>
+__device__ __forceinline__ void bwd_view(const GaussLocal &G, const float *sh, const gs_camera &c,
+                                         const ViewLocal &L, float4 g0, float4 g1, float *dmu,
+                                         float *dS)
 {
-    extern __shared__ gs_camera s_cams[];
-    for (int k = threadIdx.x; k < p.V; k += blockDim.x) s_cams[k] = p.cams[k];
-    __syncthreads();
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= (FULL ? p.count : p.n)) return;
-    const int64_t i = FULL ? p.first + j : j;
-    GaussLocal G;
-    load_gauss(p, i, G);
-    const float *sh = p.sh + (int64_t)3 * p.K * i;
-    float *dsh = FULL ? p.d_sh + (int64_t)3 * p.K * j : nullptr;
-    if (FULL)
-        for (int k = 0; k < 3 * p.K; ++k) dsh[k] = 0.f;
-    float dmu[3] = {0.f, 0.f, 0.f};
-    float dS[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma, symmetric (00 01 02 11 12 22)
-    float dop = 0.f;
-    for (int v = 0; v < p.V; ++v) {
-        const gs_camera &c = s_cams[v];
-        ViewLocal L;
-        project_view(p, G, sh, c, L);
-        if (!L.valid) continue;
-        const float4 *gp = reinterpret_cast<const float4 *>(p.grads + 8 * ((int64_t)v * p.n + i));
-        float4 g0 = gp[0], g1 = gp[1];
-        float du = g0.x, dv = g0.y, dA = g0.z, dB = g0.w, dC = g1.x;
-        float drgb[3] = {g1.y, g1.z, g1.w};
-        if (FULL) {
-            // SH coefficients: d rgb_raw / d sh_k = Y_k where the colour is not clamped
-            float Y[16];
-            sh_basis(p.deg, L.dir.x, L.dir.y, L.dir.z, Y);
-            for (int k = 0; k < p.K; ++k)
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    float du = g0.x, dv = g0.y, dA = g0.z, dB = g0.w, dC = g1.x;
+    float drgb[3] = {g1.y, g1.z, g1.w};
+    // colour -> direction -> mean
+    float wk[16];
 #pragma unroll
-                for (int ch = 0; ch < 3; ++ch)
-                    if (L.rgb_raw[ch] > 0.f) dsh[3 * k + ch] = fmaf(Y[k], drgb[ch], dsh[3 * k + ch]);
-            if (p.d_opacity) dop += p.d_opacity[(int64_t)v * p.n + i];
-        }
-        // colour -> direction -> mean
-        float wk[16];
-        for (int k = 0; k < p.K; ++k) {
-            float acc = 0.f;
+    for (int k = 0; k < K; ++k) {
+        float acc = 0.f;
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch)
-                if (L.rgb_raw[ch] > 0.f) acc = fmaf(drgb[ch], __ldg(sh + 3 * k + ch), acc);
-            wk[k] = acc;
-        }
-        float3 gd = sh_basis_grad_dot(p.deg, L.dir.x, L.dir.y, L.dir.z, wk);
-        float dd = L.dir.x * gd.x + L.dir.y * gd.y + L.dir.z * gd.z;
-        float il = 1.f / L.dlen;
-        dmu[0] += (gd.x - L.dir.x * dd) * il;
-        dmu[1] += (gd.y - L.dir.y * dd) * il;
-        dmu[2] += (gd.z - L.dir.z * dd) * il;
-        // 2D mean
-        float tz = L.t[2], itz = 1.f / tz, itz2 = itz * itz;
-        float dt0 = du * c.fx * itz;
-        float dt1 = dv * c.fy * itz;
-        float dt2 = -(du * c.fx * L.t[0] + dv * c.fy * L.t[1]) * itz2;
-        // conic -> 2D covariance
-        float a = L.a, b = L.b, cc = L.c;
-        float id2 = 1.f / (L.det * L.det);
-        float ga = (-cc * cc * dA + b * cc * dB - b * b * dC) * id2;
-        float gb = (2.f * b * cc * dA - (a * cc + b * b) * dB + 2.f * a * b * dC) * id2;
-        float gc = (-b * b * dA + a * b * dB - a * a * dC) * id2;
-        float G00 = ga, G01 = 0.5f * gb, G11 = gc;
-        // GT = G * T (2x3)
-        float GT[6];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            GT[j] = G00 * L.T[j] + G01 * L.T[3 + j];
-            GT[3 + j] = G01 * L.T[j] + G11 * L.T[3 + j];
-        }
-        // dSigma += T^T GT
-        dS[0] += L.T[0] * GT[0] + L.T[3] * GT[3];
-        dS[1] += L.T[0] * GT[1] + L.T[3] * GT[4];
-        dS[2] += L.T[0] * GT[2] + L.T[3] * GT[5];
-        dS[3] += L.T[1] * GT[1] + L.T[4] * GT[4];
-        dS[4] += L.T[1] * GT[2] + L.T[4] * GT[5];
-        dS[5] += L.T[2] * GT[2] + L.T[5] * GT[5];
-        // dT = 2 GT Sigma (2x3)
-        const float *S = G.Sig;
-        float dT[6];
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const float *q = GT + 3 * r;
-            dT[3 * r + 0] = 2.f * (q[0] * S[0] + q[1] * S[1] + q[2] * S[2]);
-            dT[3 * r + 1] = 2.f * (q[0] * S[1] + q[1] * S[3] + q[2] * S[4]);
-            dT[3 * r + 2] = 2.f * (q[0] * S[2] + q[1] * S[4] + q[2] * S[5]);
-        }
-        // T = J W  ->  dJ = dT W^T (only the four non-zero entries of J)
-        const float *Wm = c.viewmat;
-        float dJ00 = dT[0] * Wm[0] + dT[1] * Wm[1] + dT[2] * Wm[2];
-        float dJ02 = dT[0] * Wm[8] + dT[1] * Wm[9] + dT[2] * Wm[10];
-        float dJ11 = dT[3] * Wm[4] + dT[4] * Wm[5] + dT[5] * Wm[6];
-        float dJ12 = dT[3] * Wm[8] + dT[4] * Wm[9] + dT[5] * Wm[10];
-        dt2 += -c.fx * itz2 * dJ00 - c.fy * itz2 * dJ11;
-        if (L.clx) {
-            float ls = L.txz < 0.f ? -L.limx : L.limx;  // J02 = -fx ls / tz
-            dt2 += c.fx * ls * itz2 * dJ02;
-        } else {  // J02 = -fx tx / tz^2
-            dt0 += -c.fx * itz2 * dJ02;
-            dt2 += 2.f * c.fx * L.t[0] * itz2 * itz * dJ02;
-        }
-        if (L.cly) {
-            float ls = L.tyz < 0.f ? -L.limy : L.limy;
-            dt2 += c.fy * ls * itz2 * dJ12;
-        } else {
-            dt1 += -c.fy * itz2 * dJ12;
-            dt2 += 2.f * c.fy * L.t[1] * itz2 * itz * dJ12;
-        }
-        // t = W mu + t_w
-        dmu[0] += Wm[0] * dt0 + Wm[4] * dt1 + Wm[8] * dt2;
-        dmu[1] += Wm[1] * dt0 + Wm[5] * dt1 + Wm[9] * dt2;
-        dmu[2] += Wm[2] * dt0 + Wm[6] * dt1 + Wm[10] * dt2;
+        for (int ch = 0; ch < 3; ++ch)
+            if (L.rgb_raw[ch] > 0.f) acc = fmaf(drgb[ch], __ldg(sh + 3 * k + ch), acc);
+        wk[k] = acc;
     }
+    float3 gd = sh_basis_grad_dot(DEG, L.dir.x, L.dir.y, L.dir.z, wk);
+    float dd = L.dir.x * gd.x + L.dir.y * gd.y + L.dir.z * gd.z;
+    float il = 1.f / L.dlen;
+    dmu[0] += (gd.x - L.dir.x * dd) * il;
+    dmu[1] += (gd.y - L.dir.y * dd) * il;
+    dmu[2] += (gd.z - L.dir.z * dd) * il;
+    // 2D mean
+    float tz = L.t[2], itz = 1.f / tz, itz2 = itz * itz;
+    float dt0 = du * c.fx * itz;
+    float dt1 = dv * c.fy * itz;
+    float dt2 = -(du * c.fx * L.t[0] + dv * c.fy * L.t[1]) * itz2;
+    // conic -> 2D covariance
+    float a = L.a, b = L.b, cc = L.c;
+    float id2 = 1.f / (L.det * L.det);
+    float ga = (-cc * cc * dA + b * cc * dB - b * b * dC) * id2;
+    float gb = (2.f * b * cc * dA - (a * cc + b * b) * dB + 2.f * a * b * dC) * id2;
+    float gc = (-b * b * dA + a * b * dB - a * a * dC) * id2;
+    float G00 = ga, G01 = 0.5f * gb, G11 = gc;
+    // GT = G * T (2x3)
+    float GT[6];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        GT[j] = G00 * L.T[j] + G01 * L.T[3 + j];
+        GT[3 + j] = G01 * L.T[j] + G11 * L.T[3 + j];
+    }
+    // dSigma += T^T GT
+    dS[0] += L.T[0] * GT[0] + L.T[3] * GT[3];
+    dS[1] += L.T[0] * GT[1] + L.T[3] * GT[4];
+    dS[2] += L.T[0] * GT[2] + L.T[3] * GT[5];
+    dS[3] += L.T[1] * GT[1] + L.T[4] * GT[4];
+    dS[4] += L.T[1] * GT[2] + L.T[4] * GT[5];
+    dS[5] += L.T[2] * GT[2] + L.T[5] * GT[5];
+    // dT = 2 GT Sigma (2x3)
+    const float *S = G.Sig;
+    float dT[6];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const float *q = GT + 3 * r;
+        dT[3 * r + 0] = 2.f * (q[0] * S[0] + q[1] * S[1] + q[2] * S[2]);
+        dT[3 * r + 1] = 2.f * (q[0] * S[1] + q[1] * S[3] + q[2] * S[4]);
+        dT[3 * r + 2] = 2.f * (q[0] * S[2] + q[1] * S[4] + q[2] * S[5]);
+    }
+    // T = J W  ->  dJ = dT W^T (only the four non-zero entries of J)
+    const float *Wm = c.viewmat;
+    float dJ00 = dT[0] * Wm[0] + dT[1] * Wm[1] + dT[2] * Wm[2];
+    float dJ02 = dT[0] * Wm[8] + dT[1] * Wm[9] + dT[2] * Wm[10];
+    float dJ11 = dT[3] * Wm[4] + dT[4] * Wm[5] + dT[5] * Wm[6];
+    float dJ12 = dT[3] * Wm[8] + dT[4] * Wm[9] + dT[5] * Wm[10];
+    dt2 += -c.fx * itz2 * dJ00 - c.fy * itz2 * dJ11;
+    if (L.clx) {
+        float ls = L.txz < 0.f ? -L.limx : L.limx;  // J02 = -fx ls / tz
+        dt2 += c.fx * ls * itz2 * dJ02;
+    } else {  // J02 = -fx tx / tz^2
+        dt0 += -c.fx * itz2 * dJ02;
+        dt2 += 2.f * c.fx * L.t[0] * itz2 * itz * dJ02;
+    }
+    if (L.cly) {
+        float ls = L.tyz < 0.f ? -L.limy : L.limy;
+        dt2 += c.fy * ls * itz2 * dJ12;
+    } else {
+        dt1 += -c.fy * itz2 * dJ12;
+        dt2 += 2.f * c.fy * L.t[1] * itz2 * itz * dJ12;
+    }
+    // t = W mu + t_w
+    dmu[0] += Wm[0] * dt0 + Wm[4] * dt1 + Wm[8] * dt2;
+    dmu[1] += Wm[1] * dt0 + Wm[5] * dt1 + Wm[9] * dt2;
+    dmu[2] += Wm[2] * dt0 + Wm[6] * dt1 + Wm[10] * dt2;
+}
+
+// dL/dSigma -> dL/d(un-normalised quaternion) and dL/ds; writes d_mean and
+// d_quat of row j.
+__device__ __forceinline__ void bwd_finish(const ProjectParams &p, const GaussLocal &G, int64_t j,
+                                           const float *dmu, const float *dS, float *ds)
+{
     // Sigma = M M^T, M = R diag(s): dR = 2 dSigma M diag(s)
     float dSf[9] = {dS[0], dS[1], dS[2], dS[1], dS[3], dS[4], dS[2], dS[4], dS[5]};
     float M[9];
@@ -383,7 +367,8 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(ProjectParams p)
     for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int c = 0; c < 3; ++c) M[3 * r + c] = G.R[3 * r + c] * G.s[c];
-    float dR[9], ds[3] = {0.f, 0.f, 0.f};
+    float dR[9];
+    ds[0] = ds[1] = ds[2] = 0.f;
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
@@ -410,11 +395,131 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(ProjectParams p)
     reinterpret_cast<float4 *>(p.d_quat)[j] =
         make_float4((dqn[0] - w * dot) * iq, (dqn[1] - x * dot) * iq, (dqn[2] - y * dot) * iq,
                     (dqn[3] - z * dot) * iq);
+}
+
+// FULL = false: gradients wrt mean and rotation of every Gaussian (Stage 1).
+// FULL = true: gradients wrt every parameter of Gaussians [first, first + count)
+// (Stage 2), written at row j = i - first.
+template <bool FULL, int DEG>
+__global__ void __launch_bounds__(128) project_bwd_kernel(ProjectParams p)
+{
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    extern __shared__ gs_camera s_cams[];
+    for (int k = threadIdx.x; k < p.V; k += blockDim.x) s_cams[k] = p.cams[k];
+    __syncthreads();
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= (FULL ? p.count : p.n)) return;
+    const int64_t i = FULL ? p.first + j : j;
+    GaussLocal G;
+    load_gauss(p, i, G);
+    const float *sh = p.sh + (int64_t)3 * K * i;
+    float *dsh = FULL ? p.d_sh + (int64_t)3 * K * j : nullptr;
+    if (FULL)
+#pragma unroll
+        for (int k = 0; k < 3 * K; ++k) dsh[k] = 0.f;
+    float dmu[3] = {0.f, 0.f, 0.f};
+    float dS[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma, symmetric (00 01 02 11 12 22)
+    float dop = 0.f;
+    for (int v = 0; v < p.V; ++v) {
+        const gs_camera &c = s_cams[v];
+        ViewLocal L;
+        project_view<DEG>(p, G, sh, c, L);
+        if (!L.valid) continue;
+        const float4 *gp = reinterpret_cast<const float4 *>(p.grads + 8 * ((int64_t)v * p.n + i));
+        float4 g0 = gp[0], g1 = gp[1];
+        float drgb[3] = {g1.y, g1.z, g1.w};
+        if (FULL) {
+            // SH coefficients: d rgb_raw / d sh_k = Y_k where the colour is not clamped
+            float Y[16];
+            sh_basis(DEG, L.dir.x, L.dir.y, L.dir.z, Y);
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch)
+                    if (L.rgb_raw[ch] > 0.f) dsh[3 * k + ch] = fmaf(Y[k], drgb[ch], dsh[3 * k + ch]);
+            if (p.d_opacity) dop += p.d_opacity[(int64_t)v * p.n + i];
+        }
+        bwd_view<DEG>(G, sh, c, L, g0, g1, dmu, dS);
+    }
+    float ds[3];
+    bwd_finish(p, G, j, dmu, dS, ds);
     if (FULL) {
         p.d_scale[3 * j] = ds[0];
         p.d_scale[3 * j + 1] = ds[1];
         p.d_scale[3 * j + 2] = ds[2];
         p.d_ologit[j] = dop * G.op * (1.f - G.op);  // opacity = sigmoid(logit)
+    }
+}
+
+// Stage-1 reverse with the views of a Gaussian in parallel: VP adjacent lanes
+// (VP the power of two >= V, <= 32) take one Gaussian, lane v its view v;
+// the per-view sums of dL/dmu and dL/dSigma are reduced over the lanes with
+// shuffles and the group's first lane finishes the Gaussian.
+template <int DEG, int VP>
+__global__ void __launch_bounds__(128) project_bwd_views_kernel(ProjectParams p)
+{
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    extern __shared__ gs_camera s_cams[];
+    for (int k = threadIdx.x; k < p.V; k += blockDim.x) s_cams[k] = p.cams[k];
+    __syncthreads();
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = t / VP;
+    const int v = (int)(t % VP);
+    const bool live = i < p.n;
+    float dmu[3] = {0.f, 0.f, 0.f};
+    float dS[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    GaussLocal G;
+    if (live) {
+        load_gauss(p, i, G);
+        if (v < p.V) {
+            const float *sh = p.sh + (int64_t)3 * K * i;
+            const gs_camera &c = s_cams[v];
+            ViewLocal L;
+            project_view<DEG>(p, G, sh, c, L);
+            if (L.valid) {
+                const float4 *gp = reinterpret_cast<const float4 *>(p.grads + 8 * ((int64_t)v * p.n + i));
+                bwd_view<DEG>(G, sh, c, L, gp[0], gp[1], dmu, dS);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = VP / 2; o > 0; o >>= 1) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) dmu[a] += __shfl_xor_sync(0xffffffffu, dmu[a], o);
+#pragma unroll
+        for (int a = 0; a < 6; ++a) dS[a] += __shfl_xor_sync(0xffffffffu, dS[a], o);
+    }
+    if (live && v == 0) {
+        float ds[3];
+        bwd_finish(p, G, i, dmu, dS, ds);
+    }
+}
+
+template <int DEG>
+static void launch_bwd_views(const ProjectParams &p, size_t shm, cudaStream_t s)
+{
+    const int threads = 128;
+    auto go = [&](auto vp) {
+        constexpr int VP = decltype(vp)::value;
+        const int blocks = (int)ceil_div(p.n * VP, threads);
+        project_bwd_views_kernel<DEG, VP><<<blocks, threads, shm, s>>>(p);
+    };
+    if (p.V <= 1) go(std::integral_constant<int, 1>());
+    else if (p.V <= 2) go(std::integral_constant<int, 2>());
+    else if (p.V <= 4) go(std::integral_constant<int, 4>());
+    else if (p.V <= 8) go(std::integral_constant<int, 8>());
+    else if (p.V <= 16) go(std::integral_constant<int, 16>());
+    else go(std::integral_constant<int, 32>());
+}
+
+template <bool FULL>
+static void launch_bwd(const ProjectParams &p, int blocks, int threads, size_t shm, cudaStream_t s)
+{
+    switch (p.deg) {
+    case 0: project_bwd_kernel<FULL, 0><<<blocks, threads, shm, s>>>(p); break;
+    case 1: project_bwd_kernel<FULL, 1><<<blocks, threads, shm, s>>>(p); break;
+    case 2: project_bwd_kernel<FULL, 2><<<blocks, threads, shm, s>>>(p); break;
+    default: project_bwd_kernel<FULL, 3><<<blocks, threads, shm, s>>>(p); break;
     }
 }
 
@@ -469,7 +574,14 @@ extern "C" gs_status gs_project(const gs_gaussians *g, const gs_camera *d_cams, 
     int threads = 256;
     int blocks = (int)ceil_div(p.n, threads);
     note_launch();
-    project_fwd_kernel<<<blocks, threads, sizeof(gs_camera) * V, as_stream(stream)>>>(p);
+    const size_t shm = sizeof(gs_camera) * V;
+    cudaStream_t s = as_stream(stream);
+    switch (p.deg) {
+    case 0: project_fwd_kernel<0><<<blocks, threads, shm, s>>>(p); break;
+    case 1: project_fwd_kernel<1><<<blocks, threads, shm, s>>>(p); break;
+    case 2: project_fwd_kernel<2><<<blocks, threads, shm, s>>>(p); break;
+    default: project_fwd_kernel<3><<<blocks, threads, shm, s>>>(p); break;
+    }
     return launch_status("gs_project");
 }
 
@@ -489,7 +601,18 @@ extern "C" gs_status gs_project_bwd(const gs_gaussians *g, const gs_camera *d_ca
     int threads = 128;
     int blocks = (int)ceil_div(p.n, threads);
     note_launch();
-    project_bwd_kernel<false><<<blocks, threads, sizeof(gs_camera) * V, as_stream(stream)>>>(p);
+    const size_t shm = sizeof(gs_camera) * V;
+    cudaStream_t s = as_stream(stream);
+    if (V <= 32) {
+        switch (p.deg) {
+        case 0: launch_bwd_views<0>(p, shm, s); break;
+        case 1: launch_bwd_views<1>(p, shm, s); break;
+        case 2: launch_bwd_views<2>(p, shm, s); break;
+        default: launch_bwd_views<3>(p, shm, s); break;
+        }
+    } else {
+        launch_bwd<false>(p, blocks, threads, shm, s);
+    }
     return launch_status("gs_project_bwd");
 }
 
@@ -520,6 +643,6 @@ extern "C" gs_status gs_project_bwd_full(const gs_gaussians *g, const gs_camera 
     int threads = 128;
     int blocks = (int)ceil_div(count, threads);
     note_launch();
-    project_bwd_kernel<true><<<blocks, threads, sizeof(gs_camera) * V, as_stream(stream)>>>(p);
+    launch_bwd<true>(p, blocks, threads, sizeof(gs_camera) * V, as_stream(stream));
     return launch_status("gs_project_bwd_full");
 }
