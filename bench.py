@@ -201,6 +201,18 @@ def config_dict(scene, parallelism):
             "l2": "inputs larger than L2 (no flush)"}
 
 
+def aggregate_timing(ms, world, device):
+    """Max over ranks of the time per step (every rank has passed the same
+    barrier-bracketed region) and the whole-job seconds per frame: each rank
+    trains its own frames, so the job finishes world frames per max time."""
+    import torch
+    t = torch.tensor([float(ms)], device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, ms_max * ITERS_PER_FRAME / 1e3 / world
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_ours(args):
     import torch
@@ -350,11 +362,7 @@ def run_ours(args):
                               "pairs": st.raster.count()}), flush=True)
         return
     st.raster.check()
-    ms_all = torch.tensor([ms], device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(ms_all, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(ms_all.item())
-    s_per_frame = ms_max * ITERS_PER_FRAME / 1e3 / world  # whole-job: frames of all ranks
+    ms_max, s_per_frame = aggregate_timing(ms, world, dev)
 
     # per-stage breakdown (separate, instrumented pass)
     ev.clear()

@@ -144,6 +144,12 @@ GS_API uint64_t gs_launch_count(void);
 /* Number of tensor-core MLP blocks that gave up a bounded wait on their MMA
  * completion barrier (0 in normal operation; reads device memory, syncs). */
 GS_API int gs_tc_timeouts(void);
+/* Failure-detection self-test (the paper has no counterpart): one block waits,
+ * with the tensor-core kernels' bounded mbarrier wait, on a barrier that
+ * nothing arrives on, giving up after `tries` attempts (1 .. 2^20); writes
+ * GS_ERR_TIMEOUT to *d_status (device int32) when the wait ran out (always,
+ * by construction) and GS_OK otherwise.  The context stays usable. */
+GS_API gs_status gs_tc_wait_selftest(uint32_t tries, int32_t *d_status, gs_stream stream);
 
 /* ------------------------------------------------------------ projection */
 

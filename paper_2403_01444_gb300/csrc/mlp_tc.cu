@@ -708,6 +708,26 @@ extern "C" gs_status ntc_fused_bwd(const float *mean, const float *quat, const f
     return launch_bwd<bf16, true>(p, as_stream(stream));
 }
 
+// Self-test of the bounded wait: one block initialises an mbarrier that
+// nothing arrives on and waits for it with the MLP kernels' wait helper.
+__global__ void tc_wait_selftest_kernel(uint32_t tries, int32_t *status)
+{
+    __shared__ __align__(8) unsigned long long mbar;
+    const uint32_t m = gs3::tc::smem_u32(&mbar);
+    if (threadIdx.x == 0) gs3::tc::mbar_init(m, 1);
+    __syncthreads();
+    const bool ok = __syncthreads_and(gs3::tc::mbar_wait(m, 0u, tries));
+    if (threadIdx.x == 0) *status = ok ? GS_OK : GS_ERR_TIMEOUT;
+}
+
+extern "C" gs_status gs_tc_wait_selftest(uint32_t tries, int32_t *d_status, gs_stream stream)
+{
+    GS_REQUIRE(d_status && tries > 0 && tries <= (1u << 20), "gs_tc_wait_selftest: bad arguments");
+    note_launch();
+    tc_wait_selftest_kernel<<<1, 128, 0, as_stream(stream)>>>(tries, d_status);
+    return launch_status("gs_tc_wait_selftest");
+}
+
 extern "C" int gs_tc_timeouts(void)
 {
     int v = 0;

@@ -431,3 +431,8 @@ def gs_sh_rotate(quat_from, quat_to, sh_in, n, sh_deg, sh_out, stream=None):
     _check("gs_sh_rotate", lib().gs_sh_rotate(_ptr(quat_from), _ptr(quat_to), _ptr(sh_in), c_int64(n),
                                               c_int(sh_deg), _ptr(sh_out), _stream(stream)))
 
+
+def gs_tc_wait_selftest(tries, d_status, stream=None):
+    _check("gs_tc_wait_selftest", lib().gs_tc_wait_selftest(ctypes.c_uint32(tries), _ptr(d_status),
+                                                            _stream(stream)))
+
