@@ -106,11 +106,17 @@ __global__ void __launch_bounds__(SORT_THREADS) scan_digit_rows_kernel(uint32_t 
     if (threadIdx.x == 0) hist[(int64_t)RADIX * G + d] = s_carry;
 }
 
+// Ranked scatter of one pass.  Each tile of SORT_TILE items is first put in
+// digit order in shared memory (stable), then written out so consecutive
+// threads store consecutive positions of each digit's run (coalesced).
 __global__ void __launch_bounds__(SORT_THREADS, 4) radix_scatter_kernel(SortPass s)
 {
     __shared__ uint32_t s_off[RADIX];
     __shared__ uint32_t s_tot[RADIX];
+    __shared__ uint32_t s_lst[RADIX];
+    __shared__ uint32_t s_ws[SORT_WARPS];
     __shared__ uint32_t s_wh[SORT_WARPS][RADIX];
+    __shared__ uint32_t s_k[SORT_TILE], s_v[SORT_TILE];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;
     int64_t beg, end;
@@ -161,16 +167,37 @@ __global__ void __launch_bounds__(SORT_THREADS, 4) radix_scatter_kernel(SortPass
                 run += c;
             }
             s_tot[tid] = run;
+            // block-local start of digit tid: exclusive scan of the totals
+            uint32_t inc = run;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            if (lane == 31) s_ws[warp] = inc;
+            __syncthreads();
+            uint32_t before = 0;
+            for (int w = 0; w < warp; ++w) before += s_ws[w];
+            s_lst[tid] = before + inc - run;
         }
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < SORT_ITEMS; ++j) {
             uint32_t d = dig[j];
             if (d < RADIX) {
-                uint32_t pos = s_off[d] + s_wh[warp][d] + rank[j];
-                s.kout[pos] = key[j];
-                s.vout[pos] = val[j];
+                uint32_t lp = s_lst[d] + s_wh[warp][d] + rank[j];
+                s_k[lp] = key[j];
+                s_v[lp] = val[j];
             }
+        }
+        __syncthreads();
+        const int cnt = (int)min((int64_t)SORT_TILE, end - t0);
+        for (int i = tid; i < cnt; i += SORT_THREADS) {
+            const uint32_t k = s_k[i], v = s_v[i];
+            const uint32_t d = digit_of(s, k, v);
+            const uint32_t pos = s_off[d] + ((uint32_t)i - s_lst[d]);
+            s.kout[pos] = k;
+            s.vout[pos] = v;
         }
         __syncthreads();
         s_off[tid] += s_tot[tid];

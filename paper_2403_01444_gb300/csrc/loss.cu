@@ -117,7 +117,9 @@ __global__ void __launch_bounds__(LTHREADS) ssim_fwd_kernel(LossParams p)
             f[m][o] = acc;
         }
     }
-    double ssum = 0.0, lsum = 0.0;
+    // per-thread and per-warp sums in FP32 (at most VSEG * 32 terms), the
+    // block's and the final reduction in FP64
+    float ssum = 0.f, lsum = 0.f;
     const int gx = x0 + c;
 #pragma unroll
     for (int o = 0; o < VSEG; ++o) {
@@ -136,8 +138,8 @@ __global__ void __launch_bounds__(LTHREADS) ssim_fwd_kernel(LossParams p)
         p.ca[oo] = ds_dmx - 2.f * mx * ds_dsxx - my * ds_dsxy;
         p.cb[oo] = ds_dsxx;
         p.cc[oo] = ds_dsxy;
-        ssum += (double)sv;
-        lsum += (double)fabsf(sx[r + LH][c + LH] - sy[r + LH][c + LH]);
+        ssum += sv;
+        lsum += fabsf(sx[r + LH][c + LH] - sy[r + LH][c + LH]);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -145,8 +147,8 @@ __global__ void __launch_bounds__(LTHREADS) ssim_fwd_kernel(LossParams p)
         lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
     }
     if ((tid & 31) == 0) {
-        red[0][tid >> 5] = ssum;
-        red[1][tid >> 5] = lsum;
+        red[0][tid >> 5] = (double)ssum;
+        red[1][tid >> 5] = (double)lsum;
     }
     __syncthreads();
     if (tid == 0) {
