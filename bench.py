@@ -731,6 +731,28 @@ def ctypes_u64():
 FLOPS_TESTED, FLOPS_FWD_ADDED, FLOPS_BWD_ADDED = 12, 9, 47
 
 
+def recorded_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the ncu capture summarised under
+    profiles/ (dram__bytes_read.sum + dram__bytes_write.sum), or None when no
+    capture is recorded or the kernel's sources changed since it was taken."""
+    import glob
+    import hashlib
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", kernel + "_traffic_*.md"))):
+        fields = {}
+        for line in open(path):
+            if ":" in line and not line.startswith(("|", "#", " ")):
+                k, v = line.split(":", 1)
+                fields[k.strip()] = v.strip()
+        if "traffic_bytes_per_launch" not in fields or "sources_sha256" not in fields:
+            continue
+        h = hashlib.sha256()
+        for f in fields.get("sources", "").split():
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        if h.hexdigest() == fields["sources_sha256"]:
+            return int(fields["traffic_bytes_per_launch"])
+    return None
+
+
 def roofline_for(stage, ms, pairs, pair_counts, n, V, W, H, cfg, hbm_gbs, src, sm_mhz):
     """Roofline of one launch of the stage's kernels: compositing is bound by
     FP32 arithmetic (FLOPs of the evaluated pairs over the FP32 FMA peak of
@@ -744,7 +766,8 @@ def roofline_for(stage, ms, pairs, pair_counts, n, V, W, H, cfg, hbm_gbs, src, s
         achieved = flops / (ms * 1e-3) / 1e12
         peak = kNumSMs * 128 * 2 * sm_mhz * 1e6 / 1e12
         return {"bound": "alu", "kernel": stage, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": recorded_traffic(stage),
                 "algorithmic_flops": flops, "pairs_evaluated": tested, "pairs_added": added,
                 "ms": ms, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_mhz}
     K = (cfg.sh_deg + 1) ** 2
@@ -761,7 +784,7 @@ def roofline_for(stage, ms, pairs, pair_counts, n, V, W, H, cfg, hbm_gbs, src, s
     }.get(stage, 0)
     achieved = bytes_ / (ms * 1e-3) / 1e9
     return {"bound": "hbm", "kernel": stage, "achieved": achieved, "peak": hbm_gbs,
-            "unit": "GB/s", "frac": achieved / hbm_gbs, "traffic": None,
+            "unit": "GB/s", "frac": achieved / hbm_gbs, "traffic": recorded_traffic(stage),
             "algorithmic_bytes": bytes_, "ms": ms, "peak_source": src}
 
 
