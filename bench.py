@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-converge", action="store_true", help="skip the equal-PSNR comparison")
     ap.add_argument("--no-render", action="store_true", help="skip the render-only measurement")
     ap.add_argument("--no-stage2", action="store_true", help="skip the Stage-2 measurement")
+    ap.add_argument("--no-large", action="store_true", help="skip the 1M-Gaussian, 16-view run")
     ap.add_argument("--stream-frames", type=int, default=3,
                     help="frames of the streaming run (0: skip)")
     ap.add_argument("--bin", type=int, default=0,
@@ -504,6 +505,11 @@ def run_ours(args):
         graphs = None
         torch.cuda.empty_cache()
         stage2 = stage2_workload(dev)
+    large = None
+    if not args.no_large and rank == 0:
+        graphs = None
+        torch.cuda.empty_cache()
+        large = large_workload(dev)
     stream_res = None
     if args.stream_frames > 0 and rank == 0:
         graphs = None
@@ -533,7 +539,7 @@ def run_ours(args):
                 "warmup_loss": wl, "warmup_s": t_warm,
                 "roofline": roof, "raster_fwd_bwd_roofline": raster_roof,
                 "render_only": render_only, "bin_autotune": tune, "bin_tiles": bin_side,
-                "stage2": stage2, "stream": stream_res,
+                "stage2": stage2, "stream": stream_res, "large": large,
                 "paper_context": {"s_per_frame": 12.0, "fps_render": 200,
                                   "hardware": "one RTX 3090", "workload": "N3DV, real video",
                                   "note": "context only: other hardware, data and precision"},
@@ -625,6 +631,52 @@ def stage2_workload(dev, warm_iters=300):
             "ms_total": ms, "ms_per_iter": ms / 100, "wall_s": wall, "spawned": spawned,
             "added_final": added_final, "psnr_train_views_stage1": p1, "psnr_train_views_stage2": p2,
             "random_spawn_ablation": {"psnr_train_views": p_rand, "added_final": n_rand}}
+
+
+def large_workload(dev, iters=20):
+    """The 1M-Gaussian workload: all 16 views of 1920x1080 rendered in one
+    launch per Stage-1 iteration, the whole iteration (cache, projection,
+    binning, compositing, loss, reverse, Adam) replayed as one CUDA graph,
+    mixed precision; iters timed iterations after the capture."""
+    import torch
+    from paper_2403_01444_gb300 import gs3, scenes
+    from paper_2403_01444_gb300.engine import NTC, Rasterizer, Stage1, warmup
+    scene = scenes.make_scene(5)
+    cfg = scene.cfg
+    W, H, V = cfg.W, cfg.H, cfg.views_per_batch
+    G = gs3.Gaussians.from_numpy(scene.prev)
+    Gt = gs3.Gaussians.from_numpy(scene.target)
+    cd = gs3.cameras_to_device(scene.cams)
+    rt = Rasterizer(Gt.n, V, W, H, 1 << 24, dev)
+    rt.fit_capacity(Gt, cd, margin=1.2)
+    tg = rt.img.clone()
+    del rt
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(13)
+    grid = gs3.hashgrid()
+    table = rng.uniform(-1e-4, 1e-4, size=(gs3.ntc_hashgrid_entries(grid), 2)).astype(np.float32)
+    Ws = [w.astype(np.float32) for w in scenes.random_mlp([32, 64, 64, 7], rng)]
+    ntc = NTC(table, Ws, grid, gs3.GS_MLP_BF16, dev)
+    warmup(ntc, G, iters=300)
+    st = Stage1(G, ntc, V, W, H, capacity=1 << 24)
+    pairs = st.raster.fit_capacity(G, cd, *st.transform(), margin=1.3)
+    graph = st.capture([(cd, tg)])[0]
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(iters):
+        graph.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    st.raster.check()
+    ms = e0.elapsed_time(e1) / iters
+    return {"workload": "1M Gaussians SH3, 16 views 1920x1080 in one launch per iteration, "
+                        "whole iteration one CUDA graph, mixed precision",
+            "ms_per_iter": ms, "s_per_frame": ms * ITERS_PER_FRAME / 1e3,
+            "bin_pairs_per_iter": int(pairs), "pixels_per_iter": V * W * H}
 
 
 def stream_workload(dev, n_frames, warm_table_mlp, ntc):

@@ -1,5 +1,5 @@
 """Parity at the benchmark's full sizes, in the launch configuration the
-benchmark times (bins of 8x8 tiles, 4-view launches where a view is
+benchmark times (bins of 4x4 tiles, 4-view launches where a view is
 compared), on outputs the FP64 oracle can compute in seconds: one full view
 of the 250K-Gaussian 1352x1014 and the 1M-Gaussian 1920x1080 workloads, the
 full-resolution binning of one view, and the mixed-precision image error of
@@ -62,7 +62,7 @@ def test_full_size_view_render_and_gradients(cfg_index, view):
     r = oracle.render(g, cams, window=win)
     G = gs3.Gaussians.from_numpy(g)
     cd = gs3.cameras_to_device(cams)
-    rast = Rasterizer(g.n, 1, W, H, 1 << 22, DEV)  # bins of 8x8 tiles, as timed
+    rast = Rasterizer(g.n, 1, W, H, 1 << 22, DEV, bin=4)  # bins of 4x4 tiles, as timed
     rast.fit_capacity(G, cd)
     img = rast.img.cpu().numpy()
     ok = (r["ambig"] == 0) & crop[None]
