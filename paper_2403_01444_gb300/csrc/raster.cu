@@ -50,13 +50,17 @@ __device__ __forceinline__ void flush_stats(unsigned long long *stats, uint32_t 
 
 // power and alpha of one (pixel, Gaussian) pair.  Written with explicit
 // roundings so the forward and the reverse pass take bit-identical decisions.
+// The offset monomials dx^2, dx dy, dy^2 are returned for the reverse pass.
 __device__ __forceinline__ float pair_power(float2 xy, float4 co, float px, float py, float &dx,
-                                            float &dy)
+                                            float &dy, float &dxx, float &dxy, float &dyy)
 {
     dx = __fsub_rn(px, xy.x);
     dy = __fsub_rn(py, xy.y);
-    float q = fmaf(co.z, __fmul_rn(dy, dy), __fmul_rn(co.x, __fmul_rn(dx, dx)));
-    return fmaf(-0.5f, q, -__fmul_rn(co.y, __fmul_rn(dx, dy)));
+    dxx = __fmul_rn(dx, dx);
+    dxy = __fmul_rn(dx, dy);
+    dyy = __fmul_rn(dy, dy);
+    float q = fmaf(co.z, dyy, __fmul_rn(co.x, dxx));
+    return fmaf(-0.5f, q, -__fmul_rn(co.y, dxy));
 }
 
 __device__ __forceinline__ float pair_alpha_raw(float4 co, float power)
@@ -180,7 +184,8 @@ __global__ void __launch_bounds__(FT) raster_fwd_kernel(RasterParams p)
             float dx, dy;
             float4 co = s_co[j];
             if (STATS) ++n_tested;
-            float power = pair_power(s_xy[j], co, pxf, pyf, dx, dy);
+            float dxx, dxy, dyy;
+            float power = pair_power(s_xy[j], co, pxf, pyf, dx, dy, dxx, dxy, dyy);
             if (power > 0.f) continue;
             float alpha = fminf(kAlphaCap, pair_alpha_raw(co, power));
             if (alpha < kAlphaMin) continue;
@@ -249,8 +254,8 @@ template <bool WANT_OP>
 __device__ __forceinline__ bool unblend_one(PixBwd &P, float2 xy, float4 co, float4 c,
                                             float pxf, float pyf, float *v)
 {
-    float dx, dy;
-    float power = pair_power(xy, co, pxf, pyf, dx, dy);
+    float dx, dy, dxx, dxy, dyy;
+    float power = pair_power(xy, co, pxf, pyf, dx, dy, dxx, dxy, dyy);
     if (power > 0.f) return false;
     float G = __expf(power);
     float araw = __fmul_rn(co.w, G);
@@ -266,15 +271,30 @@ __device__ __forceinline__ bool unblend_one(PixBwd &P, float2 xy, float4 co, flo
     P.B1 = fmaf(alpha, c.y - P.B1, P.B1);
     P.B2 = fmaf(alpha, c.z - P.B2, P.B2);
     if (araw < kAlphaCap) {
+        // moments of dL/dpower over the pair offsets; the record's mean and
+        // conic gradients are linear in them and formed once per tile
         float dpow = dalpha * alpha;
-        v[0] = fmaf(dpow, co.x * dx + co.y * dy, v[0]);
-        v[1] = fmaf(dpow, co.z * dy + co.y * dx, v[1]);
-        v[2] = fmaf(-0.5f * dpow, dx * dx, v[2]);
-        v[3] = fmaf(-dpow, dx * dy, v[3]);
-        v[4] = fmaf(-0.5f * dpow, dy * dy, v[4]);
+        v[0] = fmaf(dpow, dx, v[0]);
+        v[1] = fmaf(dpow, dy, v[1]);
+        v[2] = fmaf(dpow, dxx, v[2]);
+        v[3] = fmaf(dpow, dxy, v[3]);
+        v[4] = fmaf(dpow, dyy, v[4]);
         if (WANT_OP) v[8] = fmaf(dalpha, G, v[8]);
     }
     return true;
+}
+
+// Record gradients from the tile sums of the moments: with power =
+// -0.5 (A dx^2 + C dy^2) - B dx dy and dx = px - u,
+//   dL/du = A S_x + B S_y,  dL/dv = C S_y + B S_x,
+//   dL/dA = -S_xx / 2,  dL/dB = -S_xy,  dL/dC = -S_yy / 2,
+// S_. = sum of dL/dpower times the offsets' monomials.  h = 0 holds
+// (S_x, S_y, S_xx, S_xy), h = 1 holds (S_yy, r, g, b).
+__device__ __forceinline__ float4 moments_to_grads(float4 s, float4 co, int h)
+{
+    if (h == 0)
+        return make_float4(fmaf(co.x, s.x, co.y * s.y), fmaf(co.z, s.y, co.y * s.x), -0.5f * s.z, -s.w);
+    return make_float4(-0.5f * s.x, s.y, s.z, s.w);
 }
 
 template <bool WANT_OP, bool BINNED, int PPT, bool STATS>
@@ -398,7 +418,8 @@ __global__ void __launch_bounds__(256 / PPT) raster_bwd_kernel(RasterParams p)
                     sum.w += s_part[w][j][h + 3];
                 }
                 if (sum.x != 0.f || sum.y != 0.f || sum.z != 0.f || sum.w != 0.f)
-                    atomicAdd(reinterpret_cast<float4 *>(p.grads + 8 * (vb + s_g[clo + j]) + h), sum);
+                    atomicAdd(reinterpret_cast<float4 *>(p.grads + 8 * (vb + s_g[clo + j]) + h),
+                              moments_to_grads(sum, s_co[clo + j], h));
             }
             if (WANT_OP) {
                 for (int j = tid; j < ccnt; j += NT) {
