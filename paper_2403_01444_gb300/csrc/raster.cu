@@ -180,6 +180,7 @@ __global__ void __launch_bounds__(FT) raster_fwd_kernel(RasterParams p)
                                        __int_as_float(k));
         }
         __syncthreads();
+#pragma unroll 2
         for (int j = 0; !done && j < cnt; ++j) {
             float dx, dy;
             float4 co = s_co[j];
@@ -372,6 +373,7 @@ __global__ void __launch_bounds__(256 / PPT) raster_bwd_kernel(RasterParams p)
         __syncthreads();
         for (int chi = cnt; chi > 0; chi -= BWD_CHUNK) {
             const int clo = max(0, chi - BWD_CHUNK);
+#pragma unroll 2
             for (int j = chi - 1; j >= clo; --j) {
                 float v[NV];
 #pragma unroll
