@@ -471,7 +471,9 @@ class Streamer:
                  Vb: int, W: int, H: int, heldout_dev=None, stage2: bool = True,
                  iters1: int = 150, iters2: int = 100, added_capacity: int = 300_000,
                  device="cuda", bin: int = DEFAULT_BIN, graphs: bool = True,
-                 sh_rotation: bool = True):
+                 sh_rotation: bool = True, save_dir: Optional[str] = None):
+        self.frames_done = 0
+        self.save_dir = save_dir
         clone = lambda t: t.clone()
         self.g = Gaussians(clone(g0.mean), clone(g0.quat), g0.scale, g0.opacity_logit, clone(g0.sh),
                            g0.sh_deg)
@@ -550,8 +552,11 @@ class Streamer:
         t_all = time.perf_counter()
         mt, qt = self._stage1(get(0))
         for t in range(n_frames):
-            rec = {"frame": t + 1}
+            rec = {"frame": self.frames_done + 1}
             main.synchronize()  # frame t's Stage 1 is done
+            # the frame's cache as stored (FP16 table, BF16 MLP), before the
+            # next frame's Stage 1 restarts it from the warm-up parameters
+            cache = (self.ntc.table.shadow.clone(), self.ntc.mlp.shadow.clone())
             if heldout_gt is not None and self.heldout is not None:
                 # the previous frame's Gaussians unchanged
                 rec["psnr_carried"] = self._psnr(self.g, heldout_gt[t])
@@ -581,10 +586,51 @@ class Streamer:
                     rec["added"] = self.st2.n_add
                 self.side.synchronize()
             rec["storage_bytes"] = cache_bytes + rec.get("added", 0) * 4 * (11 + 3 * K)
+            if self.save_dir is not None:
+                rec["file"] = self._save_frame(rec["frame"], cache)
             records.append(rec)
+            self.frames_done += 1
         torch.cuda.synchronize()
         self.wall_s = time.perf_counter() - t_all
         return records
+
+
+    def _save_frame(self, frame: int, cache) -> str:
+        """The frame's record (what the next frame does not carry): the cache
+        that transforms the previous frame's Gaussians and the frame's added
+        Gaussians, as npz in save_dir."""
+        import os
+        os.makedirs(self.save_dir, exist_ok=True)
+        path = os.path.join(self.save_dir, "frame_%05d.npz" % frame)
+        added = (self.st2.rows[self.st2.cur][:self.st2.n_add].cpu().numpy()
+                 if self.st2 is not None else np.zeros((0, 11 + 3 * (self.g.sh_deg + 1) ** 2), np.float32))
+        np.savez(path, table_f16=cache[0].cpu().numpy(),
+                 mlp_bf16=cache[1].view(torch.int16).cpu().numpy(), added_rows=added,
+                 sh_deg=self.g.sh_deg)
+        return path
+
+    def checkpoint(self, path: str):
+        """Everything a later run needs to continue the video from the next
+        frame: the carried Gaussians (transformed means and rotations, SH as
+        rotated) and the cache's warm-up parameters."""
+        g = self.g
+        np.savez(path, frames_done=self.frames_done, mean=g.mean.cpu().numpy(),
+                 quat=g.quat.cpu().numpy(), sh=g.sh.cpu().numpy(),
+                 scale=g.scale.cpu().numpy(), opacity_logit=g.opacity_logit.cpu().numpy(),
+                 sh_deg=g.sh_deg, warm_table=self.warm[0].cpu().numpy(),
+                 warm_mlp=self.warm[1].cpu().numpy())
+
+    def resume(self, path: str):
+        """Continue from a checkpoint written by checkpoint()."""
+        d = np.load(path)
+        dev = self.g.mean.device
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+        assert int(d["sh_deg"]) == self.g.sh_deg and d["mean"].shape[0] == self.g.n
+        self.g.mean.copy_(t(d["mean"]))
+        self.g.quat.copy_(t(d["quat"]))
+        self.g.sh.copy_(t(d["sh"]))
+        self.warm = (t(d["warm_table"]), t(d["warm_mlp"]))
+        self.frames_done = int(d["frames_done"])
 
 
 def render_dev(g: Gaussians, cams_dev, V: int, W: int, H: int, mean=None, quat=None,
