@@ -158,8 +158,9 @@ GS_API gs_status gs_tc_wait_selftest(uint32_t tries, int32_t *d_status, gs_strea
  *   t = R mu + t_w; cull if t_z <= 0.2
  *   Sigma = R(q) diag(s)^2 R(q)^T; J = perspective Jacobian at t with
  *   t_x/t_z, t_y/t_z clamped to 1.3x the half field of view
- *   Sigma2d = J W Sigma W^T J^T + 0.3 I; cull if det <= 0
- *   conic = Sigma2d^-1 (FP64 when the FP32 condition estimate exceeds 1e6)
+ *   Sigma2d = J W Sigma W^T J^T + 0.3 I, det(Sigma2d) > 0 for finite input
+ *   conic = Sigma2d^-1, its determinant summed from non-negative terms
+ *   (Cauchy-Binet on P = J W R(q) diag(s)) so that needles keep FP32 accuracy
  *   radius = ceil(3 sqrt(lambda_max)), lambda_max = mid + sqrt(max(0.1, mid^2 - det))
  *   mean2d = (fx t_x / t_z + cx, fy t_y / t_z + cy)
  *   tile rect x in [floor((u - r)/16), floor((u + r + 15)/16)) clamped to the

@@ -646,8 +646,8 @@ extern "C" gs_status ntc_fused_fwd(const float *mean, const float *quat, int64_t
                                    int order, float *mean_out, float *quat_out, float *raw7,
                                    void *enc_save, gs_stream stream)
 {
-    GS_REQUIRE(mean && quat && grid && table_f16 && w && mean_out && quat_out && raw7 && enc_save &&
-                   n >= 0,
+    GS_REQUIRE(grid && table_f16 && w && n >= 0, "ntc_fused_fwd: null grid, table or weights");
+    GS_REQUIRE(n == 0 || (mean && quat && mean_out && quat_out && raw7 && enc_save),
                "ntc_fused_fwd: null argument");
     GS_REQUIRE(w->precision == GS_MLP_BF16 && w->w_bf16, "ntc_fused_fwd: needs BF16 MLP weights");
     GS_REQUIRE(order == 0 || order == 1, "ntc_fused_fwd: order must be 0 or 1");
@@ -680,8 +680,8 @@ extern "C" gs_status ntc_fused_bwd(const float *mean, const float *quat, const f
                                    const float *d_quat_out, const float *d_scale, float *dW,
                                    float *d_table, gs_stream stream)
 {
-    GS_REQUIRE(mean && quat && raw7 && enc_save && grid && w && d_mean_out && d_quat_out && dW &&
-                   d_table && n >= 0,
+    GS_REQUIRE(grid && w && dW && d_table && n >= 0, "ntc_fused_bwd: null grid, weights or gradients");
+    GS_REQUIRE(n == 0 || (mean && quat && raw7 && enc_save && d_mean_out && d_quat_out),
                "ntc_fused_bwd: null argument");
     GS_REQUIRE(w->precision == GS_MLP_BF16 && w->w_bf16, "ntc_fused_bwd: needs BF16 MLP weights");
     GS_REQUIRE(order == 0 || order == 1, "ntc_fused_bwd: order must be 0 or 1");

@@ -440,10 +440,11 @@ extern "C" gs_status ntc_encode_fwd(const float *mean, int64_t n, const gs_hashg
     GridParams g;
     int64_t total;
     GS_REQUIRE(grid_params(grid, g, total), "ntc_encode_fwd: invalid hash grid");
-    GS_REQUIRE(mean && table && enc && n >= 0, "ntc_encode_fwd: null argument");
     GS_REQUIRE(table_dtype == GS_F16 || table_dtype == GS_F32, "ntc_encode_fwd: table dtype");
     GS_REQUIRE(enc_dtype == GS_F32 || enc_dtype == GS_BF16, "ntc_encode_fwd: enc dtype");
+    GS_REQUIRE(n >= 0, "ntc_encode_fwd: negative n");
     if (n == 0) return GS_OK;
+    GS_REQUIRE(mean && table && enc, "ntc_encode_fwd: null argument");
     int blocks = (int)ceil_div(n, 128);
     cudaStream_t s = as_stream(stream);
     note_launch();
@@ -466,9 +467,10 @@ extern "C" gs_status ntc_encode_bwd(const float *mean, int64_t n, const gs_hashg
     GridParams g;
     int64_t total;
     GS_REQUIRE(grid_params(grid, g, total), "ntc_encode_bwd: invalid hash grid");
-    GS_REQUIRE(mean && d_enc && d_table && n >= 0, "ntc_encode_bwd: null argument");
-    GS_REQUIRE(aligned(d_table, 8) && aligned(d_enc, 8), "ntc_encode_bwd: misaligned");
+    GS_REQUIRE(n >= 0, "ntc_encode_bwd: negative n");
     if (n == 0) return GS_OK;
+    GS_REQUIRE(mean && d_enc && d_table, "ntc_encode_bwd: null argument");
+    GS_REQUIRE(aligned(d_table, 8) && aligned(d_enc, 8), "ntc_encode_bwd: misaligned");
     encode_bwd_kernel<<<(int)ceil_div(n, 128), 128, 0, as_stream(stream)>>>(mean, n, g, d_enc, d_table);
     return launch_status("ntc_encode_bwd");
 }
@@ -476,9 +478,10 @@ extern "C" gs_status ntc_encode_bwd(const float *mean, int64_t n, const gs_hashg
 extern "C" gs_status ntc_mlp_fwd(const void *enc, int enc_dtype, int64_t n, const gs_mlp *w,
                                 float *raw7, gs_stream stream)
 {
-    GS_REQUIRE(enc && w && raw7 && n >= 0, "ntc_mlp_fwd: null argument");
+    GS_REQUIRE(w && n >= 0, "ntc_mlp_fwd: null weights or negative n");
     GS_REQUIRE(enc_dtype == GS_F32 || enc_dtype == GS_BF16, "ntc_mlp_fwd: enc dtype");
     if (n == 0) return GS_OK;
+    GS_REQUIRE(enc && raw7, "ntc_mlp_fwd: null argument");
     if (w->precision == GS_MLP_BF16) return mlp_tc_fwd(enc, enc_dtype, n, w, raw7, as_stream(stream));
     GS_REQUIRE(w->precision == GS_MLP_FP32 && w->w_f32, "ntc_mlp_fwd: bad precision / weights");
     int blocks = (int)ceil_div(n, 128);
@@ -496,9 +499,10 @@ extern "C" gs_status ntc_mlp_bwd(const void *enc, int enc_dtype, int64_t n, cons
                                 const float *d_raw7, const float *d_scale, float *dW, float *d_enc,
                                 gs_stream stream)
 {
-    GS_REQUIRE(enc && w && d_raw7 && dW && n >= 0, "ntc_mlp_bwd: null argument");
+    GS_REQUIRE(w && dW && n >= 0, "ntc_mlp_bwd: null weights or negative n");
     GS_REQUIRE(enc_dtype == GS_F32 || enc_dtype == GS_BF16, "ntc_mlp_bwd: enc dtype");
     if (n == 0) return GS_OK;
+    GS_REQUIRE(enc && d_raw7, "ntc_mlp_bwd: null argument");
     if (w->precision == GS_MLP_BF16)
         return mlp_tc_bwd(enc, enc_dtype, n, w, d_raw7, d_scale, dW, d_enc, as_stream(stream));
     GS_REQUIRE(w->precision == GS_MLP_FP32 && w->w_f32, "ntc_mlp_bwd: bad precision / weights");
@@ -522,11 +526,11 @@ extern "C" gs_status ntc_apply(const float *mean, const float *quat, const float
                               const float *aabb, int order, float *mean_out, float *quat_out,
                               gs_stream stream)
 {
-    GS_REQUIRE(mean && quat && raw7 && aabb && mean_out && quat_out && n >= 0,
-               "ntc_apply: null argument");
     GS_REQUIRE(order == 0 || order == 1, "ntc_apply: order must be 0 or 1");
-    GS_REQUIRE(aligned(quat, 16) && aligned(quat_out, 16), "ntc_apply: quaternions misaligned");
+    GS_REQUIRE(n >= 0, "ntc_apply: negative n");
     if (n == 0) return GS_OK;
+    GS_REQUIRE(mean && quat && raw7 && aabb && mean_out && quat_out, "ntc_apply: null argument");
+    GS_REQUIRE(aligned(quat, 16) && aligned(quat_out, 16), "ntc_apply: quaternions misaligned");
     Box b = Box::from(aabb);
     note_launch();
     apply_kernel<<<(int)ceil_div(n, 256), 256, 0, as_stream(stream)>>>(mean, quat, raw7, n, b, order,
@@ -538,11 +542,12 @@ extern "C" gs_status ntc_apply_bwd(const float *mean, const float *quat, const f
                                   int64_t n, const float *aabb, int order, const float *d_mean_out,
                                   const float *d_quat_out, float *d_raw7, gs_stream stream)
 {
-    GS_REQUIRE(mean && quat && raw7 && aabb && d_mean_out && d_quat_out && d_raw7 && n >= 0,
-               "ntc_apply_bwd: null argument");
     GS_REQUIRE(order == 0 || order == 1, "ntc_apply_bwd: order must be 0 or 1");
-    GS_REQUIRE(aligned(quat, 16) && aligned(d_quat_out, 16), "ntc_apply_bwd: misaligned");
+    GS_REQUIRE(n >= 0, "ntc_apply_bwd: negative n");
     if (n == 0) return GS_OK;
+    GS_REQUIRE(mean && quat && raw7 && aabb && d_mean_out && d_quat_out && d_raw7,
+               "ntc_apply_bwd: null argument");
+    GS_REQUIRE(aligned(quat, 16) && aligned(d_quat_out, 16), "ntc_apply_bwd: misaligned");
     Box b = Box::from(aabb);
     note_launch();
     apply_bwd_kernel<<<(int)ceil_div(n, 256), 256, 0, as_stream(stream)>>>(
@@ -564,8 +569,9 @@ extern "C" gs_status ntc_warmup_loss(const float *raw7, int64_t n, float *d_raw7
 extern "C" gs_status gs_check_finite(const float *g, int64_t n, gs_train_state *d_state,
                                      gs_stream stream)
 {
-    GS_REQUIRE(g && d_state && n >= 0, "gs_check_finite: null argument");
+    GS_REQUIRE(d_state && n >= 0, "gs_check_finite: null state or negative n");
     if (n == 0) return GS_OK;
+    GS_REQUIRE(g, "gs_check_finite: null argument");
     int blocks = (int)std::min<int64_t>(ceil_div(n, 256), kNumSMs * 8);
     note_launch();
     check_finite_kernel<<<blocks, 256, 0, as_stream(stream)>>>(g, n, d_state);
@@ -576,10 +582,11 @@ extern "C" gs_status adam_step(float *p, float *g, float *m, float *v, int64_t n
                                const gs_train_state *d_state, void *shadow, int shadow_dtype,
                                gs_stream stream)
 {
-    GS_REQUIRE(p && g && m && v && hp && d_state && n >= 0, "adam_step: null argument");
+    GS_REQUIRE(hp && d_state && n >= 0, "adam_step: null hyper-parameters / state or negative n");
     GS_REQUIRE(shadow == nullptr || shadow_dtype == GS_F16 || shadow_dtype == GS_BF16,
                "adam_step: shadow dtype must be GS_F16 or GS_BF16");
     if (n == 0) return GS_OK;
+    GS_REQUIRE(p && g && m && v, "adam_step: null argument");
     GS_REQUIRE(aligned(p, 16) && aligned(g, 16) && aligned(m, 16) && aligned(v, 16) &&
                    (shadow == nullptr || aligned(shadow, 8)),
                "adam_step: arrays must be 16-byte aligned (shadow 8)");

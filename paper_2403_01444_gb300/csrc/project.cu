@@ -166,37 +166,35 @@ __device__ __forceinline__ void project_view(const ProjectParams &p, const Gauss
         L.T[j] = j00 * Wm[j] + j02 * Wm[8 + j];
         L.T[3 + j] = j11 * Wm[4 + j] + j12 * Wm[8 + j];
     }
-    const float *S = G.Sig;
-    float u0[3], u1[3];  // Sig * T0, Sig * T1
-    u0[0] = S[0] * L.T[0] + S[1] * L.T[1] + S[2] * L.T[2];
-    u0[1] = S[1] * L.T[0] + S[3] * L.T[1] + S[4] * L.T[2];
-    u0[2] = S[2] * L.T[0] + S[4] * L.T[1] + S[5] * L.T[2];
-    u1[0] = S[0] * L.T[3] + S[1] * L.T[4] + S[2] * L.T[5];
-    u1[1] = S[1] * L.T[3] + S[3] * L.T[4] + S[4] * L.T[5];
-    u1[2] = S[2] * L.T[3] + S[4] * L.T[4] + S[5] * L.T[5];
-    L.a = L.T[0] * u0[0] + L.T[1] * u0[1] + L.T[2] * u0[2] + 0.3f;
-    L.b = L.T[0] * u1[0] + L.T[1] * u1[1] + L.T[2] * u1[2];
-    L.c = L.T[3] * u1[0] + L.T[4] * u1[1] + L.T[5] * u1[2] + 0.3f;
-    float det = L.a * L.c - L.b * L.b;
-    float tr = L.a + L.c;
-    if (tr * tr > 1.0e6f * det) {
-        // ill-conditioned footprint: determinant and inverse in FP64
-        double da = L.a, db = L.b, dc = L.c;
-        double dd = da * dc - db * db;
-        if (!(dd > 0.0)) return;
-        L.det = (float)dd;
-        L.conic[0] = (float)(dc / dd);
-        L.conic[1] = (float)(-db / dd);
-        L.conic[2] = (float)(da / dd);
-        if (!(L.det > 0.f)) return;
-    } else {
-        if (!(det > 0.f)) return;
-        L.det = det;
-        float id = 1.f / det;
-        L.conic[0] = L.c * id;
-        L.conic[1] = -L.b * id;
-        L.conic[2] = L.a * id;
+    // 2D covariance T Sigma T^T + 0.3 I through P = T R diag(s) (2x3), so
+    // that T Sigma T^T = P P^T.  Its determinant by the Cauchy-Binet formula,
+    //   det(P P^T + 0.3 I) = sum of the squared 2x2 minors of P
+    //                        + 0.3 (|P_0|^2 + |P_1|^2) + 0.09,
+    // is a sum of non-negative terms: no cancellation, even for a needle
+    // whose a c - b^2 would cancel to nothing in FP32.
+    float P[6];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float m0 = G.R[k] * G.s[k], m1 = G.R[3 + k] * G.s[k], m2 = G.R[6 + k] * G.s[k];
+        P[k] = L.T[0] * m0 + L.T[1] * m1 + L.T[2] * m2;
+        P[3 + k] = L.T[3] * m0 + L.T[4] * m1 + L.T[5] * m2;
     }
+    const float pa = P[0] * P[0] + P[1] * P[1] + P[2] * P[2];
+    const float pc = P[3] * P[3] + P[4] * P[4] + P[5] * P[5];
+    L.a = pa + 0.3f;
+    L.b = P[0] * P[3] + P[1] * P[4] + P[2] * P[5];
+    L.c = pc + 0.3f;
+    const float m01 = P[0] * P[4] - P[1] * P[3];
+    const float m02 = P[0] * P[5] - P[2] * P[3];
+    const float m12 = P[1] * P[5] - P[2] * P[4];
+    const float det = m01 * m01 + m02 * m02 + m12 * m12 + 0.3f * (pa + pc) + 0.09f;
+    const float tr = L.a + L.c;
+    if (!(det > 0.f)) return;   // only for non-finite inputs
+    L.det = det;
+    const float id = 1.f / det;
+    L.conic[0] = L.c * id;
+    L.conic[1] = -L.b * id;
+    L.conic[2] = L.a * id;
     float mid = 0.5f * tr;
     float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - L.det));
     L.radius = (int)ceilf(3.f * sqrtf(lam));
@@ -559,12 +557,12 @@ extern "C" gs_status gs_project(const gs_gaussians *g, const gs_camera *d_cams, 
     ProjectParams p{};
     gs_status st = fill_params(g, d_cams, V, W, H, p);
     if (st != GS_OK) return st;
+    if (p.n == 0) return GS_OK;   // empty arrays may be null
     GS_REQUIRE(out && out->mean2d && out->conic_opacity && out->rgb && out->depth && out->radius &&
                    out->tiles_touched,
                "gs_project: null output");
     GS_REQUIRE(aligned(out->mean2d, 8) && aligned(out->conic_opacity, 16),
                "gs_project: mean2d / conic_opacity misaligned");
-    if (p.n == 0) return GS_OK;
     p.mean2d = reinterpret_cast<float2 *>(out->mean2d);
     p.conic_op = reinterpret_cast<float4 *>(out->conic_opacity);
     p.rgb = out->rgb;
@@ -592,9 +590,9 @@ extern "C" gs_status gs_project_bwd(const gs_gaussians *g, const gs_camera *d_ca
     ProjectParams p{};
     gs_status st = fill_params(g, d_cams, V, W, H, p);
     if (st != GS_OK) return st;
+    if (p.n == 0) return GS_OK;
     GS_REQUIRE(grads && d_mean && d_quat, "gs_project_bwd: null argument");
     GS_REQUIRE(aligned(grads, 16) && aligned(d_quat, 16), "gs_project_bwd: misaligned arrays");
-    if (p.n == 0) return GS_OK;
     p.grads = grads;
     p.d_mean = d_mean;
     p.d_quat = d_quat;
@@ -625,12 +623,12 @@ extern "C" gs_status gs_project_bwd_full(const gs_gaussians *g, const gs_camera 
     ProjectParams p{};
     gs_status st = fill_params(g, d_cams, V, W, H, p);
     if (st != GS_OK) return st;
-    GS_REQUIRE(grads && d_mean && d_quat && d_scale && d_opacity_logit && d_sh,
-               "gs_project_bwd_full: null argument");
     GS_REQUIRE(first >= 0 && count >= 0 && first + count <= g->n,
                "gs_project_bwd_full: range [first, first + count) outside the Gaussians");
-    GS_REQUIRE(aligned(grads, 16) && aligned(d_quat, 16), "gs_project_bwd_full: misaligned arrays");
     if (count == 0) return GS_OK;
+    GS_REQUIRE(grads && d_mean && d_quat && d_scale && d_opacity_logit && d_sh,
+               "gs_project_bwd_full: null argument");
+    GS_REQUIRE(aligned(grads, 16) && aligned(d_quat, 16), "gs_project_bwd_full: misaligned arrays");
     p.grads = grads;
     p.d_opacity = d_opacity;
     p.first = first;

@@ -451,7 +451,7 @@ static gs_status fill(const gs_projected *proj, int64_t n, int V, int W, int H, 
     p.rgb = proj->rgb;
     p.radius = proj->radius;
     GS_REQUIRE(bin >= 1 && bin <= 64, "raster: bin must be 1..64 tiles");
-    GS_REQUIRE(bin == 1 || proj->radius, "raster: binned lists need the radius array");
+    GS_REQUIRE(bin == 1 || n == 0 || proj->radius, "raster: binned lists need the radius array");
     p.vals = vals;
     p.ranges = reinterpret_cast<const uint2 *>(ranges);
     p.n = n;
@@ -520,11 +520,13 @@ extern "C" gs_status gs_raster_bwd(const gs_projected *proj, int64_t n, int V, i
     RasterParams p{};
     gs_status st = fill(proj, n, V, W, H, bin, bg, vals, ranges, p);
     if (st != GS_OK) return st;
-    GS_REQUIRE(T_final && last && d_img && grads, "gs_raster_bwd: null argument");
+    GS_REQUIRE(T_final && last && d_img && (grads || n == 0), "gs_raster_bwd: null argument");
     GS_REQUIRE(aligned(grads, 16), "gs_raster_bwd: grads must be 16-byte aligned");
     cudaStream_t s = as_stream(stream);
-    cudaMemsetAsync(grads, 0, sizeof(float) * 8 * n * V, s);
-    if (d_opacity) cudaMemsetAsync(d_opacity, 0, sizeof(float) * n * V, s);
+    if (n > 0) {
+        cudaMemsetAsync(grads, 0, sizeof(float) * 8 * n * V, s);
+        if (d_opacity) cudaMemsetAsync(d_opacity, 0, sizeof(float) * n * V, s);
+    }
     p.T_final = const_cast<float *>(T_final);
     p.last = const_cast<int32_t *>(last);
     p.d_img = d_img;
