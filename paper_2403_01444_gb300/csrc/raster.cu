@@ -10,6 +10,30 @@ constexpr int FT = 256;         // forward: threads per 16x16 tile, one pixel ea
 #define BWD_PIXELS_PER_THREAD 2  // backward: pixels per thread (256 / this threads per tile)
 #endif
 constexpr int BWD_CHUNK = 32;    // records per backward reduction chunk
+#ifndef RASTER_WARP_BLOCKS
+#define RASTER_WARP_BLOCKS 1     // 1: each warp owns a compact block of the tile; 0: rows
+#endif
+
+// Pixel of lane l in warp w, pixel k of the thread (k < ppt), for a 16x16
+// tile split into 256 / (32 ppt) warps.  Blocks: a warp owns a compact
+// rectangle (8x4 for one pixel per thread, 8x8 for two, 16x8 for four or
+// more) whose pixels tend to share records and list ends; a thread's pixels
+// are vertically adjacent.  Rows: thread t owns column t % 16 of rows
+// t / 16 + k * (16 / ppt).
+__device__ __forceinline__ void tile_pixel(int tid, int ppt, int k, int &x, int &y)
+{
+    if (RASTER_WARP_BLOCKS) {
+        const int w = tid >> 5, l = tid & 31;
+        const int rw = ppt >= 4 ? 16 : 8;         // warp rectangle width
+        const int wpr = 16 / rw;                  // warps per tile row
+        const int rows = (32 / rw) * ppt;         // warp rectangle height
+        x = (w % wpr) * rw + l % rw;
+        y = (w / wpr) * rows + (l / rw) * ppt + k;
+    } else {
+        x = tid & 15;
+        y = (tid >> 4) + k * (16 / ppt);
+    }
+}
 
 struct RasterParams {
     const float2 *mean2d;
@@ -148,8 +172,10 @@ __global__ void __launch_bounds__(FT) raster_fwd_kernel(RasterParams p)
     const int tile = blockIdx.x, view = blockIdx.y;
     const int tid = threadIdx.x;
     const int tx_t = tile % p.tx, ty_t = tile / p.tx;
-    const int px = tx_t * 16 + (tid & 15);
-    const int py = ty_t * 16 + (tid >> 4);
+    int px, py;
+    tile_pixel(tid, 1, 0, px, py);
+    px += tx_t * 16;
+    py += ty_t * 16;
     const bool inside = px < p.W && py < p.H;
     const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
     const int binid = (ty_t / p.bin) * p.bins_x + tx_t / p.bin;
@@ -303,7 +329,6 @@ __global__ void __launch_bounds__(256 / PPT) raster_bwd_kernel(RasterParams p)
 {
     constexpr int NT = 256 / PPT;        // threads per tile
     constexpr int NW = NT / 32;          // warps per tile
-    constexpr int ROWSTEP = 16 / PPT;    // a thread's pixels: rows r0, r0 + ROWSTEP, ...
     constexpr int NV = WANT_OP ? 9 : 8;
     __shared__ float2 s_xy[NT];
     __shared__ float4 s_co[NT];
@@ -315,8 +340,9 @@ __global__ void __launch_bounds__(256 / PPT) raster_bwd_kernel(RasterParams p)
     const int tile = blockIdx.x, view = blockIdx.y;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tx_t = tile % p.tx, ty_t = tile / p.tx;
-    const int px = tx_t * 16 + (tid & 15);
-    const int r0 = tid >> 4;
+    int px, py0;
+    tile_pixel(tid, PPT, 0, px, py0);
+    px += tx_t * 16;
     const float pxf = (float)px + 0.5f;
     const int binid = (ty_t / p.bin) * p.bins_x + tx_t / p.bin;
     const uint2 range = p.ranges[(int64_t)view * p.bins + binid];
@@ -327,7 +353,9 @@ __global__ void __launch_bounds__(256 / PPT) raster_bwd_kernel(RasterParams p)
     int mylast = 0;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
-        const int py = ty_t * 16 + r0 + k * ROWSTEP;
+        int pxk, py;  // pxk == px - tx_t * 16
+        tile_pixel(tid, PPT, k, pxk, py);
+        py += ty_t * 16;
         pyf[k] = (float)py + 0.5f;
         P[k] = PixBwd{0, 1.f, 0.f, 0.f, 0.f, p.bg0, p.bg1, p.bg2};
         if (px < p.W && py < p.H) {
