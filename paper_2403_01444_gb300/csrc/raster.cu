@@ -246,7 +246,11 @@ __global__ void __launch_bounds__(FT) raster_fwd_kernel(RasterParams p)
 
 // Sum 8 per-lane values over the warp with 9 shuffles: each butterfly stage
 // hands half of the remaining values to the partner lane.  Lane l returns the
-// warp total of value index 4*bit4(l) + 2*bit3(l) + bit2(l).
+// warp total of value index 4*bit4(l) + 2*bit3(l) + bit2(l) = l >> 2.  With
+// FULL false the last two stages are left out (7 shuffles) and lane l returns
+// the sum of that value over the 8 lanes that share l & 3: the warp total is
+// the sum of lanes 4 (l >> 2) .. 4 (l >> 2) + 3.
+template <bool FULL = true>
 __device__ __forceinline__ float warp_reduce8(const float *v)
 {
     const int lane = threadIdx.x & 31;
@@ -266,15 +270,20 @@ __device__ __forceinline__ float warp_reduce8(const float *v)
     }
     float send = b2 ? b[0] : b[1];
     float c = (b2 ? b[1] : b[0]) + __shfl_xor_sync(0xffffffffu, send, 4);
-    c += __shfl_xor_sync(0xffffffffu, c, 2);
-    c += __shfl_xor_sync(0xffffffffu, c, 1);
+    if (FULL) {
+        c += __shfl_xor_sync(0xffffffffu, c, 2);
+        c += __shfl_xor_sync(0xffffffffu, c, 1);
+    }
     return c;
 }
 
-// Back-to-front state of one pixel.
+// Back-to-front state of one pixel.  With B the colour composited behind
+// the current Gaussian (background included), Eq. 4 gives
+//   dL/dalpha_i = T_i dC . (c_i - B_i+1),  B_i = alpha_i c_i + (1 - alpha_i) B_i+1,
+// and since dC = dL/dC is fixed per pixel only S = dC . B is carried.
 struct PixBwd {
     int last;
-    float T, dC0, dC1, dC2, B0, B1, B2;
+    float T, dC0, dC1, dC2, S;
 };
 
 template <bool WANT_OP>
@@ -293,10 +302,9 @@ __device__ __forceinline__ bool unblend_one(PixBwd &P, float2 xy, float4 co, flo
     v[5] = fmaf(P.dC0, w, v[5]);
     v[6] = fmaf(P.dC1, w, v[6]);
     v[7] = fmaf(P.dC2, w, v[7]);
-    float dalpha = P.T * (P.dC0 * (c.x - P.B0) + P.dC1 * (c.y - P.B1) + P.dC2 * (c.z - P.B2));
-    P.B0 = fmaf(alpha, c.x - P.B0, P.B0);
-    P.B1 = fmaf(alpha, c.y - P.B1, P.B1);
-    P.B2 = fmaf(alpha, c.z - P.B2, P.B2);
+    const float diff = fmaf(P.dC2, c.z, fmaf(P.dC1, c.y, P.dC0 * c.x)) - P.S;
+    float dalpha = P.T * diff;
+    P.S = fmaf(alpha, diff, P.S);
     if (araw < kAlphaCap) {
         // moments of dL/dpower over the pair offsets; the record's mean and
         // conic gradients are linear in them and formed once per tile
@@ -335,7 +343,11 @@ __global__ void __launch_bounds__(256 / PPT) raster_bwd_kernel(RasterParams p)
     __shared__ float4 s_rgbk[NT];  // colour and (bit pattern of) the list position
     __shared__ uint32_t s_g[NT];
     __shared__ int s_wcnt[NW];
-    __shared__ float s_part[NW][BWD_CHUNK][NV];
+    // per-warp partial sums of each record of the chunk: 4 partials of each
+    // of the 8 values (lane l holds partial l & 3 of value l >> 2), and the
+    // opacity gradient
+    __shared__ float4 s_part[NW][BWD_CHUNK][8];
+    __shared__ float s_pop[WANT_OP ? NW : 1][BWD_CHUNK];
     __shared__ int s_max;
     const int tile = blockIdx.x, view = blockIdx.y;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -357,7 +369,7 @@ __global__ void __launch_bounds__(256 / PPT) raster_bwd_kernel(RasterParams p)
         tile_pixel(tid, PPT, k, pxk, py);
         py += ty_t * 16;
         pyf[k] = (float)py + 0.5f;
-        P[k] = PixBwd{0, 1.f, 0.f, 0.f, 0.f, p.bg0, p.bg1, p.bg2};
+        P[k] = PixBwd{0, 1.f, 0.f, 0.f, 0.f, 0.f};
         if (px < p.W && py < p.H) {
             int64_t pix = (int64_t)view * HW + (int64_t)py * p.W + px;
             P[k].last = p.last[pix];
@@ -366,6 +378,7 @@ __global__ void __launch_bounds__(256 / PPT) raster_bwd_kernel(RasterParams p)
             P[k].dC0 = di[0];
             P[k].dC1 = di[HW];
             P[k].dC2 = di[2 * HW];
+            P[k].S = fmaf(P[k].dC2, p.bg2, fmaf(P[k].dC1, p.bg1, P[k].dC0 * p.bg0));
         }
         mylast = max(mylast, P[k].last);
     }
@@ -422,16 +435,16 @@ __global__ void __launch_bounds__(256 / PPT) raster_bwd_kernel(RasterParams p)
                         }
                     }
                 }
+                float *part = reinterpret_cast<float *>(&s_part[warp][j - clo][0]);
                 if (__any_sync(0xffffffffu, contrib)) {
-                    float r = warp_reduce8(v);
-                    if ((lane & 3) == 0) s_part[warp][j - clo][lane >> 2] = r;
+                    part[lane] = warp_reduce8<false>(v);
                     if (WANT_OP) {
                         float ro = warp_sum(v[NV - 1]);
-                        if (lane == 0) s_part[warp][j - clo][NV - 1] = ro;
+                        if (lane == 0) s_pop[warp][j - clo] = ro;
                     }
-                } else if ((lane & 3) == 0) {
-                    s_part[warp][j - clo][lane >> 2] = 0.f;
-                    if (WANT_OP && lane == 0) s_part[warp][j - clo][NV - 1] = 0.f;
+                } else {
+                    part[lane] = 0.f;
+                    if (WANT_OP && lane == 0) s_pop[warp][j - clo] = 0.f;
                 }
             }
             __syncthreads();
@@ -442,10 +455,12 @@ __global__ void __launch_bounds__(256 / PPT) raster_bwd_kernel(RasterParams p)
                 float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
                 for (int w = 0; w < NW; ++w) {
-                    sum.x += s_part[w][j][h];
-                    sum.y += s_part[w][j][h + 1];
-                    sum.z += s_part[w][j][h + 2];
-                    sum.w += s_part[w][j][h + 3];
+                    const float4 a = s_part[w][j][h], b = s_part[w][j][h + 1];
+                    const float4 c = s_part[w][j][h + 2], d = s_part[w][j][h + 3];
+                    sum.x += (a.x + a.y) + (a.z + a.w);
+                    sum.y += (b.x + b.y) + (b.z + b.w);
+                    sum.z += (c.x + c.y) + (c.z + c.w);
+                    sum.w += (d.x + d.y) + (d.z + d.w);
                 }
                 if (sum.x != 0.f || sum.y != 0.f || sum.z != 0.f || sum.w != 0.f)
                     atomicAdd(reinterpret_cast<float4 *>(p.grads + 8 * (vb + s_g[clo + j]) + h),
@@ -455,7 +470,7 @@ __global__ void __launch_bounds__(256 / PPT) raster_bwd_kernel(RasterParams p)
                 for (int j = tid; j < ccnt; j += NT) {
                     float sum = 0.f;
 #pragma unroll
-                    for (int w = 0; w < NW; ++w) sum += s_part[w][j][NV - 1];
+                    for (int w = 0; w < NW; ++w) sum += s_pop[w][j];
                     if (sum != 0.f) atomicAdd(p.d_opacity + vb + s_g[clo + j], sum);
                 }
             }
