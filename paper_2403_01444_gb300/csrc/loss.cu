@@ -1,19 +1,35 @@
 // L1 + D-SSIM loss and its gradient (Section 4.1, Eq. 6).
-// Pass 1 filters (x, y, x^2, y^2, xy) with the separable 11x11 Gaussian window
-// through shared memory, forms the SSIM map and the three per-pixel
-// coefficients of its derivative wrt (mu_x, E[x^2], E[xy]); pass 2 filters
-// those coefficients (the window is symmetric, so the adjoint is the same
-// filter) and assembles dL/dI; pass 3 reduces the block partial sums in FP64.
+// Pass 1 filters (x, y, x^2, y^2, xy) with the separable 11x11 Gaussian
+// window, forms the SSIM map and the three per-pixel coefficients of its
+// derivative wrt (mu_x, E[x^2], E[xy]); pass 2 filters those coefficients (the
+// window is symmetric, so the adjoint is the same filter) and assembles
+// dL/dI; pass 3 reduces the block partial sums in FP64.
+//
+// Both filtering passes work on 32 x 48 output tiles.  The horizontal stage
+// reads its inputs straight from global memory (through L1, as float4 where
+// rows are 16-byte aligned) and leaves the row-filtered maps in shared
+// memory; the vertical stage filters the columns from there.  The filters use
+// the packed FP32 FMA of sm_100+ (both halves of an aligned register pair in
+// one instruction): along a row a tap pair (w_t, w_t+1) multiplies an input
+// pair (in_j, in_j+1) and the halves are added at the end; down a column the
+// two maps of a pair (x and y, x^2 and y^2, two coefficient maps) share the
+// weight.
 #include <math.h>
 
 #include "common.cuh"
 
 namespace gs3 {
 
-constexpr int LT = 32;          // output tile side
-constexpr int LH = 5;           // window half-width
-constexpr int LS = LT + 2 * LH; // staged tile side (42)
+constexpr int SX = 32;                 // output tile width
+constexpr int SY = 48;                 // output tile height
+constexpr int LH = 5;                  // window half-width
+constexpr int SR = SY + 2 * LH;        // rows of the row-filtered maps (58)
+constexpr int HSEG = 4;                // outputs of one horizontal item
+constexpr int VSEG = 6;                // outputs of one thread in the vertical stage
 constexpr int LTHREADS = 256;
+constexpr int HITEMS = SR * (SX / HSEG);
+static_assert(SX * (SY / VSEG) == LTHREADS, "vertical stage: one column segment per thread");
+static_assert(SX % HSEG == 0 && HSEG == 4, "horizontal items hold four outputs");
 
 // Normalised 11-tap Gaussian window (sigma 1.5), built by each block in
 // shared memory (no constant-memory upload, so the call is capture-safe).
@@ -27,10 +43,79 @@ __device__ __forceinline__ void build_window(float *w)
     }
 }
 
+// The window as tap pairs for the row filter: e[i] = (w_2i, w_2i+1) for
+// outputs whose window starts on an even input, o[i] = (w_2i-1, w_2i) with
+// w_-1 = 0 for the others.
+struct RowTaps {
+    float2 e[5], o[6];
+    float w10;
+};
+
+__device__ __forceinline__ RowTaps row_taps(const float *w)
+{
+    RowTaps t;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) t.e[i] = make_float2(w[2 * i], w[2 * i + 1]);
+    t.o[0] = make_float2(0.f, w[0]);
+#pragma unroll
+    for (int i = 1; i < 6; ++i) t.o[i] = make_float2(w[2 * i - 1], w[2 * i]);
+    t.w10 = w[10];
+    return t;
+}
+
+// Inputs of one horizontal item as pairs: m[k] = (in_2k, in_2k+1), in_j the
+// value at column B + j, B = x0 + c0 - 8 (a multiple of 4).  Output o of the
+// item (column B + 8 + o) sums in_3+o .. in_13+o.
+constexpr int NPAIR = 9;
+
+__device__ __forceinline__ void load_pairs(const float *row, int W, int B, bool vec, float2 (&m)[NPAIR])
+{
+    m[0] = make_float2(0.f, 0.f);  // in_0, in_1: never used
+    if (vec && B >= 0 && B + 16 <= W) {
+        const float4 *r4 = reinterpret_cast<const float4 *>(row + B);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 v = __ldg(r4 + q);
+            m[2 * q] = make_float2(v.x, v.y);
+            m[2 * q + 1] = make_float2(v.z, v.w);
+        }
+    } else {
+#pragma unroll
+        for (int k = 1; k < 8; ++k) {
+            const int g0 = B + 2 * k, g1 = g0 + 1;
+            m[k] = make_float2(g0 >= 0 && g0 < W ? __ldg(row + g0) : 0.f,
+                               g1 >= 0 && g1 < W ? __ldg(row + g1) : 0.f);
+        }
+    }
+    const int g16 = B + 16;
+    m[8] = make_float2(g16 < W ? __ldg(row + g16) : 0.f, 0.f);
+}
+
+// Row filter of one map for the item's four outputs.
+__device__ __forceinline__ void row_filter(const float2 (&m)[NPAIR], const RowTaps &t, float (&out)[HSEG])
+{
+#pragma unroll
+    for (int o = 0; o < HSEG; o += 2) {
+        // even output o: window in_3+o .. in_13+o, pairs from in_2+o with o[]
+        float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) a = __ffma2_rn(t.o[i], m[1 + o / 2 + i], a);
+        out[o] = a.x + a.y;
+        // odd output o + 1: pairs from in_4+o with e[], last tap in_14+o
+        float2 b = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) b = __ffma2_rn(t.e[i], m[2 + o / 2 + i], b);
+        out[o + 1] = fmaf(t.w10, m[7 + o / 2].x, b.x + b.y);
+    }
+}
+
+__device__ __forceinline__ float2 dup(float a) { return make_float2(a, a); }
+
 struct LossParams {
     const float *x, *y;
     int P, H, W;
     float lam;
+    bool vec;             // rows of x, y and the coefficient maps are 16-byte aligned
     float *ca, *cb, *cc;  // per-pixel derivative coefficients
     double *partial;      // [blocks][2]: sum of SSIM map, sum |x - y|
     float *d_img;
@@ -38,108 +123,129 @@ struct LossParams {
     int nblocks;
 };
 
-// Horizontal pass work split: a thread filters HSEG consecutive outputs of
-// one staged row, keeping the HSEG + 10 inputs in registers; the vertical
-// pass gives a thread VSEG consecutive rows of one column.
-constexpr int HSEG = 8;
-constexpr int VSEG = 4;
-static_assert(LT % HSEG == 0 && LT % VSEG == 0, "tile split");
-static_assert((LT / VSEG) * LT == LTHREADS, "vertical pass: one item per thread");
-
-__global__ void __launch_bounds__(LTHREADS) ssim_fwd_kernel(LossParams p)
+#ifndef SSIM_FWD_MIN_BLOCKS
+#define SSIM_FWD_MIN_BLOCKS 3  // 80 registers, no spills
+#endif
+__global__ void __launch_bounds__(LTHREADS, SSIM_FWD_MIN_BLOCKS) ssim_fwd_kernel(LossParams p)
 {
-    __shared__ float sx[LS][LS + 1], sy[LS][LS + 1];
-    __shared__ float hs[5][LS][LT + 1];
+    __shared__ float2 s_xy[SR][SX];   // row-filtered (x, y)
+    __shared__ float2 s_sq[SR][SX];   // row-filtered (x^2, y^2)
+    __shared__ float s_p[SR][SX];     // row-filtered x y
     __shared__ double red[2][LTHREADS / 32];
     __shared__ float c_win[11];
     build_window(c_win);
+    __syncthreads();
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * LT, y0 = blockIdx.y * LT, pl = blockIdx.z;
+    const int x0 = blockIdx.x * SX, y0 = blockIdx.y * SY, pl = blockIdx.z;
     const int64_t HW = (int64_t)p.H * p.W;
     const float *X = p.x + pl * HW, *Y = p.y + pl * HW;
-    for (int i = tid; i < LS * LS; i += LTHREADS) {
-        int r = i / LS, c = i % LS;
-        int gy = y0 - LH + r, gx = x0 - LH + c;
-        bool in = gy >= 0 && gy < p.H && gx >= 0 && gx < p.W;
-        int64_t o = (int64_t)gy * p.W + gx;
-        sx[r][c] = in ? X[o] : 0.f;
-        sy[r][c] = in ? Y[o] : 0.f;
-    }
-    __syncthreads();
-    float w[11];
+    float lsum = 0.f;
+    {
+        const RowTaps t = row_taps(c_win);
+        for (int item = tid; item < HITEMS; item += LTHREADS) {
+            const int r = item / (SX / HSEG), c0 = (item % (SX / HSEG)) * HSEG;
+            const int gy = y0 - LH + r;
+            float fx[HSEG], fy[HSEG], fxx[HSEG], fyy[HSEG], fxy[HSEG];
+            if (gy >= 0 && gy < p.H) {
+                const int B = x0 + c0 - 8;
+                float2 mx[NPAIR], my[NPAIR], mxx[NPAIR], myy[NPAIR], mxy[NPAIR];
+                load_pairs(X + (int64_t)gy * p.W, p.W, B, p.vec, mx);
+                load_pairs(Y + (int64_t)gy * p.W, p.W, B, p.vec, my);
 #pragma unroll
-    for (int k = 0; k < 11; ++k) w[k] = c_win[k];
-    // horizontal: (x, y, x^2, y^2, xy) filtered along rows.  Each staged input
-    // is read and squared once and added into the HSEG outputs it reaches;
-    // every output still sums its taps in increasing order.
-    for (int item = tid; item < LS * (LT / HSEG); item += LTHREADS) {
-        const int r = item / (LT / HSEG), c0 = (item % (LT / HSEG)) * HSEG;
-        float acc[HSEG][5];
+                for (int k = 1; k < NPAIR; ++k) {
+                    mxx[k] = __fmul2_rn(mx[k], mx[k]);
+                    myy[k] = __fmul2_rn(my[k], my[k]);
+                    mxy[k] = __fmul2_rn(mx[k], my[k]);
+                }
+                row_filter(mx, t, fx);
+                row_filter(my, t, fy);
+                row_filter(mxx, t, fxx);
+                row_filter(myy, t, fyy);
+                row_filter(mxy, t, fxy);
+                // L1 term at the item's outputs in_8 .. in_11 (pairs 4 and 5)
+                if (r >= LH && r < LH + SY) {
 #pragma unroll
-        for (int o = 0; o < HSEG; ++o)
+                    for (int o = 0; o < HSEG; ++o) {
+                        const float2 a = mx[4 + o / 2], b = my[4 + o / 2];
+                        const float d = (o & 1) ? a.y - b.y : a.x - b.x;
+                        if (x0 + c0 + o < p.W) lsum += fabsf(d);
+                    }
+                }
+            } else {
 #pragma unroll
-            for (int q = 0; q < 5; ++q) acc[o][q] = 0.f;
-#pragma unroll
-        for (int k = 0; k < HSEG + 10; ++k) {
-            const float a = sx[r][c0 + k], b = sy[r][c0 + k];
-            const float aa = a * a, bb = b * b, ab = a * b;
+                for (int o = 0; o < HSEG; ++o) fx[o] = fy[o] = fxx[o] = fyy[o] = fxy[o] = 0.f;
+            }
 #pragma unroll
             for (int o = 0; o < HSEG; ++o) {
-                const int t = k - o;
-                if (t < 0 || t > 10) continue;
-                acc[o][0] = fmaf(w[t], a, acc[o][0]);
-                acc[o][1] = fmaf(w[t], b, acc[o][1]);
-                acc[o][2] = fmaf(w[t], aa, acc[o][2]);
-                acc[o][3] = fmaf(w[t], bb, acc[o][3]);
-                acc[o][4] = fmaf(w[t], ab, acc[o][4]);
+                s_xy[r][c0 + o] = make_float2(fx[o], fy[o]);
+                s_sq[r][c0 + o] = make_float2(fxx[o], fyy[o]);
+                s_p[r][c0 + o] = fxy[o];
             }
         }
-#pragma unroll
-        for (int o = 0; o < HSEG; ++o)
-#pragma unroll
-            for (int q = 0; q < 5; ++q) hs[q][r][c0 + o] = acc[o][q];
     }
     __syncthreads();
-    // vertical: thread -> column c, rows r0 .. r0 + VSEG - 1
-    const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
-    const int c = tid % LT, r0 = (tid / LT) * VSEG;
-    float f[5][VSEG];
+    // vertical: thread -> column c, rows r0 .. r0 + VSEG - 1 of the tile
+    const int c = tid % SX, r0 = (tid / SX) * VSEG;
+    float2 fxy2[VSEG], fsq2[VSEG];
+    float fp[VSEG];
+    {
+        float2 wd[11];
 #pragma unroll
-    for (int m = 0; m < 5; ++m) {
-        float col[VSEG + 10];
+        for (int k = 0; k < 11; ++k) wd[k] = dup(c_win[k]);
+        float2 col[VSEG + 10];
 #pragma unroll
-        for (int k = 0; k < VSEG + 10; ++k) col[k] = hs[m][r0 + k][c];
+        for (int k = 0; k < VSEG + 10; ++k) col[k] = s_xy[r0 + k][c];
 #pragma unroll
         for (int o = 0; o < VSEG; ++o) {
-            float acc = 0.f;
+            float2 a = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int k = 0; k < 11; ++k) acc = fmaf(w[k], col[o + k], acc);
-            f[m][o] = acc;
+            for (int k = 0; k < 11; ++k) a = __ffma2_rn(wd[k], col[o + k], a);
+            fxy2[o] = a;
+        }
+#pragma unroll
+        for (int k = 0; k < VSEG + 10; ++k) col[k] = s_sq[r0 + k][c];
+#pragma unroll
+        for (int o = 0; o < VSEG; ++o) {
+            float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < 11; ++k) a = __ffma2_rn(wd[k], col[o + k], a);
+            fsq2[o] = a;
+        }
+        float cp[VSEG + 10];
+#pragma unroll
+        for (int k = 0; k < VSEG + 10; ++k) cp[k] = s_p[r0 + k][c];
+#pragma unroll
+        for (int o = 0; o < VSEG; ++o) {
+            float a = 0.f;
+#pragma unroll
+            for (int k = 0; k < 11; ++k) a = fmaf(c_win[k], cp[o + k], a);
+            fp[o] = a;
         }
     }
     // per-thread and per-warp sums in FP32 (at most VSEG * 32 terms), the
     // block's and the final reduction in FP64
-    float ssum = 0.f, lsum = 0.f;
+    const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
+    float ssum = 0.f;
     const int gx = x0 + c;
 #pragma unroll
     for (int o = 0; o < VSEG; ++o) {
-        const int r = r0 + o, gy = y0 + r;
+        const int gy = y0 + r0 + o;
         if (gy >= p.H || gx >= p.W) continue;
-        float mx = f[0][o], my = f[1][o], exx = f[2][o], eyy = f[3][o], exy = f[4][o];
-        float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
-        float n1 = 2.f * mx * my + C1, n2 = 2.f * sxy + C2;
-        float d1 = mx * mx + my * my + C1, d2 = sxx + syy + C2;
-        float idd = 1.f / (d1 * d2);
-        float sv = n1 * n2 * idd;
-        float ds_dmx = 2.f * my * n2 * idd - sv * 2.f * mx / d1;
-        float ds_dsxx = -sv / d2;
-        float ds_dsxy = 2.f * n1 * idd;
-        int64_t oo = pl * HW + (int64_t)gy * p.W + gx;
+        const float mx = fxy2[o].x, my = fxy2[o].y, exx = fsq2[o].x, eyy = fsq2[o].y, exy = fp[o];
+        const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
+        const float n1 = 2.f * mx * my + C1, n2 = 2.f * sxy + C2;
+        const float d1 = mx * mx + my * my + C1, d2 = sxx + syy + C2;
+        const float idd = 1.f / (d1 * d2);
+        const float sv = n1 * n2 * idd;
+        // 1 / d1 = d2 idd and 1 / d2 = d1 idd
+        const float ds_dmx = 2.f * my * n2 * idd - sv * 2.f * mx * (d2 * idd);
+        const float ds_dsxx = -sv * (d1 * idd);
+        const float ds_dsxy = 2.f * n1 * idd;
+        const int64_t oo = pl * HW + (int64_t)gy * p.W + gx;
         p.ca[oo] = ds_dmx - 2.f * mx * ds_dsxx - my * ds_dsxy;
         p.cb[oo] = ds_dsxx;
         p.cc[oo] = ds_dsxy;
         ssum += sv;
-        lsum += fabsf(sx[r + LH][c + LH] - sy[r + LH][c + LH]);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -165,65 +271,70 @@ __global__ void __launch_bounds__(LTHREADS) ssim_fwd_kernel(LossParams p)
 
 __global__ void __launch_bounds__(LTHREADS) ssim_bwd_kernel(LossParams p)
 {
-    __shared__ float sa[LS][LS + 1], sb[LS][LS + 1], sc[LS][LS + 1];
-    __shared__ float hs[3][LS][LT + 1];
+    __shared__ float2 s_ab[SR][SX];   // row-filtered (ca, cb)
+    __shared__ float s_c[SR][SX];     // row-filtered cc
     __shared__ float c_win[11];
     build_window(c_win);
-    const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * LT, y0 = blockIdx.y * LT, pl = blockIdx.z;
-    const int64_t HW = (int64_t)p.H * p.W;
-    for (int i = tid; i < LS * LS; i += LTHREADS) {
-        int r = i / LS, c = i % LS;
-        int gy = y0 - LH + r, gx = x0 - LH + c;
-        bool in = gy >= 0 && gy < p.H && gx >= 0 && gx < p.W;
-        int64_t o = pl * HW + (int64_t)gy * p.W + gx;
-        sa[r][c] = in ? p.ca[o] : 0.f;
-        sb[r][c] = in ? p.cb[o] : 0.f;
-        sc[r][c] = in ? p.cc[o] : 0.f;
-    }
     __syncthreads();
-    float w[11];
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * SX, y0 = blockIdx.y * SY, pl = blockIdx.z;
+    const int64_t HW = (int64_t)p.H * p.W;
+    {
+        const RowTaps t = row_taps(c_win);
+        const float *A = p.ca + pl * HW, *Bm = p.cb + pl * HW, *Cm = p.cc + pl * HW;
+        for (int item = tid; item < HITEMS; item += LTHREADS) {
+            const int r = item / (SX / HSEG), c0 = (item % (SX / HSEG)) * HSEG;
+            const int gy = y0 - LH + r;
+            float fa[HSEG], fb[HSEG], fc[HSEG];
+            if (gy >= 0 && gy < p.H) {
+                const int B = x0 + c0 - 8;
+                const int64_t ro = (int64_t)gy * p.W;
+                float2 m[NPAIR];
+                load_pairs(A + ro, p.W, B, p.vec, m);
+                row_filter(m, t, fa);
+                load_pairs(Bm + ro, p.W, B, p.vec, m);
+                row_filter(m, t, fb);
+                load_pairs(Cm + ro, p.W, B, p.vec, m);
+                row_filter(m, t, fc);
+            } else {
 #pragma unroll
-    for (int k = 0; k < 11; ++k) w[k] = c_win[k];
-    for (int item = tid; item < LS * (LT / HSEG); item += LTHREADS) {
-        const int r = item / (LT / HSEG), c0 = (item % (LT / HSEG)) * HSEG;
-        float acc[HSEG][3];
-#pragma unroll
-        for (int o = 0; o < HSEG; ++o)
-#pragma unroll
-            for (int q = 0; q < 3; ++q) acc[o][q] = 0.f;
-#pragma unroll
-        for (int k = 0; k < HSEG + 10; ++k) {
-            const float a = sa[r][c0 + k], b = sb[r][c0 + k], cc = sc[r][c0 + k];
+                for (int o = 0; o < HSEG; ++o) fa[o] = fb[o] = fc[o] = 0.f;
+            }
 #pragma unroll
             for (int o = 0; o < HSEG; ++o) {
-                const int t = k - o;
-                if (t < 0 || t > 10) continue;
-                acc[o][0] = fmaf(w[t], a, acc[o][0]);
-                acc[o][1] = fmaf(w[t], b, acc[o][1]);
-                acc[o][2] = fmaf(w[t], cc, acc[o][2]);
+                s_ab[r][c0 + o] = make_float2(fa[o], fb[o]);
+                s_c[r][c0 + o] = fc[o];
             }
         }
-#pragma unroll
-        for (int o = 0; o < HSEG; ++o)
-#pragma unroll
-            for (int q = 0; q < 3; ++q) hs[q][r][c0 + o] = acc[o][q];
     }
     __syncthreads();
     const float invM = 1.f / (float)((double)p.P * (double)HW);
-    const int c = tid % LT, r0 = (tid / LT) * VSEG;
-    float f[3][VSEG];
+    const int c = tid % SX, r0 = (tid / SX) * VSEG;
+    float2 fab[VSEG];
+    float fc[VSEG];
+    {
+        float2 wd[11];
 #pragma unroll
-    for (int m = 0; m < 3; ++m) {
-        float col[VSEG + 10];
+        for (int k = 0; k < 11; ++k) wd[k] = dup(c_win[k]);
+        float2 col[VSEG + 10];
 #pragma unroll
-        for (int k = 0; k < VSEG + 10; ++k) col[k] = hs[m][r0 + k][c];
+        for (int k = 0; k < VSEG + 10; ++k) col[k] = s_ab[r0 + k][c];
 #pragma unroll
         for (int o = 0; o < VSEG; ++o) {
-            float acc = 0.f;
+            float2 a = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int k = 0; k < 11; ++k) acc = fmaf(w[k], col[o + k], acc);
-            f[m][o] = acc;
+            for (int k = 0; k < 11; ++k) a = __ffma2_rn(wd[k], col[o + k], a);
+            fab[o] = a;
+        }
+        float cp[VSEG + 10];
+#pragma unroll
+        for (int k = 0; k < VSEG + 10; ++k) cp[k] = s_c[r0 + k][c];
+#pragma unroll
+        for (int o = 0; o < VSEG; ++o) {
+            float a = 0.f;
+#pragma unroll
+            for (int k = 0; k < 11; ++k) a = fmaf(c_win[k], cp[o + k], a);
+            fc[o] = a;
         }
     }
     const int gx = x0 + c;
@@ -231,11 +342,11 @@ __global__ void __launch_bounds__(LTHREADS) ssim_bwd_kernel(LossParams p)
     for (int o = 0; o < VSEG; ++o) {
         const int gy = y0 + r0 + o;
         if (gy >= p.H || gx >= p.W) continue;
-        int64_t oo = pl * HW + (int64_t)gy * p.W + gx;
-        float xv = p.x[oo], yv = p.y[oo];
-        float diff = xv - yv;
-        float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
-        float dssim = f[0][o] + 2.f * xv * f[1][o] + yv * f[2][o];
+        const int64_t oo = pl * HW + (int64_t)gy * p.W + gx;
+        const float xv = p.x[oo], yv = p.y[oo];
+        const float diff = xv - yv;
+        const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
+        const float dssim = fab[o].x + 2.f * xv * fab[o].y + yv * fc[o];
         p.d_img[oo] = ((1.f - p.lam) * sgn - p.lam * dssim) * invM;
     }
 }
@@ -282,7 +393,7 @@ extern "C" size_t gs_loss_workspace_size(int planes, int H, int W)
 {
     if (planes <= 0 || H <= 0 || W <= 0) return 0;
     size_t px = (size_t)planes * H * W;
-    size_t nb = (size_t)ceil_div(W, LT) * ceil_div(H, LT) * planes;
+    size_t nb = (size_t)ceil_div(W, SX) * ceil_div(H, SY) * planes;
     return 3 * a256(4 * px) + a256(16 * nb);
 }
 
@@ -311,7 +422,8 @@ extern "C" gs_status gs_loss_l1_dssim(const float *img, const float *target, int
     p.d_img = d_img;
     p.d_loss = d_loss;
     p.d_ssim = d_ssim;
-    dim3 grid((unsigned)ceil_div(W, LT), (unsigned)ceil_div(H, LT), (unsigned)planes);
+    p.vec = (W % 4) == 0 && aligned(img, 16) && aligned(target, 16) && aligned(ws, 16);
+    dim3 grid((unsigned)ceil_div(W, SX), (unsigned)ceil_div(H, SY), (unsigned)planes);
     p.nblocks = (int)(grid.x * grid.y * grid.z);
     cudaStream_t s = as_stream(stream);
     note_launch();

@@ -236,9 +236,11 @@ def test_mixed_precision_training_tracks_fp32_training():
     """The 50K-Gaussian, 8-view RBF-motion frame trained for 150 iterations
     from the same cache initialisation with the FP32 cache (SIMT MLP, FP32
     table) and with the mixed-precision one (FP16 table, BF16 tensor-core
-    MLP, loss scaling): both train and their final losses agree within 10 %;
-    the held-out PSNRs (an ill-posed view, sensitive to where each run
-    settles) within 1.5 dB."""
+    MLP, loss scaling): both train, their final losses agree within 10 % and
+    the PSNRs of the training views within 0.25 dB.  The held-out view is not
+    constrained by the eight training views, so where two trajectories settle
+    there is not bounded by the arithmetic (1.5 dB apart in one run whose
+    training losses agreed to 0.5 %): both only have to exceed 35 dB there."""
     sc = scenes.make_scene(2)
     W, H = sc.cfg.W, sc.cfg.H
     G = gs3.Gaussians.from_numpy(sc.prev)
@@ -260,9 +262,13 @@ def test_mixed_precision_training_tracks_fp32_training():
         st.raster.check()
         mt, qt = st.transform()
         img = render(G, [sc.heldout], W, H, mt, qt)
-        out[prec] = (losses, -10 * math.log10(((img - gt_ho) ** 2).mean().item()))
-    (l32, p32), (l16, p16) = out[gs3.GS_MLP_FP32], out[gs3.GS_MLP_BF16]
-    print("final loss fp32 %.5f bf16 %.5f; held-out PSNR fp32 %.2f bf16 %.2f" % (l32[-1], l16[-1], p32, p16))
+        tr = render(G, sc.cams, W, H, mt, qt)
+        out[prec] = (losses, -10 * math.log10(((img - gt_ho) ** 2).mean().item()),
+                     -10 * math.log10(((tr - targets) ** 2).mean().item()))
+    (l32, p32, t32), (l16, p16, t16) = out[gs3.GS_MLP_FP32], out[gs3.GS_MLP_BF16]
+    print("final loss fp32 %.5f bf16 %.5f; training-view PSNR fp32 %.2f bf16 %.2f; "
+          "held-out PSNR fp32 %.2f bf16 %.2f" % (l32[-1], l16[-1], t32, t16, p32, p16))
     assert l16[-1] < 0.8 * l16[0] and l32[-1] < 0.8 * l32[0]
     assert abs(l16[-1] - l32[-1]) <= 0.10 * l32[-1]
-    assert abs(p16 - p32) <= 1.5
+    assert abs(t16 - t32) <= 0.25
+    assert p16 > 35.0 and p32 > 35.0
