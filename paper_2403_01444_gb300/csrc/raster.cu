@@ -10,6 +10,9 @@ constexpr int FT = 256;         // forward: threads per 16x16 tile, one pixel ea
 #define BWD_PIXELS_PER_THREAD 2  // backward: pixels per thread (256 / this threads per tile)
 #endif
 constexpr int BWD_CHUNK = 32;    // records per backward reduction chunk
+#ifndef FWD_PIXELS_PER_THREAD
+#define FWD_PIXELS_PER_THREAD 2  // forward: pixels per thread (1 or 2)
+#endif
 #ifndef RASTER_WARP_BLOCKS
 #define RASTER_WARP_BLOCKS 1     // 1: each warp owns a compact block of the tile; 0: rows
 #endif
@@ -85,6 +88,22 @@ __device__ __forceinline__ float pair_power(float2 xy, float4 co, float px, floa
     dyy = __fmul_rn(dy, dy);
     float q = fmaf(co.z, dyy, __fmul_rn(co.x, dxx));
     return fmaf(-0.5f, q, -__fmul_rn(co.y, dxy));
+}
+
+// pair_power for the two pixels (px, py.x) and (px, py.y) of one column:
+// the same roundings, the row-dependent terms two per packed instruction.
+__device__ __forceinline__ float2 pair_power2(float2 xy, float4 co, float px, float2 py, float &dx,
+                                              float2 &dy, float &dxx, float2 &dxy, float2 &dyy)
+{
+    dx = __fsub_rn(px, xy.x);
+    dy = make_float2(__fsub_rn(py.x, xy.y), __fsub_rn(py.y, xy.y));
+    dxx = __fmul_rn(dx, dx);
+    dxy = __fmul2_rn(make_float2(dx, dx), dy);
+    dyy = __fmul2_rn(dy, dy);
+    const float axx = __fmul_rn(co.x, dxx);
+    const float2 q = __ffma2_rn(make_float2(co.z, co.z), dyy, make_float2(axx, axx));
+    const float2 nb = __fmul2_rn(make_float2(-co.y, -co.y), dxy);   // -(B dx dy), exact negation
+    return __ffma2_rn(make_float2(-0.5f, -0.5f), q, nb);
 }
 
 __device__ __forceinline__ float pair_alpha_raw(float4 co, float power)
@@ -244,6 +263,100 @@ __global__ void __launch_bounds__(FT) raster_fwd_kernel(RasterParams p)
     }
 }
 
+// Forward with two vertically adjacent pixels per thread (128 threads per
+// tile): the record loads and the column offset are shared and the pair's
+// quadratic forms are evaluated two per packed instruction.
+template <bool BINNED, bool STATS>
+__global__ void __launch_bounds__(FT / 2) raster_fwd2_kernel(RasterParams p)
+{
+    constexpr int NT = FT / 2;
+    __shared__ float2 s_xy[NT];
+    __shared__ float4 s_co[NT];
+    __shared__ float4 s_rgbk[NT];  // colour and (bit pattern of) the list position
+    __shared__ int s_wcnt[NT / 32];
+    const int tile = blockIdx.x, view = blockIdx.y;
+    const int tid = threadIdx.x;
+    const int tx_t = tile % p.tx, ty_t = tile / p.tx;
+    int px, py0;
+    tile_pixel(tid, 2, 0, px, py0);
+    px += tx_t * 16;
+    py0 += ty_t * 16;
+    const bool in0 = px < p.W && py0 < p.H, in1 = px < p.W && py0 + 1 < p.H;
+    const float pxf = (float)px + 0.5f;
+    const float2 pyf = make_float2((float)py0 + 0.5f, (float)py0 + 1.5f);
+    const int binid = (ty_t / p.bin) * p.bins_x + tx_t / p.bin;
+    const uint2 range = p.ranges[(int64_t)view * p.bins + binid];
+    const int total = (int)(range.y - range.x);
+    const int64_t vb = (int64_t)view * p.n;
+    float T[2] = {1.f, 1.f}, C0[2] = {0.f, 0.f}, C1[2] = {0.f, 0.f}, C2[2] = {0.f, 0.f};
+    int last[2] = {0, 0};
+    bool done[2] = {!in0, !in1};
+    uint32_t n_tested = 0, n_contrib = 0;
+    for (int base = 0; base < total; base += NT) {
+        if (__syncthreads_count(done[0] && done[1]) == NT) break;
+        const int k = base + tid;
+        int64_t o = 0;
+        bool keep = false;
+        float2 m;
+        float4 co;
+        if (k < total) {
+            o = vb + p.vals[range.x + k];
+            keep = keep_record<BINNED>(p, o, tx_t, ty_t, m, co);
+        }
+        int cnt;
+        const int slot = compact_slot<NT>(keep, s_wcnt, cnt);
+        if (slot >= 0) {
+            s_xy[slot] = m;
+            s_co[slot] = co;
+            s_rgbk[slot] = make_float4(p.rgb[3 * o], p.rgb[3 * o + 1], p.rgb[3 * o + 2],
+                                       __int_as_float(k));
+        }
+        __syncthreads();
+        for (int j = 0; !(done[0] && done[1]) && j < cnt; ++j) {
+            const float4 cj = s_co[j];
+            float dx, dxx;
+            float2 dy, dxy, dyy;
+            const float2 pw = pair_power2(s_xy[j], cj, pxf, pyf, dx, dy, dxx, dxy, dyy);
+            const float pwv[2] = {pw.x, pw.y};
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                if (done[q]) continue;
+                if (STATS) ++n_tested;
+                const float power = pwv[q];
+                if (power > 0.f) continue;
+                const float alpha = fminf(kAlphaCap, pair_alpha_raw(cj, power));
+                if (alpha < kAlphaMin) continue;
+                const float test_T = T[q] * (1.f - alpha);
+                if (test_T < kTEps) {
+                    done[q] = true;
+                    continue;
+                }
+                const float w = alpha * T[q];
+                const float4 ck = s_rgbk[j];
+                C0[q] = fmaf(ck.x, w, C0[q]);
+                C1[q] = fmaf(ck.y, w, C1[q]);
+                C2[q] = fmaf(ck.z, w, C2[q]);
+                T[q] = test_T;
+                last[q] = __float_as_int(ck.w) + 1;
+                if (STATS) ++n_contrib;
+            }
+        }
+    }
+    if (STATS) flush_stats(p.stats, n_tested, n_contrib);
+    const int64_t HW = (int64_t)p.H * p.W;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        if (!(q == 0 ? in0 : in1)) continue;
+        const int64_t pix = (int64_t)(py0 + q) * p.W + px;
+        float *im = p.img + (int64_t)view * 3 * HW + pix;
+        im[0] = fmaf(T[q], p.bg0, C0[q]);
+        im[HW] = fmaf(T[q], p.bg1, C1[q]);
+        im[2 * HW] = fmaf(T[q], p.bg2, C2[q]);
+        p.T_final[(int64_t)view * HW + pix] = T[q];
+        p.last[(int64_t)view * HW + pix] = last[q];
+    }
+}
+
 // Sum 8 per-lane values over the warp with 9 shuffles: each butterfly stage
 // hands half of the remaining values to the partner lane.  Lane l returns the
 // warp total of value index 4*bit4(l) + 2*bit3(l) + bit2(l) = l >> 2.  With
@@ -287,11 +400,9 @@ struct PixBwd {
 };
 
 template <bool WANT_OP>
-__device__ __forceinline__ bool unblend_one(PixBwd &P, float2 xy, float4 co, float4 c,
-                                            float pxf, float pyf, float *v)
+__device__ __forceinline__ bool unblend_at(PixBwd &P, float4 co, float4 c, float power, float dx,
+                                           float dy, float dxx, float dxy, float dyy, float *v)
 {
-    float dx, dy, dxx, dxy, dyy;
-    float power = pair_power(xy, co, pxf, pyf, dx, dy, dxx, dxy, dyy);
     if (power > 0.f) return false;
     float G = __expf(power);
     float araw = __fmul_rn(co.w, G);
@@ -317,6 +428,15 @@ __device__ __forceinline__ bool unblend_one(PixBwd &P, float2 xy, float4 co, flo
         if (WANT_OP) v[8] = fmaf(dalpha, G, v[8]);
     }
     return true;
+}
+
+template <bool WANT_OP>
+__device__ __forceinline__ bool unblend_one(PixBwd &P, float2 xy, float4 co, float4 c,
+                                            float pxf, float pyf, float *v)
+{
+    float dx, dy, dxx, dxy, dyy;
+    const float power = pair_power(xy, co, pxf, pyf, dx, dy, dxx, dxy, dyy);
+    return unblend_at<WANT_OP>(P, co, c, power, dx, dy, dxx, dxy, dyy, v);
 }
 
 // Record gradients from the tile sums of the moments: with power =
@@ -425,13 +545,34 @@ __global__ void __launch_bounds__(256 / PPT) raster_bwd_kernel(RasterParams p)
                 if (pos < mylast) {
                     float2 xy = s_xy[j];
                     float4 cc = s_co[j];
-#pragma unroll
-                    for (int q = 0; q < PPT; ++q) {
-                        if (pos < P[q].last) {
+                    if (PPT == 2) {
+                        // the thread's two pixels share a column: one packed evaluation
+                        float dx, dxx;
+                        float2 dy, dxy, dyy;
+                        const float2 pw = pair_power2(xy, cc, pxf, make_float2(pyf[0], pyf[PPT - 1]),
+                                                      dx, dy, dxx, dxy, dyy);
+                        if (pos < P[0].last) {
                             if (STATS) ++n_tested;
-                            bool h = unblend_one<WANT_OP>(P[q], xy, cc, c, pxf, pyf[q], v);
+                            bool h = unblend_at<WANT_OP>(P[0], cc, c, pw.x, dx, dy.x, dxx, dxy.x, dyy.x, v);
                             if (STATS) n_contrib += h;
                             contrib |= h;
+                        }
+                        if (pos < P[PPT - 1].last) {
+                            if (STATS) ++n_tested;
+                            bool h = unblend_at<WANT_OP>(P[PPT - 1], cc, c, pw.y, dx, dy.y, dxx, dxy.y,
+                                                         dyy.y, v);
+                            if (STATS) n_contrib += h;
+                            contrib |= h;
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < PPT; ++q) {
+                            if (pos < P[q].last) {
+                                if (STATS) ++n_tested;
+                                bool h = unblend_one<WANT_OP>(P[q], xy, cc, c, pxf, pyf[q], v);
+                                if (STATS) n_contrib += h;
+                                contrib |= h;
+                            }
                         }
                     }
                 }
@@ -543,6 +684,16 @@ extern "C" gs_status gs_raster_fwd(const gs_projected *proj, int64_t n, int V, i
     dim3 grid(p.tx * p.ty, V);
     note_launch();
     cudaStream_t s = as_stream(stream);
+#if FWD_PIXELS_PER_THREAD == 2
+    if (bin > 1 && p.stats)
+        raster_fwd2_kernel<true, true><<<grid, FT / 2, 0, s>>>(p);
+    else if (bin > 1)
+        raster_fwd2_kernel<true, false><<<grid, FT / 2, 0, s>>>(p);
+    else if (p.stats)
+        raster_fwd2_kernel<false, true><<<grid, FT / 2, 0, s>>>(p);
+    else
+        raster_fwd2_kernel<false, false><<<grid, FT / 2, 0, s>>>(p);
+#else
     if (bin > 1 && p.stats)
         raster_fwd_kernel<true, true><<<grid, FT, 0, s>>>(p);
     else if (bin > 1)
@@ -551,6 +702,7 @@ extern "C" gs_status gs_raster_fwd(const gs_projected *proj, int64_t n, int V, i
         raster_fwd_kernel<false, true><<<grid, FT, 0, s>>>(p);
     else
         raster_fwd_kernel<false, false><<<grid, FT, 0, s>>>(p);
+#endif
     return launch_status("gs_raster_fwd");
 }
 
