@@ -671,6 +671,47 @@ class DirectOpt:
         return capture_graphs(self.step, batches)
 
 
+class TargetFeeder:
+    """Training targets resident in pinned host memory, fed to the device one
+    step ahead.  Batch b's targets go host -> device into dev[b] (the buffer
+    its step, eager or a captured graph, reads) on a copy stream while the
+    previous step runs: `before(b)` makes the compute stream wait for that
+    copy, `after(b)` marks dev[b] free again and starts the copy of the next
+    batch, which waits until the step that last read its buffer is done."""
+
+    def __init__(self, host: List[torch.Tensor], dev: List[torch.Tensor]):
+        if len(host) != len(dev) or not host:
+            raise ValueError("TargetFeeder: one pinned host batch per device buffer")
+        for h, d in zip(host, dev):
+            if not h.is_pinned() or h.shape != d.shape or d.device.type != "cuda":
+                raise ValueError("TargetFeeder: pinned host batches shaped like the device buffers")
+        self.host, self.dev = host, dev
+        self.copy_stream = torch.cuda.Stream(device=dev[0].device)
+        self.ready = [torch.cuda.Event() for _ in dev]
+        self.free = [torch.cuda.Event() for _ in dev]
+        self.bytes_per_step = host[0].numel() * host[0].element_size()
+
+    def _copy(self, b: int):
+        with torch.cuda.stream(self.copy_stream):
+            self.copy_stream.wait_event(self.free[b])
+            self.dev[b].copy_(self.host[b], non_blocking=True)
+            self.ready[b].record(self.copy_stream)
+
+    def start(self, b: int, stream=None):
+        """Record every buffer free on `stream` and copy batch b."""
+        stream = stream or torch.cuda.current_stream()
+        for e in self.free:
+            e.record(stream)
+        self._copy(b)
+
+    def before(self, b: int, stream=None):
+        (stream or torch.cuda.current_stream()).wait_event(self.ready[b])
+
+    def after(self, b: int, next_b: int, stream=None):
+        self.free[b].record(stream or torch.cuda.current_stream())
+        self._copy(next_b)
+
+
 def capture_graphs(step_fn, batches):
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())

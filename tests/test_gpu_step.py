@@ -274,3 +274,31 @@ def test_mixed_precision_training_tracks_fp32_training():
     assert abs(l16[-1] - l32[-1]) <= 0.10 * l32[-1]
     assert abs(t16 - t32) <= 1.0
     assert p16 > 35.0 and p32 > 35.0
+
+
+def test_target_feeder_orders_copies_and_steps():
+    """Batches fed one step ahead from pinned host memory arrive whole before
+    the step that reads them: every step, from the first (device buffers
+    start as NaN), sees exactly its batch (sums taken on the compute stream,
+    with matrix products in between keeping it busy)."""
+    from paper_2403_01444_gb300.engine import TargetFeeder
+    rng = np.random.default_rng(90)
+    nb, shape = 3, (2, 3, 64, 80)
+    host = [torch.from_numpy(rng.uniform(size=shape).astype(np.float32)).pin_memory() for _ in range(nb)]
+    dev = [torch.full(shape, float("nan"), device=DEV) for _ in range(nb)]   # unread until copied
+    feeder = TargetFeeder(host, dev)
+    want = [float(h.double().sum()) for h in host]
+    got = []
+    feeder.start(0)
+    big = torch.rand(2048, 2048, device=DEV)
+    for i in range(12):
+        b = i % nb
+        feeder.before(b)
+        for _ in range(3):
+            big = big @ big / 2048.0          # keeps the compute stream busy
+        got.append(dev[b].double().sum())
+        feeder.after(b, (i + 1) % nb)
+    torch.cuda.synchronize()
+    for i, g in enumerate(got):
+        assert abs(float(g) - want[i % nb]) <= 1e-9 * abs(want[i % nb])
+    assert feeder.bytes_per_step == 2 * 3 * 64 * 80 * 4
