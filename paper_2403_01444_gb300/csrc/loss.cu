@@ -269,7 +269,10 @@ __global__ void __launch_bounds__(LTHREADS, SSIM_FWD_MIN_BLOCKS) ssim_fwd_kernel
     }
 }
 
-__global__ void __launch_bounds__(LTHREADS) ssim_bwd_kernel(LossParams p)
+#ifndef SSIM_BWD_MIN_BLOCKS
+#define SSIM_BWD_MIN_BLOCKS 3
+#endif
+__global__ void __launch_bounds__(LTHREADS, SSIM_BWD_MIN_BLOCKS) ssim_bwd_kernel(LossParams p)
 {
     __shared__ float2 s_ab[SR][SX];   // row-filtered (ca, cb)
     __shared__ float s_c[SR][SX];     // row-filtered cc
@@ -289,13 +292,14 @@ __global__ void __launch_bounds__(LTHREADS) ssim_bwd_kernel(LossParams p)
             if (gy >= 0 && gy < p.H) {
                 const int B = x0 + c0 - 8;
                 const int64_t ro = (int64_t)gy * p.W;
-                float2 m[NPAIR];
-                load_pairs(A + ro, p.W, B, p.vec, m);
-                row_filter(m, t, fa);
-                load_pairs(Bm + ro, p.W, B, p.vec, m);
-                row_filter(m, t, fb);
-                load_pairs(Cm + ro, p.W, B, p.vec, m);
-                row_filter(m, t, fc);
+                // all three rows in flight before any filtering
+                float2 ma[NPAIR], mb[NPAIR], mc[NPAIR];
+                load_pairs(A + ro, p.W, B, p.vec, ma);
+                load_pairs(Bm + ro, p.W, B, p.vec, mb);
+                load_pairs(Cm + ro, p.W, B, p.vec, mc);
+                row_filter(ma, t, fa);
+                row_filter(mb, t, fb);
+                row_filter(mc, t, fc);
             } else {
 #pragma unroll
                 for (int o = 0; o < HSEG; ++o) fa[o] = fb[o] = fc[o] = 0.f;
@@ -310,6 +314,17 @@ __global__ void __launch_bounds__(LTHREADS) ssim_bwd_kernel(LossParams p)
     __syncthreads();
     const float invM = 1.f / (float)((double)p.P * (double)HW);
     const int c = tid % SX, r0 = (tid / SX) * VSEG;
+    const int gx = x0 + c;
+    // the images at this thread's outputs, loaded before the column filters
+    float xv[VSEG], yv[VSEG];
+#pragma unroll
+    for (int o = 0; o < VSEG; ++o) {
+        const int gy = y0 + r0 + o;
+        const bool in = gy < p.H && gx < p.W;
+        const int64_t oo = pl * HW + (int64_t)gy * p.W + gx;
+        xv[o] = in ? __ldg(p.x + oo) : 0.f;
+        yv[o] = in ? __ldg(p.y + oo) : 0.f;
+    }
     float2 fab[VSEG];
     float fc[VSEG];
     {
@@ -337,16 +352,14 @@ __global__ void __launch_bounds__(LTHREADS) ssim_bwd_kernel(LossParams p)
             fc[o] = a;
         }
     }
-    const int gx = x0 + c;
 #pragma unroll
     for (int o = 0; o < VSEG; ++o) {
         const int gy = y0 + r0 + o;
         if (gy >= p.H || gx >= p.W) continue;
         const int64_t oo = pl * HW + (int64_t)gy * p.W + gx;
-        const float xv = p.x[oo], yv = p.y[oo];
-        const float diff = xv - yv;
+        const float diff = xv[o] - yv[o];
         const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
-        const float dssim = fab[o].x + 2.f * xv * fab[o].y + yv * fc[o];
+        const float dssim = fab[o].x + 2.f * xv[o] * fab[o].y + yv[o] * fc[o];
         p.d_img[oo] = ((1.f - p.lam) * sgn - p.lam * dssim) * invM;
     }
 }
