@@ -10,6 +10,7 @@ namespace gs3 {
 
 struct ProjectParams {
     const float *mean, *quat, *scale, *opl, *sh;
+    bool sh_vec4;  // sh is 16-byte aligned
     int64_t n;
     int deg, K;
     const gs_camera *cams;
@@ -216,9 +217,9 @@ __device__ __forceinline__ void project_view(const ProjectParams &p, const Gauss
     float r0 = 0.f, r1 = 0.f, r2 = 0.f;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        r0 = fmaf(Y[k], __ldg(sh + 3 * k), r0);
-        r1 = fmaf(Y[k], __ldg(sh + 3 * k + 1), r1);
-        r2 = fmaf(Y[k], __ldg(sh + 3 * k + 2), r2);
+        r0 = fmaf(Y[k], sh[3 * k], r0);
+        r1 = fmaf(Y[k], sh[3 * k + 1], r1);
+        r2 = fmaf(Y[k], sh[3 * k + 2], r2);
     }
     L.rgb_raw[0] = r0 + 0.5f;
     L.rgb_raw[1] = r1 + 0.5f;
@@ -227,7 +228,10 @@ __device__ __forceinline__ void project_view(const ProjectParams &p, const Gauss
 }
 
 template <int DEG>
-__global__ void __launch_bounds__(256) project_fwd_kernel(ProjectParams p)
+#ifndef PROJ_FWD_MIN_BLOCKS
+#define PROJ_FWD_MIN_BLOCKS 1
+#endif
+__global__ void __launch_bounds__(256, PROJ_FWD_MIN_BLOCKS) project_fwd_kernel(ProjectParams p)
 {
     constexpr int K = (DEG + 1) * (DEG + 1);
     extern __shared__ gs_camera s_cams[];
@@ -237,7 +241,24 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ProjectParams p)
     if (i >= p.n) return;
     GaussLocal G;
     load_gauss(p, i, G);
-    const float *sh = p.sh + (int64_t)3 * K * i;
+    // the Gaussian's SH coefficients once, for every view (float4 when each
+    // Gaussian's 3K floats keep 16-byte alignment)
+    float sh[3 * K];
+    const float *shg = p.sh + (int64_t)3 * K * i;
+    if ((3 * K) % 4 == 0 && p.sh_vec4) {
+        const float4 *s4 = reinterpret_cast<const float4 *>(shg);
+#pragma unroll
+        for (int q = 0; q < 3 * K / 4; ++q) {
+            const float4 t = __ldg(s4 + q);
+            sh[4 * q] = t.x;
+            sh[4 * q + 1] = t.y;
+            sh[4 * q + 2] = t.z;
+            sh[4 * q + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 3 * K; ++q) sh[q] = __ldg(shg + q);
+    }
     for (int v = 0; v < p.V; ++v) {
         ViewLocal L;
         project_view<DEG>(p, G, sh, s_cams[v], L);
@@ -535,6 +556,7 @@ static gs_status fill_params(const gs_gaussians *g, const gs_camera *d_cams, int
     p.scale = g->scale;
     p.opl = g->opacity_logit;
     p.sh = g->sh;
+    p.sh_vec4 = aligned(g->sh, 16);
     p.n = g->n;
     p.deg = g->sh_deg;
     p.K = (g->sh_deg + 1) * (g->sh_deg + 1);
