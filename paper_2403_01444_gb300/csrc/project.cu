@@ -227,10 +227,33 @@ __device__ __forceinline__ void project_view(const ProjectParams &p, const Gauss
     L.valid = true;
 }
 
+// Gaussian i's SH coefficients into registers (float4 loads when each
+// Gaussian's 3K floats keep 16-byte alignment).
 template <int DEG>
+__device__ __forceinline__ void load_sh(const ProjectParams &p, int64_t i, float (&sh)[3 * (DEG + 1) * (DEG + 1)])
+{
+    constexpr int N = 3 * (DEG + 1) * (DEG + 1);
+    const float *shg = p.sh + (int64_t)N * i;
+    if (N % 4 == 0 && p.sh_vec4) {
+        const float4 *s4 = reinterpret_cast<const float4 *>(shg);
+#pragma unroll
+        for (int q = 0; q < N / 4; ++q) {
+            const float4 t = __ldg(s4 + q);
+            sh[4 * q] = t.x;
+            sh[4 * q + 1] = t.y;
+            sh[4 * q + 2] = t.z;
+            sh[4 * q + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < N; ++q) sh[q] = __ldg(shg + q);
+    }
+}
+
 #ifndef PROJ_FWD_MIN_BLOCKS
 #define PROJ_FWD_MIN_BLOCKS 1
 #endif
+template <int DEG>
 __global__ void __launch_bounds__(256, PROJ_FWD_MIN_BLOCKS) project_fwd_kernel(ProjectParams p)
 {
     constexpr int K = (DEG + 1) * (DEG + 1);
@@ -241,24 +264,9 @@ __global__ void __launch_bounds__(256, PROJ_FWD_MIN_BLOCKS) project_fwd_kernel(P
     if (i >= p.n) return;
     GaussLocal G;
     load_gauss(p, i, G);
-    // the Gaussian's SH coefficients once, for every view (float4 when each
-    // Gaussian's 3K floats keep 16-byte alignment)
+    // the Gaussian's SH coefficients once, for every view
     float sh[3 * K];
-    const float *shg = p.sh + (int64_t)3 * K * i;
-    if ((3 * K) % 4 == 0 && p.sh_vec4) {
-        const float4 *s4 = reinterpret_cast<const float4 *>(shg);
-#pragma unroll
-        for (int q = 0; q < 3 * K / 4; ++q) {
-            const float4 t = __ldg(s4 + q);
-            sh[4 * q] = t.x;
-            sh[4 * q + 1] = t.y;
-            sh[4 * q + 2] = t.z;
-            sh[4 * q + 3] = t.w;
-        }
-    } else {
-#pragma unroll
-        for (int q = 0; q < 3 * K; ++q) sh[q] = __ldg(shg + q);
-    }
+    load_sh<DEG>(p, i, sh);
     for (int v = 0; v < p.V; ++v) {
         ViewLocal L;
         project_view<DEG>(p, G, sh, s_cams[v], L);
@@ -302,7 +310,7 @@ __device__ __forceinline__ void bwd_view(const GaussLocal &G, const float *sh, c
         float acc = 0.f;
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch)
-            if (L.rgb_raw[ch] > 0.f) acc = fmaf(drgb[ch], __ldg(sh + 3 * k + ch), acc);
+            if (L.rgb_raw[ch] > 0.f) acc = fmaf(drgb[ch], sh[3 * k + ch], acc);
         wk[k] = acc;
     }
     float3 gd = sh_basis_grad_dot(DEG, L.dir.x, L.dir.y, L.dir.z, wk);
@@ -491,7 +499,8 @@ __global__ void __launch_bounds__(128) project_bwd_views_kernel(ProjectParams p)
     if (live) {
         load_gauss(p, i, G);
         if (v < p.V) {
-            const float *sh = p.sh + (int64_t)3 * K * i;
+            float sh[3 * K];
+            load_sh<DEG>(p, i, sh);
             const gs_camera &c = s_cams[v];
             ViewLocal L;
             project_view<DEG>(p, G, sh, c, L);
