@@ -7,6 +7,8 @@
 #include <stdarg.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "ntc.cuh"
 
@@ -66,47 +68,51 @@ __device__ __forceinline__ float2 load_feat<float>(const float *table, uint32_t 
     return reinterpret_cast<const float2 *>(table)[row];
 }
 
+// One thread per (Gaussian, level): threadIdx.x is the level, threadIdx.y
+// the Gaussian within the block, so a Gaussian's levels gather in parallel
+// and its 2L outputs are written by adjacent threads.
 template <typename TT, typename ET>
 __global__ void __launch_bounds__(128) encode_fwd_kernel(const float *mean, int64_t n, GridParams g,
                                                          const TT *table, ET *enc)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float3 m = make_float3(mean[3 * i], mean[3 * i + 1], mean[3 * i + 2]);
-    ET *out = enc + i * (int64_t)(2 * g.L);
-    for (int l = 0; l < g.L; ++l) {
-        uint32_t idx[8];
-        float w[8];
-        level_corners(g, l, m, idx, w);
-        float f0 = 0.f, f1 = 0.f;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.y + threadIdx.y;
+    const int l = threadIdx.x;
+    if (i >= n || l >= g.L) return;
+    const float3 m = make_float3(mean[3 * i], mean[3 * i + 1], mean[3 * i + 2]);
+    uint32_t idx[8];
+    float w[8];
+    level_corners(g, l, m, idx, w);
+    float2 t[8];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            float2 t = load_feat<TT>(table, idx[c]);
-            f0 = fmaf(w[c], t.x, f0);
-            f1 = fmaf(w[c], t.y, f1);
-        }
-        store2(out + 2 * l, f0, f1);
+    for (int c = 0; c < 8; ++c) t[c] = load_feat<TT>(table, idx[c]);
+    float f0 = 0.f, f1 = 0.f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        f0 = fmaf(w[c], t[c].x, f0);
+        f1 = fmaf(w[c], t[c].y, f1);
     }
+    store2(enc + i * (int64_t)(2 * g.L) + 2 * l, f0, f1);
 }
 
 __global__ void __launch_bounds__(128) encode_bwd_kernel(const float *mean, int64_t n, GridParams g,
                                                          const float *d_enc, float *d_table)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float3 m = make_float3(mean[3 * i], mean[3 * i + 1], mean[3 * i + 2]);
-    const float2 *gi = reinterpret_cast<const float2 *>(d_enc + i * (int64_t)(2 * g.L));
-    for (int l = 0; l < g.L; ++l) {
-        float2 gg = gi[l];
-        if (gg.x == 0.f && gg.y == 0.f) continue;
-        uint32_t idx[8];
-        float w[8];
-        level_corners(g, l, m, idx, w);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.y + threadIdx.y;
+    const int l = threadIdx.x;
+    if (i >= n || l >= g.L) return;
+    const float2 gg = reinterpret_cast<const float2 *>(d_enc + i * (int64_t)(2 * g.L))[l];
+    if (gg.x == 0.f && gg.y == 0.f) return;
+    const float3 m = make_float3(mean[3 * i], mean[3 * i + 1], mean[3 * i + 2]);
+    uint32_t idx[8];
+    float w[8];
+    level_corners(g, l, m, idx, w);
 #pragma unroll
-        for (int c = 0; c < 8; ++c)
-            atomicAdd(reinterpret_cast<float2 *>(d_table) + idx[c], make_float2(w[c] * gg.x, w[c] * gg.y));
-    }
+    for (int c = 0; c < 8; ++c)
+        atomicAdd(reinterpret_cast<float2 *>(d_table) + idx[c], make_float2(w[c] * gg.x, w[c] * gg.y));
 }
+
+// Block shape of the encoding kernels: (levels, Gaussians per block).
+static dim3 encode_block(const GridParams &g) { return dim3(g.L, std::max(1, 128 / g.L)); }
 
 // ------------------------------------------------------------ MLP (SIMT)
 template <typename ET>
@@ -445,18 +451,19 @@ extern "C" gs_status ntc_encode_fwd(const float *mean, int64_t n, const gs_hashg
     GS_REQUIRE(n >= 0, "ntc_encode_fwd: negative n");
     if (n == 0) return GS_OK;
     GS_REQUIRE(mean && table && enc, "ntc_encode_fwd: null argument");
-    int blocks = (int)ceil_div(n, 128);
+    const dim3 blk = encode_block(g);
+    const unsigned blocks = (unsigned)ceil_div(n, blk.y);
     cudaStream_t s = as_stream(stream);
     note_launch();
     if (table_dtype == GS_F16 && enc_dtype == GS_F32)
-        encode_fwd_kernel<__half, float><<<blocks, 128, 0, s>>>(mean, n, g, (const __half *)table, (float *)enc);
+        encode_fwd_kernel<__half, float><<<blocks, blk, 0, s>>>(mean, n, g, (const __half *)table, (float *)enc);
     else if (table_dtype == GS_F16)
-        encode_fwd_kernel<__half, __nv_bfloat16><<<blocks, 128, 0, s>>>(mean, n, g, (const __half *)table,
+        encode_fwd_kernel<__half, __nv_bfloat16><<<blocks, blk, 0, s>>>(mean, n, g, (const __half *)table,
                                                                         (__nv_bfloat16 *)enc);
     else if (enc_dtype == GS_F32)
-        encode_fwd_kernel<float, float><<<blocks, 128, 0, s>>>(mean, n, g, (const float *)table, (float *)enc);
+        encode_fwd_kernel<float, float><<<blocks, blk, 0, s>>>(mean, n, g, (const float *)table, (float *)enc);
     else
-        encode_fwd_kernel<float, __nv_bfloat16><<<blocks, 128, 0, s>>>(mean, n, g, (const float *)table,
+        encode_fwd_kernel<float, __nv_bfloat16><<<blocks, blk, 0, s>>>(mean, n, g, (const float *)table,
                                                                       (__nv_bfloat16 *)enc);
     return launch_status("ntc_encode_fwd");
 }
@@ -471,7 +478,9 @@ extern "C" gs_status ntc_encode_bwd(const float *mean, int64_t n, const gs_hashg
     if (n == 0) return GS_OK;
     GS_REQUIRE(mean && d_enc && d_table, "ntc_encode_bwd: null argument");
     GS_REQUIRE(aligned(d_table, 8) && aligned(d_enc, 8), "ntc_encode_bwd: misaligned");
-    encode_bwd_kernel<<<(int)ceil_div(n, 128), 128, 0, as_stream(stream)>>>(mean, n, g, d_enc, d_table);
+    const dim3 blk = encode_block(g);
+    note_launch();
+    encode_bwd_kernel<<<(unsigned)ceil_div(n, blk.y), blk, 0, as_stream(stream)>>>(mean, n, g, d_enc, d_table);
     return launch_status("ntc_encode_bwd");
 }
 
