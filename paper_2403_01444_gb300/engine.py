@@ -60,7 +60,8 @@ class Rasterizer:
     def set_n(self, n: int):
         """Number of Gaussians of the next calls (<= n_max); the per-record
         arrays are [V][n] views of the same storage."""
-        assert 0 <= n <= self.n_max
+        if not 0 <= n <= self.n_max:
+            raise ValueError("Rasterizer.set_n: %d Gaussians outside [0, %d]" % (n, self.n_max))
         self.n = n
         V = self.V
         sub = lambda t, *tail: t.view(-1)[:V * n * int(np.prod(tail or (1,)))].view(V, n, *tail)
@@ -163,9 +164,12 @@ class NTC:
         self.grid = grid
         self.precision = precision
         self.entries = gs3.ntc_hashgrid_entries(grid)
-        assert table.shape == (self.entries, 2), (table.shape, self.entries)
+        if table.shape != (self.entries, 2):
+            raise ValueError("NTC: table of shape %s, the grid has %d entries x 2 features"
+                             % (table.shape, self.entries))
         w = np.concatenate([x.reshape(-1) for x in weights]).astype(np.float32)
-        assert w.size == gs3.MLP_PARAMS
+        if w.size != gs3.MLP_PARAMS:
+            raise ValueError("NTC: %d MLP weights, expected %d" % (w.size, gs3.MLP_PARAMS))
         tab = torch.from_numpy(np.ascontiguousarray(table, np.float32)).to(device)
         self.table = AdamBuffers(tab, lr, torch.float16)
         self.mlp = AdamBuffers(torch.from_numpy(w).to(device), lr, torch.bfloat16)
@@ -625,7 +629,9 @@ class Streamer:
         d = np.load(path)
         dev = self.g.mean.device
         t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-        assert int(d["sh_deg"]) == self.g.sh_deg and d["mean"].shape[0] == self.g.n
+        if int(d["sh_deg"]) != self.g.sh_deg or d["mean"].shape[0] != self.g.n:
+            raise ValueError("Streamer.resume: checkpoint of %d Gaussians (SH %d), this run has %d (SH %d)"
+                             % (d["mean"].shape[0], int(d["sh_deg"]), self.g.n, self.g.sh_deg))
         self.g.mean.copy_(t(d["mean"]))
         self.g.quat.copy_(t(d["quat"]))
         self.g.sh.copy_(t(d["sh"]))

@@ -112,7 +112,9 @@ def _check(name, st):
 def _ptr(t: Optional[torch.Tensor]):
     if t is None:
         return None
-    assert t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor, got %s on %s%s"
+                         % (t.dtype, t.device, "" if t.is_contiguous() else " (not contiguous)"))
     return c_void_p(t.data_ptr())
 
 
