@@ -9,7 +9,17 @@ constexpr int FT = 256;         // forward: threads per 16x16 tile, one pixel ea
 #ifndef BWD_PIXELS_PER_THREAD
 #define BWD_PIXELS_PER_THREAD 2  // backward: pixels per thread (256 / this threads per tile)
 #endif
-constexpr int BWD_CHUNK = 32;    // records per backward reduction chunk
+#ifndef BWD_CHUNK_RECORDS
+#define BWD_CHUNK_RECORDS 32
+#endif
+constexpr int BWD_CHUNK = BWD_CHUNK_RECORDS;  // records per backward reduction chunk
+#ifndef BWD_UNROLL
+#define BWD_UNROLL 2
+#endif
+#ifndef FWD_UNROLL
+#define FWD_UNROLL 4
+#endif
+constexpr int kBwdUnroll = BWD_UNROLL, kFwdUnroll = FWD_UNROLL;
 #ifndef FWD_PIXELS_PER_THREAD
 #define FWD_PIXELS_PER_THREAD 2  // forward: pixels per thread (1 or 2)
 #endif
@@ -312,6 +322,7 @@ __global__ void __launch_bounds__(FT / 2) raster_fwd2_kernel(RasterParams p)
                                        __int_as_float(k));
         }
         __syncthreads();
+#pragma unroll kFwdUnroll
         for (int j = 0; !(done[0] && done[1]) && j < cnt; ++j) {
             const float4 cj = s_co[j];
             float dx, dxx;
@@ -534,7 +545,7 @@ __global__ void __launch_bounds__(256 / PPT) raster_bwd_kernel(RasterParams p)
         __syncthreads();
         for (int chi = cnt; chi > 0; chi -= BWD_CHUNK) {
             const int clo = max(0, chi - BWD_CHUNK);
-#pragma unroll 2
+#pragma unroll kBwdUnroll
             for (int j = chi - 1; j >= clo; --j) {
                 float v[NV];
 #pragma unroll
