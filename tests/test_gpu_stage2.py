@@ -311,3 +311,50 @@ def test_stage2_recovers_an_emerging_object():
     # the random-spawn ablation is reported, not asserted: with the per-epoch
     # split and prune both sets of added Gaussians end near the object here
     assert results["random"][2] > 0
+
+
+def test_stage2_degenerate_counts():
+    """Nothing above the gradient threshold: no index selected and a spawn of
+    zero rows leaves the added set unchanged; every added Gaussian below the
+    opacity threshold: quantity control keeps none; an empty source: an empty
+    result.  No error flag in any case."""
+    rng = np.random.default_rng(87)
+    deg, n = 1, 300
+    g = scenes.make_gaussians(n, deg, rng)
+    G = gs3.Gaussians.from_numpy(g)
+    acc = torch.full((n,), 1e-9, device=DEV)
+    den = torch.ones(n, dtype=torch.int32, device=DEV)
+    idx = torch.full((n,), -7, dtype=torch.int32, device=DEV)
+    nsel = torch.full((1,), 99, dtype=torch.int64, device=DEV)
+    gs3.gs_select_above(acc, den, n, 1e-3, idx, nsel)
+    torch.cuda.synchronize()
+    assert int(nsel.item()) == 0
+    rows, m, v, a = _added_buffers(64, deg)
+    rows.fill_(3.0)
+    nadd = torch.tensor([5], dtype=torch.int64, device=DEV)
+    err = torch.zeros(1, dtype=torch.int32, device=DEV)
+    gs3.gs_added_spawn(G, idx, nsel, torch.zeros(n, 3, device=DEV), 0.1, a, nadd, err)
+    torch.cuda.synchronize()
+    assert int(nadd.item()) == 5 and int(err.item()) == 0 and float(rows.min()) == 3.0
+    # all below tau_alpha
+    P = gs3.added_cols(deg)
+    src_rows, sm, sv, src = _added_buffers(n, deg)
+    r = rng.normal(size=(n, P)).astype(np.float32)
+    r[:, 10] = np.log(0.001 / 0.999)                       # opacity 0.001 < 0.01
+    src_rows.copy_(_t(r))
+    dst_rows, dm, dv, dst = _added_buffers(2 * n, deg)
+    nd = torch.full((1,), 42, dtype=torch.int64, device=DEV)
+    big = torch.ones(n, device=DEV)                        # all above tau_grad, but pruned first
+    gs3.gs_added_densify_prune(src, n, big, den, 2e-4, 0.01, 0.8, 0.1, torch.zeros(n, 3, device=DEV),
+                               dst, nd, err)
+    torch.cuda.synchronize()
+    assert int(nd.item()) == 0 and int(err.item()) == 0
+    want, keep, split = s2.densify_prune(r.astype(np.float64), np.ones(n), np.ones(n, np.int64),
+                                         2e-4, 0.01, 0.8, np.zeros((n, 3)))
+    assert want.shape[0] == 0 and not keep.any() and not split.any()
+    # empty source
+    nd.fill_(42)
+    gs3.gs_added_densify_prune(src, 0, big, den, 2e-4, 0.01, 0.8, 0.1, torch.zeros(n, 3, device=DEV),
+                               dst, nd, err)
+    torch.cuda.synchronize()
+    assert int(nd.item()) == 0 and int(err.item()) == 0
