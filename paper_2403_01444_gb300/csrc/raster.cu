@@ -116,9 +116,40 @@ __device__ __forceinline__ float2 pair_power2(float2 xy, float4 co, float px, fl
     return __ffma2_rn(make_float2(-0.5f, -0.5f), q, nb);
 }
 
+#ifndef RASTER_LOG2_CONIC
+#define RASTER_LOG2_CONIC 1
+#endif
+// With RASTER_LOG2_CONIC the staged conic is scaled by log2(e) (scale_conic),
+// so pair_power yields the power in base-2 units and G = 2^power comes from
+// one ex2.approx; G, alpha and dL/dpower keep their natural-unit meaning.
+// moments_to_grads takes the unscaled conic (unscale_conic).
+constexpr float kLog2e = 1.4426950408889634f, kLn2 = 0.6931471805599453f;
+
+__device__ __forceinline__ float4 scale_conic(float4 co)
+{
+    return RASTER_LOG2_CONIC ? make_float4(co.x * kLog2e, co.y * kLog2e, co.z * kLog2e, co.w) : co;
+}
+
+__device__ __forceinline__ float4 unscale_conic(float4 co)
+{
+    return RASTER_LOG2_CONIC ? make_float4(co.x * kLn2, co.y * kLn2, co.z * kLn2, co.w) : co;
+}
+
+// G = exp(power) for a power from pair_power on a staged conic.
+__device__ __forceinline__ float pair_gauss(float power)
+{
+#if RASTER_LOG2_CONIC
+    float g;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(g) : "f"(power));
+    return g;
+#else
+    return __expf(power);
+#endif
+}
+
 __device__ __forceinline__ float pair_alpha_raw(float4 co, float power)
 {
-    return __fmul_rn(co.w, __expf(power));
+    return __fmul_rn(co.w, pair_gauss(power));
 }
 
 constexpr float kAlphaMin = 1.0f / 255.0f;
@@ -230,7 +261,7 @@ __global__ void __launch_bounds__(FT) raster_fwd_kernel(RasterParams p)
         const int slot = compact_slot<FT>(keep, s_wcnt, cnt);
         if (slot >= 0) {
             s_xy[slot] = m;
-            s_co[slot] = co;
+            s_co[slot] = scale_conic(co);
             s_rgbk[slot] = make_float4(p.rgb[3 * o], p.rgb[3 * o + 1], p.rgb[3 * o + 2],
                                        __int_as_float(k));
         }
@@ -317,7 +348,7 @@ __global__ void __launch_bounds__(FT / 2) raster_fwd2_kernel(RasterParams p)
         const int slot = compact_slot<NT>(keep, s_wcnt, cnt);
         if (slot >= 0) {
             s_xy[slot] = m;
-            s_co[slot] = co;
+            s_co[slot] = scale_conic(co);
             s_rgbk[slot] = make_float4(p.rgb[3 * o], p.rgb[3 * o + 1], p.rgb[3 * o + 2],
                                        __int_as_float(k));
         }
@@ -415,7 +446,7 @@ __device__ __forceinline__ bool unblend_at(PixBwd &P, float4 co, float4 c, float
                                            float dy, float dxx, float dxy, float dyy, float *v)
 {
     if (power > 0.f) return false;
-    float G = __expf(power);
+    float G = pair_gauss(power);
     float araw = __fmul_rn(co.w, G);
     float alpha = fminf(kAlphaCap, araw);
     if (alpha < kAlphaMin) return false;
@@ -538,7 +569,7 @@ __global__ void __launch_bounds__(256 / PPT) raster_bwd_kernel(RasterParams p)
         if (slot >= 0) {
             s_g[slot] = g;
             s_xy[slot] = m;
-            s_co[slot] = co;
+            s_co[slot] = scale_conic(co);
             s_rgbk[slot] = make_float4(p.rgb[3 * o], p.rgb[3 * o + 1], p.rgb[3 * o + 2],
                                        __int_as_float(k));
         }
@@ -616,7 +647,7 @@ __global__ void __launch_bounds__(256 / PPT) raster_bwd_kernel(RasterParams p)
                 }
                 if (sum.x != 0.f || sum.y != 0.f || sum.z != 0.f || sum.w != 0.f)
                     atomicAdd(reinterpret_cast<float4 *>(p.grads + 8 * (vb + s_g[clo + j]) + h),
-                              moments_to_grads(sum, s_co[clo + j], h));
+                              moments_to_grads(sum, unscale_conic(s_co[clo + j]), h));
             }
             if (WANT_OP) {
                 for (int j = tid; j < ccnt; j += NT) {
