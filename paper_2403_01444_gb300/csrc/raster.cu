@@ -172,12 +172,16 @@ __device__ __forceinline__ bool ellipse_hits_tile(float2 m, float4 co, int tx_t,
     const float ya = (float)(ty_t * 16) + 0.5f - m.y, yb = ya + 15.f;
     if (xa <= 0.f && xb >= 0.f && ya <= 0.f && yb >= 0.f) return true;
     const float A = co.x, B = co.y, C = co.z;
+    // the 1-D minimisers need not be exact: q at any point of an edge bounds
+    // its minimum from above, and a minimiser off by a rounding moves q by a
+    // second-order amount, far inside the margin
+    const float bA = B * __frcp_rn(A), bC = B * __frcp_rn(C);
     auto qx = [&](float dx) {  // min over dy in [ya, yb] at fixed dx
-        float dy = fminf(fmaxf(-B * dx / C, ya), yb);
+        float dy = fminf(fmaxf(-bC * dx, ya), yb);
         return A * dx * dx + 2.f * B * dx * dy + C * dy * dy;
     };
     auto qy = [&](float dy) {  // min over dx in [xa, xb] at fixed dy
-        float dx = fminf(fmaxf(-B * dy / A, xa), xb);
+        float dx = fminf(fmaxf(-bA * dy, xa), xb);
         return A * dx * dx + 2.f * B * dx * dy + C * dy * dy;
     };
     float q = fminf(fminf(qx(xa), qx(xb)), fminf(qy(ya), qy(yb)));
