@@ -31,17 +31,6 @@ constexpr int HITEMS = SR * (SX / HSEG);
 static_assert(SX * (SY / VSEG) == LTHREADS, "vertical stage: one column segment per thread");
 static_assert(SX % HSEG == 0 && HSEG == 4, "horizontal items hold four outputs");
 
-// Normalised 11-tap Gaussian window (sigma 1.5), built by each block in
-// shared memory (no constant-memory upload, so the call is capture-safe).
-__device__ __forceinline__ void build_window(float *w)
-{
-    if (threadIdx.x < 11) {
-        float s = 0.f;
-        for (int i = 0; i < 11; ++i) s += expf(-(float)((i - 5) * (i - 5)) / 4.5f);
-        int i = threadIdx.x;
-        w[i] = expf(-(float)((i - 5) * (i - 5)) / 4.5f) / s;
-    }
-}
 
 // The window as tap pairs for the row filter: e[i] = (w_2i, w_2i+1) for
 // outputs whose window starts on an even input, o[i] = (w_2i-1, w_2i) with
@@ -112,6 +101,7 @@ __device__ __forceinline__ void row_filter(const float2 (&m)[NPAIR], const RowTa
 __device__ __forceinline__ float2 dup(float a) { return make_float2(a, a); }
 
 struct LossParams {
+    float win[11];        // normalised 11-tap Gaussian window (sigma 1.5), set on the host
     const float *x, *y;
     int P, H, W;
     float lam;
@@ -132,9 +122,7 @@ __global__ void __launch_bounds__(LTHREADS, SSIM_FWD_MIN_BLOCKS) ssim_fwd_kernel
     __shared__ float2 s_sq[SR][SX];   // row-filtered (x^2, y^2)
     __shared__ float s_p[SR][SX];     // row-filtered x y
     __shared__ double red[2][LTHREADS / 32];
-    __shared__ float c_win[11];
-    build_window(c_win);
-    __syncthreads();
+    const float *c_win = p.win;
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * SX, y0 = blockIdx.y * SY, pl = blockIdx.z;
     const int64_t HW = (int64_t)p.H * p.W;
@@ -276,9 +264,7 @@ __global__ void __launch_bounds__(LTHREADS, SSIM_BWD_MIN_BLOCKS) ssim_bwd_kernel
 {
     __shared__ float2 s_ab[SR][SX];   // row-filtered (ca, cb)
     __shared__ float s_c[SR][SX];     // row-filtered cc
-    __shared__ float c_win[11];
-    build_window(c_win);
-    __syncthreads();
+    const float *c_win = p.win;
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * SX, y0 = blockIdx.y * SY, pl = blockIdx.z;
     const int64_t HW = (int64_t)p.H * p.W;
@@ -420,6 +406,11 @@ extern "C" gs_status gs_loss_l1_dssim(const float *img, const float *target, int
                "gs_loss_l1_dssim: workspace too small");
     GS_REQUIRE(aligned(ws, 256), "gs_loss_l1_dssim: workspace must be 256-byte aligned");
     LossParams p{};
+    {
+        double w[11], sum = 0.0;
+        for (int i = 0; i < 11; ++i) sum += (w[i] = exp(-(double)((i - 5) * (i - 5)) / 4.5));
+        for (int i = 0; i < 11; ++i) p.win[i] = (float)(w[i] / sum);
+    }
     p.x = img;
     p.y = target;
     p.P = planes;
