@@ -14,9 +14,12 @@
 // pair (in_j, in_j+1) and the halves are added at the end; down a column the
 // two maps of a pair (x and y, x^2 and y^2, two coefficient maps) share the
 // weight.
+#include <cuda.h>
+#include <mutex>
 #include <math.h>
 
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace gs3 {
 
@@ -116,29 +119,103 @@ struct LossParams {
 #ifndef SSIM_FWD_MIN_BLOCKS
 #define SSIM_FWD_MIN_BLOCKS 3  // 80 registers, no spills
 #endif
-__global__ void __launch_bounds__(LTHREADS, SSIM_FWD_MIN_BLOCKS) ssim_fwd_kernel(LossParams p)
+// TMA staging of the forward's input window: columns x0 - 8 .. x0 + 39 (TW,
+// a 16-byte aligned start) and rows y0 - LH .. y0 + SY + LH - 1 of one plane
+// of each image, zero-filled outside the image by the copy itself.  Two
+// stages of TH rows, each on its own mbarrier: the row filter works through
+// the first half of the window while the second is still in flight.
+constexpr int TW = 48;
+constexpr int TH = SR / 2;   // 29 rows per stage
+static_assert(SR % 2 == 0 && TH * (SX / HSEG) <= LTHREADS, "one round of items per stage");
+constexpr uint32_t kTmaStageBytes = 2u * TH * TW * sizeof(float);   // x and y, one stage
+// each (image, stage) buffer starts on a 128-byte boundary, as the copies require
+constexpr int kTmaBufFloats = ((TH * TW * (int)sizeof(float) + 127) / 128) * 128 / (int)sizeof(float);
+constexpr uint32_t kTmaSmem = 4u * kTmaBufFloats * sizeof(float) + 128;  // + alignment slack
+
+template <bool TMA>
+__global__ void __launch_bounds__(LTHREADS, SSIM_FWD_MIN_BLOCKS)
+    ssim_fwd_kernel(LossParams p, const __grid_constant__ CUtensorMap tmx,
+                    const __grid_constant__ CUtensorMap tmy)
 {
     __shared__ float2 s_xy[SR][SX];   // row-filtered (x, y)
     __shared__ float2 s_sq[SR][SX];   // row-filtered (x^2, y^2)
     __shared__ float s_p[SR][SX];     // row-filtered x y
     __shared__ double red[2][LTHREADS / 32];
+    __shared__ __align__(8) unsigned long long s_mbar[2];
+    extern __shared__ __align__(128) unsigned char s_dyn[];   // TMA: [image][stage][TH][TW] floats
+    float *s_in = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(s_dyn) + 127) & ~uintptr_t(127));
     const float *c_win = p.win;
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * SX, y0 = blockIdx.y * SY, pl = blockIdx.z;
     const int64_t HW = (int64_t)p.H * p.W;
     const float *X = p.x + pl * HW, *Y = p.y + pl * HW;
     float lsum = 0.f;
+    bool ok = true;
+    if (TMA) {
+        if (tid == 0) {
+            tc::mbar_init(tc::smem_u32(&s_mbar[0]), 1);
+            tc::mbar_init(tc::smem_u32(&s_mbar[1]), 1);
+        }
+        __syncthreads();
+        if (tid == 0) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t mbar = tc::smem_u32(&s_mbar[h]);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar),
+                             "r"(kTmaStageBytes)
+                             : "memory");
+                asm volatile(
+                    "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                    " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(tc::smem_u32(s_in + h * kTmaBufFloats)),
+                    "l"(reinterpret_cast<uint64_t>(&tmx)), "r"(x0 - 8), "r"(y0 - LH + h * TH), "r"(pl),
+                    "r"(mbar)
+                    : "memory");
+                asm volatile(
+                    "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                    " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(tc::smem_u32(s_in + (2 + h) * kTmaBufFloats)),
+                    "l"(reinterpret_cast<uint64_t>(&tmy)), "r"(x0 - 8), "r"(y0 - LH + h * TH), "r"(pl),
+                    "r"(mbar)
+                    : "memory");
+            }
+        }
+    }
     {
         const RowTaps t = row_taps(c_win);
-        for (int item = tid; item < HITEMS; item += LTHREADS) {
+        for (int round = 0; round < (TMA ? 2 : (HITEMS + LTHREADS - 1) / LTHREADS); ++round) {
+            int item;
+            if (TMA) {
+                // stage `round` holds rows TH round .. TH round + TH - 1; bounded
+                // wait, and a block that gives up writes NaN outputs (the loss
+                // and, through the gradient, the non-finite check report it)
+                ok = __syncthreads_and(ok && tc::mbar_wait(tc::smem_u32(&s_mbar[round]), 0, tc::kWaitTries));
+                if (tid >= TH * (SX / HSEG)) continue;
+                item = round * TH * (SX / HSEG) + tid;
+            } else {
+                item = round * LTHREADS + tid;
+                if (item >= HITEMS) continue;
+            }
             const int r = item / (SX / HSEG), c0 = (item % (SX / HSEG)) * HSEG;
             const int gy = y0 - LH + r;
             float fx[HSEG], fy[HSEG], fxx[HSEG], fyy[HSEG], fxy[HSEG];
-            if (gy >= 0 && gy < p.H) {
+            if (TMA || (gy >= 0 && gy < p.H)) {
                 const int B = x0 + c0 - 8;
                 float2 mx[NPAIR], my[NPAIR], mxx[NPAIR], myy[NPAIR], mxy[NPAIR];
-                load_pairs(X + (int64_t)gy * p.W, p.W, B, p.vec, mx);
-                load_pairs(Y + (int64_t)gy * p.W, p.W, B, p.vec, my);
+                if (TMA) {
+                    const int h = r / TH, rl = r - h * TH;   // stage and row within it
+                    const float2 *rx =
+                        reinterpret_cast<const float2 *>(s_in + h * kTmaBufFloats + rl * TW + c0);
+                    const float2 *ry =
+                        reinterpret_cast<const float2 *>(s_in + (2 + h) * kTmaBufFloats + rl * TW + c0);
+                    mx[0] = my[0] = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int k = 1; k < NPAIR; ++k) {
+                        mx[k] = rx[k];
+                        my[k] = ry[k];
+                    }
+                } else {
+                    load_pairs(X + (int64_t)gy * p.W, p.W, B, p.vec, mx);
+                    load_pairs(Y + (int64_t)gy * p.W, p.W, B, p.vec, my);
+                }
 #pragma unroll
                 for (int k = 1; k < NPAIR; ++k) {
                     mxx[k] = __fmul2_rn(mx[k], mx[k]);
@@ -151,7 +228,7 @@ __global__ void __launch_bounds__(LTHREADS, SSIM_FWD_MIN_BLOCKS) ssim_fwd_kernel
                 row_filter(myy, t, fyy);
                 row_filter(mxy, t, fxy);
                 // L1 term at the item's outputs in_8 .. in_11 (pairs 4 and 5)
-                if (r >= LH && r < LH + SY) {
+                if (r >= LH && r < LH + SY && gy < p.H) {
 #pragma unroll
                     for (int o = 0; o < HSEG; ++o) {
                         const float2 a = mx[4 + o / 2], b = my[4 + o / 2];
@@ -230,10 +307,11 @@ __global__ void __launch_bounds__(LTHREADS, SSIM_FWD_MIN_BLOCKS) ssim_fwd_kernel
         const float ds_dsxx = -sv * (d1 * idd);
         const float ds_dsxy = 2.f * n1 * idd;
         const int64_t oo = pl * HW + (int64_t)gy * p.W + gx;
-        p.ca[oo] = ds_dmx - 2.f * mx * ds_dsxx - my * ds_dsxy;
-        p.cb[oo] = ds_dsxx;
-        p.cc[oo] = ds_dsxy;
-        ssum += sv;
+        const float bad = ok ? 0.f : __int_as_float(0x7fc00000);   // NaN when the copy gave up
+        p.ca[oo] = ds_dmx - 2.f * mx * ds_dsxx - my * ds_dsxy + bad;
+        p.cb[oo] = ds_dsxx + bad;
+        p.cc[oo] = ds_dsxy + bad;
+        ssum += sv + bad;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -384,6 +462,38 @@ __global__ void __launch_bounds__(1024) loss_final_kernel(LossParams p)
 
 static size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
+#ifndef SSIM_TMA
+#define SSIM_TMA 1
+#endif
+
+// Tiled TMA map of a [planes][H][W] FP32 image stack with a TW x TH box.
+// False (and the L1 path is used) when the driver entry point is missing or
+// the rows are not 16-byte aligned.
+static bool make_plane_map(CUtensorMap *m, const float *base, int planes, int H, int W)
+{
+    typedef CUresult (*EncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                    const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                    const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static EncodeTiled encode = [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            fn = nullptr;
+        return reinterpret_cast<EncodeTiled>(fn);
+    }();
+    if (!encode || W % 4 != 0 || !aligned(base, 16)) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)planes};
+    const cuuint64_t strides[2] = {(cuuint64_t)W * sizeof(float), (cuuint64_t)H * W * sizeof(float)};
+    const cuuint32_t box[3] = {(cuuint32_t)TW, (cuuint32_t)TH, 1u};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box,
+                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace gs3
 
 using namespace gs3;
@@ -430,8 +540,20 @@ extern "C" gs_status gs_loss_l1_dssim(const float *img, const float *target, int
     dim3 grid((unsigned)ceil_div(W, SX), (unsigned)ceil_div(H, SY), (unsigned)planes);
     p.nblocks = (int)(grid.x * grid.y * grid.z);
     cudaStream_t s = as_stream(stream);
+    CUtensorMap tmx{}, tmy{};
+    const bool tma = SSIM_TMA && p.vec && make_plane_map(&tmx, img, planes, H, W) &&
+                     make_plane_map(&tmy, target, planes, H, W);
     note_launch();
-    ssim_fwd_kernel<<<grid, LTHREADS, 0, s>>>(p);
+    if (tma) {
+        static std::once_flag once;
+        std::call_once(once, [] {
+            cudaFuncSetAttribute((const void *)ssim_fwd_kernel<true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem);
+        });
+        ssim_fwd_kernel<true><<<grid, LTHREADS, kTmaSmem, s>>>(p, tmx, tmy);
+    } else {
+        ssim_fwd_kernel<false><<<grid, LTHREADS, 0, s>>>(p, tmx, tmy);
+    }
     note_launch();
     ssim_bwd_kernel<<<grid, LTHREADS, 0, s>>>(p);
     note_launch();
