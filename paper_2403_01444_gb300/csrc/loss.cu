@@ -7,8 +7,9 @@
 //
 // Both filtering passes work on 32 x 48 output tiles.  The horizontal stage
 // reads its inputs straight from global memory (through L1, as float4 where
-// rows are 16-byte aligned) and leaves the row-filtered maps in shared
-// memory; the vertical stage filters the columns from there.  The filters use
+// rows are 16-byte aligned; in pass 1 with such rows the tile's input window
+// comes into shared memory by TMA instead) and leaves the row-filtered maps
+// in shared memory; the vertical stage filters the columns from there.  The filters use
 // the packed FP32 FMA of sm_100+ (both halves of an aligned register pair in
 // one instruction): along a row a tap pair (w_t, w_t+1) multiplies an input
 // pair (in_j, in_j+1) and the halves are added at the end; down a column the
@@ -187,7 +188,8 @@ __global__ void __launch_bounds__(LTHREADS, SSIM_FWD_MIN_BLOCKS)
                 // stage `round` holds rows TH round .. TH round + TH - 1; bounded
                 // wait, and a block that gives up writes NaN outputs (the loss
                 // and, through the gradient, the non-finite check report it)
-                ok = __syncthreads_and(ok && tc::mbar_wait(tc::smem_u32(&s_mbar[round]), 0, tc::kWaitTries));
+                const bool got = tc::mbar_wait(tc::smem_u32(&s_mbar[round]), 0, tc::kWaitTries);
+                ok = __syncthreads_and(ok && got);
                 if (tid >= TH * (SX / HSEG)) continue;
                 item = round * TH * (SX / HSEG) + tid;
             } else {
