@@ -17,7 +17,7 @@ constexpr int BWD_CHUNK = BWD_CHUNK_RECORDS;  // records per backward reduction 
 #define BWD_UNROLL 2
 #endif
 #ifndef FWD_UNROLL
-#define FWD_UNROLL 4
+#define FWD_UNROLL 8
 #endif
 constexpr int kBwdUnroll = BWD_UNROLL, kFwdUnroll = FWD_UNROLL;
 #ifndef FWD_PIXELS_PER_THREAD
