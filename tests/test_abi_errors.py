@@ -1,0 +1,87 @@
+"""Synchronous argument errors of the C-ABI boundary: a call with a bad
+argument returns GS_ERR_INVALID_ARG before anything is launched and leaves a
+message for gs_last_error.  Every call here fails its argument check before
+any device work, so no GPU is needed; the pointers are never dereferenced."""
+from ctypes import byref, c_float, c_int64, c_size_t, c_void_p
+
+import pytest
+
+from paper_2403_01444_gb300 import build, gs3
+
+FAKE = c_void_p(0x10000)   # a 16-byte aligned address no call below reaches
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return gs3.lib()
+
+
+def _fails(L, status, *words):
+    assert status == gs3.GS_ERR_INVALID_ARG
+    msg = L.gs_last_error().decode()
+    for w in words:
+        assert w in msg, msg
+
+
+def _gauss(n=10, deg=1):
+    return gs3.GsGaussians(FAKE, FAKE, FAKE, FAKE, FAKE, n, deg)
+
+
+def _proj():
+    return gs3.GsProjected(FAKE, FAKE, FAKE, FAKE, FAKE, FAKE)
+
+
+def test_projection_rejects_bad_arguments(L):
+    g, out = _gauss(), _proj()
+    _fails(L, L.gs_project(None, FAKE, 1, 64, 48, byref(out), None), "gs_project", "null")
+    _fails(L, L.gs_project(byref(g), FAKE, 0, 64, 48, byref(out), None), "V must be")
+    _fails(L, L.gs_project(byref(g), FAKE, 65, 64, 48, byref(out), None), "V must be")   # GS_MAX_VIEWS + 1
+    _fails(L, L.gs_project(byref(g), FAKE, 1, 0, 48, byref(out), None), "image size")
+    _fails(L, L.gs_project(byref(_gauss(deg=4)), FAKE, 1, 64, 48, byref(out), None), "sh_deg")
+    _fails(L, L.gs_project(byref(_gauss(n=-1)), FAKE, 1, 64, 48, byref(out), None), "n out of range")
+    misaligned = gs3.GsGaussians(FAKE, c_void_p(0x10004), FAKE, FAKE, FAKE, 10, 1)
+    _fails(L, L.gs_project(byref(misaligned), FAKE, 1, 64, 48, byref(out), None), "aligned")
+
+
+def test_binning_and_compositing_reject_bad_arguments(L):
+    p = _proj()
+    # bins outside 1..64 tiles
+    _fails(L, L.gs_bin_sort(byref(p), c_int64(10), 1, 64, 48, 0, c_int64(100), FAKE, FAKE, None,
+                            FAKE, FAKE, FAKE, c_size_t(1 << 20), None), "bin")
+    _fails(L, L.gs_raster_fwd(byref(p), c_int64(10), 1, 64, 48, 65, None, FAKE, FAKE, FAKE, FAKE,
+                              FAKE, None, None), "bin")
+    # views outside 1..GS_MAX_VIEWS, image too large
+    _fails(L, L.gs_raster_fwd(byref(p), c_int64(10), 0, 64, 48, 1, None, FAKE, FAKE, FAKE, FAKE,
+                              FAKE, None, None), "bad n or V")
+    _fails(L, L.gs_raster_fwd(byref(p), c_int64(10), 1, 20000, 48, 1, None, FAKE, FAKE, FAKE, FAKE,
+                              FAKE, None, None), "image size")
+
+
+def test_loss_rejects_bad_shapes_and_small_workspaces(L):
+    L.gs_loss_workspace_size.restype = c_size_t
+    need = L.gs_loss_workspace_size(3, 48, 64)
+    assert need > 0
+    _fails(L, L.gs_loss_l1_dssim(FAKE, FAKE, 0, 48, 64, c_float(0.2), FAKE, FAKE, None, FAKE,
+                                 c_size_t(need), None), "bad shape")
+    _fails(L, L.gs_loss_l1_dssim(FAKE, FAKE, 3, 48, 64, c_float(0.2), FAKE, FAKE, None, FAKE,
+                                 c_size_t(need - 1), None), "workspace too small")
+    _fails(L, L.gs_loss_l1_dssim(FAKE, FAKE, 3, 48, 64, c_float(0.2), FAKE, FAKE, None,
+                                 c_void_p(0x10010), c_size_t(need), None), "256-byte aligned")
+
+
+def test_cache_and_optimiser_reject_bad_arguments(L):
+    bad_grid = gs3.hashgrid()
+    bad_grid.levels = 0
+    _fails(L, L.ntc_encode_fwd(FAKE, c_int64(10), byref(bad_grid), FAKE, gs3.GS_F16, FAKE,
+                               gs3.GS_F32, None), "invalid hash grid")
+    good = gs3.hashgrid()
+    _fails(L, L.ntc_encode_fwd(FAKE, c_int64(10), byref(good), FAKE, gs3.GS_BF16, FAKE, gs3.GS_F32,
+                               None), "table dtype")
+    _fails(L, L.adam_step(FAKE, FAKE, FAKE, FAKE, c_int64(16), None, FAKE, None, gs3.GS_NONE, None),
+           "adam_step")
+    _fails(L, L.gs_sh_rotate(FAKE, FAKE, FAKE, c_int64(10), 4, FAKE, None), "sh_deg")
+    # empty inputs are valid and do nothing (no device work either)
+    assert L.gs_sh_rotate(FAKE, FAKE, FAKE, c_int64(0), 3, FAKE, None) == gs3.GS_OK
+    assert L.ntc_encode_fwd(None, c_int64(0), byref(good), None, gs3.GS_F16, None, gs3.GS_F32,
+                            None) == gs3.GS_OK
