@@ -283,7 +283,6 @@ def run_ours(args):
     from paper_2403_01444_gb300 import gs3, scenes
     from paper_2403_01444_gb300.engine import (TargetFeeder, NTC, DirectOpt, Rasterizer, Renderer, Stage1,
                                                autotune_bin, warmup)
-    import oracle  # only for the grid size of the initial table (host integer layout)
 
     if args.small:
         scene = scenes.make_scene(CFG_INDEX, n_gauss=100_000)

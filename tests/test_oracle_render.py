@@ -167,6 +167,116 @@ def test_two_gaussians_blend_and_swap():
     np.testing.assert_allclose(img2[0, :, 16, 16], c2 * a2 + c1 * a1 * (1 - a2), rtol=1e-6)
 
 
+@pytest.mark.parametrize("ologit", [5.0, 10.0])
+def test_alpha_cap_closed_form(ologit):
+    """Eq. 4 with the 0.99 cap: an isotropic Gaussian of opacity above 0.99
+    (logit 5: o = 0.99331; logit 10: o = 0.99995) on the optical axis.  On the
+    disc where o G >= 0.99 the pixel is exactly 0.99 c and 0.01 of the light
+    is left: T (1 - 0.99) = 0.01 is far above the 1e-4 cutoff, so the Gaussian
+    is added.  Outside the disc the pixel is c o G.  (Were the cutoff tested
+    on the uncapped alpha, the logit-10 centre would give T (1 - alpha) =
+    5e-5 < 1e-4 and stay empty; a cap of 0.999 would give 0.999 c.)"""
+    W, H = 96, 72
+    cam = scenes.look_at_camera((0.0, 0.0, 4.0), W, H)
+    c = np.array([0.7, 0.2, 0.45])
+    g = _one_gaussian((0, 0, 0), (1, 0, 0, 0), (1.0,) * 3, ologit, c)
+    r = oracle.render(g, [cam])
+    var = (cam.fx * 1.0 / 4.0) ** 2 + 0.3
+    o = 1.0 / (1.0 + math.exp(-float(np.float32(ologit))))
+    assert o > 0.99
+    want = np.zeros((3, H, W))
+    want_T = np.ones((H, W))
+    capped = 0
+    for j in range(H):
+        for i in range(W):
+            x = o * math.exp(-0.5 * ((i + 0.5 - W / 2) ** 2 + (j + 0.5 - H / 2) ** 2) / var)
+            assert abs(x - 0.99) > 1e-9 and abs(x - 1 / 255) > 1e-9  # no pixel on a threshold
+            if x >= 0.99:
+                want[:, j, i], want_T[j, i] = 0.99 * c, 0.01
+                capped += 1
+            elif x >= 1 / 255:
+                want[:, j, i], want_T[j, i] = c * x, 1.0 - x
+    assert capped >= 8
+    np.testing.assert_allclose(r["img"][0], want, atol=1e-12)
+    np.testing.assert_allclose(r["T_final"][0], want_T, atol=1e-12)
+
+
+def _stack_records(opacities, W=32, H=32, conic=(0.002, 0.0, 0.002)):
+    """Gaussians centred on the pixel centre (16.5, 16.5), in depth order,
+    with broad footprints (float64 records)."""
+    n = len(opacities)
+    f = lambda a: np.array([a], np.float64)
+    return dict(mean2d=f([[16.5, 16.5]] * n), conic=f([list(conic)] * n),
+                opacity=f(list(opacities)), depth=f([1.0 + k for k in range(n)]),
+                rgb=f([[0.9, 0.1, 0.3], [0.2, 0.8, 0.4], [0.5, 0.5, 1.0]][:n]),
+                radius=np.array([[40] * n], np.int32))
+
+
+def test_alpha_cap_then_cutoff_sequence():
+    """At the shared centre (power 0): a Gaussian of opacity 0.999 is capped
+    to alpha 0.99 (T 1 -> 0.01), one of opacity 0.5 is added (T -> 0.005), and
+    a third capped one would leave T (1 - 0.99) = 5e-5 < 1e-4, so the loop
+    stops without adding it: C = 0.99 c1 + 0.01 * 0.5 c2, T_final = 0.005,
+    last = 2 (Eq. 4 with the cap, the 1e-4 cutoff tested on the capped alpha)."""
+    rec = _stack_records([0.999, 0.5, 0.999])
+    img, Tf, last, _ = oracle.raster_fwd(rec, 32, 32)
+    c1, c2 = rec["rgb"][0, 0], rec["rgb"][0, 1]
+    np.testing.assert_allclose(img[0, :, 16, 16], 0.99 * c1 + 0.005 * c2, rtol=0, atol=1e-15)
+    assert abs(Tf[0, 16, 16] - 0.005) < 1e-15
+    assert last[0, 16, 16] == 2
+
+
+def test_alpha_cap_zero_gradient_finite_differences():
+    """Through a capped pixel alpha = 0.99 is constant, so the pixel has no
+    gradient with respect to the capped Gaussian's opacity, conic or 2D mean,
+    and its colour gradient is 0.99 T; the Gaussian behind still receives its
+    gradients through T = 0.01.  The image gradient is non-zero only on
+    pixels well inside the capped disc (o G >= 0.99 (1 + 1e-4)), where central
+    differences with h = 1e-6 cross no decision: analytic reverse and finite
+    differences must agree, and the capped Gaussian's opacity, conic and mean
+    gradients must vanish."""
+    W = H = 32
+    rec = _stack_records([0.9995, 0.6], W, H, conic=(0.004, 0.0005, 0.003))
+    rec["mean2d"][0, 1] = [18.2, 15.1]
+    rec["conic"][0, 1] = [0.02, -0.004, 0.015]
+    yy, xx = np.mgrid[0:H, 0:W] + 0.5
+    dx, dy = xx - 16.5, yy - 16.5
+    A, B, C = rec["conic"][0, 0]
+    x1 = rec["opacity"][0, 0] * np.exp(-0.5 * (A * dx * dx + C * dy * dy) - B * dx * dy)
+    inside = x1 >= 0.99 * (1 + 1e-4)
+    assert inside.sum() >= 12 and not inside.all()
+    rng = np.random.default_rng(17)
+    dimg = rng.normal(size=(1, 3, H, W)) * inside[None, None]
+    img, Tf, last, _ = oracle.raster_fwd(rec, W, H)
+    grads, dop = oracle.raster_bwd(rec, W, H, Tf, last, dimg, want_opacity=True)
+    # the capped Gaussian: no opacity / conic / mean gradient, colour gradient 0.99 * sum dimg
+    assert np.all(grads[0, 0, :5] == 0) and dop[0, 0] == 0
+    np.testing.assert_allclose(grads[0, 0, 5:], 0.99 * dimg[0].sum((1, 2)), rtol=1e-12)
+    # the Gaussian behind receives gradients (through T = 0.01)
+    assert np.abs(grads[0, 1, :5]).max() > 1e-6 and abs(dop[0, 1]) > 1e-6
+
+    def f(r):
+        return np.sum(oracle.raster_fwd(r, W, H)[0] * dimg)
+
+    h = 1e-6
+    for i in range(2):
+        for key, comp, gi in [("mean2d", 0, 0), ("mean2d", 1, 1), ("conic", 0, 2), ("conic", 1, 3),
+                              ("conic", 2, 4), ("rgb", 0, 5), ("rgb", 1, 6), ("rgb", 2, 7),
+                              ("opacity", None, None)]:
+            rp = {k: v.copy() for k, v in rec.items()}
+            rm = {k: v.copy() for k, v in rec.items()}
+            if comp is None:
+                rp[key][0, i] += h
+                rm[key][0, i] -= h
+                want = dop[0, i]
+            else:
+                rp[key][0, i, comp] += h
+                rm[key][0, i, comp] -= h
+                want = grads[0, i, gi]
+            fd = (f(rp) - f(rm)) / (2 * h)
+            assert abs(fd - want) <= 1e-7 * max(1.0, abs(fd)), (i, key, comp, fd, want)
+
+
 def test_transmittance_invariants():
     W, H = 80, 64
     rec = _records(2, 400, W, H, 14)
