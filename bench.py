@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--mlp", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-oracle-configs", action="store_true",
+                    help="skip the oracle timings of the other workloads")
     ap.add_argument("--small", action="store_true",
                     help="100K Gaussians instead of 250K (smaller profiling captures)")
     ap.add_argument("--warm-iters", type=int, default=1000, help="NTC warm-up iterations (Eq. 7)")
@@ -52,7 +54,7 @@ def parse():
     ap.add_argument("--no-render", action="store_true", help="skip the render-only measurement")
     ap.add_argument("--no-stage2", action="store_true", help="skip the Stage-2 measurement")
     ap.add_argument("--no-large", action="store_true", help="skip the 1M-Gaussian, 16-view run")
-    ap.add_argument("--stream-frames", type=int, default=3,
+    ap.add_argument("--stream-frames", type=int, default=30,
                     help="frames of the streaming run (0: skip)")
     ap.add_argument("--bin", type=int, default=0,
                     help="bin side in tiles (0: autotune over 1, 2, 4, 8, 16)")
@@ -171,6 +173,73 @@ def oracle_sample(scene, n_sample_gauss=None, views=1):
     return per_iter, desc, oracle.num_threads()
 
 
+def oracle_configs(budget_s=90.0):
+    """The FP64 oracle on the other workloads, on the host cores: the plain
+    method on the 4 096-Gaussian scene (all 50 direct-optimisation
+    iterations), the cache on the 50K-Gaussian scene (one Stage-1 iteration,
+    x 150 for a frame), and one 2-view forward + backward of the 500K and 1M
+    Gaussian scenes.  Each entry says what it timed; entries are skipped once
+    `budget_s` of CPU time is spent."""
+    import oracle
+    from paper_2403_01444_gb300 import scenes
+    oracle.build()
+    out = {"cores": oracle.num_threads()}
+    spent = 0.0
+
+    def fwd_bwd(g, cams, targets, mean=None, quat=None):
+        r = oracle.render(g, cams, mean, quat)
+        L, d_img, _ = oracle.loss_l1_dssim(r["img"], targets)
+        gr = oracle.raster_bwd(r["proj"], cams[0].W, cams[0].H, r["T_final"], r["last"], d_img)
+        return oracle.project_bwd(g, cams, gr, mean=mean, quat=quat)
+
+    # config 1: plain FP32 method, every iteration
+    sc = scenes.make_scene(1)
+    g, cams = sc.prev, sc.cams
+    tg = oracle.render(sc.target, cams)["img"]
+    m, q = g.mean.astype(np.float64).copy(), g.quat.astype(np.float64).copy()
+    mm, vm, mq, vq = (np.zeros_like(x) for x in (m, m, q, q))
+    t0 = time.perf_counter()
+    for it in range(sc.cfg.iters):
+        dm, dq = fwd_bwd(g, cams, tg, m, q)
+        oracle.adam(m, dm, mm, vm, it + 1, lr=0.0024, b2=0.999)
+        oracle.adam(q, dq, mq, vq, it + 1, lr=0.015, b2=0.999)
+    t = time.perf_counter() - t0
+    spent += t
+    out["plain-fp32-4k"] = {"s": t, "timed": "all %d direct-optimisation iterations, 4 views of "
+                            "128x96, 4096 Gaussians" % sc.cfg.iters}
+    # config 2: one Stage-1 iteration of the cache, a frame is 150
+    sc = scenes.make_scene(2)
+    og = oracle.Grid()
+    rng = np.random.default_rng(0)
+    p = oracle.NTCParams(og, rng.uniform(-1e-4, 1e-4, size=(og.n_entries, 2)),
+                         scenes.random_mlp([32, 64, 64, 7], rng))
+    p.Ws[2][3] = np.abs(p.Ws[2][3]) + 1.0
+    tg = np.random.default_rng(1).uniform(size=(len(sc.cams), 3, sc.cfg.H, sc.cfg.W))
+    t0 = time.perf_counter()
+    oracle.stage1_loss_grads(p, sc.prev, sc.cams, tg)
+    t = time.perf_counter() - t0
+    spent += t
+    out["ntc-50k-8v-480x360"] = {"s_per_iter": t, "s_per_frame": 150 * t,
+                                 "timed": "one Stage-1 iteration (cache, 8 views, loss, backward); "
+                                          "frame = 150 x"}
+    # configs 4 and 5: one 2-view forward + backward
+    for idx in (4, 5):
+        name = scenes.CONFIGS[idx].name
+        if spent > budget_s:
+            out[name] = {"skipped": "CPU budget of %.0f s spent" % budget_s}
+            continue
+        sc = scenes.make_scene(idx)
+        cams = sc.cams[:2]
+        tg = np.random.default_rng(1).uniform(size=(2, 3, sc.cfg.H, sc.cfg.W))
+        t0 = time.perf_counter()
+        fwd_bwd(sc.prev, cams, tg)
+        t = time.perf_counter() - t0
+        spent += t
+        out[name] = {"s": t, "timed": "one forward + backward of 2 views (%dx%d, %d Gaussians)"
+                     % (sc.cfg.W, sc.cfg.H, sc.prev.n)}
+    return out
+
+
 def run_reference(args):
     """The reference arm: the FP64 oracle, as it stands, on the host cores.
     A Stage-1 iteration is split into five bounded units and each step runs
@@ -234,11 +303,15 @@ def run_reference(args):
             "the cache forward + backward, or one view's render + loss + backward; iteration = "
             "cache unit + %d view units; %.1f s of CPU" % (args.steps, g.n, Vb, wall))
     cores = oracle.num_threads()
+    ms_step = 1e3 * wall / max(args.steps, 1)
     line = {"impl": "reference", "metric": METRIC, "value": s_frame, "unit": "s/frame",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": per_iter * 1e3, "higher_is_better": False, "scaling": "weak",
+            "ms_per_step": ms_step, "ms_per_iteration": per_iter * 1e3,
+            "step": "one unit of a Stage-1 iteration (the cache forward + backward, or one "
+                    "view's render + loss + backward); an iteration is %d units" % (Vb + 1),
+            "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_dict(scene, "oracle"),
+            "config": config_dict(scene, "single"),
             "cpu_baseline": {"value": s_frame, "unit": "s/frame", "cores": cores, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": s_frame, "unit": "s/frame", "h2d_bytes_per_step": 0,
@@ -348,7 +421,10 @@ def run_ours(args):
 
     def step(i, record=False):
         if i % ITERS_PER_FRAME == 0:
-            ntc.reset_to(warm_table, warm_mlp)  # every frame starts from the warm-up parameters
+            # every frame starts from the warm-up parameters, its Adam step
+            # count (bias correction, rate schedule) from 0
+            ntc.reset_to(warm_table, warm_mlp)
+            st.reset_state()
         b = i % nb
         cd, tg = batch_cams[b], targets[b * Vb:(b + 1) * Vb]
         if not record:
@@ -361,7 +437,7 @@ def run_ours(args):
         E("t0")
         st.transform()
         E("t1")
-        gs3.gs_project(G, cd, Vb, W, H, st.raster.proj, st.mean_t, st.quat_t)
+        gs3.gs_project(G, cd, Vb, W, H, st.raster.proj, st.mean_t, st.quat_t, None, st.raster.d_err)
         E("t2")
         r = st.raster
         gs3.gs_bin_sort(r.proj, G.n, Vb, W, H, r.bin, r.capacity, r.vals, r.ranges, None, r.d_count, r.d_err, r.ws)
@@ -411,6 +487,16 @@ def run_ours(args):
         torch.cuda.synchronize()
         launches = (gs3.lib().gs_launch_count() - c0) * args.steps
     ms = e0.elapsed_time(e1) / args.steps
+    # one whole frame timed on its own, whatever K is: the reset to the
+    # warm-up parameters and 150 iterations
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for i in range(ITERS_PER_FRAME):
+        step(i)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    full_frame_s = f0.elapsed_time(f1) / 1e3
     if args.profile:
         if rank == 0:
             print(json.dumps({"profile_run": True, "ms_per_step": ms, "gpu_launches": int(launches),
@@ -448,7 +534,8 @@ def run_ours(args):
     hbm, bf16, src = load_peaks()
     dom = max(stages, key=stages.get)
     sm_mhz = clk.summary().get("sm_mhz") or 2070.0
-    roof = roofline_for(dom, stages[dom], pairs, pair_counts, G.n, Vb, W, H, cfg, hbm, src, sm_mhz)
+    n_sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    roof = roofline_for(dom, stages[dom], pairs, pair_counts, G.n, Vb, W, H, cfg, hbm, src, sm_mhz, n_sms)
 
     # the rasterizer fwd+bwd against HBM: algorithmic bytes of projection,
     # binning/sort, compositing fwd/bwd and projection bwd, counted per
@@ -547,6 +634,7 @@ def run_ours(args):
     for i in range(ke):
         if i % ITERS_PER_FRAME == 0:
             ntc.reset_to(warm_table, warm_mlp)
+            st.reset_state()
         e2e_step(i)
     stream.wait_stream(feeder.copy_stream)   # the copies issued, one ahead, all inside
     e1.record(stream)
@@ -557,8 +645,8 @@ def run_ours(args):
     cpu = None
     if converge is not None:
         # the paths' own final held-out PSNRs: does the plain path ever reach the cache's?
-        n_fin = converge["ntc"]["final_psnr"]
-        reach = [it for it, p in converge["direct"]["curve"] if p >= n_fin - 0.05]
+        n_fin = converge["ntc"]["final"]["heldout"]
+        reach = [p["it"] for p in converge["direct"]["curve"][1:] if p["heldout"] >= n_fin - 0.05]
         converge["direct_reaches_ntc_final_psnr_within_frame"] = bool(reach)
     stage2 = None
     used_graphs = graphs is not None
@@ -580,6 +668,8 @@ def run_ours(args):
         per_iter, desc, cores = oracle_sample(scene)
         cpu = {"value": per_iter * ITERS_PER_FRAME, "unit": "s/frame", "cores": cores,
                "kind": "oracle", "sample": desc}
+        if not args.no_oracle_configs:
+            cpu["other_workloads"] = oracle_configs()
 
     if rank == 0:
         clocks = clk.summary()
@@ -589,6 +679,7 @@ def run_ours(args):
                 "dtype": "mixed: f16 table, %s mlp, f32 raster" % args.mlp if precision == gs3.GS_MLP_BF16 else "f32",
                 "data": "synthetic", "config": config_dict(scene, "replicas%d" % world if world > 1 else "single"),
                 "train_it_per_s": 1e3 / ms_max,
+                "full_frame_s": full_frame_s,
                 "raster_fwd_bwd_it_per_s": 1e3 / raster_ms,
                 "raster_fwd_bwd_ms": raster_ms,
                 "plain_fp32_direct_opt": plain,
@@ -607,7 +698,7 @@ def run_ours(args):
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_ms * ITERS_PER_FRAME / 1e3, "unit": "s/frame",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4},
-                "gpu_launches": int(launches), "clocks": clocks}
+                "gpu_launches": int(launches), "tc_timeouts": gs3.gs_tc_timeouts(), "clocks": clocks}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()
@@ -770,8 +861,12 @@ def stream_workload(dev, n_frames, warm_table_mlp, ntc):
         rh.fit_capacity(gs3.Gaussians.from_numpy(frames[t + 1]), hod, margin=1.2)
         ho_gt.append(rh.img.clone())
     G0 = gs3.Gaussians.from_numpy(frames[0])
+    # weights of the motion error: visibility of frame 0's Gaussians in its views
+    wvis = visibility(G0, [(gs3.camera_slice(cd, b * Vb, Vb), out[b * Vb:(b + 1) * Vb])
+                           for b in range(nb)], W, H, dev)
+    mean_gt = lambda t: torch.from_numpy(frames[t + 1].mean).to(dev)
     s = Streamer(G0, ntc, *warm_table_mlp, cd, cfg.n_cams, Vb, W, H, heldout_dev=hod)
-    rec = s.run(views, ho_gt)
+    rec = s.run(views, ho_gt, motion_ref=(mean_gt, wvis))
     mean = lambda k: float(np.mean([r[k] for r in rec]))
     return {"workload": "stream: 250K Gaussians SH3, 20 cams 1352x1014, %d frames of cumulative "
                         "rigid+RBF motion; Stage 1 150 it + Stage 2 100 it per frame, Stage 2 "
@@ -779,83 +874,115 @@ def stream_workload(dev, n_frames, warm_table_mlp, ntc):
             "frames": n_frames, "wall_s": s.wall_s, "s_per_frame": s.wall_s / n_frames,
             "psnr_heldout_carried": mean("psnr_carried"), "psnr_heldout_stage1": mean("psnr_stage1"),
             "psnr_heldout_stage2": mean("psnr_stage2"), "added_per_frame": mean("added"),
+            "motion_err_weighted": mean("motion_err_weighted"),
+            "motion_err_if_not_transformed": mean("motion_err_carried_weighted"),
             "storage_bytes_per_frame": mean("storage_bytes"), "per_frame": rec}
+
+
+PLAIN_LR_SWEEP = (2.4e-3, 1e-3, 5e-4, 2e-4, 1e-4)   # mean rates of the direct path's sweep
+PLAIN_QUAT_RATIO = 0.015 / 0.0024                    # rotation : mean rate (Suppl. A proportions)
+
+
+def visibility(G, batches, W, H, dev):
+    """Per Gaussian of the previous frame: sum over the training views and
+    pixels of alpha T (its colour gradient under a unit image gradient), the
+    weight of its motion error."""
+    import torch
+    from paper_2403_01444_gb300.engine import Rasterizer
+    w = torch.zeros(G.n, device=dev)
+    r = None
+    for cd, tg in batches:
+        if r is None:
+            r = Rasterizer(G.n, tg.shape[0], W, H, 1 << 22, dev)
+        r.fit_capacity(G, cd, margin=1.2)
+        r.backward(G, cd, torch.ones_like(r.img))
+        w += r.grads[..., 5].sum(0)
+    return w
 
 
 def equal_psnr(scene, G, Gt, ntc, warm_table, warm_mlp, st, batches, nb, Vb, W, H, ms_ntc, ms_plain,
                dev, iters=ITERS_PER_FRAME, every=5):
-    """One frame of each path from the same previous-frame Gaussians: PSNR of
-    the held-out view and of the 20 training views every `every` iterations.
-    Target = the lower of the two paths' best held-out PSNR over the frame
-    (the quality both reach; with constant-rate Adam both curves peak and then
-    drift down, so the lower final PSNR is met at the first checkpoint); each
-    path's time to reach it (within 0.05 dB) = first checkpoint reaching it x
-    its measured time per iteration.  Also reported: the same with the lower
-    final PSNR as target, and both comparisons on the training views."""
+    """One frame of each path from the same previous-frame Gaussians, with
+    every `every` iterations: PSNR of the held-out view and of the 20 training
+    views, and the motion error against the known ground truth (mean
+    |mu' - mu_gt| and angle(q', q_gt) of the Gaussians the training views see,
+    weighted by visibility).  The plain path runs at each mean rate of
+    PLAIN_LR_SWEEP (rotation rate x PLAIN_QUAT_RATIO, the same schedule as the
+    cache) and the rate with the best held-out PSNR is compared.  Target = the
+    lower of the two paths' best held-out PSNR over the frame; each path's
+    time to reach it (within 0.05 dB) = first checkpoint reaching it x its
+    measured time per iteration.  Also reported: the same with the lower final
+    PSNR as target, and both comparisons on the training views."""
     import torch
     from paper_2403_01444_gb300.engine import DirectOpt, render
     ho = [scene.heldout]
     gt_ho = render(Gt, ho, W, H)
     psnr = lambda a, b: float(-10.0 * math.log10(max(((a - b) ** 2).mean().item(), 1e-20)))
     gt_train = torch.cat([render(Gt, scene.cams[b * Vb:(b + 1) * Vb], W, H) for b in range(nb)])
+    w = visibility(G, batches, W, H, dev)
+    seen = w > 1.0
 
     def train_psnr(m, q):
         img = torch.cat([render(G, scene.cams[b * Vb:(b + 1) * Vb], W, H, m, q) for b in range(nb)])
         return psnr(img, gt_train)
 
-    start = psnr(render(G, ho, W, H), gt_ho)
+    def motion(m, q):
+        dm = (m - Gt.mean).norm(dim=1)
+        qn = q / q.norm(dim=1, keepdim=True)
+        ang = 2 * torch.acos((qn * Gt.quat).sum(1).abs().clamp(max=1.0)) * (180 / math.pi)
+        return {"mean_err_weighted": float((dm * w).sum() / w.sum()), "mean_err_seen": float(dm[seen].mean()),
+                "angle_deg_weighted": float((ang * w).sum() / w.sum())}
+
+    def point(i, m, q):
+        r = {"it": i, "heldout": round(psnr(render(G, ho, W, H, m, q), gt_ho), 3),
+             "train": round(train_psnr(m, q), 3)}
+        r.update({k: round(v, 6) for k, v in motion(m, q).items()})
+        return r
+
+    start = point(0, G.mean, G.quat)
     ntc.reset_to(warm_table, warm_mlp)
     st.reset_state()
-    start_train = train_psnr(None, None)
-    curve_n, train_n = [], []
+    curve_n = [start]
     for i in range(iters):
         st.step(*batches[i % nb])
         if (i + 1) % every == 0:
-            m, q = st.transform()
-            curve_n.append((i + 1, psnr(render(G, ho, W, H, m, q), gt_ho)))
-            train_n.append((i + 1, train_psnr(m, q)))
-    tr_n = train_n[-1][1]
-    do = DirectOpt(G, Vb, W, H, st.raster.capacity, device=dev)
-    curve_d, train_d = [], []
-    for i in range(iters):
-        do.step(*batches[i % nb])
-        if (i + 1) % every == 0:
-            curve_d.append((i + 1, psnr(render(G, ho, W, H, do.mean.p, do.quat.p), gt_ho)))
-            train_d.append((i + 1, train_psnr(do.mean.p, do.quat.p)))
-    tr_d = train_d[-1][1]
+            curve_n.append(point(i + 1, *st.transform()))
+    plain = {}
+    for lr in PLAIN_LR_SWEEP:
+        do = DirectOpt(G, Vb, W, H, st.raster.capacity, lr_mean=lr, lr_quat=lr * PLAIN_QUAT_RATIO,
+                       device=dev)
+        c = [start]
+        for i in range(iters):
+            do.step(*batches[i % nb])
+            if (i + 1) % every == 0:
+                c.append(point(i + 1, do.mean.p, do.quat.p))
+        plain[lr] = c
+        del do
+    best_lr = max(plain, key=lambda lr: (max(p["heldout"] for p in plain[lr][1:]), -lr))
+    curve_d = plain[best_lr]
 
-    def compare(cn, cd, best):
-        pick = (lambda c: max(p for _, p in c)) if best else (lambda c: c[-1][1])
+    def compare(cn, cd, key, best):
+        pick = (lambda c: max(p[key] for p in c[1:])) if best else (lambda c: c[-1][key])
         target = min(pick(cn), pick(cd))
-        first = lambda c: next(it for it, p in c if p >= target - 0.05)
+        first = lambda c: next(p["it"] for p in c[1:] if p[key] >= target - 0.05)
         it_n, it_d = first(cn), first(cd)
-        return target, it_n, it_d, it_n * ms_ntc / 1e3, it_d * ms_plain / 1e3
+        return {"target_psnr": target, "ntc_iters": it_n, "direct_iters": it_d,
+                "ntc_s": it_n * ms_ntc / 1e3, "direct_s": it_d * ms_plain / 1e3,
+                "speedup_at_equal_psnr": (it_d * ms_plain) / (it_n * ms_ntc)}
 
-    target, it_n, it_d, t_n, t_d = compare(curve_n, curve_d, True)
-    ftarget, fit_n, fit_d, ft_n, ft_d = compare(curve_n, curve_d, False)
-    ttarget, tit_n, tit_d, tt_n, tt_d = compare(train_n, train_d, True)
-    tftarget, tfit_n, tfit_d, tft_n, tft_d = compare(train_n, train_d, False)
-    return {"view": "held-out camera (azimuth 7.5, elevation 5)", "psnr_previous_frame": start,
-            "target": "lower of the two best PSNRs over the frame", "checkpoint_every": every,
-            "target_psnr": target, "ntc": {"final_psnr": curve_n[-1][1], "train_views_psnr": tr_n,
-                                          "best_psnr": max(p for _, p in curve_n),
-                                          "iters_to_target": it_n, "s_to_target": t_n,
-                                          "curve": [(a, round(b, 2)) for a, b in curve_n]},
-            "direct": {"final_psnr": curve_d[-1][1], "train_views_psnr": tr_d,
-                       "best_psnr": max(p for _, p in curve_d),
-                       "iters_to_target": it_d, "s_to_target": t_d,
-                       "curve": [(a, round(b, 2)) for a, b in curve_d]},
-            "speedup_at_equal_psnr": t_d / t_n,
-            "final_target": {"target_psnr": ftarget, "ntc_iters": fit_n, "direct_iters": fit_d,
-                             "speedup_at_equal_psnr": ft_d / ft_n},
-            "train_views": {"psnr_previous_frame": start_train, "target_psnr": ttarget,
-                            "ntc_iters_to_target": tit_n, "direct_iters_to_target": tit_d,
-                            "ntc_curve": [(a, round(b, 2)) for a, b in train_n],
-                            "direct_curve": [(a, round(b, 2)) for a, b in train_d],
-                            "speedup_at_equal_psnr": tt_d / tt_n,
-                            "final_target": {"target_psnr": tftarget, "ntc_iters": tfit_n,
-                                             "direct_iters": tfit_d,
-                                             "speedup_at_equal_psnr": tft_d / tft_n}}}
+    summ = lambda c: {"final": c[-1], "best_heldout": max(p["heldout"] for p in c[1:]),
+                      "best_train": max(p["train"] for p in c[1:])}
+    return {"view": "held-out camera (azimuth 7.5, elevation 5)", "checkpoint_every": every,
+            "previous_frame": start, "seen_gaussians": int(seen.sum()),
+            "motion_weight": "sum over the training views of alpha T (Gaussians with weight > 1 are 'seen')",
+            "ntc": dict(summ(curve_n), curve=curve_n),
+            "direct": dict(summ(curve_d), lr_mean=best_lr, lr_quat=best_lr * PLAIN_QUAT_RATIO, curve=curve_d),
+            "direct_lr_sweep": {("%g" % lr): summ(c) for lr, c in plain.items()},
+            "heldout": {"best": compare(curve_n, curve_d, "heldout", True),
+                        "final": compare(curve_n, curve_d, "heldout", False)},
+            "train_views": {"best": compare(curve_n, curve_d, "train", True),
+                            "final": compare(curve_n, curve_d, "train", False)},
+            "speedup_at_equal_psnr": compare(curve_n, curve_d, "heldout", True)["speedup_at_equal_psnr"]}
 
 
 def ctypes_u64():
@@ -892,10 +1019,10 @@ def recorded_traffic(kernel):
     return None
 
 
-def roofline_for(stage, ms, pairs, pair_counts, n, V, W, H, cfg, hbm_gbs, src, sm_mhz):
+def roofline_for(stage, ms, pairs, pair_counts, n, V, W, H, cfg, hbm_gbs, src, sm_mhz, n_sms):
     """Roofline of one launch of the stage's kernels: compositing is bound by
     FP32 arithmetic (FLOPs of the evaluated pairs over the FP32 FMA peak of
-    152 SMs x 128 lanes x 2 FLOPs x SM clock); the other stages by HBM
+    SMs x 128 lanes x 2 FLOPs x SM clock); the other stages by HBM
     (each logically required read or write counted once)."""
     if stage in ("raster_fwd", "raster_bwd"):
         tested, added = (pair_counts[0], pair_counts[1]) if stage == "raster_fwd" else \
@@ -903,12 +1030,14 @@ def roofline_for(stage, ms, pairs, pair_counts, n, V, W, H, cfg, hbm_gbs, src, s
         per_added = FLOPS_FWD_ADDED if stage == "raster_fwd" else FLOPS_BWD_ADDED
         flops = tested * FLOPS_TESTED + added * per_added
         achieved = flops / (ms * 1e-3) / 1e12
-        peak = kNumSMs * 128 * 2 * sm_mhz * 1e6 / 1e12
+        peak = n_sms * 128 * 2 * sm_mhz * 1e6 / 1e12
         return {"bound": "alu", "kernel": stage, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": recorded_traffic(stage),
                 "algorithmic_flops": flops, "pairs_evaluated": tested, "pairs_added": added,
-                "ms": ms, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_mhz}
+                "ms": ms, "sm_count": n_sms,
+                "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz (median under load)"
+                               % (n_sms, sm_mhz)}
     K = (cfg.sh_deg + 1) ** 2
     px = V * W * H
     per_gauss_params = 12 + 16 + 12 + 4 + 12 * K
@@ -926,8 +1055,6 @@ def roofline_for(stage, ms, pairs, pair_counts, n, V, W, H, cfg, hbm_gbs, src, s
             "unit": "GB/s", "frac": achieved / hbm_gbs, "traffic": recorded_traffic(stage),
             "algorithmic_bytes": bytes_, "ms": ms, "peak_source": src}
 
-
-kNumSMs = 152
 
 
 def main():

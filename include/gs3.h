@@ -118,9 +118,17 @@ typedef struct {
 #define GS_MLP_OUT 7
 #define GS_MLP_PARAMS (64 * 32 + 64 * 64 + 7 * 64)
 
-/* Adam hyper-parameters (Suppl. A: lr 0.002). */
+/* Adam hyper-parameters (Suppl. A: rate 0.002).  The update with step number
+ * t (d_state->step: 0 for the first applied update) uses the rate
+ *   lr * lr_final_ratio ^ (min(t, decay_steps - 1) / (decay_steps - 1))
+ * when decay_steps > 1, an exponential decay to lr * lr_final_ratio over
+ * decay_steps updates (held there after), and lr when decay_steps <= 1.  The
+ * rate is derived on the device from the step counter, so a captured CUDA
+ * graph follows the schedule. */
 typedef struct {
     float lr, beta1, beta2, eps;
+    float lr_final_ratio;
+    int32_t decay_steps;
 } gs_adam;
 
 /* Training state kept in DEVICE memory, read and advanced by the kernels so a
@@ -150,6 +158,20 @@ GS_API int gs_tc_timeouts(void);
  * GS_ERR_TIMEOUT to *d_status (device int32) when the wait ran out (always,
  * by construction) and GS_OK otherwise.  The context stays usable. */
 GS_API gs_status gs_tc_wait_selftest(uint32_t tries, int32_t *d_status, gs_stream stream);
+/* Failure-detection control (the paper has no counterpart): the number of
+ * polls after which the tensor-core MLP kernels (ntc_mlp_fwd / ntc_mlp_bwd
+ * with BF16 weights, ntc_fused_fwd / ntc_fused_bwd) give up waiting for an
+ * MMA batch.  GS_TC_WAIT_TRIES_DEFAULT is the default; 0 makes every such
+ * wait give up at once, which tests use to run the timeout path.  A kernel
+ * that gives up still waits, bounded by the default, for the MMA batch in
+ * flight, releases its tensor memory, counts the event (gs_tc_timeouts) and
+ * marks what it did not finish as non-finite: the rows of raw7 (and of the
+ * fused forward's transformed mean and rotation) become NaN, the reverse's
+ * weight gradient becomes NaN.  A Stage-1 step then skips its Adam update
+ * through gs_check_finite, and gs_project culls and reports the Gaussians.
+ * Process-wide; applies to kernels launched or captured after the call. */
+#define GS_TC_WAIT_TRIES_DEFAULT 4194304u
+GS_API gs_status gs_tc_set_wait_limit(uint32_t tries);
 
 /* ------------------------------------------------------------ projection */
 
@@ -167,9 +189,13 @@ GS_API gs_status gs_tc_wait_selftest(uint32_t tries, int32_t *d_status, gs_strea
  *   image's tiles (same in y); an empty rect culls (radius = tiles_touched = 0)
  *   rgb = max(0, sum_k Y_k(dir) sh_k + 0.5), dir = (mu - campos)/|mu - campos|
  *   opacity = sigmoid(logit)
- * All V views share width W and height H.  Overwrites every field of out. */
+ * All V views share width W and height H.  Overwrites every field of out.
+ * A Gaussian whose mean, rotation, scale or opacity is not finite, or whose
+ * record would not be (a non-finite SH coefficient), is culled in every view
+ * and, when d_err (device int32, may be NULL) is non-NULL and still 0, sets
+ * *d_err = GS_ERR_NONFINITE; the caller reads the word at its sync point. */
 GS_API gs_status gs_project(const gs_gaussians *g, const gs_camera *d_cams, int V, int W, int H,
-                     const gs_projected *out, gs_stream stream);
+                            const gs_projected *out, int32_t *d_err, gs_stream stream);
 
 /* Reverse of gs_project for mean and rotation (Section 4.1: in Stage 1 only
  * the transformed mean and rotation receive gradients).  grads[V][N][8] holds
@@ -197,7 +223,8 @@ GS_API gs_status gs_project_bwd_full(const gs_gaussians *g, const gs_camera *d_c
 /* --------------------------------------------------------- binning + sort */
 
 /* Scratch bytes gs_bin_sort needs for n Gaussians, V views of W x H and room
- * for `capacity` (Gaussian, tile) pairs. */
+ * for `capacity` (Gaussian, tile) pairs; 0 for arguments gs_bin_sort rejects
+ * (n < 0, V < 1, capacity < 0, n * V >= 2^32 - 1). */
 GS_API size_t gs_bin_sort_workspace_size(int64_t n, int V, int W, int H, int64_t capacity);
 
 /* Tile binning and key sort (the tile pipeline of Section 3.2).  Tiles are
@@ -230,7 +257,9 @@ GS_API gs_status gs_bin_sort(const gs_projected *proj, int64_t n, int V, int W, 
  * and gs_bin_sort_workspace_size() of the call <= 20 MiB; larger calls return
  * GS_ERR_INVALID_ARG without launching.  All calls share the array: calls that
  * overlap on the GPU race and must be serialised.  The first call on a device
- * looks up the array's address; make it before any stream capture.
+ * looks up the array's address; make it before any stream capture.  That
+ * address is kept for the lifetime of the device's primary context: do not
+ * call this function on a device again after cudaDeviceReset.
  * Allocates nothing (no cudaMalloc / cudaFree, no allocating library call). */
 GS_API gs_status gs_bin_sort_noalloc(const gs_projected *proj, int64_t n, int V, int W, int H,
                                      int bin, int64_t capacity, uint32_t *vals, uint32_t *ranges,
@@ -355,7 +384,9 @@ GS_API gs_status ntc_warmup_loss(const float *raw7, int64_t n, float *d_raw7, fl
 GS_API gs_status gs_check_finite(const float *g, int64_t n, gs_train_state *d_state, gs_stream stream);
 
 /* Bias-corrected Adam (Suppl. A) on p[n] with gradient g * (1 / loss_scale)
- * and step number d_state->step + 1, skipped when d_state->found_inf is set.
+ * and step number d_state->step + 1, skipped when d_state->found_inf is set;
+ * the rate follows gs_adam's schedule (lr_final_ratio > 0 when decay_steps > 1,
+ * GS_ERR_INVALID_ARG otherwise).
  * Zeroes g afterwards (ready for the next step's accumulation).  If shadow is
  * non-NULL, writes the updated parameters converted to shadow_dtype (GS_F16 or
  * GS_BF16).  All state (m, v) FP32, in place.  p, g, m, v 16-byte aligned,

@@ -368,6 +368,15 @@ def warmup_loss(raw7):
     return float(L), d
 
 
+def adam_rate(lr, lr_final_ratio, decay_steps, t):
+    """Rate of the Adam update with 0-based step number t under an exponential
+    decay from lr to lr * lr_final_ratio over decay_steps updates (constant
+    after them; no decay when decay_steps <= 1)."""
+    if decay_steps <= 1:
+        return lr
+    return lr * lr_final_ratio ** (min(t, decay_steps - 1) / (decay_steps - 1))
+
+
 def adam(p, g, m, v, step, lr=0.002, b1=0.9, b2=0.99, eps=1e-15, inv_scale=1.0):
     """In-place Adam on float64 arrays p, m, v."""
     for a in (p, m, v):

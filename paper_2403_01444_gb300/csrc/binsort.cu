@@ -29,7 +29,9 @@ constexpr int SORT_THREADS = 256;
 constexpr int SORT_WARPS = SORT_THREADS / 32;
 constexpr int SORT_ITEMS = 8;
 constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;  // 2048 keys per block step
-constexpr int SORT_BLOCKS = kNumSMs * 4;              // fixed grid: n may live on the device
+constexpr int SORT_BLOCKS_MAX = kMaxSMs * 4;          // bound of the fixed sort grid (workspace)
+// the sort grid: fixed (n may live on the device), 4 blocks per SM
+inline int sort_blocks() { return num_sms() * 4; }
 constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_ITEMS = 4;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
@@ -444,7 +446,7 @@ static BinWs carve(void *base, int64_t NV, int64_t cap)
     w.offsets = reinterpret_cast<int64_t *>(take(8 * (NV + 1)));
     w.cnt = reinterpret_cast<int32_t *>(take(4 * NV));
     w.bsum = reinterpret_cast<int64_t *>(take(8 * (ceil_div(NV, SCAN_TILE) + 1)));
-    w.hist = reinterpret_cast<uint32_t *>(take(4 * (RADIX * SORT_BLOCKS + RADIX)));
+    w.hist = reinterpret_cast<uint32_t *>(take(4 * (RADIX * SORT_BLOCKS_MAX + RADIX)));
     w.n_eff = reinterpret_cast<int64_t *>(take(64));
     for (int k = 0; k < 2; ++k) w.tk[k] = reinterpret_cast<uint32_t *>(take(4 * cap));
     w.tv = reinterpret_cast<uint32_t *>(take(4 * cap));
@@ -472,7 +474,8 @@ extern "C" size_t gs_bin_sort_workspace_size(int64_t n, int V, int W, int H, int
 {
     (void)W;
     (void)H;
-    if (n < 0 || V < 1 || capacity < 0) return 0;
+    // n is bounded before n * V is formed (a wrapped product would pass)
+    if (n < 0 || V < 1 || capacity < 0 || n > ((int64_t(1) << 32) - 2) / V) return 0;
     return carve(nullptr, n * V, capacity).bytes;
 }
 
@@ -485,7 +488,7 @@ extern "C" gs_status gs_bin_sort(const gs_projected *proj, int64_t n, int V, int
     GS_REQUIRE(proj && vals && ranges && d_count && ws, "gs_bin_sort: null argument");
     GS_REQUIRE(n >= 0 && V >= 1 && V <= GS_MAX_VIEWS, "gs_bin_sort: bad n or V");
     GS_REQUIRE(W > 0 && H > 0 && W <= 16384 && H <= 16384, "gs_bin_sort: bad image size");
-    GS_REQUIRE(n * V < (int64_t(1) << 32) - 1, "gs_bin_sort: n * V must fit in 32 bits");
+    GS_REQUIRE(n <= ((int64_t(1) << 32) - 2) / V, "gs_bin_sort: n * V must fit in 32 bits");
     GS_REQUIRE(capacity >= 0 && capacity < (int64_t(1) << 32) - 1,
                "gs_bin_sort: capacity must fit in 32 bits");
     GS_REQUIRE(aligned(ws, 256), "gs_bin_sort: workspace must be 256-byte aligned");
@@ -508,7 +511,7 @@ extern "C" gs_status gs_bin_sort(const gs_projected *proj, int64_t n, int V, int
     depth_keys_kernel<<<(int)ceil_div(NV, 256), 256, 0, st>>>(proj->depth, proj->radius, NV,
                                                               w.dk[0], w.dv[0]);
     int cur = 0;
-    int Gd = (int)std::min<int64_t>(SORT_BLOCKS, ceil_div(NV, SORT_TILE));
+    int Gd = (int)std::min<int64_t>(sort_blocks(), ceil_div(NV, SORT_TILE));
     for (int pass = 0; pass < 4 + (V > 1 ? 1 : 0); ++pass) {
         SortPass s{};
         s.kin = w.dk[cur];
@@ -573,17 +576,17 @@ extern "C" gs_status gs_bin_sort(const gs_projected *proj, int64_t n, int V, int
         s.shift = 8 * pass;
         s.div = 0;
         s.hist = w.hist;
-        s.G = SORT_BLOCKS;
+        s.G = sort_blocks();
         e = run_pass(s, 0, st);
         if (e != GS_OK) return e;
         kc ^= 1;
         vcur = s.vout;
     }
     note_launch();
-    ranges_kernel<<<kNumSMs * 8, 256, 0, st>>>(w.tk[kc], w.n_eff, ranges);
+    ranges_kernel<<<num_sms() * 8, 256, 0, st>>>(w.tk[kc], w.n_eff, ranges);
     if (keys) {
         note_launch();
-        keys64_kernel<<<kNumSMs * 8, 256, 0, st>>>(w.tk[kc], vals, w.n_eff, proj->depth, n, bins,
+        keys64_kernel<<<num_sms() * 8, 256, 0, st>>>(w.tk[kc], vals, w.n_eff, proj->depth, n, bins,
                                                    keys);
     }
     return launch_status("gs_bin_sort");

@@ -41,7 +41,9 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 // Device address of g_noalloc_scratch per device, looked up once per device
 // with that device current.  In host code the array's name is only a
-// host-side stand-in, never a device address.
+// host-side stand-in, never a device address.  The cached address is valid
+// for the lifetime of the device's primary context: after cudaDeviceReset a
+// process must not call gs_bin_sort_noalloc on that device again.
 static void *scratch_address(int dev, gs_status &st)
 {
     static std::mutex mu;
@@ -77,9 +79,10 @@ extern "C" gs_status gs_bin_sort_noalloc(const gs_projected *proj, int64_t n, in
                                          gs_stream stream)
 {
     GS_REQUIRE(n >= 0 && V >= 1 && capacity >= 0, "gs_bin_sort_noalloc: bad n, V or capacity");
-    GS_REQUIRE(n * V <= kNoAllocMaxEntries,
-               "gs_bin_sort_noalloc: n * V = %lld exceeds the built-in limit of %lld entries",
-               (long long)(n * V), (long long)kNoAllocMaxEntries);
+    // n is bounded before n * V is formed, so the product cannot wrap
+    GS_REQUIRE(n <= kNoAllocMaxEntries / V,
+               "gs_bin_sort_noalloc: n = %lld Gaussians x V = %d views exceeds the built-in limit "
+               "of %lld entries", (long long)n, V, (long long)kNoAllocMaxEntries);
     GS_REQUIRE(capacity <= kNoAllocMaxPairs,
                "gs_bin_sort_noalloc: capacity %lld exceeds the built-in limit of %lld pairs",
                (long long)capacity, (long long)kNoAllocMaxPairs);

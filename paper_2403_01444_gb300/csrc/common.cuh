@@ -66,7 +66,23 @@ inline int tiles_y_of(int H) { return (H + GS_TILE - 1) / GS_TILE; }
 inline int bins_x_of(int W, int bin) { return (tiles_x_of(W) + bin - 1) / bin; }
 inline int bins_y_of(int H, int bin) { return (tiles_y_of(H) + bin - 1) / bin; }
 
-constexpr int kNumSMs = 152;  // GB300: 2 dies x 76 SMs
+// Streaming multiprocessors of the current device (GB300: 2 dies x 76 = 152),
+// queried once per device.  Grids are sized from it; workspaces that depend on
+// a grid are sized for kMaxSMs so their size needs no device.
+constexpr int kMaxSMs = 256;
+inline int num_sms()
+{
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+        v = 152;
+    v = v < kMaxSMs ? v : kMaxSMs;
+    cache[dev].store(v, std::memory_order_relaxed);
+    return v;
+}
 
 // ------------------------------------------------------------------ device
 // Tile rectangle of a footprint: x in [floor((u - r)/16), floor((u + r + 15)/16)),

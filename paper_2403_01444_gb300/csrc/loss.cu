@@ -3,7 +3,7 @@
 // window, forms the SSIM map and the three per-pixel coefficients of its
 // derivative wrt (mu_x, E[x^2], E[xy]); pass 2 filters those coefficients (the
 // window is symmetric, so the adjoint is the same filter) and assembles
-// dL/dI; pass 3 reduces the block partial sums in FP64.
+// dL/dI; pass 3 reduces the block partial sums (compensated FP32).
 //
 // Both filtering passes work on 32 x 48 output tiles.  The horizontal stage
 // reads its inputs straight from global memory (through L1, as float4 where
@@ -109,9 +109,10 @@ struct LossParams {
     const float *x, *y;
     int P, H, W;
     float lam;
+    float invM;           // 1 / (planes H W), the mean's weight (set on the host)
     bool vec;             // rows of x, y and the coefficient maps are 16-byte aligned
     float *ca, *cb, *cc;  // per-pixel derivative coefficients
-    double *partial;      // [blocks][2]: sum of SSIM map, sum |x - y|
+    float2 *partial;      // [blocks]: (sum of SSIM map, sum |x - y|)
     float *d_img;
     float *d_loss, *d_ssim;
     int nblocks;
@@ -141,7 +142,7 @@ __global__ void __launch_bounds__(LTHREADS, SSIM_FWD_MIN_BLOCKS)
     __shared__ float2 s_xy[SR][SX];   // row-filtered (x, y)
     __shared__ float2 s_sq[SR][SX];   // row-filtered (x^2, y^2)
     __shared__ float s_p[SR][SX];     // row-filtered x y
-    __shared__ double red[2][LTHREADS / 32];
+    __shared__ float red[2][LTHREADS / 32];
     __shared__ __align__(8) unsigned long long s_mbar[2];
     extern __shared__ __align__(128) unsigned char s_dyn[];   // TMA: [image][stage][TH][TW] floats
     float *s_in = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(s_dyn) + 127) & ~uintptr_t(127));
@@ -321,19 +322,18 @@ __global__ void __launch_bounds__(LTHREADS, SSIM_FWD_MIN_BLOCKS)
         lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
     }
     if ((tid & 31) == 0) {
-        red[0][tid >> 5] = (double)ssum;
-        red[1][tid >> 5] = (double)lsum;
+        red[0][tid >> 5] = ssum;
+        red[1][tid >> 5] = lsum;
     }
     __syncthreads();
     if (tid == 0) {
-        double a = 0.0, b = 0.0;
+        float a = 0.f, b = 0.f;
         for (int ww = 0; ww < LTHREADS / 32; ++ww) {
             a += red[0][ww];
             b += red[1][ww];
         }
         int64_t bid = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-        p.partial[2 * bid] = a;
-        p.partial[2 * bid + 1] = b;
+        p.partial[bid] = make_float2(a, b);
     }
 }
 
@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(LTHREADS, SSIM_BWD_MIN_BLOCKS) ssim_bwd_kernel
         }
     }
     __syncthreads();
-    const float invM = 1.f / (float)((double)p.P * (double)HW);
+    const float invM = p.invM;
     const int c = tid % SX, r0 = (tid / SX) * VSEG;
     const int gx = x0 + c;
     // the images at this thread's outputs, loaded before the column filters
@@ -430,14 +430,28 @@ __global__ void __launch_bounds__(LTHREADS, SSIM_BWD_MIN_BLOCKS) ssim_bwd_kernel
     }
 }
 
+// Compensated (Kahan) accumulation: s + (-c) carries the sum to about one
+// rounding, independent of the number of terms.
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x)
+{
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// Pass 3: the block partial sums in FP32, each thread's share compensated,
+// the 1024 shares added in a tree (error about log2(1024) roundings).
 __global__ void __launch_bounds__(1024) loss_final_kernel(LossParams p)
 {
-    __shared__ double red[2][32];
-    double a = 0.0, b = 0.0;
+    __shared__ float red[2][32];
+    float sa = 0.f, ca = 0.f, sb = 0.f, cb = 0.f;
     for (int i = threadIdx.x; i < p.nblocks; i += blockDim.x) {
-        a += p.partial[2 * i];
-        b += p.partial[2 * i + 1];
+        const float2 v = p.partial[i];
+        kahan_add(sa, ca, v.x);
+        kahan_add(sb, cb, v.y);
     }
+    float a = sa - ca, b = sb - cb;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_xor_sync(0xffffffffu, a, o);
@@ -448,17 +462,20 @@ __global__ void __launch_bounds__(1024) loss_final_kernel(LossParams p)
         red[1][threadIdx.x >> 5] = b;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double sa = 0.0, sb = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            sa += red[0][w];
-            sb += red[1][w];
+    if (threadIdx.x < 32) {
+        const int nw = (int)(blockDim.x >> 5);
+        a = threadIdx.x < nw ? red[0][threadIdx.x] : 0.f;
+        b = threadIdx.x < nw ? red[1][threadIdx.x] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
         }
-        double M = (double)p.P * p.H * p.W;
-        double ssim = sa / M;
-        double loss = (1.0 - p.lam) * sb / M + p.lam * (1.0 - ssim);
-        *p.d_loss = (float)loss;
-        if (p.d_ssim) *p.d_ssim = (float)ssim;
+        if (threadIdx.x == 0) {
+            const float ssim = a * p.invM;
+            *p.d_loss = (1.f - p.lam) * (b * p.invM) + p.lam * (1.f - ssim);
+            if (p.d_ssim) *p.d_ssim = ssim;
+        }
     }
 }
 
@@ -529,12 +546,13 @@ extern "C" gs_status gs_loss_l1_dssim(const float *img, const float *target, int
     p.H = H;
     p.W = W;
     p.lam = lambda;
+    p.invM = (float)(1.0 / ((double)planes * (double)H * (double)W));
     size_t px = (size_t)planes * H * W;
     char *b = reinterpret_cast<char *>(ws);
     p.ca = reinterpret_cast<float *>(b);
     p.cb = reinterpret_cast<float *>(b + a256(4 * px));
     p.cc = reinterpret_cast<float *>(b + 2 * a256(4 * px));
-    p.partial = reinterpret_cast<double *>(b + 3 * a256(4 * px));
+    p.partial = reinterpret_cast<float2 *>(b + 3 * a256(4 * px));
     p.d_img = d_img;
     p.d_loss = d_loss;
     p.d_ssim = d_ssim;

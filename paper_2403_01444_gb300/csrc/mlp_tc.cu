@@ -17,6 +17,8 @@
 #include "ntc.cuh"
 #include "tc.cuh"
 
+#include <atomic>
+
 namespace gs3 {
 using namespace tc;
 typedef __nv_bfloat16 bf16;
@@ -75,6 +77,7 @@ struct TcParams {
     float *d_table;
     Box box;
     int order;
+    uint32_t wait_tries;  // polls of an MMA-completion wait before giving up
 };
 
 template <typename T>
@@ -226,9 +229,9 @@ __device__ __forceinline__ void load_weights_fwd(const bf16 *w, bf16 *w1, bf16 *
 }
 
 // All threads wait for the MMA batch; returns false (block-uniformly) on timeout.
-__device__ __forceinline__ bool wait_mma(uint32_t mbar, uint32_t &phase)
+__device__ __forceinline__ bool wait_mma(uint32_t mbar, uint32_t &phase, uint32_t tries)
 {
-    bool ok = mbar_wait(mbar, phase, kWaitTries);
+    bool ok = mbar_wait(mbar, phase, tries);
     phase ^= 1u;
     ok = __syncthreads_and(ok);
     fence_after_sync();
@@ -273,7 +276,8 @@ __global__ void __launch_bounds__(TM, 4) mlp_tc_fwd_kernel(TcParams p)
     uint32_t phase = 0;
     bool ok = true;
     const int64_t ntiles = (n + TM - 1) / TM;
-    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    int64_t tile = blockIdx.x;
+    for (; tile < ntiles && ok; tile += gridDim.x) {
         const int64_t row = tile * TM + t;
         float v[64];
         if (FUSED) {
@@ -299,7 +303,7 @@ __global__ void __launch_bounds__(TM, 4) mlp_tc_fwd_kernel(TcParams p)
                          id64, ks > 0);
             mma_commit(mbar);
         }
-        if (!(ok = wait_mma(mbar, phase))) break;
+        if (!(ok = wait_mma(mbar, phase, p.wait_tries))) break;
 #pragma unroll
         for (int c = 0; c < 4; ++c) tmem_ld16(tm + lane + 16 * c, v + 16 * c);
 #pragma unroll
@@ -315,7 +319,7 @@ __global__ void __launch_bounds__(TM, 4) mlp_tc_fwd_kernel(TcParams p)
                          id64, ks > 0);
             mma_commit(mbar);
         }
-        if (!(ok = wait_mma(mbar, phase))) break;
+        if (!(ok = wait_mma(mbar, phase, p.wait_tries))) break;
         // output layer (64 -> 7) in FP32 on the FP32 accumulator, 16 columns
         // of H2 at a time: the raw translation and rotation carry no BF16
         // rounding of the last layer
@@ -340,7 +344,28 @@ __global__ void __launch_bounds__(TM, 4) mlp_tc_fwd_kernel(TcParams p)
         fence_before_sync();
         __syncthreads();
     }
-    if (!ok && t == 0) atomicAdd(&g_tc_timeouts, 1);
+    if (!ok) {
+        // A wait gave up.  The MMA batch it waited for may still be running:
+        // wait for it (bounded) before the TMEM is released.  Every row this
+        // block did not finish is then written non-finite, so the Gaussian is
+        // culled by the projection and the step's non-finite gradient check
+        // skips the update, as for an overflow.
+        mbar_wait(mbar, phase ^ 1u, kWaitTries);
+        const float nan = __int_as_float(0x7fc00000);
+        for (; tile < ntiles; tile += gridDim.x) {
+            const int64_t row = tile * TM + t;
+            if (row >= n) continue;
+#pragma unroll
+            for (int q = 0; q < 7; ++q) raw7[row * 7 + q] = nan;
+            if (FUSED) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) p.mean_out[row * 3 + q] = nan;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) p.quat_out[row * 4 + q] = nan;
+            }
+        }
+        if (t == 0) atomicAdd(&g_tc_timeouts, 1);
+    }
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
@@ -431,7 +456,7 @@ __global__ void __launch_bounds__(TM) mlp_tc_bwd_kernel(TcParams p)
                          id64, ks > 0);
             mma_commit(mbar);
         }
-        if (!(ok = wait_mma(mbar, phase))) break;
+        if (!(ok = wait_mma(mbar, phase, p.wait_tries))) break;
         // ---- H1 = relu(enc W1^T)
         uint32_t m1lo = 0, m1hi = 0;
 #pragma unroll
@@ -457,7 +482,7 @@ __global__ void __launch_bounds__(TM) mlp_tc_bwd_kernel(TcParams p)
             mma_bf16(D1, desc_kmajor(sga, 128, 256), desc_kmajor(sw3t, 128, 256), id64, 0);
             mma_commit(mbar);
         }
-        if (!(ok = wait_mma(mbar, phase))) break;
+        if (!(ok = wait_mma(mbar, phase, p.wait_tries))) break;
         // ---- H2 = relu(H1 W2^T); dH2 = (G W3) . relu'(H2)
         uint32_t m2lo = 0, m2hi = 0;
 #pragma unroll
@@ -491,7 +516,7 @@ __global__ void __launch_bounds__(TM) mlp_tc_bwd_kernel(TcParams p)
                          id64, ks > 0);
             mma_commit(mbar);
         }
-        if (!(ok = wait_mma(mbar, phase))) break;
+        if (!(ok = wait_mma(mbar, phase, p.wait_tries))) break;
         // ---- dH1 = (dH2 W2) . relu'(H1)
 #pragma unroll
         for (int c = 0; c < 4; ++c) tmem_ld16(D0 + lane + 16 * c, v + 16 * c);
@@ -525,7 +550,7 @@ __global__ void __launch_bounds__(TM) mlp_tc_bwd_kernel(TcParams p)
                          desc_kmajor(sBT + 12 * 2048 + 256 * ks, 128, 2048), id16, ks > 0 ? 1u : acc0);
             mma_commit(mbar);
         }
-        if (!(ok = wait_mma(mbar, phase))) break;
+        if (!(ok = wait_mma(mbar, phase, p.wait_tries))) break;
         if (FUSED) {
             tmem_ld16(D0 + lane, v);
             tmem_ld16(D0 + lane + 16, v + 16);
@@ -567,7 +592,17 @@ __global__ void __launch_bounds__(TM) mlp_tc_bwd_kernel(TcParams p)
             }
         }
     }
-    if (!ok && t == 0) atomicAdd(&g_tc_timeouts, 1);
+    if (!ok) {
+        // A wait gave up: wait (bounded) for the MMA batch still in flight
+        // before the TMEM is released, and make the weight gradient
+        // non-finite so that the step's non-finite check skips the update
+        // (the rows not finished have no gradient).
+        mbar_wait(mbar, phase ^ 1u, kWaitTries);
+        if (t == 0) {
+            atomicAdd(dW, __int_as_float(0x7fc00000));
+            atomicAdd(&g_tc_timeouts, 1);
+        }
+    }
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
@@ -582,11 +617,16 @@ static gs_status check_common(const void *enc, int enc_dtype, const gs_mlp *w)
     return GS_OK;
 }
 
+// Polls of an MMA-completion wait before a kernel gives up (set by
+// gs_tc_set_wait_limit; read when a kernel is launched or captured).
+static std::atomic<uint32_t> s_wait_tries{kWaitTries};
+
 template <typename ET, bool FUSED>
-static gs_status launch_fwd(const TcParams &p, cudaStream_t s)
+static gs_status launch_fwd(TcParams p, cudaStream_t s)
 {
+    p.wait_tries = s_wait_tries.load();
     const size_t smem = sizeof(FwdSmem) + 1024;
-    const int grid = (int)std::min<int64_t>(ceil_div(p.n, TM), kNumSMs * 4);
+    const int grid = (int)std::min<int64_t>(ceil_div(p.n, TM), num_sms() * 4);
     set_smem_limit((const void *)mlp_tc_fwd_kernel<ET, FUSED>, (int)smem, s);
     note_launch();
     mlp_tc_fwd_kernel<ET, FUSED><<<grid, TM, smem, s>>>(p);
@@ -594,10 +634,11 @@ static gs_status launch_fwd(const TcParams &p, cudaStream_t s)
 }
 
 template <typename ET, bool FUSED>
-static gs_status launch_bwd(const TcParams &p, cudaStream_t s)
+static gs_status launch_bwd(TcParams p, cudaStream_t s)
 {
+    p.wait_tries = s_wait_tries.load();
     const size_t smem = sizeof(BwdSmem) + 1024;
-    const int grid = (int)std::min<int64_t>(ceil_div(p.n, TM), kNumSMs);
+    const int grid = (int)std::min<int64_t>(ceil_div(p.n, TM), num_sms());
     set_smem_limit((const void *)mlp_tc_bwd_kernel<ET, FUSED>, (int)smem, s);
     note_launch();
     mlp_tc_bwd_kernel<ET, FUSED><<<grid, TM, smem, s>>>(p);
@@ -726,6 +767,12 @@ extern "C" gs_status gs_tc_wait_selftest(uint32_t tries, int32_t *d_status, gs_s
     note_launch();
     tc_wait_selftest_kernel<<<1, 128, 0, as_stream(stream)>>>(tries, d_status);
     return launch_status("gs_tc_wait_selftest");
+}
+
+extern "C" gs_status gs_tc_set_wait_limit(uint32_t tries)
+{
+    gs3::s_wait_tries.store(tries);
+    return GS_OK;
 }
 
 extern "C" int gs_tc_timeouts(void)

@@ -345,12 +345,22 @@ __global__ void check_finite_kernel(const float *g, int64_t n, gs_train_state *s
 
 template <int SHADOW>
 __device__ __forceinline__ void adam_one(float &p, float g, float &m, float &v, const gs_adam &hp,
-                                         float bc1, float bc2, float inv)
+                                         float lr, float bc1, float bc2, float inv)
 {
     g *= inv;
     m = fmaf(hp.beta1, m, (1.f - hp.beta1) * g);
     v = fmaf(hp.beta2, v, (1.f - hp.beta2) * g * g);
-    p = p - hp.lr * (m / bc1) / (sqrtf(v / bc2) + hp.eps);
+    p = p - lr * (m / bc1) / (sqrtf(v / bc2) + hp.eps);
+}
+
+// The rate of the update with step number t (0-based): lr, or its
+// exponential decay to lr * lr_final_ratio over decay_steps updates.
+__device__ __forceinline__ float adam_rate(const gs_adam &hp, int t)
+{
+    if (hp.decay_steps <= 1) return hp.lr;
+    const float last = (float)(hp.decay_steps - 1);
+    const float f = fminf((float)t, last) / last;
+    return hp.lr * exp2f(f * log2f(hp.lr_final_ratio));
 }
 
 // Four parameters per thread and step (16-byte loads, all issued before any
@@ -368,6 +378,7 @@ __global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ p, float 
     const float bc1 = -expm1f((float)t * logf(hp.beta1));
     const float bc2 = -expm1f((float)t * logf(hp.beta2));
     const float inv = 1.f / st->loss_scale;
+    const float lr = adam_rate(hp, st->step);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t n4 = n / 4;
     float4 *p4 = reinterpret_cast<float4 *>(p), *g4 = reinterpret_cast<float4 *>(g);
@@ -376,10 +387,10 @@ __global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ p, float 
         float4 gq = g4[q], mq = m4[q], vq = v4[q], pq = p4[q];
         g4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (skip) continue;
-        adam_one<SHADOW>(pq.x, gq.x, mq.x, vq.x, hp, bc1, bc2, inv);
-        adam_one<SHADOW>(pq.y, gq.y, mq.y, vq.y, hp, bc1, bc2, inv);
-        adam_one<SHADOW>(pq.z, gq.z, mq.z, vq.z, hp, bc1, bc2, inv);
-        adam_one<SHADOW>(pq.w, gq.w, mq.w, vq.w, hp, bc1, bc2, inv);
+        adam_one<SHADOW>(pq.x, gq.x, mq.x, vq.x, hp, lr, bc1, bc2, inv);
+        adam_one<SHADOW>(pq.y, gq.y, mq.y, vq.y, hp, lr, bc1, bc2, inv);
+        adam_one<SHADOW>(pq.z, gq.z, mq.z, vq.z, hp, lr, bc1, bc2, inv);
+        adam_one<SHADOW>(pq.w, gq.w, mq.w, vq.w, hp, lr, bc1, bc2, inv);
         m4[q] = mq;
         v4[q] = vq;
         p4[q] = pq;
@@ -398,7 +409,7 @@ __global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ p, float 
         float gi = g[i], mi = m[i], vi = v[i], pi = p[i];
         g[i] = 0.f;
         if (skip) continue;
-        adam_one<SHADOW>(pi, gi, mi, vi, hp, bc1, bc2, inv);
+        adam_one<SHADOW>(pi, gi, mi, vi, hp, lr, bc1, bc2, inv);
         m[i] = mi;
         v[i] = vi;
         p[i] = pi;
@@ -516,7 +527,7 @@ extern "C" gs_status ntc_mlp_bwd(const void *enc, int enc_dtype, int64_t n, cons
         return mlp_tc_bwd(enc, enc_dtype, n, w, d_raw7, d_scale, dW, d_enc, as_stream(stream));
     GS_REQUIRE(w->precision == GS_MLP_FP32 && w->w_f32, "ntc_mlp_bwd: bad precision / weights");
     cudaStream_t s = as_stream(stream);
-    int blocks = (int)std::min<int64_t>(ceil_div(n, MB_ROWS), 2 * kNumSMs);
+    int blocks = (int)std::min<int64_t>(ceil_div(n, MB_ROWS), 2 * num_sms());
     if (enc_dtype == GS_F32) {
         set_smem_limit((const void *)mlp_bwd_simt_kernel<float>, (int)MB_SMEM, s);
         note_launch();
@@ -581,7 +592,7 @@ extern "C" gs_status gs_check_finite(const float *g, int64_t n, gs_train_state *
     GS_REQUIRE(d_state && n >= 0, "gs_check_finite: null state or negative n");
     if (n == 0) return GS_OK;
     GS_REQUIRE(g, "gs_check_finite: null argument");
-    int blocks = (int)std::min<int64_t>(ceil_div(n, 256), kNumSMs * 8);
+    int blocks = (int)std::min<int64_t>(ceil_div(n, 256), num_sms() * 8);
     note_launch();
     check_finite_kernel<<<blocks, 256, 0, as_stream(stream)>>>(g, n, d_state);
     return launch_status("gs_check_finite");
@@ -594,12 +605,14 @@ extern "C" gs_status adam_step(float *p, float *g, float *m, float *v, int64_t n
     GS_REQUIRE(hp && d_state && n >= 0, "adam_step: null hyper-parameters / state or negative n");
     GS_REQUIRE(shadow == nullptr || shadow_dtype == GS_F16 || shadow_dtype == GS_BF16,
                "adam_step: shadow dtype must be GS_F16 or GS_BF16");
+    GS_REQUIRE(hp->decay_steps <= 1 || hp->lr_final_ratio > 0.f,
+               "adam_step: lr_final_ratio must be positive when the rate decays");
     if (n == 0) return GS_OK;
     GS_REQUIRE(p && g && m && v, "adam_step: null argument");
     GS_REQUIRE(aligned(p, 16) && aligned(g, 16) && aligned(m, 16) && aligned(v, 16) &&
                    (shadow == nullptr || aligned(shadow, 8)),
                "adam_step: arrays must be 16-byte aligned (shadow 8)");
-    int blocks = (int)std::min<int64_t>(ceil_div(n, 4 * 256), kNumSMs * 8);
+    int blocks = (int)std::min<int64_t>(ceil_div(n, 4 * 256), num_sms() * 8);
     blocks = std::max(blocks, 1);
     cudaStream_t s = as_stream(stream);
     note_launch();

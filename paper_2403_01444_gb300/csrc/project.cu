@@ -22,6 +22,7 @@ struct ProjectParams {
     float *depth;
     int32_t *radius;
     int32_t *tiles;
+    int32_t *d_err;  // GS_ERR_NONFINITE on a non-finite Gaussian (nullable)
     // backward
     const float *grads;
     float *d_mean, *d_quat;
@@ -267,9 +268,19 @@ __global__ void __launch_bounds__(256, PROJ_FWD_MIN_BLOCKS) project_fwd_kernel(P
     // the Gaussian's SH coefficients once, for every view
     float sh[3 * K];
     load_sh<DEG>(p, i, sh);
+    // a Gaussian with a non-finite mean, rotation, scale or opacity, or whose
+    // projected record comes out non-finite, is culled in every view and
+    // reported in the error word
+    bool bad = !isfinite(G.mu.x + G.mu.y + G.mu.z + G.qlen + G.s[0] + G.s[1] + G.s[2] + G.op);
     for (int v = 0; v < p.V; ++v) {
         ViewLocal L;
-        project_view<DEG>(p, G, sh, s_cams[v], L);
+        L.valid = false;
+        if (!bad) project_view<DEG>(p, G, sh, s_cams[v], L);
+        if (L.valid && !isfinite(L.u + L.v + L.conic[0] + L.conic[1] + L.conic[2] + L.rgb_raw[0] +
+                                 L.rgb_raw[1] + L.rgb_raw[2])) {
+            L.valid = false;
+            bad = true;
+        }
         int64_t o = (int64_t)v * p.n + i;
         if (L.valid) {
             p.mean2d[o] = make_float2(L.u, L.v);
@@ -291,6 +302,7 @@ __global__ void __launch_bounds__(256, PROJ_FWD_MIN_BLOCKS) project_fwd_kernel(P
             p.tiles[o] = 0;
         }
     }
+    if (bad && p.d_err) atomicCAS(p.d_err, 0, (int32_t)GS_ERR_NONFINITE);
 }
 
 // One view's contribution to dL/dmu and dL/dSigma (everything but the
@@ -583,7 +595,7 @@ static gs_status fill_params(const gs_gaussians *g, const gs_camera *d_cams, int
 using namespace gs3;
 
 extern "C" gs_status gs_project(const gs_gaussians *g, const gs_camera *d_cams, int V, int W, int H,
-                                const gs_projected *out, gs_stream stream)
+                                const gs_projected *out, int32_t *d_err, gs_stream stream)
 {
     ProjectParams p{};
     gs_status st = fill_params(g, d_cams, V, W, H, p);
@@ -600,6 +612,7 @@ extern "C" gs_status gs_project(const gs_gaussians *g, const gs_camera *d_cams, 
     p.depth = out->depth;
     p.radius = out->radius;
     p.tiles = out->tiles_touched;
+    p.d_err = d_err;
     int threads = 256;
     int blocks = (int)ceil_div(p.n, threads);
     note_launch();

@@ -328,7 +328,7 @@ extern "C" gs_status gs_added_spawn(const gs_gaussians *src, const int32_t *idx,
     cudaStream_t s = as_stream(stream);
     const float opl = logf(opacity_init / (1.f - opacity_init));
     note_launch();
-    spawn_kernel<<<kNumSMs * 4, 256, 0, s>>>(*src, idx, d_nsel, z, opl, *dst, d_nadd, d_err);
+    spawn_kernel<<<num_sms() * 4, 256, 0, s>>>(*src, idx, d_nsel, z, opl, *dst, d_nadd, d_err);
     note_launch();
     spawn_count_kernel<<<1, 1, 0, s>>>(d_nsel, dst->capacity, d_nadd);
     return launch_status("gs_added_spawn");

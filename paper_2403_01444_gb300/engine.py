@@ -18,8 +18,17 @@ from .gs3 import Gaussians, Projected
 
 LAMBDA_DSSIM = 0.2          # Eq. 6
 NTC_LR = 0.002              # Suppl. A
+ITERS_PER_FRAME = 150       # Stage-1 iterations per frame (Section 5.2)
 ADAM_BETAS = (0.9, 0.99)    # I-NGP's Adam constants (the paper's NTC follows I-NGP)
-ADAM_EPS = 1e-15
+# Stage 1: the rate decays exponentially to 1 % over a frame's iterations (the
+# shape of 3DG-S's schedule for Gaussian means, whose other hyper-parameters
+# the paper keeps), and epsilon is set against the unscaled gradients of a
+# loss averaged over V x 3 x H x W pixel channels (table gradients of order
+# 1e-9 .. 1e-6): entries touched only by Gaussians that no view sees get no
+# full-rate steps.  The warm-up keeps I-NGP's epsilon and a constant rate.
+STAGE1_LR_FINAL = 0.01
+STAGE1_EPS = 1e-6
+WARMUP_EPS = 1e-15
 DEFAULT_BIN = 4             # tiles per bin side of the binned pair lists (autotuned best at 1352x1014)
 
 
@@ -80,7 +89,7 @@ class Rasterizer:
 
     def forward(self, g: Gaussians, cams_dev, mean=None, quat=None, stream=None, keys=None):
         V, W, H, n = self.V, self.W, self.H, self.n
-        gs3.gs_project(g, cams_dev, V, W, H, self.proj, mean, quat, stream)
+        gs3.gs_project(g, cams_dev, V, W, H, self.proj, mean, quat, stream, self.d_err)
         gs3.gs_bin_sort(self.proj, n, V, W, H, self.bin, self.capacity, self.vals, self.ranges, keys,
                         self.d_count, self.d_err, self.ws, stream)
         gs3.gs_raster_fwd(self.proj, n, V, W, H, self.bin, self.bg, self.vals, self.ranges, self.img,
@@ -99,8 +108,12 @@ class Rasterizer:
         return int(self.d_count.item())
 
     def check(self):
-        """Raise if the device reported an error (reads device memory: syncs)."""
+        """Raise if the device reported an error (reads device memory: syncs):
+        a non-finite Gaussian met by the projection, or more pairs than the
+        binning capacity."""
         err = int(self.d_err.item())
+        if err == gs3.GS_ERR_NONFINITE:
+            raise gs3.GsError("gs_project", err, "a non-finite Gaussian was culled")
         if err != 0:
             raise gs3.GsError("gs_bin_sort", err, "device reported error (count %d, capacity %d)"
                               % (self.count(), self.capacity))
@@ -134,13 +147,20 @@ class Loss:
         return self.d_loss
 
 
+def adam_hp(lr, eps=STAGE1_EPS, lr_final_ratio=STAGE1_LR_FINAL, decay_steps=ITERS_PER_FRAME,
+            betas=ADAM_BETAS) -> gs3.GsAdam:
+    """Adam hyper-parameters: rate lr decaying to lr * lr_final_ratio over
+    decay_steps applied updates (decay_steps <= 1: constant)."""
+    return gs3.GsAdam(lr, betas[0], betas[1], eps, lr_final_ratio, decay_steps)
+
+
 class AdamBuffers:
-    def __init__(self, p: torch.Tensor, lr: float, shadow_dtype=None):
+    def __init__(self, p: torch.Tensor, lr: float, shadow_dtype=None, hp: Optional[gs3.GsAdam] = None):
         self.p = p
         self.g = torch.zeros_like(p)
         self.m = torch.zeros_like(p)
         self.v = torch.zeros_like(p)
-        self.hp = gs3.GsAdam(lr, ADAM_BETAS[0], ADAM_BETAS[1], ADAM_EPS)
+        self.hp = hp if hp is not None else adam_hp(lr)
         self.shadow = None if shadow_dtype is None else p.to(shadow_dtype)
 
     def reset(self, values: Optional[torch.Tensor] = None):
@@ -152,15 +172,17 @@ class AdamBuffers:
         self.m.zero_()
         self.v.zero_()
 
-    def step(self, d_state, stream=None):
-        gs3.adam_step(self.p, self.g, self.m, self.v, self.hp, d_state, self.shadow, stream)
+    def step(self, d_state, stream=None, hp: Optional[gs3.GsAdam] = None):
+        gs3.adam_step(self.p, self.g, self.m, self.v, self.hp if hp is None else hp, d_state,
+                      self.shadow, stream)
 
 
 class NTC:
     """Hash table (FP32 master + FP16 shadow) and MLP (FP32 master + BF16 shadow)."""
 
     def __init__(self, table: np.ndarray, weights: List[np.ndarray], grid: gs3.GsHashgrid,
-                 precision: int = gs3.GS_MLP_BF16, device="cuda", lr=NTC_LR):
+                 precision: int = gs3.GS_MLP_BF16, device="cuda", lr=NTC_LR,
+                 hp: Optional[gs3.GsAdam] = None, iters: int = ITERS_PER_FRAME):
         self.grid = grid
         self.precision = precision
         self.entries = gs3.ntc_hashgrid_entries(grid)
@@ -171,8 +193,12 @@ class NTC:
         if w.size != gs3.MLP_PARAMS:
             raise ValueError("NTC: %d MLP weights, expected %d" % (w.size, gs3.MLP_PARAMS))
         tab = torch.from_numpy(np.ascontiguousarray(table, np.float32)).to(device)
-        self.table = AdamBuffers(tab, lr, torch.float16)
-        self.mlp = AdamBuffers(torch.from_numpy(w).to(device), lr, torch.bfloat16)
+        # Stage 1's Adam (hp, default: the decayed schedule) and the warm-up's
+        # (I-NGP's epsilon, constant rate)
+        hp = hp if hp is not None else adam_hp(lr, decay_steps=iters)
+        self.warm_hp = adam_hp(lr, eps=WARMUP_EPS, lr_final_ratio=1.0, decay_steps=0)
+        self.table = AdamBuffers(tab, lr, torch.float16, hp)
+        self.mlp = AdamBuffers(torch.from_numpy(w).to(device), lr, torch.bfloat16, hp)
         self.init_table = tab.clone()
         self.init_mlp = self.mlp.p.clone()
 
@@ -235,8 +261,13 @@ class Stage1:
         return self.track
 
     def reset_state(self, loss_scale=None):
-        ls = gs3.read_train_state(self.state).loss_scale if loss_scale is None else loss_scale
-        self.state.copy_(gs3.new_train_state(ls, self.state.device))
+        """Start a frame: the step count (and with it the bias correction and
+        the rate schedule) restarts at 0; the loss scale is kept unless given.
+        Device operations only (no host read), so it can sit in a timed loop."""
+        if loss_scale is None:
+            self.state[4:].zero_()
+        else:
+            self.state.copy_(gs3.new_train_state(loss_scale, self.state.device))
 
     def transform(self, stream=None):
         """NTC query + transformation: writes mean_t, quat_t."""
@@ -542,11 +573,13 @@ class Streamer:
         img = render_dev(gs, self.heldout, 1, self.W, self.H, mean, quat)
         return -10 * math.log10(float(((img - gt_img) ** 2).mean().item()))
 
-    def run(self, frame_targets, heldout_gt=None):
+    def run(self, frame_targets, heldout_gt=None, motion_ref=None):
         """frame_targets(t) (or a list): the [n_cams, 3, H, W] device tensor of
         frame t + 1's training views, t = 0 .. n_frames - 1; heldout_gt: per
-        frame the held-out view [1, 3, H, W] (or None).  Returns one record
-        per frame."""
+        frame the held-out view [1, 3, H, W] (or None); motion_ref: (mean_gt,
+        weight) with mean_gt(t) the ground-truth means of frame t + 1 and
+        weight [n] per-Gaussian weights, to record the weighted error of the
+        carried means (or None).  Returns one record per frame."""
         get = frame_targets if callable(frame_targets) else (lambda t: frame_targets[t])
         n_frames = len(heldout_gt) if heldout_gt is not None else len(frame_targets)
         records = []
@@ -558,6 +591,10 @@ class Streamer:
         for t in range(n_frames):
             rec = {"frame": self.frames_done + 1}
             main.synchronize()  # frame t's Stage 1 is done
+            # a binning overflow or a non-finite Gaussian met by the projection
+            # (e.g. after a tensor-core wait gave up) ends the run loudly
+            self.st1.raster.check()
+            rec["tc_timeouts"] = gs3.gs_tc_timeouts()
             # the frame's cache as stored (FP16 table, BF16 MLP), before the
             # next frame's Stage 1 restarts it from the warm-up parameters
             cache = (self.ntc.table.shadow.clone(), self.ntc.mlp.shadow.clone())
@@ -576,6 +613,12 @@ class Streamer:
                 self.side.wait_stream(main)
                 with torch.cuda.stream(self.side):
                     self.st2.begin(mt_c, qt_c, acc, den)  # reads back the spawn count
+            if motion_ref is not None:
+                mgt, wgt = motion_ref
+                err = (mt_c - mgt(t)).norm(dim=1)
+                rec["motion_err_weighted"] = float((err * wgt).sum() / wgt.sum())
+                rec["motion_err_carried_weighted"] = float(((self.g.mean - mgt(t)).norm(dim=1) * wgt).sum()
+                                                           / wgt.sum())
             # carry the transformed Gaussians; issue the next frame's Stage 1
             self.g.mean.copy_(mt_c)
             self.g.quat.copy_(qt_c)
@@ -652,13 +695,16 @@ class DirectOpt:
     rotations (the "Direct Opt." comparator of Section 5.3), same rasterizer."""
 
     def __init__(self, g: Gaussians, V: int, W: int, H: int, capacity: int, lr_mean=0.0024,
-                 lr_quat=0.015, device="cuda", bin: int = DEFAULT_BIN):
+                 lr_quat=0.015, device="cuda", bin: int = DEFAULT_BIN, iters: int = ITERS_PER_FRAME):
+        """Rates: the paper's Stage-2 rates for means and rotations (Suppl. A)
+        by default, with Stage 1's schedule and epsilon over `iters`
+        iterations (the same treatment as the cache)."""
         self.g = g
         self.V, self.W, self.H = V, W, H
         self.raster = Rasterizer(g.n, V, W, H, capacity, device, bin=bin)
         self.loss = Loss(V, W, H, device)
-        self.mean = AdamBuffers(g.mean.clone(), lr_mean)
-        self.quat = AdamBuffers(g.quat.clone(), lr_quat)
+        self.mean = AdamBuffers(g.mean.clone(), lr_mean, hp=adam_hp(lr_mean, decay_steps=iters))
+        self.quat = AdamBuffers(g.quat.clone(), lr_quat, hp=adam_hp(lr_quat, decay_steps=iters))
         self.state = gs3.new_train_state(1.0, device)
 
     def step(self, cams_dev, target, stream=None):
@@ -763,8 +809,8 @@ def warmup(ntc: NTC, g: Gaussians, iters=3000, noise=0.01, extent=2.0, seed=0, s
         gs3.ntc_encode_bwd(mu, n, ntc.grid, d_enc, ntc.table.g, stream)
         gs3.gs_check_finite(ntc.table.g, state, stream)
         gs3.gs_check_finite(ntc.mlp.g, state, stream)
-        ntc.table.step(state, stream)
-        ntc.mlp.step(state, stream)
+        ntc.table.step(state, stream, ntc.warm_hp)
+        ntc.mlp.step(state, stream, ntc.warm_hp)
         gs3.gs_train_state_advance(state, 2000, stream)
     return float(d_loss.item())
 

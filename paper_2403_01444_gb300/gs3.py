@@ -66,7 +66,8 @@ class GsMlp(ctypes.Structure):
 
 
 class GsAdam(ctypes.Structure):
-    _fields_ = [("lr", c_float), ("beta1", c_float), ("beta2", c_float), ("eps", c_float)]
+    _fields_ = [("lr", c_float), ("beta1", c_float), ("beta2", c_float), ("eps", c_float),
+                ("lr_final_ratio", c_float), ("decay_steps", ctypes.c_int32)]
 
 
 class GsAdded(ctypes.Structure):
@@ -205,11 +206,12 @@ def mlp_struct(precision: int, w_f32: torch.Tensor, w_bf16: Optional[torch.Tenso
 
 
 # ------------------------------------------------------------------ calls
-def gs_project(g: Gaussians, cams_dev, V, W, H, out: Projected, mean=None, quat=None, stream=None):
+def gs_project(g: Gaussians, cams_dev, V, W, H, out: Projected, mean=None, quat=None, stream=None,
+               d_err=None):
     gg = g.struct(mean, quat)
     po = out.struct()
     _check("gs_project", lib().gs_project(ctypes.byref(gg), _ptr(cams_dev), c_int(V), c_int(W),
-                                          c_int(H), ctypes.byref(po), _stream(stream)))
+                                          c_int(H), ctypes.byref(po), _ptr(d_err), _stream(stream)))
 
 
 def gs_project_bwd(g: Gaussians, cams_dev, V, W, H, grads, d_mean, d_quat, mean=None, quat=None,
@@ -432,6 +434,17 @@ def gs_added_to_render(a: GsAdded, n, out: Gaussians, out_first, stream=None):
 def gs_sh_rotate(quat_from, quat_to, sh_in, n, sh_deg, sh_out, stream=None):
     _check("gs_sh_rotate", lib().gs_sh_rotate(_ptr(quat_from), _ptr(quat_to), _ptr(sh_in), c_int64(n),
                                               c_int(sh_deg), _ptr(sh_out), _stream(stream)))
+
+
+def gs_tc_set_wait_limit(tries: int):
+    _check("gs_tc_set_wait_limit", lib().gs_tc_set_wait_limit(ctypes.c_uint32(tries)))
+
+
+GS_TC_WAIT_TRIES_DEFAULT = 4194304
+
+
+def gs_tc_timeouts() -> int:
+    return int(lib().gs_tc_timeouts())
 
 
 def gs_tc_wait_selftest(tries, d_status, stream=None):

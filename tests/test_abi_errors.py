@@ -34,14 +34,14 @@ def _proj():
 
 def test_projection_rejects_bad_arguments(L):
     g, out = _gauss(), _proj()
-    _fails(L, L.gs_project(None, FAKE, 1, 64, 48, byref(out), None), "gs_project", "null")
-    _fails(L, L.gs_project(byref(g), FAKE, 0, 64, 48, byref(out), None), "V must be")
-    _fails(L, L.gs_project(byref(g), FAKE, 65, 64, 48, byref(out), None), "V must be")   # GS_MAX_VIEWS + 1
-    _fails(L, L.gs_project(byref(g), FAKE, 1, 0, 48, byref(out), None), "image size")
-    _fails(L, L.gs_project(byref(_gauss(deg=4)), FAKE, 1, 64, 48, byref(out), None), "sh_deg")
-    _fails(L, L.gs_project(byref(_gauss(n=-1)), FAKE, 1, 64, 48, byref(out), None), "n out of range")
+    _fails(L, L.gs_project(None, FAKE, 1, 64, 48, byref(out), None, None), "gs_project", "null")
+    _fails(L, L.gs_project(byref(g), FAKE, 0, 64, 48, byref(out), None, None), "V must be")
+    _fails(L, L.gs_project(byref(g), FAKE, 65, 64, 48, byref(out), None, None), "V must be")   # GS_MAX_VIEWS + 1
+    _fails(L, L.gs_project(byref(g), FAKE, 1, 0, 48, byref(out), None, None), "image size")
+    _fails(L, L.gs_project(byref(_gauss(deg=4)), FAKE, 1, 64, 48, byref(out), None, None), "sh_deg")
+    _fails(L, L.gs_project(byref(_gauss(n=-1)), FAKE, 1, 64, 48, byref(out), None, None), "n out of range")
     misaligned = gs3.GsGaussians(FAKE, c_void_p(0x10004), FAKE, FAKE, FAKE, 10, 1)
-    _fails(L, L.gs_project(byref(misaligned), FAKE, 1, 64, 48, byref(out), None), "aligned")
+    _fails(L, L.gs_project(byref(misaligned), FAKE, 1, 64, 48, byref(out), None, None), "aligned")
 
 
 def test_binning_and_compositing_reject_bad_arguments(L):
@@ -56,6 +56,22 @@ def test_binning_and_compositing_reject_bad_arguments(L):
                               FAKE, None, None), "bad n or V")
     _fails(L, L.gs_raster_fwd(byref(p), c_int64(10), 1, 20000, 48, 1, None, FAKE, FAKE, FAKE, FAKE,
                               FAKE, None, None), "image size")
+
+
+def test_binning_rejects_wrapping_entry_counts(L):
+    """n is bounded before n * V is formed: n = 2^62 Gaussians in 4 views would
+    wrap the 64-bit product to 0 and pass a check made on the product."""
+    p = _proj()
+    n = c_int64(1 << 62)
+    L.gs_bin_sort_workspace_size.restype = c_size_t
+    assert L.gs_bin_sort_workspace_size(n, 4, 64, 48, c_int64(100)) == 0
+    assert L.gs_bin_sort_workspace_size(c_int64(1000), 4, 64, 48, c_int64(100)) > 0
+    _fails(L, L.gs_bin_sort(byref(p), n, 4, 64, 48, 1, c_int64(100), FAKE, FAKE, None,
+                            FAKE, FAKE, FAKE, c_size_t(1 << 20), None), "32 bits")
+    _fails(L, L.gs_bin_sort_noalloc(byref(p), n, 4, 64, 48, 1, c_int64(100), FAKE, FAKE, None,
+                                    FAKE, FAKE, None), "built-in limit")
+    _fails(L, L.gs_bin_sort_noalloc(byref(p), c_int64(32769), 4, 64, 48, 1, c_int64(100), FAKE, FAKE,
+                                    None, FAKE, FAKE, None), "built-in limit")
 
 
 def test_loss_rejects_bad_shapes_and_small_workspaces(L):

@@ -51,7 +51,7 @@ def _unambiguous(g, cams, margin=1e-3, mean=None, quat=None):
 
 
 @pytest.mark.parametrize("cfg_index,view", [(3, 7), (5, 3)])
-def test_full_size_view_render_and_gradients(cfg_index, view):
+def test_full_size_view_render_and_gradients(cfg_index, view, record_property):
     sc = scenes.make_scene(cfg_index)
     cams = [sc.cams[view]]
     W, H = sc.cfg.W, sc.cfg.H
@@ -68,7 +68,10 @@ def test_full_size_view_render_and_gradients(cfg_index, view):
     ok = (r["ambig"] == 0) & crop[None]
     # dense views flag many pixels (depth ties within FP32 reach whose swap
     # could move the pixel by more than 2.5e-5); half the crop must remain
-    assert ok.sum() > 0.5 * crop.sum(), ok.sum() / crop.sum()
+    frac = float(ok.sum() / crop.sum())
+    record_property("certified_fraction", frac)
+    print("config %d view %d: %.3f of the central crop certified (FP32 image)" % (cfg_index, view, frac))
+    assert frac > 0.8, frac
     okc = np.broadcast_to(ok[:, None], img.shape)
     assert np.abs(img - r["img"])[okc].max() <= 1e-4
     # backward of the same view against the oracle's, on the crop's unambiguous pixels
@@ -169,7 +172,7 @@ def _reach(g, cams, mean, quat, d_mu, d_q):
 
 
 @pytest.mark.parametrize("cfg_index", [1, 2, 3, 4, 5])
-def test_mixed_precision_cache_and_image(cfg_index):
+def test_mixed_precision_cache_and_image(cfg_index, record_property):
     """The mixed-precision cache (FP16 table, BF16 tensor-core MLP with an FP32
     output layer) against the FP64 oracle holding the same FP32 master
     parameters, on one view of every workload:
@@ -238,7 +241,13 @@ def test_mixed_precision_cache_and_image(cfg_index):
     img = render(gs3.Gaussians.from_numpy(sub), cams, W, H, m[kd].contiguous(),
                  q[kd].contiguous()).cpu().numpy()
     ok = (want["ambig"] == 0) & crop[None]
-    assert ok.sum() > 0.1 * crop.sum(), ok.sum() / crop.sum()
+    frac = float(ok.sum() / crop.sum())
+    record_property("certified_fraction", frac)
+    record_property("thinned_every", thin)
+    print("config %d: %.3f of the central crop certified (mixed precision, every %d-th Gaussian)"
+          % (cfg_index, frac, thin))
+    # measured 0.88, 0.67, 0.19, 0.22, 0.25 for configs 1..5
+    assert frac > {1: 0.8, 2: 0.55, 3: 0.15, 4: 0.15, 5: 0.2}[cfg_index], frac
     err = np.abs(img - want["img"])
     assert err[np.broadcast_to(ok[:, None], img.shape)].max() <= 2e-3
     # PSNR of the whole scene's crop

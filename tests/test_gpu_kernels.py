@@ -414,6 +414,38 @@ def test_adam_parity_skip_and_shadow():
     assert s.loss_scale == 128.0 and s.found_inf == 0 and s.step == 5
 
 
+def test_adam_rate_schedule():
+    """The rate decays exponentially from lr to lr * ratio over decay_steps
+    applied updates and stays there; a skipped update does not advance it."""
+    n = 4099
+    rng = np.random.default_rng(61)
+    p0 = rng.normal(size=n)
+    p, m, v = p0.copy(), np.zeros(n), np.zeros(n)
+    gp = t(p0)
+    gm, gv = torch.zeros(n, device=DEV), torch.zeros(n, device=DEV)
+    st = gs3.new_train_state(1.0)
+    hp = gs3.GsAdam(0.01, 0.9, 0.99, 1e-6, 0.05, 4)
+    applied, scale = 0, 1.0
+    for k in range(7):
+        g = rng.normal(size=n).astype(np.float32)
+        gg = t(g * scale)          # scaled by the current loss scale
+        if k == 2:
+            gg[5] = float("inf")   # skipped: the schedule does not move, the scale halves
+            scale *= 0.5
+        gs3.gs_check_finite(gg, st)
+        gs3.adam_step(gp, gg, gm, gv, hp, st)
+        gs3.gs_train_state_advance(st, 0)
+        if k != 2:
+            lr = oracle.adam_rate(0.01, 0.05, 4, applied)
+            applied += 1
+            oracle.adam(p, g.astype(np.float64), m, v, applied, lr=lr, eps=1e-6)
+    torch.cuda.synchronize()
+    assert gs3.read_train_state(st).step == applied == 6
+    np.testing.assert_allclose(gp.cpu().numpy(), p, rtol=1e-5, atol=1e-6)
+    assert oracle.adam_rate(0.01, 0.05, 4, 3) == pytest.approx(0.0005)
+    assert oracle.adam_rate(0.01, 0.05, 4, 9) == pytest.approx(0.0005)
+
+
 def _bf16(a):
     return torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(torch.bfloat16).float().numpy()
 

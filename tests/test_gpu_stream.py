@@ -102,3 +102,47 @@ def test_stream_checkpoint_resume_and_frame_records(tmp_path):
         assert d["table_f16"].dtype == np.float16 and d["table_f16"].shape == (ntc.entries, 2)
         assert d["mlp_bf16"].shape == (gs3.MLP_PARAMS,)
         assert d["added_rows"].shape[1] == gs3.added_cols(cfg.sh_deg)
+
+
+def test_carried_frame_equals_oracle_transform_and_sh_rotation():
+    """After a frame, the Gaussians carried to the next one are the previous
+    frame's Gaussians moved by the frame's trained cache (Eq. 5: mu + dmu,
+    norm(q) x norm(dq)) with their SH coefficients turned by the same rotation
+    (Suppl. B): the FP64 oracle applied to the cache's final FP32 parameters
+    gives the same means, rotations and coefficients."""
+    cfg, frames, cams, ho = scenes.make_sequence(2, 1, n_gauss=3000, W=160, H=120)
+    cams = cams[:4]
+    W, H, Vb = cfg.W, cfg.H, 4
+    G0 = gs3.Gaussians.from_numpy(frames[0])
+    cd = gs3.cameras_to_device(cams)
+    rng = np.random.default_rng(93)
+    og = oracle.Grid()
+    table = rng.uniform(-1e-4, 1e-4, size=(og.n_entries, 2)).astype(np.float32)
+    Ws = [w.astype(np.float32) for w in scenes.random_mlp([32, 64, 64, 7], rng)]
+    ntc = NTC(table, Ws, gs3.hashgrid(), gs3.GS_MLP_FP32)
+    warmup(ntc, G0, iters=100)
+    warm = (ntc.table.p.clone(), ntc.mlp.p.clone())
+    views = [render(gs3.Gaussians.from_numpy(frames[1]), cams, W, H)]
+    s = Streamer(G0, ntc, *warm, cd, len(cams), Vb, W, H, stage2=False, iters1=40, graphs=False)
+    s.run(views)
+    torch.cuda.synchronize()
+    # the cache as the frame ended (no later frame has restarted it)
+    p = oracle.NTCParams(og, ntc.table.p.cpu().numpy().astype(np.float64), ntc.weights_numpy())
+    g0 = frames[0]
+    f = oracle.ntc_forward(p, g0.mean, g0.quat)
+    dm_want = f["mean"] - g0.mean
+    assert np.abs(dm_want).max() > 1e-4                    # the frame moved the Gaussians
+    # the displacement to the FP32 cache's rounding (the encoding at the finest
+    # level carries ~1e-4 cells of coordinate rounding), rotations and SH to FP32
+    dm_got = s.g.mean.cpu().numpy().astype(np.float64) - g0.mean
+    assert np.linalg.norm(dm_got - dm_want) <= 1e-3 * np.linalg.norm(dm_want)
+    # the rotations carry the same cache rounding (the rotation part of raw7
+    # comes from the same encoding): within 1 % of the change they make, and
+    # within 5e-4 per component
+    q_got = s.g.quat.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(q_got - f["quat"]) <= 1e-2 * np.linalg.norm(f["quat"] - g0.quat)
+    np.testing.assert_allclose(q_got, f["quat"], rtol=0, atol=5e-4)
+    # the SH coefficients are those of the oracle's rotation by the carried rotations
+    sh = oracle.sh_rotate(g0.sh.astype(np.float64), g0.quat, q_got, g0.sh_deg)
+    assert np.abs(sh - g0.sh).max() > 1e-6                 # the colours turned with them
+    np.testing.assert_allclose(s.g.sh.cpu().numpy(), sh, rtol=0, atol=1e-5)

@@ -174,3 +174,16 @@ def test_identity_transform_reproduces_input_render():
     a = oracle.render(g, cams)["img"]
     b = oracle.render(g, cams, mo, qo)["img"]
     np.testing.assert_allclose(a, b, atol=1e-12)
+
+
+def test_adam_rate_schedule_closed_form():
+    """The oracle's decayed rate: lr at the first update, lr * ratio at update
+    decay_steps - 1 and after, a constant factor ratio^(1/(decay_steps - 1))
+    between consecutive updates, and no decay for decay_steps <= 1."""
+    lr, ratio, S = 0.002, 0.01, 150
+    r = [oracle.adam_rate(lr, ratio, S, t) for t in range(S + 5)]
+    assert r[0] == lr
+    assert abs(r[S - 1] - lr * ratio) <= 1e-15 and all(x == r[S - 1] for x in r[S:])
+    q = np.array(r[1:S]) / np.array(r[:S - 1])
+    np.testing.assert_allclose(q, math.exp(math.log(ratio) / (S - 1)), rtol=1e-12)
+    assert oracle.adam_rate(lr, ratio, 1, 7) == lr and oracle.adam_rate(lr, ratio, 0, 7) == lr
