@@ -1,14 +1,12 @@
 // Front-to-back alpha compositing (Section 3.2, Eq. 4) and its reverse.
-// One 16x16 tile per block, one pixel per thread; the tile's depth-sorted
-// records are staged through shared memory in batches.
+// One 16x16 tile per 128-thread block, two vertically adjacent pixels per
+// thread evaluated together in packed FP32; the tile's depth-sorted records
+// are staged through shared memory in batches of 128.
 #include "common.cuh"
 
 namespace gs3 {
 
-constexpr int FT = 256;         // forward: threads per 16x16 tile, one pixel each
-#ifndef BWD_PIXELS_PER_THREAD
-#define BWD_PIXELS_PER_THREAD 2  // backward: pixels per thread (256 / this threads per tile)
-#endif
+constexpr int NT = 128;          // threads per 16x16 tile: two pixels each
 #ifndef BWD_CHUNK_RECORDS
 #define BWD_CHUNK_RECORDS 32
 #endif
@@ -20,9 +18,6 @@ constexpr int BWD_CHUNK = BWD_CHUNK_RECORDS;  // records per backward reduction 
 #define FWD_UNROLL 8
 #endif
 constexpr int kBwdUnroll = BWD_UNROLL, kFwdUnroll = FWD_UNROLL;
-#ifndef FWD_PIXELS_PER_THREAD
-#define FWD_PIXELS_PER_THREAD 2  // forward: pixels per thread (1 or 2)
-#endif
 #ifndef RASTER_WARP_BLOCKS
 #define RASTER_WARP_BLOCKS 1     // 1: each warp owns a compact block of the tile; 0: rows
 #endif
@@ -85,23 +80,11 @@ __device__ __forceinline__ void flush_stats(unsigned long long *stats, uint32_t 
     }
 }
 
-// power and alpha of one (pixel, Gaussian) pair.  Written with explicit
-// roundings so the forward and the reverse pass take bit-identical decisions.
-// The offset monomials dx^2, dx dy, dy^2 are returned for the reverse pass.
-__device__ __forceinline__ float pair_power(float2 xy, float4 co, float px, float py, float &dx,
-                                            float &dy, float &dxx, float &dxy, float &dyy)
-{
-    dx = __fsub_rn(px, xy.x);
-    dy = __fsub_rn(py, xy.y);
-    dxx = __fmul_rn(dx, dx);
-    dxy = __fmul_rn(dx, dy);
-    dyy = __fmul_rn(dy, dy);
-    float q = fmaf(co.z, dyy, __fmul_rn(co.x, dxx));
-    return fmaf(-0.5f, q, -__fmul_rn(co.y, dxy));
-}
-
-// pair_power for the two pixels (px, py.x) and (px, py.y) of one column:
-// the same roundings, the row-dependent terms two per packed instruction.
+// power of one record at the two pixels (px, py.x) and (px, py.y) of a
+// column, -0.5 (A dx^2 + C dy^2) - B dx dy, with explicit roundings so that
+// the forward and the reverse pass take bit-identical decisions; the offset
+// monomials dx^2, dx dy, dy^2 are returned for the reverse pass.  The
+// row-dependent terms go two per packed instruction.
 __device__ __forceinline__ float2 pair_power2(float2 xy, float4 co, float px, float2 py, float &dx,
                                               float2 &dy, float &dxx, float2 &dxy, float2 &dyy)
 {
@@ -147,12 +130,10 @@ __device__ __forceinline__ float pair_gauss(float power)
 #endif
 }
 
-__device__ __forceinline__ float pair_alpha_raw(float4 co, float power)
-{
-    return __fmul_rn(co.w, pair_gauss(power));
-}
-
-constexpr float kAlphaMin = 1.0f / 255.0f;
+// alpha >= 1/255 (Eq. 4's skip) is tested as power >= pmin on the base-2
+// power, pmin = -log2(255 o) staged with the record: forward and reverse take
+// the same decision, which differs from the test on alpha only within the
+// rounding of the exponential
 constexpr float kAlphaCap = 0.99f;
 constexpr float kTEps = 1e-4f;
 
@@ -226,96 +207,15 @@ __device__ __forceinline__ int compact_slot(bool keep, int *s_wcnt, int &count)
     return keep ? off + __popc(b & ((1u << lane) - 1u)) : -1;
 }
 
-template <bool BINNED, bool STATS>
-__global__ void __launch_bounds__(FT) raster_fwd_kernel(RasterParams p)
-{
-    __shared__ float2 s_xy[FT];
-    __shared__ float4 s_co[FT];
-    __shared__ float4 s_rgbk[FT];  // colour and (bit pattern of) the list position
-    __shared__ int s_wcnt[FT / 32];
-    const int tile = blockIdx.x, view = blockIdx.y;
-    const int tid = threadIdx.x;
-    const int tx_t = tile % p.tx, ty_t = tile / p.tx;
-    int px, py;
-    tile_pixel(tid, 1, 0, px, py);
-    px += tx_t * 16;
-    py += ty_t * 16;
-    const bool inside = px < p.W && py < p.H;
-    const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
-    const int binid = (ty_t / p.bin) * p.bins_x + tx_t / p.bin;
-    const uint2 range = p.ranges[(int64_t)view * p.bins + binid];
-    const int total = (int)(range.y - range.x);
-    const int64_t vb = (int64_t)view * p.n;
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    int last = 0;
-    bool done = !inside;
-    uint32_t n_tested = 0, n_contrib = 0;
-    for (int base = 0; base < total; base += FT) {
-        if (__syncthreads_count(done) == FT) break;
-        const int k = base + tid;
-        int64_t o = 0;
-        bool keep = false;
-        float2 m;
-        float4 co;
-        if (k < total) {
-            o = vb + p.vals[range.x + k];
-            keep = keep_record<BINNED>(p, o, tx_t, ty_t, m, co);
-        }
-        int cnt;
-        const int slot = compact_slot<FT>(keep, s_wcnt, cnt);
-        if (slot >= 0) {
-            s_xy[slot] = m;
-            s_co[slot] = scale_conic(co);
-            s_rgbk[slot] = make_float4(p.rgb[3 * o], p.rgb[3 * o + 1], p.rgb[3 * o + 2],
-                                       __int_as_float(k));
-        }
-        __syncthreads();
-#pragma unroll 2
-        for (int j = 0; !done && j < cnt; ++j) {
-            float dx, dy;
-            float4 co = s_co[j];
-            if (STATS) ++n_tested;
-            float dxx, dxy, dyy;
-            float power = pair_power(s_xy[j], co, pxf, pyf, dx, dy, dxx, dxy, dyy);
-            if (power > 0.f) continue;
-            float alpha = fminf(kAlphaCap, pair_alpha_raw(co, power));
-            if (alpha < kAlphaMin) continue;
-            float test_T = T * (1.f - alpha);
-            if (test_T < kTEps) {
-                done = true;
-                break;
-            }
-            float w = alpha * T;
-            const float4 ck = s_rgbk[j];
-            C0 = fmaf(ck.x, w, C0);
-            C1 = fmaf(ck.y, w, C1);
-            C2 = fmaf(ck.z, w, C2);
-            T = test_T;
-            last = __float_as_int(ck.w) + 1;
-            if (STATS) ++n_contrib;
-        }
-    }
-    if (STATS) flush_stats(p.stats, n_tested, n_contrib);
-    if (inside) {
-        int64_t HW = (int64_t)p.H * p.W;
-        int64_t pix = (int64_t)py * p.W + px;
-        float *im = p.img + (int64_t)view * 3 * HW + pix;
-        im[0] = fmaf(T, p.bg0, C0);
-        im[HW] = fmaf(T, p.bg1, C1);
-        im[2 * HW] = fmaf(T, p.bg2, C2);
-        p.T_final[(int64_t)view * HW + pix] = T;
-        p.last[(int64_t)view * HW + pix] = last;
-    }
-}
-
 // Forward with two vertically adjacent pixels per thread (128 threads per
-// tile): the record loads and the column offset are shared and the pair's
-// quadratic forms are evaluated two per packed instruction.
+// tile): the record loads and the column offset are shared, and the pair of
+// pixels is evaluated in packed FP32 (quadratic forms, alpha, transmittance,
+// colour), two lanes of a register pair per instruction.  The arithmetic of an
+// added pixel is the scalar one, rounding for rounding.
 template <bool BINNED, bool STATS>
-__global__ void __launch_bounds__(FT / 2) raster_fwd2_kernel(RasterParams p)
+__global__ void __launch_bounds__(NT) raster_fwd2_kernel(RasterParams p)
 {
-    constexpr int NT = FT / 2;
-    __shared__ float2 s_xy[NT];
+    __shared__ float4 s_xy[NT];
     __shared__ float4 s_co[NT];
     __shared__ float4 s_rgbk[NT];  // colour and (bit pattern of) the list position
     __shared__ int s_wcnt[NT / 32];
@@ -351,7 +251,7 @@ __global__ void __launch_bounds__(FT / 2) raster_fwd2_kernel(RasterParams p)
         int cnt;
         const int slot = compact_slot<NT>(keep, s_wcnt, cnt);
         if (slot >= 0) {
-            s_xy[slot] = m;
+            s_xy[slot] = make_float4(m.x, m.y, -__log2f(255.f * co.w), 0.f);
             s_co[slot] = scale_conic(co);
             s_rgbk[slot] = make_float4(p.rgb[3 * o], p.rgb[3 * o + 1], p.rgb[3 * o + 2],
                                        __int_as_float(k));
@@ -360,32 +260,38 @@ __global__ void __launch_bounds__(FT / 2) raster_fwd2_kernel(RasterParams p)
 #pragma unroll kFwdUnroll
         for (int j = 0; !(done[0] && done[1]) && j < cnt; ++j) {
             const float4 cj = s_co[j];
+            const float4 xyp = s_xy[j];
             float dx, dxx;
             float2 dy, dxy, dyy;
-            const float2 pw = pair_power2(s_xy[j], cj, pxf, pyf, dx, dy, dxx, dxy, dyy);
-            const float pwv[2] = {pw.x, pw.y};
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                if (done[q]) continue;
-                if (STATS) ++n_tested;
-                const float power = pwv[q];
-                if (power > 0.f) continue;
-                const float alpha = fminf(kAlphaCap, pair_alpha_raw(cj, power));
-                if (alpha < kAlphaMin) continue;
-                const float test_T = T[q] * (1.f - alpha);
-                if (test_T < kTEps) {
-                    done[q] = true;
-                    continue;
-                }
-                const float w = alpha * T[q];
-                const float4 ck = s_rgbk[j];
-                C0[q] = fmaf(ck.x, w, C0[q]);
-                C1[q] = fmaf(ck.y, w, C1[q]);
-                C2[q] = fmaf(ck.z, w, C2[q]);
-                T[q] = test_T;
-                last[q] = __float_as_int(ck.w) + 1;
-                if (STATS) ++n_contrib;
-            }
+            const float2 pw = pair_power2(make_float2(xyp.x, xyp.y), cj, pxf, pyf, dx, dy, dxx, dxy, dyy);
+            const bool t0 = !done[0] && pw.x <= 0.f && pw.x >= xyp.z;   // pixel takes part
+            const bool t1 = !done[1] && pw.y <= 0.f && pw.y >= xyp.z;
+            if (STATS) n_tested += !done[0] + !done[1];
+            if (!(t0 || t1)) continue;
+            // both pixels in packed FP32; a pixel that does not take part, or
+            // whose transmittance would fall below the cutoff, adds nothing
+            const float g0 = t0 ? pair_gauss(pw.x) : 0.f, g1 = t1 ? pair_gauss(pw.y) : 0.f;
+            const float2 araw = __fmul2_rn(make_float2(cj.w, cj.w), make_float2(g0, g1));
+            const float2 alpha = make_float2(fminf(kAlphaCap, araw.x), fminf(kAlphaCap, araw.y));
+            const float2 om = __ffma2_rn(alpha, make_float2(-1.f, -1.f), make_float2(1.f, 1.f));
+            const float2 tT = __fmul2_rn(make_float2(T[0], T[1]), om);
+            const bool stop0 = t0 && tT.x < kTEps, stop1 = t1 && tT.y < kTEps;
+            const bool add0 = t0 && !stop0, add1 = t1 && !stop1;
+            done[0] |= stop0;
+            done[1] |= stop1;
+            const float2 w = __fmul2_rn(make_float2(add0 ? alpha.x : 0.f, add1 ? alpha.y : 0.f),
+                                        make_float2(T[0], T[1]));
+            const float4 ck = s_rgbk[j];
+            const float2 c0 = __ffma2_rn(make_float2(ck.x, ck.x), w, make_float2(C0[0], C0[1]));
+            const float2 c1 = __ffma2_rn(make_float2(ck.y, ck.y), w, make_float2(C1[0], C1[1]));
+            const float2 c2 = __ffma2_rn(make_float2(ck.z, ck.z), w, make_float2(C2[0], C2[1]));
+            C0[0] = c0.x; C0[1] = c0.y;
+            C1[0] = c1.x; C1[1] = c1.y;
+            C2[0] = c2.x; C2[1] = c2.y;
+            const int kk = __float_as_int(ck.w) + 1;
+            if (add0) { T[0] = tT.x; last[0] = kk; }
+            if (add1) { T[1] = tT.y; last[1] = kk; }
+            if (STATS) n_contrib += add0 + add1;
         }
     }
     if (STATS) flush_stats(p.stats, n_tested, n_contrib);
@@ -436,55 +342,6 @@ __device__ __forceinline__ float warp_reduce8(const float *v)
     return c;
 }
 
-// Back-to-front state of one pixel.  With B the colour composited behind
-// the current Gaussian (background included), Eq. 4 gives
-//   dL/dalpha_i = T_i dC . (c_i - B_i+1),  B_i = alpha_i c_i + (1 - alpha_i) B_i+1,
-// and since dC = dL/dC is fixed per pixel only S = dC . B is carried.
-struct PixBwd {
-    int last;
-    float T, dC0, dC1, dC2, S;
-};
-
-template <bool WANT_OP>
-__device__ __forceinline__ bool unblend_at(PixBwd &P, float4 co, float4 c, float power, float dx,
-                                           float dy, float dxx, float dxy, float dyy, float *v)
-{
-    if (power > 0.f) return false;
-    float G = pair_gauss(power);
-    float araw = __fmul_rn(co.w, G);
-    float alpha = fminf(kAlphaCap, araw);
-    if (alpha < kAlphaMin) return false;
-    P.T = __fdividef(P.T, 1.f - alpha);
-    float w = alpha * P.T;
-    v[5] = fmaf(P.dC0, w, v[5]);
-    v[6] = fmaf(P.dC1, w, v[6]);
-    v[7] = fmaf(P.dC2, w, v[7]);
-    const float diff = fmaf(P.dC2, c.z, fmaf(P.dC1, c.y, P.dC0 * c.x)) - P.S;
-    float dalpha = P.T * diff;
-    P.S = fmaf(alpha, diff, P.S);
-    if (araw < kAlphaCap) {
-        // moments of dL/dpower over the pair offsets; the record's mean and
-        // conic gradients are linear in them and formed once per tile
-        float dpow = dalpha * alpha;
-        v[0] = fmaf(dpow, dx, v[0]);
-        v[1] = fmaf(dpow, dy, v[1]);
-        v[2] = fmaf(dpow, dxx, v[2]);
-        v[3] = fmaf(dpow, dxy, v[3]);
-        v[4] = fmaf(dpow, dyy, v[4]);
-        if (WANT_OP) v[8] = fmaf(dalpha, G, v[8]);
-    }
-    return true;
-}
-
-template <bool WANT_OP>
-__device__ __forceinline__ bool unblend_one(PixBwd &P, float2 xy, float4 co, float4 c,
-                                            float pxf, float pyf, float *v)
-{
-    float dx, dy, dxx, dxy, dyy;
-    const float power = pair_power(xy, co, pxf, pyf, dx, dy, dxx, dxy, dyy);
-    return unblend_at<WANT_OP>(P, co, c, power, dx, dy, dxx, dxy, dyy, v);
-}
-
 // Record gradients from the tile sums of the moments: with power =
 // -0.5 (A dx^2 + C dy^2) - B dx dy and dx = px - u,
 //   dL/du = A S_x + B S_y,  dL/dv = C S_y + B S_x,
@@ -498,20 +355,78 @@ __device__ __forceinline__ float4 moments_to_grads(float4 s, float4 co, int h)
     return make_float4(-0.5f * s.x, s.y, s.z, s.w);
 }
 
-template <bool WANT_OP, bool BINNED, int PPT, bool STATS>
-__global__ void __launch_bounds__(256 / PPT) raster_bwd_kernel(RasterParams p)
+// Reverse with the thread's two vertically adjacent pixels evaluated together
+// in packed FP32 (two lanes of a register pair per instruction).  A pixel
+// that does not take part in a record (past its list end, or the record's
+// power outside [pmin, 0]) gets alpha = 0, which leaves its transmittance,
+// its colour-behind term and the sums exactly as they are.
+struct PixBwd2 {
+    int last0, last1;
+    float2 T, dC0, dC1, dC2, S;
+};
+
+__device__ __forceinline__ float rcp_approx(float x)
 {
-    constexpr int NT = 256 / PPT;        // threads per tile
-    constexpr int NW = NT / 32;          // warps per tile
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+template <bool WANT_OP>
+__device__ __forceinline__ int unblend_pair(PixBwd2 &P, int pos, float4 co, float4 c, float2 pw, float pmin,
+                                             float dx, float2 dy, float dxx, float2 dxy, float2 dyy,
+                                             float *v)
+{
+    const bool in0 = pos < P.last0 && pw.x <= 0.f && pw.x >= pmin;
+    const bool in1 = pos < P.last1 && pw.y <= 0.f && pw.y >= pmin;
+    if (!(in0 || in1)) return 0;
+    const float g0 = in0 ? pair_gauss(pw.x) : 0.f, g1 = in1 ? pair_gauss(pw.y) : 0.f;
+    const float2 araw = __fmul2_rn(f2(co.w), make_float2(g0, g1));
+    const float2 alpha = make_float2(fminf(kAlphaCap, araw.x), fminf(kAlphaCap, araw.y));
+    const float2 om = __ffma2_rn(alpha, f2(-1.f), f2(1.f));   // 1 - alpha
+    P.T = __fmul2_rn(P.T, make_float2(in0 ? rcp_approx(om.x) : 1.f, in1 ? rcp_approx(om.y) : 1.f));
+    const float2 w = __fmul2_rn(alpha, P.T);
+    const float2 c0 = __fmul2_rn(P.dC0, w), c1 = __fmul2_rn(P.dC1, w), c2 = __fmul2_rn(P.dC2, w);
+    v[5] = c0.x + c0.y;
+    v[6] = c1.x + c1.y;
+    v[7] = c2.x + c2.y;
+    float2 t = __fmul2_rn(P.dC0, f2(c.x));
+    t = __ffma2_rn(P.dC1, f2(c.y), t);
+    t = __ffma2_rn(P.dC2, f2(c.z), t);
+    const float2 diff = __ffma2_rn(P.S, f2(-1.f), t);          // dC . c - S
+    const float2 dalpha = __fmul2_rn(P.T, diff);
+    P.S = __ffma2_rn(alpha, diff, P.S);
+    // moments of dL/dpower over the pair offsets (no gradient through a capped alpha)
+    float2 dpow = __fmul2_rn(dalpha, alpha);
+    if (!(araw.x < kAlphaCap)) dpow.x = 0.f;
+    if (!(araw.y < kAlphaCap)) dpow.y = 0.f;
+    const float sd = dpow.x + dpow.y;
+    v[0] = sd * dx;
+    v[2] = sd * dxx;
+    const float2 m1 = __fmul2_rn(dpow, dy), m3 = __fmul2_rn(dpow, dxy), m4 = __fmul2_rn(dpow, dyy);
+    v[1] = m1.x + m1.y;
+    v[3] = m3.x + m3.y;
+    v[4] = m4.x + m4.y;
+    if (WANT_OP) {
+        const float2 gm = make_float2(araw.x < kAlphaCap ? g0 : 0.f, araw.y < kAlphaCap ? g1 : 0.f);
+        const float2 op = __fmul2_rn(dalpha, gm);
+        v[8] = op.x + op.y;
+    }
+    return (int)in0 + (int)in1;
+}
+
+template <bool WANT_OP, bool BINNED, bool STATS>
+__global__ void __launch_bounds__(NT) raster_bwd2_kernel(RasterParams p)
+{
+    constexpr int NW = NT / 32;
     constexpr int NV = WANT_OP ? 9 : 8;
-    __shared__ float2 s_xy[NT];
+    __shared__ float4 s_xy[NT];
     __shared__ float4 s_co[NT];
     __shared__ float4 s_rgbk[NT];  // colour and (bit pattern of) the list position
     __shared__ uint32_t s_g[NT];
     __shared__ int s_wcnt[NW];
-    // per-warp partial sums of each record of the chunk: 4 partials of each
-    // of the 8 values (lane l holds partial l & 3 of value l >> 2), and the
-    // opacity gradient
     __shared__ float4 s_part[NW][BWD_CHUNK][8];
     __shared__ float s_pop[WANT_OP ? NW : 1][BWD_CHUNK];
     __shared__ int s_max;
@@ -519,35 +434,41 @@ __global__ void __launch_bounds__(256 / PPT) raster_bwd_kernel(RasterParams p)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tx_t = tile % p.tx, ty_t = tile / p.tx;
     int px, py0;
-    tile_pixel(tid, PPT, 0, px, py0);
+    tile_pixel(tid, 2, 0, px, py0);
     px += tx_t * 16;
+    py0 += ty_t * 16;
     const float pxf = (float)px + 0.5f;
+    const float2 pyf = make_float2((float)py0 + 0.5f, (float)py0 + 1.5f);
     const int binid = (ty_t / p.bin) * p.bins_x + tx_t / p.bin;
     const uint2 range = p.ranges[(int64_t)view * p.bins + binid];
     const int64_t vb = (int64_t)view * p.n;
     const int64_t HW = (int64_t)p.H * p.W;
-    PixBwd P[PPT];
-    float pyf[PPT];
-    int mylast = 0;
+    PixBwd2 P;
+    P.last0 = P.last1 = 0;
+    float Tq[2] = {1.f, 1.f}, d0[2] = {0.f, 0.f}, d1[2] = {0.f, 0.f}, d2[2] = {0.f, 0.f}, Sq[2] = {0.f, 0.f};
+    int lq[2] = {0, 0};
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        int pxk, py;  // pxk == px - tx_t * 16
-        tile_pixel(tid, PPT, k, pxk, py);
-        py += ty_t * 16;
-        pyf[k] = (float)py + 0.5f;
-        P[k] = PixBwd{0, 1.f, 0.f, 0.f, 0.f, 0.f};
+    for (int k = 0; k < 2; ++k) {
+        const int py = py0 + k;
         if (px < p.W && py < p.H) {
             int64_t pix = (int64_t)view * HW + (int64_t)py * p.W + px;
-            P[k].last = p.last[pix];
-            P[k].T = p.T_final[pix];
+            lq[k] = p.last[pix];
+            Tq[k] = p.T_final[pix];
             const float *di = p.d_img + (int64_t)view * 3 * HW + (int64_t)py * p.W + px;
-            P[k].dC0 = di[0];
-            P[k].dC1 = di[HW];
-            P[k].dC2 = di[2 * HW];
-            P[k].S = fmaf(P[k].dC2, p.bg2, fmaf(P[k].dC1, p.bg1, P[k].dC0 * p.bg0));
+            d0[k] = di[0];
+            d1[k] = di[HW];
+            d2[k] = di[2 * HW];
+            Sq[k] = fmaf(d2[k], p.bg2, fmaf(d1[k], p.bg1, d0[k] * p.bg0));
         }
-        mylast = max(mylast, P[k].last);
     }
+    P.last0 = lq[0];
+    P.last1 = lq[1];
+    P.T = make_float2(Tq[0], Tq[1]);
+    P.dC0 = make_float2(d0[0], d0[1]);
+    P.dC1 = make_float2(d1[0], d1[1]);
+    P.dC2 = make_float2(d2[0], d2[1]);
+    P.S = make_float2(Sq[0], Sq[1]);
+    const int mylast = max(lq[0], lq[1]);
     if (tid == 0) s_max = 0;
     __syncthreads();
     if (mylast > 0) atomicMax(&s_max, mylast);
@@ -555,7 +476,6 @@ __global__ void __launch_bounds__(256 / PPT) raster_bwd_kernel(RasterParams p)
     const int maxlast = s_max;
     uint32_t n_tested = 0, n_contrib = 0;
     for (int hi = maxlast; hi > 0; hi -= NT) {
-        // candidates [lo, hi) of the bin list, compacted to this tile's records
         const int lo = max(0, hi - NT);
         const int k = lo + tid;
         int64_t o = 0;
@@ -572,7 +492,7 @@ __global__ void __launch_bounds__(256 / PPT) raster_bwd_kernel(RasterParams p)
         const int slot = compact_slot<NT>(keep, s_wcnt, cnt);
         if (slot >= 0) {
             s_g[slot] = g;
-            s_xy[slot] = m;
+            s_xy[slot] = make_float4(m.x, m.y, -__log2f(255.f * co.w), 0.f);
             s_co[slot] = scale_conic(co);
             s_rgbk[slot] = make_float4(p.rgb[3 * o], p.rgb[3 * o + 1], p.rgb[3 * o + 2],
                                        __int_as_float(k));
@@ -583,44 +503,24 @@ __global__ void __launch_bounds__(256 / PPT) raster_bwd_kernel(RasterParams p)
 #pragma unroll kBwdUnroll
             for (int j = chi - 1; j >= clo; --j) {
                 float v[NV];
-#pragma unroll
-                for (int q = 0; q < NV; ++q) v[q] = 0.f;
                 const float4 c = s_rgbk[j];
                 const int pos = __float_as_int(c.w);
                 bool contrib = false;
                 if (pos < mylast) {
-                    float2 xy = s_xy[j];
-                    float4 cc = s_co[j];
-                    if (PPT == 2) {
-                        // the thread's two pixels share a column: one packed evaluation
-                        float dx, dxx;
-                        float2 dy, dxy, dyy;
-                        const float2 pw = pair_power2(xy, cc, pxf, make_float2(pyf[0], pyf[PPT - 1]),
-                                                      dx, dy, dxx, dxy, dyy);
-                        if (pos < P[0].last) {
-                            if (STATS) ++n_tested;
-                            bool h = unblend_at<WANT_OP>(P[0], cc, c, pw.x, dx, dy.x, dxx, dxy.x, dyy.x, v);
-                            if (STATS) n_contrib += h;
-                            contrib |= h;
-                        }
-                        if (pos < P[PPT - 1].last) {
-                            if (STATS) ++n_tested;
-                            bool h = unblend_at<WANT_OP>(P[PPT - 1], cc, c, pw.y, dx, dy.y, dxx, dxy.y,
-                                                         dyy.y, v);
-                            if (STATS) n_contrib += h;
-                            contrib |= h;
-                        }
-                    } else {
+                    const float4 xyp = s_xy[j];
+                    const float4 cc = s_co[j];
+                    float dx, dxx;
+                    float2 dy, dxy, dyy;
+                    const float2 pw = pair_power2(make_float2(xyp.x, xyp.y), cc, pxf, pyf, dx, dy, dxx, dxy, dyy);
+                    if (STATS) n_tested += (pos < P.last0) + (pos < P.last1);
+                    const int taking = unblend_pair<WANT_OP>(P, pos, cc, c, pw, xyp.z, dx, dy, dxx, dxy,
+                                                             dyy, v);
+                    if (STATS) n_contrib += taking;
+                    contrib = taking > 0;
+                }
+                if (!contrib) {
 #pragma unroll
-                        for (int q = 0; q < PPT; ++q) {
-                            if (pos < P[q].last) {
-                                if (STATS) ++n_tested;
-                                bool h = unblend_one<WANT_OP>(P[q], xy, cc, c, pxf, pyf[q], v);
-                                if (STATS) n_contrib += h;
-                                contrib |= h;
-                            }
-                        }
-                    }
+                    for (int q = 0; q < NV; ++q) v[q] = 0.f;
                 }
                 float *part = reinterpret_cast<float *>(&s_part[warp][j - clo][0]);
                 if (__any_sync(0xffffffffu, contrib)) {
@@ -636,7 +536,6 @@ __global__ void __launch_bounds__(256 / PPT) raster_bwd_kernel(RasterParams p)
             }
             __syncthreads();
             const int ccnt = chi - clo;
-            // tile-wide sums: thread t -> (record t/2, half t%2), one float4 atomic
             if (tid < 2 * ccnt) {
                 int j = tid >> 1, h = (tid & 1) * 4;
                 float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -702,12 +601,10 @@ static gs_status fill(const gs_projected *proj, int64_t n, int V, int W, int H, 
 template <bool WANT_OP, bool BINNED>
 static void launch_bwd(const RasterParams &p, dim3 grid, cudaStream_t s)
 {
-    constexpr int PPT = BWD_PIXELS_PER_THREAD;
-    constexpr int NT = 256 / PPT;
     if (p.stats)
-        raster_bwd_kernel<WANT_OP, BINNED, PPT, true><<<grid, NT, 0, s>>>(p);
+        raster_bwd2_kernel<WANT_OP, BINNED, true><<<grid, NT, 0, s>>>(p);
     else
-        raster_bwd_kernel<WANT_OP, BINNED, PPT, false><<<grid, NT, 0, s>>>(p);
+        raster_bwd2_kernel<WANT_OP, BINNED, false><<<grid, NT, 0, s>>>(p);
 }
 
 }  // namespace gs3
@@ -730,25 +627,14 @@ extern "C" gs_status gs_raster_fwd(const gs_projected *proj, int64_t n, int V, i
     dim3 grid(p.tx * p.ty, V);
     note_launch();
     cudaStream_t s = as_stream(stream);
-#if FWD_PIXELS_PER_THREAD == 2
     if (bin > 1 && p.stats)
-        raster_fwd2_kernel<true, true><<<grid, FT / 2, 0, s>>>(p);
+        raster_fwd2_kernel<true, true><<<grid, NT, 0, s>>>(p);
     else if (bin > 1)
-        raster_fwd2_kernel<true, false><<<grid, FT / 2, 0, s>>>(p);
+        raster_fwd2_kernel<true, false><<<grid, NT, 0, s>>>(p);
     else if (p.stats)
-        raster_fwd2_kernel<false, true><<<grid, FT / 2, 0, s>>>(p);
+        raster_fwd2_kernel<false, true><<<grid, NT, 0, s>>>(p);
     else
-        raster_fwd2_kernel<false, false><<<grid, FT / 2, 0, s>>>(p);
-#else
-    if (bin > 1 && p.stats)
-        raster_fwd_kernel<true, true><<<grid, FT, 0, s>>>(p);
-    else if (bin > 1)
-        raster_fwd_kernel<true, false><<<grid, FT, 0, s>>>(p);
-    else if (p.stats)
-        raster_fwd_kernel<false, true><<<grid, FT, 0, s>>>(p);
-    else
-        raster_fwd_kernel<false, false><<<grid, FT, 0, s>>>(p);
-#endif
+        raster_fwd2_kernel<false, false><<<grid, NT, 0, s>>>(p);
     return launch_status("gs_raster_fwd");
 }
 
