@@ -3,21 +3,22 @@
 // The order required is that of the 64-bit key (view, tile, depth bits) with
 // ties by Gaussian index.  Instead of radix-sorting 64-bit keys of every
 // (Gaussian, tile) pair, the sort is split in two stable stages:
-//   1. the V*N (view, Gaussian) entries are sorted by (view, depth bits) --
-//      4 byte-digit passes on the FP32 depth bits plus one pass on the view;
-//   2. pairs are emitted in that order (each entry's bins row-major) and
-//      stably sorted on the (view * bins + bin) key alone, which needs
-//      ceil(log2(V * bins) / 8) passes (2 for 4 views of 1352x1014).
+//   1. the V*N (view, Gaussian) entries are sorted by depth bits -- 4
+//      byte-digit passes on the FP32 depth bits, stable, so equal depths keep
+//      the index order (the views interleave; stage 2's key holds the view);
+//   2. the pairs of every entry's bins are ordered on the (view * bins + bin)
+//      key alone, stably, so each list keeps its entries' depth order.  When
+//      the keys' difference grids fit in shared memory this is a counting
+//      sort that writes each pair once, straight to its place; otherwise the
+//      pairs are emitted in entry order and radix-sorted on the key,
+//      ceil(log2(V * bins) / 8) byte passes.
 // A bin is bin x bin tiles.  With bin = 1 the lists are the per-tile lists;
 // with larger bins every tile of a bin shares the bin's depth-ordered list and
 // the compositing kernels keep, on the fly, the entries whose footprint
 // rectangle holds their tile -- the same records in the same order as the
 // per-tile list, for far fewer pairs to sort.
-// Stage 2 keeps the depth order inside every tile, so the result equals the
-// full-key sort while moving 8 bytes per pair per pass over 2 passes instead
-// of 12 bytes over 6.  All passes are stable LSD byte passes of
-// reduce-then-scan form (histogram, one-block scan, ranked scatter): no
-// inter-block waits, deterministic output.
+// All passes are of reduce-then-scan form (counts, one-block scans, ranked
+// scatter): no inter-block waits, deterministic output.
 #include <algorithm>
 
 #include "common.cuh"
@@ -42,7 +43,6 @@ struct SortPass {
     const int64_t *d_n;  // device count (NULL: use n_host)
     int64_t n_host;
     int shift;
-    uint32_t div;        // != 0: digit = value / div (the view of a (view, Gaussian) entry)
     uint32_t *hist;      // [RADIX][G]
     int G;
 };
@@ -59,7 +59,7 @@ __device__ __forceinline__ void block_range(int64_t n, int G, int b, int64_t &be
 
 __device__ __forceinline__ uint32_t digit_of(const SortPass &s, uint32_t k, uint32_t v)
 {
-    return s.div ? (v / s.div) : ((k >> s.shift) & (RADIX - 1));
+    return (k >> s.shift) & (RADIX - 1);
 }
 
 __global__ void __launch_bounds__(SORT_THREADS) radix_hist_kernel(SortPass s)
@@ -70,16 +70,17 @@ __global__ void __launch_bounds__(SORT_THREADS) radix_hist_kernel(SortPass s)
     int64_t beg, end;
     block_range(pass_n(s), s.G, blockIdx.x, beg, end);
     for (int64_t i = beg + threadIdx.x; i < end; i += SORT_THREADS) {
-        uint32_t d = s.div ? (s.vin[i] / s.div) : ((s.kin[i] >> s.shift) & (RADIX - 1));
+        uint32_t d = (s.kin[i] >> s.shift) & (RADIX - 1);
         atomicAdd(&h[d], 1u);
     }
     __syncthreads();
     s.hist[threadIdx.x * s.G + blockIdx.x] = h[threadIdx.x];
 }
 
-// Per digit d (one block each): exclusive scan, in place, of the G block
-// counts hist[d][0..G), and the digit's total in hist[RADIX * G + d].
-__global__ void __launch_bounds__(SORT_THREADS) scan_digit_rows_kernel(uint32_t *hist, int G)
+// Per row d (one block each; a digit of a radix pass or a key of the
+// counting sort): exclusive scan, in place, of the G block counts
+// hist[d][0..G), and the row's total in hist[rows * G + d].
+__global__ void __launch_bounds__(SORT_THREADS) scan_digit_rows_kernel(uint32_t *hist, int G, int rows)
 {
     __shared__ uint32_t s_w[SORT_WARPS];
     __shared__ uint32_t s_carry;
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(SORT_THREADS) scan_digit_rows_kernel(uint32_t 
         if (threadIdx.x == SORT_THREADS - 1) s_carry = before + inc;
         __syncthreads();
     }
-    if (threadIdx.x == 0) hist[(int64_t)RADIX * G + d] = s_carry;
+    if (threadIdx.x == 0) hist[(int64_t)rows * G + d] = s_carry;
 }
 
 // Ranked scatter of one pass.  Each tile of SORT_TILE items is first put in
@@ -418,6 +419,238 @@ __global__ void keys64_kernel(const uint32_t *tk, const uint32_t *vals, const in
     }
 }
 
+// ------------------------------------------- stage 2 as a counting sort
+// When the keys' difference grids fit in shared memory, stage 2 sorts the
+// pairs by key without materialising them: every warp owns a contiguous
+// segment of the (view, depth)-ordered entries.
+//  - count: each warp adds every entry's bin rectangle to a 2-D difference
+//    grid of its view ((bins_y + 1) x (bins_x + 1) cells: +1 at two corners,
+//    -1 at the other two); prefix sums along rows and columns turn the grid
+//    into the warp's pair count per key.  The block's counts per key go to
+//    hist[key][block].
+//  - scan: per key, exclusive over blocks (scan_digit_rows_kernel); then
+//    over keys, giving each key's range, the total and the capacity check.
+//  - place: the warp counts again, turns counts into running positions (key
+//    base + earlier blocks + earlier warps of the block), and walks its
+//    entries' pairs in order, 32 per step, each at its key's running
+//    position (ranks within a step by __match_any_sync).
+// Every list then holds its pairs in the entries' depth order: the same
+// result as the stable key sort, bit for bit.
+constexpr int CS_WARPS = 16;
+constexpr int CS_THREADS = CS_WARPS * 32;
+constexpr int CS_MAX_CELLS = 2048;  // grid cells per warp: 16 x 2048 x 4 B = 128 KB of shared memory
+
+struct CsParams {
+    const uint32_t *svals;   // sorted (view, Gaussian) entries: view * n + g
+    const float2 *mean2d;
+    const int32_t *radius;
+    const float *depth;
+    int64_t NV, n;
+    int tx, ty, bin, bins_x, bins_y, bins, V;
+    int gx, cells;           // grid row length bins_x + 1; cells per warp V (bins_y + 1) (bins_x + 1)
+    int G;                   // blocks
+    uint32_t *hist;          // [V * bins][G] block counts, then per key [V * bins] bases
+    const int64_t *n_eff;
+    uint32_t *vals;
+    uint64_t *keys;          // optional
+};
+
+__device__ __forceinline__ void cs_segment(int64_t NV, int G, int &gw, int64_t &beg, int64_t &end)
+{
+    gw = blockIdx.x * CS_WARPS + (threadIdx.x >> 5);
+    const int64_t nw = (int64_t)G * CS_WARPS;
+    const int64_t per = (NV + nw - 1) / nw;
+    beg = min(NV, (int64_t)gw * per);
+    end = min(NV, beg + per);
+}
+
+__device__ __forceinline__ void cs_rect(const CsParams &p, uint32_t sv, int &x0, int &y0, int &x1, int &y1)
+{
+    x0 = y0 = x1 = y1 = 0;
+    const int r = p.radius[sv];
+    if (r > 0) {
+        const float2 m = p.mean2d[sv];
+        bin_rect(m.x, m.y, r, p.tx, p.ty, p.bin, x0, y0, x1, y1);
+    }
+}
+
+// This warp's pair counts per key, in its grid row of s (int32 cells, the
+// per-view grids of (bins_y + 1) x (bins_x + 1) cells one after another).
+__device__ __forceinline__ void cs_warp_counts(const CsParams &p, int *s, int64_t beg, int64_t end)
+{
+    const int lane = threadIdx.x & 31;
+    int *g = s + (threadIdx.x >> 5) * p.cells;
+    for (int c = lane; c < p.cells; c += 32) g[c] = 0;
+    __syncwarp();
+    for (int64_t i = beg + lane; i < end; i += 32) {
+        const uint32_t sv = p.svals[i];
+        int x0, y0, x1, y1;
+        cs_rect(p, sv, x0, y0, x1, y1);
+        if (x1 > x0) {
+            int *v = g + (int)(sv / (uint32_t)p.n) * (p.bins_y + 1) * p.gx;
+            atomicAdd(v + y0 * p.gx + x0, 1);
+            atomicAdd(v + y0 * p.gx + x1, -1);
+            atomicAdd(v + y1 * p.gx + x0, -1);
+            atomicAdd(v + y1 * p.gx + x1, 1);
+        }
+    }
+    __syncwarp();
+    // prefix sums along the rows, then down the columns, of every view's grid
+    const int rows = p.V * (p.bins_y + 1);
+    for (int r = lane; r < rows; r += 32) {
+        int run = 0;
+        int *row = g + r * p.gx;
+        for (int x = 0; x < p.gx; ++x) row[x] = (run += row[x]);
+    }
+    __syncwarp();
+    for (int c = lane; c < p.V * p.gx; c += 32) {
+        int *col = g + (c / p.gx) * (p.bins_y + 1) * p.gx + c % p.gx;
+        int run = 0;
+        for (int y = 0; y <= p.bins_y; ++y) col[y * p.gx] = (run += col[y * p.gx]);
+    }
+    __syncwarp();
+}
+
+// Grid cell of key (view, bin): the prefix sums leave the count of bin (x, y)
+// of view v at cell v (bins_y + 1) gx + y gx + x.
+__device__ __forceinline__ int cs_cell(const CsParams &p, int key)
+{
+    const int v = key / p.bins, b = key - v * p.bins;
+    const int y = b / p.bins_x, x = b - y * p.bins_x;
+    return (v * (p.bins_y + 1) + y) * p.gx + x;
+}
+
+__global__ void __launch_bounds__(CS_THREADS) cs_count_kernel(CsParams p)
+{
+    extern __shared__ int s_grid[];  // [CS_WARPS][cells]
+    int gw;
+    int64_t beg, end;
+    cs_segment(p.NV, p.G, gw, beg, end);
+    cs_warp_counts(p, s_grid, beg, end);
+    __syncthreads();
+    const int nkeys = p.V * p.bins;
+    for (int key = threadIdx.x; key < nkeys; key += CS_THREADS) {
+        const int c = cs_cell(p, key);
+        uint32_t sum = 0;
+#pragma unroll 4
+        for (int w = 0; w < CS_WARPS; ++w) sum += (uint32_t)s_grid[w * p.cells + c];
+        p.hist[(int64_t)key * p.G + blockIdx.x] = sum;
+    }
+}
+
+// Bases of the keys (exclusive scan of the totals hist[nkeys * G + key], in
+// place), the ranges of the non-empty keys, the total and the capacity check.
+__global__ void __launch_bounds__(SCAN_THREADS) cs_keys_kernel(uint32_t *hist, int nkeys, int G,
+                                                               int64_t capacity, int64_t *d_count,
+                                                               int64_t *n_eff, int32_t *d_err,
+                                                               uint32_t *ranges)
+{
+    __shared__ int64_t s_warp[32];
+    uint32_t *tot = hist + (int64_t)nkeys * G;
+    const int per = (nkeys + SCAN_THREADS - 1) / SCAN_THREADS;
+    const int beg = threadIdx.x * per, end = min(nkeys, beg + per);
+    int64_t sum = 0;
+    for (int k = beg; k < end; ++k) sum += tot[k];
+    int64_t total;
+    int64_t run = block_scan_i64(sum, s_warp, total);
+    const bool fits = total <= capacity;
+    for (int k = beg; k < end; ++k) {
+        const uint32_t c = tot[k];
+        if (fits && c > 0) {
+            ranges[2 * (int64_t)k] = (uint32_t)run;
+            ranges[2 * (int64_t)k + 1] = (uint32_t)(run + c);
+        }
+        tot[k] = (uint32_t)run;
+        run += c;
+    }
+    if (threadIdx.x == 0) {
+        *d_count = total;
+        *n_eff = fits ? total : 0;
+        if (!fits && d_err) atomicCAS(d_err, 0, (int32_t)GS_ERR_CAPACITY);
+    }
+}
+
+__global__ void __launch_bounds__(CS_THREADS) cs_place_kernel(CsParams p)
+{
+    extern __shared__ int s_grid[];  // [CS_WARPS][cells]: counts, then running positions
+    if (*p.n_eff == 0) return;       // nothing to place, or over capacity
+    int gw;
+    int64_t beg, end;
+    cs_segment(p.NV, p.G, gw, beg, end);
+    cs_warp_counts(p, s_grid, beg, end);
+    __syncthreads();
+    const int nkeys = p.V * p.bins;
+    const uint32_t *base = p.hist + (int64_t)nkeys * p.G;
+    for (int key = threadIdx.x; key < nkeys; key += CS_THREADS) {
+        const int c = cs_cell(p, key);
+        uint32_t run = base[key] + p.hist[(int64_t)key * p.G + blockIdx.x];
+        for (int w = 0; w < CS_WARPS; ++w) {
+            const uint32_t k = (uint32_t)s_grid[w * p.cells + c];
+            s_grid[w * p.cells + c] = (int)run;
+            run += k;
+        }
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    int *g = s_grid + (threadIdx.x >> 5) * p.cells;
+    for (int64_t e0 = beg; e0 < end; e0 += 32) {
+        const int64_t i = e0 + lane;
+        const uint32_t sv = i < end ? p.svals[i] : 0u;
+        int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
+        if (i < end) cs_rect(p, sv, x0, y0, x1, y1);
+        const int w = x1 - x0, cnt = w * (y1 - y0);
+        int inc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const int off = inc - cnt;
+        const int total = __shfl_sync(0xffffffffu, inc, 31);
+        const uint32_t view = sv / (uint32_t)p.n;
+        const int cbase = (int)view * (p.bins_y + 1) * p.gx;
+        for (int s0 = 0; s0 < total; s0 += 32) {
+            const int o = s0 + lane;
+            // the entry of pair slot o: the last lane whose offset is <= o
+            int src = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int cand = src + step;
+                if (__shfl_sync(0xffffffffu, off, cand) <= o) src = cand;
+            }
+            const int so = __shfl_sync(0xffffffffu, off, src);
+            const int sw = __shfl_sync(0xffffffffu, w, src);
+            const int sx = __shfl_sync(0xffffffffu, x0, src);
+            const int sy = __shfl_sync(0xffffffffu, y0, src);
+            const int sc = __shfl_sync(0xffffffffu, cbase, src);
+            const uint32_t ssv = __shfl_sync(0xffffffffu, sv, src);
+            const bool valid = o < total;
+            int cell = -1;
+            if (valid) {
+                const int local = o - so;
+                const int dy = local / sw;
+                cell = sc + (sy + dy) * p.gx + sx + (local - dy * sw);
+            }
+            const unsigned peers = __match_any_sync(0xffffffffu, cell);
+            uint32_t pos = 0;
+            if (valid) pos = (uint32_t)g[cell] + __popc(peers & lt);
+            __syncwarp();
+            if (valid && lane == __ffs(peers) - 1) g[cell] += __popc(peers);
+            __syncwarp();
+            if (valid) {
+                const uint32_t v = ssv / (uint32_t)p.n;
+                p.vals[pos] = ssv - v * (uint32_t)p.n;
+                if (p.keys) {
+                    const int local = o - so, dy = local / sw;
+                    const uint32_t key = v * (uint32_t)p.bins + (uint32_t)((sy + dy) * p.bins_x + sx + local - dy * sw);
+                    p.keys[pos] = ((uint64_t)key << 32) | __float_as_uint(p.depth[ssv]);
+                }
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------- workspace
 struct BinWs {
     uint32_t *dk[2], *dv[2];
@@ -446,7 +679,10 @@ static BinWs carve(void *base, int64_t NV, int64_t cap)
     w.offsets = reinterpret_cast<int64_t *>(take(8 * (NV + 1)));
     w.cnt = reinterpret_cast<int32_t *>(take(4 * NV));
     w.bsum = reinterpret_cast<int64_t *>(take(8 * (ceil_div(NV, SCAN_TILE) + 1)));
-    w.hist = reinterpret_cast<uint32_t *>(take(4 * (RADIX * SORT_BLOCKS_MAX + RADIX)));
+    // the radix passes' digit counts, or the counting sort's key counts
+    const size_t hist_words = std::max<size_t>((size_t)RADIX * SORT_BLOCKS_MAX + RADIX,
+                                               (size_t)CS_MAX_CELLS * (kMaxSMs + 1));
+    w.hist = reinterpret_cast<uint32_t *>(take(4 * hist_words));
     w.n_eff = reinterpret_cast<int64_t *>(take(64));
     for (int k = 0; k < 2; ++k) w.tk[k] = reinterpret_cast<uint32_t *>(take(4 * cap));
     w.tv = reinterpret_cast<uint32_t *>(take(4 * cap));
@@ -460,7 +696,7 @@ static gs_status run_pass(SortPass s, int64_t grid_items_hint, cudaStream_t st)
     note_launch();
     radix_hist_kernel<<<s.G, SORT_THREADS, 0, st>>>(s);
     note_launch();
-    scan_digit_rows_kernel<<<RADIX, SORT_THREADS, 0, st>>>(s.hist, s.G);
+    scan_digit_rows_kernel<<<RADIX, SORT_THREADS, 0, st>>>(s.hist, s.G, RADIX);
     note_launch();
     radix_scatter_kernel<<<s.G, SORT_THREADS, 0, st>>>(s);
     return launch_status("radix pass");
@@ -512,7 +748,10 @@ extern "C" gs_status gs_bin_sort(const gs_projected *proj, int64_t n, int V, int
                                                               w.dk[0], w.dv[0]);
     int cur = 0;
     int Gd = (int)std::min<int64_t>(sort_blocks(), ceil_div(NV, SORT_TILE));
-    for (int pass = 0; pass < 4 + (V > 1 ? 1 : 0); ++pass) {
+    // depth order only: stage 2 sorts stably on a key that holds the view,
+    // so each (view, bin) list needs its view's entries in (depth, index)
+    // order, not the views grouped
+    for (int pass = 0; pass < 4; ++pass) {
         SortPass s{};
         s.kin = w.dk[cur];
         s.vin = w.dv[cur];
@@ -520,8 +759,7 @@ extern "C" gs_status gs_bin_sort(const gs_projected *proj, int64_t n, int V, int
         s.vout = w.dv[cur ^ 1];
         s.d_n = nullptr;
         s.n_host = NV;
-        s.shift = pass < 4 ? 8 * pass : 0;
-        s.div = pass < 4 ? 0u : (uint32_t)n;
+        s.shift = 8 * pass;
         s.hist = w.hist;
         s.G = Gd;
         gs_status e = run_pass(s, NV, st);
@@ -529,7 +767,46 @@ extern "C" gs_status gs_bin_sort(const gs_projected *proj, int64_t n, int V, int
         cur ^= 1;
     }
     const uint32_t *svals = w.dv[cur];
-    // ---- offsets of every entry's pairs in that order
+    // ---- stage 2 as a counting sort when the keys' grids fit in shared memory
+    const int bins_y = bins_y_of(H, bin), gx = bins_x + 1;
+    const int cells = V * (bins_y + 1) * gx;
+    if (cells <= CS_MAX_CELLS) {
+        CsParams cp{};
+        cp.svals = svals;
+        cp.mean2d = reinterpret_cast<const float2 *>(proj->mean2d);
+        cp.radius = proj->radius;
+        cp.depth = proj->depth;
+        cp.NV = NV;
+        cp.n = n;
+        cp.tx = tx;
+        cp.ty = ty;
+        cp.bin = bin;
+        cp.bins_x = bins_x;
+        cp.bins_y = bins_y;
+        cp.bins = bins;
+        cp.V = V;
+        cp.gx = gx;
+        cp.cells = cells;
+        cp.G = num_sms();
+        cp.hist = w.hist;
+        cp.n_eff = w.n_eff;
+        cp.vals = vals;
+        cp.keys = reinterpret_cast<uint64_t *>(keys);
+        const int smem = CS_WARPS * cells * (int)sizeof(int);
+        set_smem_limit((const void *)cs_count_kernel, smem, st);
+        set_smem_limit((const void *)cs_place_kernel, smem, st);
+        note_launch();
+        cs_count_kernel<<<cp.G, CS_THREADS, smem, st>>>(cp);
+        note_launch();
+        scan_digit_rows_kernel<<<(int)nkeys, SORT_THREADS, 0, st>>>(w.hist, cp.G, (int)nkeys);
+        note_launch();
+        cs_keys_kernel<<<1, SCAN_THREADS, 0, st>>>(w.hist, (int)nkeys, cp.G, capacity, d_count, w.n_eff,
+                                                   d_err, ranges);
+        note_launch();
+        cs_place_kernel<<<cp.G, CS_THREADS, smem, st>>>(cp);
+        return launch_status("gs_bin_sort");
+    }
+    // ---- otherwise: offsets of every entry's pairs in that order
     int nb = (int)ceil_div(NV, SCAN_TILE);
     note_launch();
     sorted_counts_kernel<<<(int)ceil_div(NV, 256), 256, 0, st>>>(
@@ -574,7 +851,6 @@ extern "C" gs_status gs_bin_sort(const gs_projected *proj, int64_t n, int V, int
         s.d_n = w.n_eff;
         s.n_host = 0;
         s.shift = 8 * pass;
-        s.div = 0;
         s.hist = w.hist;
         s.G = sort_blocks();
         e = run_pass(s, 0, st);

@@ -363,8 +363,12 @@ __device__ __forceinline__ float adam_rate(const gs_adam &hp, int t)
     return hp.lr * exp2f(f * log2f(hp.lr_final_ratio));
 }
 
-// Four parameters per thread and step (16-byte loads, all issued before any
-// store), then a scalar tail; the arithmetic per parameter is adam_one's.
+// Sixteen parameters per thread: four float4 groups, strided by the block
+// size so that every load is coalesced, all loaded before any is stored (16
+// loads in flight per thread); block 0 also takes the scalar tail.  The
+// arithmetic per parameter is adam_one's.
+constexpr int ADAM_GROUPS = 4;
+
 template <int SHADOW>
 __global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ p, float *__restrict__ g,
                                                    float *__restrict__ m, float *__restrict__ v,
@@ -379,33 +383,47 @@ __global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ p, float 
     const float bc2 = -expm1f((float)t * logf(hp.beta2));
     const float inv = 1.f / st->loss_scale;
     const float lr = adam_rate(hp, st->step);
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t n4 = n / 4;
     float4 *p4 = reinterpret_cast<float4 *>(p), *g4 = reinterpret_cast<float4 *>(g);
     float4 *m4 = reinterpret_cast<float4 *>(m), *v4 = reinterpret_cast<float4 *>(v);
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += stride) {
-        float4 gq = g4[q], mq = m4[q], vq = v4[q], pq = p4[q];
+    const int64_t q0 = (int64_t)blockIdx.x * blockDim.x * ADAM_GROUPS + threadIdx.x;
+    float4 gq[ADAM_GROUPS], mq[ADAM_GROUPS], vq[ADAM_GROUPS], pq[ADAM_GROUPS];
+#pragma unroll
+    for (int k = 0; k < ADAM_GROUPS; ++k) {
+        const int64_t q = q0 + (int64_t)k * blockDim.x;
+        if (q < n4) {
+            gq[k] = g4[q];
+            mq[k] = m4[q];
+            vq[k] = v4[q];
+            pq[k] = p4[q];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < ADAM_GROUPS; ++k) {
+        const int64_t q = q0 + (int64_t)k * blockDim.x;
+        if (q >= n4) continue;
         g4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (skip) continue;
-        adam_one<SHADOW>(pq.x, gq.x, mq.x, vq.x, hp, lr, bc1, bc2, inv);
-        adam_one<SHADOW>(pq.y, gq.y, mq.y, vq.y, hp, lr, bc1, bc2, inv);
-        adam_one<SHADOW>(pq.z, gq.z, mq.z, vq.z, hp, lr, bc1, bc2, inv);
-        adam_one<SHADOW>(pq.w, gq.w, mq.w, vq.w, hp, lr, bc1, bc2, inv);
-        m4[q] = mq;
-        v4[q] = vq;
-        p4[q] = pq;
+        adam_one<SHADOW>(pq[k].x, gq[k].x, mq[k].x, vq[k].x, hp, lr, bc1, bc2, inv);
+        adam_one<SHADOW>(pq[k].y, gq[k].y, mq[k].y, vq[k].y, hp, lr, bc1, bc2, inv);
+        adam_one<SHADOW>(pq[k].z, gq[k].z, mq[k].z, vq[k].z, hp, lr, bc1, bc2, inv);
+        adam_one<SHADOW>(pq[k].w, gq[k].w, mq[k].w, vq[k].w, hp, lr, bc1, bc2, inv);
+        m4[q] = mq[k];
+        v4[q] = vq[k];
+        p4[q] = pq[k];
         if (SHADOW == GS_F16) {
             __half2 *h = reinterpret_cast<__half2 *>(shadow) + 2 * q;
-            h[0] = __floats2half2_rn(pq.x, pq.y);
-            h[1] = __floats2half2_rn(pq.z, pq.w);
+            h[0] = __floats2half2_rn(pq[k].x, pq[k].y);
+            h[1] = __floats2half2_rn(pq[k].z, pq[k].w);
         }
         if (SHADOW == GS_BF16) {
             __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(shadow) + 2 * q;
-            h[0] = __floats2bfloat162_rn(pq.x, pq.y);
-            h[1] = __floats2bfloat162_rn(pq.z, pq.w);
+            h[0] = __floats2bfloat162_rn(pq[k].x, pq[k].y);
+            h[1] = __floats2bfloat162_rn(pq[k].z, pq[k].w);
         }
     }
-    for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    if (blockIdx.x != 0) return;
+    for (int64_t i = 4 * n4 + threadIdx.x; i < n; i += blockDim.x) {
         float gi = g[i], mi = m[i], vi = v[i], pi = p[i];
         g[i] = 0.f;
         if (skip) continue;
@@ -612,8 +630,7 @@ extern "C" gs_status adam_step(float *p, float *g, float *m, float *v, int64_t n
     GS_REQUIRE(aligned(p, 16) && aligned(g, 16) && aligned(m, 16) && aligned(v, 16) &&
                    (shadow == nullptr || aligned(shadow, 8)),
                "adam_step: arrays must be 16-byte aligned (shadow 8)");
-    int blocks = (int)std::min<int64_t>(ceil_div(n, 4 * 256), num_sms() * 8);
-    blocks = std::max(blocks, 1);
+    const int blocks = (int)std::max<int64_t>(ceil_div(n / 4, 256 * ADAM_GROUPS), 1);
     cudaStream_t s = as_stream(stream);
     note_launch();
     if (!shadow)

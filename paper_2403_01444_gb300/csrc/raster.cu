@@ -268,19 +268,27 @@ __global__ void __launch_bounds__(NT) raster_fwd2_kernel(RasterParams p)
             const bool t1 = !done[1] && pw.y <= 0.f && pw.y >= xyp.z;
             if (STATS) n_tested += !done[0] + !done[1];
             if (!(t0 || t1)) continue;
-            // both pixels in packed FP32; a pixel that does not take part, or
-            // whose transmittance would fall below the cutoff, adds nothing
-            const float g0 = t0 ? pair_gauss(pw.x) : 0.f, g1 = t1 ? pair_gauss(pw.y) : 0.f;
+            // a pixel that does not take part has its power masked to -inf:
+            // G = 0, alpha = 0 and its transmittance stays as it is (T * 1)
+            const float g0 = pair_gauss(t0 ? pw.x : -INFINITY), g1 = pair_gauss(t1 ? pw.y : -INFINITY);
             const float2 araw = __fmul2_rn(make_float2(cj.w, cj.w), make_float2(g0, g1));
-            const float2 alpha = make_float2(fminf(kAlphaCap, araw.x), fminf(kAlphaCap, araw.y));
+            float2 alpha = make_float2(fminf(kAlphaCap, araw.x), fminf(kAlphaCap, araw.y));
             const float2 om = __ffma2_rn(alpha, make_float2(-1.f, -1.f), make_float2(1.f, 1.f));
-            const float2 tT = __fmul2_rn(make_float2(T[0], T[1]), om);
-            const bool stop0 = t0 && tT.x < kTEps, stop1 = t1 && tT.y < kTEps;
-            const bool add0 = t0 && !stop0, add1 = t1 && !stop1;
-            done[0] |= stop0;
-            done[1] |= stop1;
-            const float2 w = __fmul2_rn(make_float2(add0 ? alpha.x : 0.f, add1 ? alpha.y : 0.f),
-                                        make_float2(T[0], T[1]));
+            const float2 Tv = make_float2(T[0], T[1]);
+            float2 tT = __fmul2_rn(Tv, om);
+            bool add0 = t0, add1 = t1;
+            if (tT.x < kTEps || tT.y < kTEps) {
+                // the pixel stops before this Gaussian (T stays >= 1e-4 otherwise,
+                // so only a pixel that takes part can get here)
+                const bool stop0 = tT.x < kTEps, stop1 = tT.y < kTEps;
+                done[0] |= stop0;
+                done[1] |= stop1;
+                add0 = add0 && !stop0;
+                add1 = add1 && !stop1;
+                if (stop0) { alpha.x = 0.f; tT.x = Tv.x; }
+                if (stop1) { alpha.y = 0.f; tT.y = Tv.y; }
+            }
+            const float2 w = __fmul2_rn(alpha, Tv);
             const float4 ck = s_rgbk[j];
             const float2 c0 = __ffma2_rn(make_float2(ck.x, ck.x), w, make_float2(C0[0], C0[1]));
             const float2 c1 = __ffma2_rn(make_float2(ck.y, ck.y), w, make_float2(C1[0], C1[1]));
@@ -288,9 +296,11 @@ __global__ void __launch_bounds__(NT) raster_fwd2_kernel(RasterParams p)
             C0[0] = c0.x; C0[1] = c0.y;
             C1[0] = c1.x; C1[1] = c1.y;
             C2[0] = c2.x; C2[1] = c2.y;
+            T[0] = tT.x;
+            T[1] = tT.y;
             const int kk = __float_as_int(ck.w) + 1;
-            if (add0) { T[0] = tT.x; last[0] = kk; }
-            if (add1) { T[1] = tT.y; last[1] = kk; }
+            last[0] = add0 ? kk : last[0];
+            last[1] = add1 ? kk : last[1];
             if (STATS) n_contrib += add0 + add1;
         }
     }
@@ -374,14 +384,15 @@ __device__ __forceinline__ float rcp_approx(float x)
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
-template <bool WANT_OP>
-__device__ __forceinline__ int unblend_pair(PixBwd2 &P, int pos, float4 co, float4 c, float2 pw, float pmin,
+template <bool WANT_OP, bool STATS>
+__device__ __forceinline__ bool unblend_pair(PixBwd2 &P, int pos, float4 co, float4 c, float2 pw, float pmin,
                                              float dx, float2 dy, float dxx, float2 dxy, float2 dyy,
-                                             float *v)
+                                             float *v, uint32_t &n_contrib)
 {
     const bool in0 = pos < P.last0 && pw.x <= 0.f && pw.x >= pmin;
     const bool in1 = pos < P.last1 && pw.y <= 0.f && pw.y >= pmin;
-    if (!(in0 || in1)) return 0;
+    if (!(in0 || in1)) return false;
+    if (STATS) n_contrib += (uint32_t)in0 + (uint32_t)in1;
     const float g0 = in0 ? pair_gauss(pw.x) : 0.f, g1 = in1 ? pair_gauss(pw.y) : 0.f;
     const float2 araw = __fmul2_rn(f2(co.w), make_float2(g0, g1));
     const float2 alpha = make_float2(fminf(kAlphaCap, araw.x), fminf(kAlphaCap, araw.y));
@@ -414,7 +425,7 @@ __device__ __forceinline__ int unblend_pair(PixBwd2 &P, int pos, float4 co, floa
         const float2 op = __fmul2_rn(dalpha, gm);
         v[8] = op.x + op.y;
     }
-    return (int)in0 + (int)in1;
+    return true;
 }
 
 template <bool WANT_OP, bool BINNED, bool STATS>
@@ -513,10 +524,8 @@ __global__ void __launch_bounds__(NT) raster_bwd2_kernel(RasterParams p)
                     float2 dy, dxy, dyy;
                     const float2 pw = pair_power2(make_float2(xyp.x, xyp.y), cc, pxf, pyf, dx, dy, dxx, dxy, dyy);
                     if (STATS) n_tested += (pos < P.last0) + (pos < P.last1);
-                    const int taking = unblend_pair<WANT_OP>(P, pos, cc, c, pw, xyp.z, dx, dy, dxx, dxy,
-                                                             dyy, v);
-                    if (STATS) n_contrib += taking;
-                    contrib = taking > 0;
+                    contrib = unblend_pair<WANT_OP, STATS>(P, pos, cc, c, pw, xyp.z, dx, dy, dxx, dxy,
+                                                           dyy, v, n_contrib);
                 }
                 if (!contrib) {
 #pragma unroll

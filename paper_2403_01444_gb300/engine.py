@@ -20,12 +20,13 @@ LAMBDA_DSSIM = 0.2          # Eq. 6
 NTC_LR = 0.002              # Suppl. A
 ITERS_PER_FRAME = 150       # Stage-1 iterations per frame (Section 5.2)
 ADAM_BETAS = (0.9, 0.99)    # I-NGP's Adam constants (the paper's NTC follows I-NGP)
-# Stage 1: the rate decays exponentially to 1 % over a frame's iterations (the
-# shape of 3DG-S's schedule for Gaussian means, whose other hyper-parameters
-# the paper keeps), and epsilon is set against the unscaled gradients of a
-# loss averaged over V x 3 x H x W pixel channels (table gradients of order
-# 1e-9 .. 1e-6): entries touched only by Gaussians that no view sees get no
-# full-rate steps.  The warm-up keeps I-NGP's epsilon and a constant rate.
+# Stage 1: the rate decays exponentially to 1 % over a frame's iterations
+# (an exponential decay as in 3DG-S's schedule for Gaussian means, whose
+# other hyper-parameters the paper keeps), and epsilon is set against the
+# unscaled gradients of a loss averaged over V x 3 x H x W pixel channels
+# (table gradients of order 1e-9 .. 1e-6): entries touched only by Gaussians
+# that no view sees get no full-rate steps.  The warm-up keeps I-NGP's
+# epsilon and a constant rate.
 STAGE1_LR_FINAL = 0.01
 STAGE1_EPS = 1e-6
 WARMUP_EPS = 1e-15
