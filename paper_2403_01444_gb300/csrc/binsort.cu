@@ -422,23 +422,40 @@ __global__ void keys64_kernel(const uint32_t *tk, const uint32_t *vals, const in
 // ------------------------------------------- stage 2 as a counting sort
 // When the keys' difference grids fit in shared memory, stage 2 sorts the
 // pairs by key without materialising them: every warp owns a contiguous
-// segment of the (view, depth)-ordered entries.
+// segment of the depth-ordered entries.
 //  - count: each warp adds every entry's bin rectangle to a 2-D difference
 //    grid of its view ((bins_y + 1) x (bins_x + 1) cells: +1 at two corners,
 //    -1 at the other two); prefix sums along rows and columns turn the grid
-//    into the warp's pair count per key.  The block's counts per key go to
-//    hist[key][block].
-//  - scan: per key, exclusive over blocks (scan_digit_rows_kernel); then
-//    over keys, giving each key's range, the total and the capacity check.
-//  - place: the warp counts again, turns counts into running positions (key
-//    base + earlier blocks + earlier warps of the block), and walks its
-//    entries' pairs in order, 32 per step, each at its key's running
-//    position (ranks within a step by __match_any_sync).
+//    into the warp's pair count per key, written to wcnt[warp][key]; the
+//    block's counts per key go to hist[key][block].
+//  - scan: per key, exclusive over the blocks (scan_digit_rows_kernel), then
+//    over the keys, giving each (block, key) its first position and each key
+//    its range, the total and the capacity check.
+//  - place: each block turns its warps' counts into running positions (key
+//    base + earlier blocks + earlier warps of the block), and each warp walks
+//    its entries' pairs in order, 32 per step, each placed at its key's
+//    running position (ranks within a step by __match_any_sync).
 // Every list then holds its pairs in the entries' depth order: the same
 // result as the stable key sort, bit for bit.
 constexpr int CS_WARPS = 16;
 constexpr int CS_THREADS = CS_WARPS * 32;
-constexpr int CS_MAX_CELLS = 2048;  // grid cells per warp: 16 x 2048 x 4 B = 128 KB of shared memory
+constexpr int CS_MAX_CELLS = 2048;       // grid cells per warp: 16 x 2048 x 4 B = 128 KB of shared memory
+constexpr int CS_MIN_ENTRIES = 256;      // entries per warp at least (bounds the count table)
+constexpr int CS_BLOCKS_PER_SM = 2;
+
+// Warps of the counting sort for NV entries on this device (a multiple of
+// CS_WARPS), and the bound of the count table's rows used to size the
+// workspace without a device.
+inline int64_t cs_warps(int64_t NV, int sms)
+{
+    const int64_t want = std::max<int64_t>(1, ceil_div(NV, CS_MIN_ENTRIES));
+    const int64_t cap = (int64_t)sms * CS_BLOCKS_PER_SM * CS_WARPS;
+    return ceil_div(std::min(want, cap), CS_WARPS) * CS_WARPS;
+}
+inline int64_t cs_warps_bound(int64_t NV)
+{
+    return ceil_div(std::max<int64_t>(1, ceil_div(NV, CS_MIN_ENTRIES)), CS_WARPS) * CS_WARPS;
+}
 
 struct CsParams {
     const uint32_t *svals;   // sorted (view, Gaussian) entries: view * n + g
@@ -448,20 +465,21 @@ struct CsParams {
     int64_t NV, n;
     int tx, ty, bin, bins_x, bins_y, bins, V;
     int gx, cells;           // grid row length bins_x + 1; cells per warp V (bins_y + 1) (bins_x + 1)
-    int G;                   // blocks
-    uint32_t *hist;          // [V * bins][G] block counts, then per key [V * bins] bases
+    int nkeys;               // V * bins
+    int64_t NW;              // warps, G = NW / CS_WARPS blocks
+    uint32_t *hist;          // [nkeys][G] block counts -> prefixes, then per key [nkeys] totals -> bases
+    uint32_t *wcnt;          // [NW][nkeys] warp counts
     const int64_t *n_eff;
     uint32_t *vals;
     uint64_t *keys;          // optional
 };
 
-__device__ __forceinline__ void cs_segment(int64_t NV, int G, int &gw, int64_t &beg, int64_t &end)
+__device__ __forceinline__ void cs_segment(const CsParams &p, int64_t &gw, int64_t &beg, int64_t &end)
 {
-    gw = blockIdx.x * CS_WARPS + (threadIdx.x >> 5);
-    const int64_t nw = (int64_t)G * CS_WARPS;
-    const int64_t per = (NV + nw - 1) / nw;
-    beg = min(NV, (int64_t)gw * per);
-    end = min(NV, beg + per);
+    gw = (int64_t)blockIdx.x * CS_WARPS + (threadIdx.x >> 5);
+    const int64_t per = (p.NV + p.NW - 1) / p.NW;
+    beg = min(p.NV, gw * per);
+    end = min(p.NV, beg + per);
 }
 
 __device__ __forceinline__ void cs_rect(const CsParams &p, uint32_t sv, int &x0, int &y0, int &x1, int &y1)
@@ -474,12 +492,22 @@ __device__ __forceinline__ void cs_rect(const CsParams &p, uint32_t sv, int &x0,
     }
 }
 
-// This warp's pair counts per key, in its grid row of s (int32 cells, the
-// per-view grids of (bins_y + 1) x (bins_x + 1) cells one after another).
-__device__ __forceinline__ void cs_warp_counts(const CsParams &p, int *s, int64_t beg, int64_t end)
+// Grid cell of key (view, bin): the prefix sums leave the count of bin (x, y)
+// of view v at cell v (bins_y + 1) gx + y gx + x.
+__device__ __forceinline__ int cs_cell(const CsParams &p, int key)
 {
+    const int v = key / p.bins, b = key - v * p.bins;
+    const int y = b / p.bins_x, x = b - y * p.bins_x;
+    return (v * (p.bins_y + 1) + y) * p.gx + x;
+}
+
+__global__ void __launch_bounds__(CS_THREADS) cs_count_kernel(CsParams p)
+{
+    extern __shared__ int s_grid[];  // [CS_WARPS][cells]
+    int64_t gw, beg, end;
+    cs_segment(p, gw, beg, end);
     const int lane = threadIdx.x & 31;
-    int *g = s + (threadIdx.x >> 5) * p.cells;
+    int *g = s_grid + (threadIdx.x >> 5) * p.cells;
     for (int c = lane; c < p.cells; c += 32) g[c] = 0;
     __syncwarp();
     for (int64_t i = beg + lane; i < end; i += 32) {
@@ -509,44 +537,26 @@ __device__ __forceinline__ void cs_warp_counts(const CsParams &p, int *s, int64_
         for (int y = 0; y <= p.bins_y; ++y) col[y * p.gx] = (run += col[y * p.gx]);
     }
     __syncwarp();
-}
-
-// Grid cell of key (view, bin): the prefix sums leave the count of bin (x, y)
-// of view v at cell v (bins_y + 1) gx + y gx + x.
-__device__ __forceinline__ int cs_cell(const CsParams &p, int key)
-{
-    const int v = key / p.bins, b = key - v * p.bins;
-    const int y = b / p.bins_x, x = b - y * p.bins_x;
-    return (v * (p.bins_y + 1) + y) * p.gx + x;
-}
-
-__global__ void __launch_bounds__(CS_THREADS) cs_count_kernel(CsParams p)
-{
-    extern __shared__ int s_grid[];  // [CS_WARPS][cells]
-    int gw;
-    int64_t beg, end;
-    cs_segment(p.NV, p.G, gw, beg, end);
-    cs_warp_counts(p, s_grid, beg, end);
+    uint32_t *row = p.wcnt + gw * p.nkeys;
+    for (int key = lane; key < p.nkeys; key += 32) row[key] = (uint32_t)g[cs_cell(p, key)];
     __syncthreads();
-    const int nkeys = p.V * p.bins;
-    for (int key = threadIdx.x; key < nkeys; key += CS_THREADS) {
+    const int G = (int)(p.NW / CS_WARPS);
+    for (int key = threadIdx.x; key < p.nkeys; key += CS_THREADS) {
         const int c = cs_cell(p, key);
         uint32_t sum = 0;
 #pragma unroll 4
         for (int w = 0; w < CS_WARPS; ++w) sum += (uint32_t)s_grid[w * p.cells + c];
-        p.hist[(int64_t)key * p.G + blockIdx.x] = sum;
+        p.hist[(int64_t)key * G + blockIdx.x] = sum;
     }
 }
 
 // Bases of the keys (exclusive scan of the totals hist[nkeys * G + key], in
 // place), the ranges of the non-empty keys, the total and the capacity check.
-__global__ void __launch_bounds__(SCAN_THREADS) cs_keys_kernel(uint32_t *hist, int nkeys, int G,
-                                                               int64_t capacity, int64_t *d_count,
-                                                               int64_t *n_eff, int32_t *d_err,
-                                                               uint32_t *ranges)
+__global__ void __launch_bounds__(SCAN_THREADS) cs_keys_kernel(uint32_t *tot, int nkeys, int64_t capacity,
+                                                               int64_t *d_count, int64_t *n_eff,
+                                                               int32_t *d_err, uint32_t *ranges)
 {
     __shared__ int64_t s_warp[32];
-    uint32_t *tot = hist + (int64_t)nkeys * G;
     const int per = (nkeys + SCAN_THREADS - 1) / SCAN_THREADS;
     const int beg = threadIdx.x * per, end = min(nkeys, beg + per);
     int64_t sum = 0;
@@ -572,28 +582,28 @@ __global__ void __launch_bounds__(SCAN_THREADS) cs_keys_kernel(uint32_t *hist, i
 
 __global__ void __launch_bounds__(CS_THREADS) cs_place_kernel(CsParams p)
 {
-    extern __shared__ int s_grid[];  // [CS_WARPS][cells]: counts, then running positions
-    if (*p.n_eff == 0) return;       // nothing to place, or over capacity
-    int gw;
-    int64_t beg, end;
-    cs_segment(p.NV, p.G, gw, beg, end);
-    cs_warp_counts(p, s_grid, beg, end);
-    __syncthreads();
-    const int nkeys = p.V * p.bins;
-    const uint32_t *base = p.hist + (int64_t)nkeys * p.G;
-    for (int key = threadIdx.x; key < nkeys; key += CS_THREADS) {
-        const int c = cs_cell(p, key);
-        uint32_t run = base[key] + p.hist[(int64_t)key * p.G + blockIdx.x];
-        for (int w = 0; w < CS_WARPS; ++w) {
-            const uint32_t k = (uint32_t)s_grid[w * p.cells + c];
-            s_grid[w * p.cells + c] = (int)run;
-            run += k;
+    extern __shared__ uint32_t s_pos[];  // [CS_WARPS][nkeys]: running positions
+    if (*p.n_eff == 0) return;           // nothing to place, or over capacity
+    int64_t gw, beg, end;
+    cs_segment(p, gw, beg, end);
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t *g = s_pos + (threadIdx.x >> 5) * p.nkeys;
+    {
+        const int G = (int)(p.NW / CS_WARPS);
+        const uint32_t *base = p.hist + (int64_t)p.nkeys * G;
+        const uint32_t *wc = p.wcnt + (int64_t)blockIdx.x * CS_WARPS * p.nkeys;
+        for (int key = threadIdx.x; key < p.nkeys; key += CS_THREADS) {
+            uint32_t run = base[key] + p.hist[(int64_t)key * G + blockIdx.x];
+#pragma unroll 4
+            for (int w = 0; w < CS_WARPS; ++w) {
+                const uint32_t c = wc[(int64_t)w * p.nkeys + key];
+                s_pos[w * p.nkeys + key] = run;
+                run += c;
+            }
         }
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    int *g = s_grid + (threadIdx.x >> 5) * p.cells;
     for (int64_t e0 = beg; e0 < end; e0 += 32) {
         const int64_t i = e0 + lane;
         const uint32_t sv = i < end ? p.svals[i] : 0u;
@@ -609,7 +619,7 @@ __global__ void __launch_bounds__(CS_THREADS) cs_place_kernel(CsParams p)
         const int off = inc - cnt;
         const int total = __shfl_sync(0xffffffffu, inc, 31);
         const uint32_t view = sv / (uint32_t)p.n;
-        const int cbase = (int)view * (p.bins_y + 1) * p.gx;
+        const int kbase = (int)view * p.bins;
         for (int s0 = 0; s0 < total; s0 += 32) {
             const int o = s0 + lane;
             // the entry of pair slot o: the last lane whose offset is <= o
@@ -623,29 +633,25 @@ __global__ void __launch_bounds__(CS_THREADS) cs_place_kernel(CsParams p)
             const int sw = __shfl_sync(0xffffffffu, w, src);
             const int sx = __shfl_sync(0xffffffffu, x0, src);
             const int sy = __shfl_sync(0xffffffffu, y0, src);
-            const int sc = __shfl_sync(0xffffffffu, cbase, src);
+            const int sk = __shfl_sync(0xffffffffu, kbase, src);
             const uint32_t ssv = __shfl_sync(0xffffffffu, sv, src);
             const bool valid = o < total;
-            int cell = -1;
+            int key = -1;
             if (valid) {
                 const int local = o - so;
                 const int dy = local / sw;
-                cell = sc + (sy + dy) * p.gx + sx + (local - dy * sw);
+                key = sk + (sy + dy) * p.bins_x + sx + (local - dy * sw);
             }
-            const unsigned peers = __match_any_sync(0xffffffffu, cell);
+            const unsigned peers = __match_any_sync(0xffffffffu, key);
             uint32_t pos = 0;
-            if (valid) pos = (uint32_t)g[cell] + __popc(peers & lt);
+            if (valid) pos = g[key] + __popc(peers & lt);
             __syncwarp();
-            if (valid && lane == __ffs(peers) - 1) g[cell] += __popc(peers);
+            if (valid && lane == __ffs(peers) - 1) g[key] += __popc(peers);
             __syncwarp();
             if (valid) {
-                const uint32_t v = ssv / (uint32_t)p.n;
-                p.vals[pos] = ssv - v * (uint32_t)p.n;
-                if (p.keys) {
-                    const int local = o - so, dy = local / sw;
-                    const uint32_t key = v * (uint32_t)p.bins + (uint32_t)((sy + dy) * p.bins_x + sx + local - dy * sw);
-                    p.keys[pos] = ((uint64_t)key << 32) | __float_as_uint(p.depth[ssv]);
-                }
+                const uint32_t gi = ssv - (uint32_t)(sk / p.bins) * (uint32_t)p.n;
+                p.vals[pos] = gi;
+                if (p.keys) p.keys[pos] = ((uint64_t)(uint32_t)key << 32) | __float_as_uint(p.depth[ssv]);
             }
         }
     }
@@ -679,9 +685,11 @@ static BinWs carve(void *base, int64_t NV, int64_t cap)
     w.offsets = reinterpret_cast<int64_t *>(take(8 * (NV + 1)));
     w.cnt = reinterpret_cast<int32_t *>(take(4 * NV));
     w.bsum = reinterpret_cast<int64_t *>(take(8 * (ceil_div(NV, SCAN_TILE) + 1)));
-    // the radix passes' digit counts, or the counting sort's key counts
+    // the radix passes' digit counts, or the counting sort's per-block and
+    // per-warp key counts
+    const int64_t cw = cs_warps_bound(NV);
     const size_t hist_words = std::max<size_t>((size_t)RADIX * SORT_BLOCKS_MAX + RADIX,
-                                               (size_t)CS_MAX_CELLS * (kMaxSMs + 1));
+                                               (size_t)CS_MAX_CELLS * (cw / CS_WARPS + 1 + cw));
     w.hist = reinterpret_cast<uint32_t *>(take(4 * hist_words));
     w.n_eff = reinterpret_cast<int64_t *>(take(64));
     for (int k = 0; k < 2; ++k) w.tk[k] = reinterpret_cast<uint32_t *>(take(4 * cap));
@@ -787,23 +795,27 @@ extern "C" gs_status gs_bin_sort(const gs_projected *proj, int64_t n, int V, int
         cp.V = V;
         cp.gx = gx;
         cp.cells = cells;
-        cp.G = num_sms();
+        cp.nkeys = (int)nkeys;
+        cp.NW = cs_warps(NV, num_sms());
+        const int G = (int)(cp.NW / CS_WARPS);
         cp.hist = w.hist;
+        cp.wcnt = w.hist + (int64_t)nkeys * (G + 1);
         cp.n_eff = w.n_eff;
         cp.vals = vals;
-        cp.keys = reinterpret_cast<uint64_t *>(keys);
-        const int smem = CS_WARPS * cells * (int)sizeof(int);
-        set_smem_limit((const void *)cs_count_kernel, smem, st);
-        set_smem_limit((const void *)cs_place_kernel, smem, st);
+        cp.keys = keys;
+        const int smem_count = CS_WARPS * cells * (int)sizeof(int);
+        const int smem_place = CS_WARPS * (int)nkeys * (int)sizeof(uint32_t);
+        set_smem_limit((const void *)cs_count_kernel, smem_count, st);
+        set_smem_limit((const void *)cs_place_kernel, smem_place, st);
         note_launch();
-        cs_count_kernel<<<cp.G, CS_THREADS, smem, st>>>(cp);
+        cs_count_kernel<<<G, CS_THREADS, smem_count, st>>>(cp);
         note_launch();
-        scan_digit_rows_kernel<<<(int)nkeys, SORT_THREADS, 0, st>>>(w.hist, cp.G, (int)nkeys);
+        scan_digit_rows_kernel<<<(int)nkeys, SORT_THREADS, 0, st>>>(w.hist, G, (int)nkeys);
         note_launch();
-        cs_keys_kernel<<<1, SCAN_THREADS, 0, st>>>(w.hist, (int)nkeys, cp.G, capacity, d_count, w.n_eff,
-                                                   d_err, ranges);
+        cs_keys_kernel<<<1, SCAN_THREADS, 0, st>>>(w.hist + (int64_t)nkeys * G, (int)nkeys, capacity, d_count,
+                                                   w.n_eff, d_err, ranges);
         note_launch();
-        cs_place_kernel<<<cp.G, CS_THREADS, smem, st>>>(cp);
+        cs_place_kernel<<<G, CS_THREADS, smem_place, st>>>(cp);
         return launch_status("gs_bin_sort");
     }
     // ---- otherwise: offsets of every entry's pairs in that order
