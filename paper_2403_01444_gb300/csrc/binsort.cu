@@ -426,30 +426,34 @@ __global__ void keys64_kernel(const uint32_t *tk, const uint32_t *vals, const in
 //  - count: each warp adds every entry's bin rectangle to a 2-D difference
 //    grid of its view ((bins_y + 1) x (bins_x + 1) cells: +1 at two corners,
 //    -1 at the other two); prefix sums along rows and columns turn the grid
-//    into the warp's pair count per key, written to wcnt[warp][key]; the
-//    block's counts per key go to hist[key][block].
+//    into the warp's pair count per key, written (16 bits) to
+//    wcnt[warp][key]; the block's counts per key go to hist[key][block], and
+//    every entry's bin rectangle and view, packed, to rect[entry].
 //  - scan: per key, exclusive over the blocks (scan_digit_rows_kernel), then
 //    over the keys, giving each (block, key) its first position and each key
 //    its range, the total and the capacity check.
-//  - place: each block turns its warps' counts into running positions (key
-//    base + earlier blocks + earlier warps of the block), and each warp walks
-//    its entries' pairs in order, 32 per step, each placed at its key's
-//    running position (ranks within a step by __match_any_sync).
+//  - place: each block keeps per key its first position (32 bits) and per
+//    (warp, key) a running offset from it (16 bits: a block's count of one
+//    key stays below 2^16), and each warp walks its entries' pairs in order,
+//    32 per step, each placed at its key's running position (ranks within a
+//    step by __match_any_sync).
 // Every list then holds its pairs in the entries' depth order: the same
 // result as the stable key sort, bit for bit.
 constexpr int CS_WARPS = 16;
 constexpr int CS_THREADS = CS_WARPS * 32;
 constexpr int CS_MAX_CELLS = 2048;       // grid cells per warp: 16 x 2048 x 4 B = 128 KB of shared memory
-constexpr int CS_MIN_ENTRIES = 256;      // entries per warp at least (bounds the count table)
-constexpr int CS_BLOCKS_PER_SM = 2;
+constexpr int CS_MIN_ENTRIES = 64;       // entries per warp at least (bounds the count table)
+constexpr int CS_MAX_ENTRIES = 4095;     // entries per warp at most: CS_WARPS x 4095 < 2^16 per block and key
+constexpr int CS_BLOCKS_PER_SM = 4;
 
 // Warps of the counting sort for NV entries on this device (a multiple of
-// CS_WARPS), and the bound of the count table's rows used to size the
-// workspace without a device.
+// CS_WARPS), and the bound of that number used to size the workspace
+// without a device.
 inline int64_t cs_warps(int64_t NV, int sms)
 {
     const int64_t want = std::max<int64_t>(1, ceil_div(NV, CS_MIN_ENTRIES));
-    const int64_t cap = (int64_t)sms * CS_BLOCKS_PER_SM * CS_WARPS;
+    const int64_t cap = std::max<int64_t>((int64_t)sms * CS_BLOCKS_PER_SM * CS_WARPS,
+                                          ceil_div(NV, CS_MAX_ENTRIES));
     return ceil_div(std::min(want, cap), CS_WARPS) * CS_WARPS;
 }
 inline int64_t cs_warps_bound(int64_t NV)
@@ -463,12 +467,14 @@ struct CsParams {
     const int32_t *radius;
     const float *depth;
     int64_t NV, n;
+    float inv_n, inv_bin;    // 1/n and 1/bin, rounded to FP32
     int tx, ty, bin, bins_x, bins_y, bins, V;
     int gx, cells;           // grid row length bins_x + 1; cells per warp V (bins_y + 1) (bins_x + 1)
     int nkeys;               // V * bins
     int64_t NW;              // warps, G = NW / CS_WARPS blocks
     uint32_t *hist;          // [nkeys][G] block counts -> prefixes, then per key [nkeys] totals -> bases
-    uint32_t *wcnt;          // [NW][nkeys] warp counts
+    uint16_t *wcnt;          // [NW][nkeys] warp counts
+    uint64_t *rect;          // [NV] packed bin rectangle and view of every entry
     const int64_t *n_eff;
     uint32_t *vals;
     uint64_t *keys;          // optional
@@ -482,14 +488,49 @@ __device__ __forceinline__ void cs_segment(const CsParams &p, int64_t &gw, int64
     end = min(p.NV, beg + per);
 }
 
+// floor(x / d) for 0 <= x, d < 2^12 from r = fl(1/d): q = (x + 1/2) / d is
+// at least 1/(2d) from every integer, and the FP32 product (x + 1/2) r is
+// within q 2^-23 < 2^-11 / d of q, so it truncates to floor(q) = floor(x / d).
+__device__ __forceinline__ int cs_div(int x, float r)
+{
+    return (int)__fmul_rn(__fadd_rn((float)x, 0.5f), r);
+}
+
+// View of entry sv = view * n + g: the FP32 estimate is within 1 of it
+// (sv / n < 64, relative error about 2^-22), one correction makes it exact.
+__device__ __forceinline__ uint32_t cs_view(const CsParams &p, uint32_t sv)
+{
+    uint32_t v = min((uint32_t)(p.V - 1), (uint32_t)__fmul_rn((float)sv, p.inv_n));
+    if (v * (uint32_t)p.n > sv) --v;
+    else if ((v + 1u) * (uint32_t)p.n <= sv) ++v;
+    return v;
+}
+
+// Bin rectangle of entry sv (empty for a culled entry): bin_rect() with the
+// divisions by bin taken by cs_div (tiles < 2^12).
 __device__ __forceinline__ void cs_rect(const CsParams &p, uint32_t sv, int &x0, int &y0, int &x1, int &y1)
 {
     x0 = y0 = x1 = y1 = 0;
     const int r = p.radius[sv];
     if (r > 0) {
         const float2 m = p.mean2d[sv];
-        bin_rect(m.x, m.y, r, p.tx, p.ty, p.bin, x0, y0, x1, y1);
+        int a0, b0, a1, b1;
+        tile_rect(m.x, m.y, r, p.tx, p.ty, a0, b0, a1, b1);
+        if (a1 > a0 && b1 > b0) {
+            x0 = cs_div(a0, p.inv_bin);
+            y0 = cs_div(b0, p.inv_bin);
+            x1 = cs_div(a1 - 1, p.inv_bin) + 1;
+            y1 = cs_div(b1 - 1, p.inv_bin) + 1;
+        }
     }
+}
+
+// Packed rectangle: x0, x1, y0, y1 in 12 bits each (bins <= 1024 a side),
+// the view in the top 16 bits.
+__device__ __forceinline__ uint64_t cs_pack(int x0, int y0, int x1, int y1, uint32_t view)
+{
+    return (uint64_t)x0 | ((uint64_t)x1 << 12) | ((uint64_t)y0 << 24) | ((uint64_t)y1 << 36) |
+           ((uint64_t)view << 48);
 }
 
 // Grid cell of key (view, bin): the prefix sums leave the count of bin (x, y)
@@ -514,8 +555,10 @@ __global__ void __launch_bounds__(CS_THREADS) cs_count_kernel(CsParams p)
         const uint32_t sv = p.svals[i];
         int x0, y0, x1, y1;
         cs_rect(p, sv, x0, y0, x1, y1);
+        const uint32_t view = cs_view(p, sv);
+        p.rect[i] = cs_pack(x0, y0, x1, y1, view);
         if (x1 > x0) {
-            int *v = g + (int)(sv / (uint32_t)p.n) * (p.bins_y + 1) * p.gx;
+            int *v = g + (int)view * (p.bins_y + 1) * p.gx;
             atomicAdd(v + y0 * p.gx + x0, 1);
             atomicAdd(v + y0 * p.gx + x1, -1);
             atomicAdd(v + y1 * p.gx + x0, -1);
@@ -536,16 +579,19 @@ __global__ void __launch_bounds__(CS_THREADS) cs_count_kernel(CsParams p)
         int run = 0;
         for (int y = 0; y <= p.bins_y; ++y) col[y * p.gx] = (run += col[y * p.gx]);
     }
-    __syncwarp();
-    uint32_t *row = p.wcnt + gw * p.nkeys;
-    for (int key = lane; key < p.nkeys; key += 32) row[key] = (uint32_t)g[cs_cell(p, key)];
     __syncthreads();
+    // per key: the warps' counts (16 bits: at most CS_MAX_ENTRIES) and the block's
     const int G = (int)(p.NW / CS_WARPS);
+    uint16_t *wc = p.wcnt + (int64_t)blockIdx.x * CS_WARPS * p.nkeys;
     for (int key = threadIdx.x; key < p.nkeys; key += CS_THREADS) {
         const int c = cs_cell(p, key);
         uint32_t sum = 0;
 #pragma unroll 4
-        for (int w = 0; w < CS_WARPS; ++w) sum += (uint32_t)s_grid[w * p.cells + c];
+        for (int w = 0; w < CS_WARPS; ++w) {
+            const uint32_t x = (uint32_t)s_grid[w * p.cells + c];
+            wc[(int64_t)w * p.nkeys + key] = (uint16_t)x;
+            sum += x;
+        }
         p.hist[(int64_t)key * G + blockIdx.x] = sum;
     }
 }
@@ -582,33 +628,43 @@ __global__ void __launch_bounds__(SCAN_THREADS) cs_keys_kernel(uint32_t *tot, in
 
 __global__ void __launch_bounds__(CS_THREADS) cs_place_kernel(CsParams p)
 {
-    extern __shared__ uint32_t s_pos[];  // [CS_WARPS][nkeys]: running positions
-    if (*p.n_eff == 0) return;           // nothing to place, or over capacity
+    // per key the block's first position, then per (warp, key) the running
+    // offset from it
+    extern __shared__ uint32_t s_base[];
+    uint16_t *s_off = reinterpret_cast<uint16_t *>(s_base + p.nkeys);
+    if (*p.n_eff == 0) return;  // nothing to place, or over capacity
     int64_t gw, beg, end;
     cs_segment(p, gw, beg, end);
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    uint32_t *g = s_pos + (threadIdx.x >> 5) * p.nkeys;
     {
         const int G = (int)(p.NW / CS_WARPS);
         const uint32_t *base = p.hist + (int64_t)p.nkeys * G;
-        const uint32_t *wc = p.wcnt + (int64_t)blockIdx.x * CS_WARPS * p.nkeys;
+        const uint16_t *wc = p.wcnt + (int64_t)blockIdx.x * CS_WARPS * p.nkeys;
         for (int key = threadIdx.x; key < p.nkeys; key += CS_THREADS) {
-            uint32_t run = base[key] + p.hist[(int64_t)key * G + blockIdx.x];
+            s_base[key] = base[key] + p.hist[(int64_t)key * G + blockIdx.x];
+            uint32_t run = 0;
 #pragma unroll 4
             for (int w = 0; w < CS_WARPS; ++w) {
                 const uint32_t c = wc[(int64_t)w * p.nkeys + key];
-                s_pos[w * p.nkeys + key] = run;
+                s_off[w * p.nkeys + key] = (uint16_t)run;
                 run += c;
             }
         }
     }
     __syncthreads();
+    uint16_t *g = s_off + (threadIdx.x >> 5) * p.nkeys;
     for (int64_t e0 = beg; e0 < end; e0 += 32) {
         const int64_t i = e0 + lane;
-        const uint32_t sv = i < end ? p.svals[i] : 0u;
-        int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
-        if (i < end) cs_rect(p, sv, x0, y0, x1, y1);
+        uint32_t sv = 0;
+        uint64_t rc = 0;
+        if (i < end) {
+            sv = p.svals[i];
+            rc = p.rect[i];
+        }
+        const int x0 = (int)(rc & 0xfff), x1 = (int)((rc >> 12) & 0xfff);
+        const int y0 = (int)((rc >> 24) & 0xfff), y1 = (int)((rc >> 36) & 0xfff);
+        const uint32_t view = (uint32_t)(rc >> 48);
         const int w = x1 - x0, cnt = w * (y1 - y0);
         int inc = cnt;
 #pragma unroll
@@ -618,8 +674,10 @@ __global__ void __launch_bounds__(CS_THREADS) cs_place_kernel(CsParams p)
         }
         const int off = inc - cnt;
         const int total = __shfl_sync(0xffffffffu, inc, 31);
-        const uint32_t view = sv / (uint32_t)p.n;
-        const int kbase = (int)view * p.bins;
+        // per entry: its first key, its Gaussian and 1/width for the slots
+        const int kfirst = (int)view * p.bins + y0 * p.bins_x + x0;
+        const uint32_t gi = sv - view * (uint32_t)p.n;
+        const float rw = cnt > 0 ? __frcp_rn((float)w) : 0.f;
         for (int s0 = 0; s0 < total; s0 += 32) {
             const int o = s0 + lane;
             // the entry of pair slot o: the last lane whose offset is <= o
@@ -631,27 +689,27 @@ __global__ void __launch_bounds__(CS_THREADS) cs_place_kernel(CsParams p)
             }
             const int so = __shfl_sync(0xffffffffu, off, src);
             const int sw = __shfl_sync(0xffffffffu, w, src);
-            const int sx = __shfl_sync(0xffffffffu, x0, src);
-            const int sy = __shfl_sync(0xffffffffu, y0, src);
-            const int sk = __shfl_sync(0xffffffffu, kbase, src);
-            const uint32_t ssv = __shfl_sync(0xffffffffu, sv, src);
+            const int sk = __shfl_sync(0xffffffffu, kfirst, src);
+            const float srw = __shfl_sync(0xffffffffu, rw, src);
+            const uint32_t sgi = __shfl_sync(0xffffffffu, gi, src);
             const bool valid = o < total;
             int key = -1;
             if (valid) {
                 const int local = o - so;
-                const int dy = local / sw;
-                key = sk + (sy + dy) * p.bins_x + sx + (local - dy * sw);
+                const int dy = cs_div(local, srw);  // local < bins <= 2048, sw <= bins_x
+                key = sk + dy * p.bins_x + (local - dy * sw);
             }
             const unsigned peers = __match_any_sync(0xffffffffu, key);
             uint32_t pos = 0;
-            if (valid) pos = g[key] + __popc(peers & lt);
+            if (valid) pos = s_base[key] + g[key] + __popc(peers & lt);
             __syncwarp();
-            if (valid && lane == __ffs(peers) - 1) g[key] += __popc(peers);
+            if (valid && lane == __ffs(peers) - 1) g[key] = (uint16_t)(g[key] + __popc(peers));
             __syncwarp();
             if (valid) {
-                const uint32_t gi = ssv - (uint32_t)(sk / p.bins) * (uint32_t)p.n;
-                p.vals[pos] = gi;
-                if (p.keys) p.keys[pos] = ((uint64_t)(uint32_t)key << 32) | __float_as_uint(p.depth[ssv]);
+                p.vals[pos] = sgi;
+                if (p.keys)
+                    p.keys[pos] = ((uint64_t)(uint32_t)key << 32) |
+                                  __float_as_uint(p.depth[(int64_t)(sk / p.bins) * p.n + sgi]);
             }
         }
     }
@@ -665,6 +723,8 @@ struct BinWs {
     uint32_t *hist;
     int64_t *n_eff;
     uint32_t *tk[2], *tv;
+    uint64_t *rect;    // counting sort; shares its space with the emit path's buffers
+    uint16_t *wcnt;
     size_t bytes;
 };
 
@@ -682,19 +742,24 @@ static BinWs carve(void *base, int64_t NV, int64_t cap)
     };
     for (int k = 0; k < 2; ++k) w.dk[k] = reinterpret_cast<uint32_t *>(take(4 * NV));
     for (int k = 0; k < 2; ++k) w.dv[k] = reinterpret_cast<uint32_t *>(take(4 * NV));
+    // the radix passes' digit counts, or the counting sort's per-block key counts
+    const int64_t cw = cs_warps_bound(NV);
+    const size_t hist_words = std::max<size_t>((size_t)RADIX * SORT_BLOCKS_MAX + RADIX,
+                                               (size_t)CS_MAX_CELLS * (cw / CS_WARPS + 1));
+    w.hist = reinterpret_cast<uint32_t *>(take(4 * hist_words));
+    w.n_eff = reinterpret_cast<int64_t *>(take(64));
+    // stage 2 takes one of two paths: their buffers share one region
+    const size_t region = o;
     w.offsets = reinterpret_cast<int64_t *>(take(8 * (NV + 1)));
     w.cnt = reinterpret_cast<int32_t *>(take(4 * NV));
     w.bsum = reinterpret_cast<int64_t *>(take(8 * (ceil_div(NV, SCAN_TILE) + 1)));
-    // the radix passes' digit counts, or the counting sort's per-block and
-    // per-warp key counts
-    const int64_t cw = cs_warps_bound(NV);
-    const size_t hist_words = std::max<size_t>((size_t)RADIX * SORT_BLOCKS_MAX + RADIX,
-                                               (size_t)CS_MAX_CELLS * (cw / CS_WARPS + 1 + cw));
-    w.hist = reinterpret_cast<uint32_t *>(take(4 * hist_words));
-    w.n_eff = reinterpret_cast<int64_t *>(take(64));
     for (int k = 0; k < 2; ++k) w.tk[k] = reinterpret_cast<uint32_t *>(take(4 * cap));
     w.tv = reinterpret_cast<uint32_t *>(take(4 * cap));
-    w.bytes = o;
+    const size_t emit_end = o;
+    o = region;
+    w.rect = reinterpret_cast<uint64_t *>(take(8 * NV));
+    w.wcnt = reinterpret_cast<uint16_t *>(take(2 * (size_t)CS_MAX_CELLS * cw));
+    w.bytes = std::max(emit_end, o);
     return w;
 }
 
@@ -796,15 +861,18 @@ extern "C" gs_status gs_bin_sort(const gs_projected *proj, int64_t n, int V, int
         cp.gx = gx;
         cp.cells = cells;
         cp.nkeys = (int)nkeys;
+        cp.inv_n = 1.0f / (float)n;
+        cp.inv_bin = 1.0f / (float)bin;
         cp.NW = cs_warps(NV, num_sms());
         const int G = (int)(cp.NW / CS_WARPS);
         cp.hist = w.hist;
-        cp.wcnt = w.hist + (int64_t)nkeys * (G + 1);
+        cp.wcnt = w.wcnt;
+        cp.rect = w.rect;
         cp.n_eff = w.n_eff;
         cp.vals = vals;
         cp.keys = keys;
         const int smem_count = CS_WARPS * cells * (int)sizeof(int);
-        const int smem_place = CS_WARPS * (int)nkeys * (int)sizeof(uint32_t);
+        const int smem_place = (int)nkeys * (int)(sizeof(uint32_t) + CS_WARPS * sizeof(uint16_t));
         set_smem_limit((const void *)cs_count_kernel, smem_count, st);
         set_smem_limit((const void *)cs_place_kernel, smem_place, st);
         note_launch();
