@@ -626,12 +626,13 @@ __global__ void __launch_bounds__(SCAN_THREADS) cs_keys_kernel(uint32_t *tot, in
     }
 }
 
-__global__ void __launch_bounds__(CS_THREADS) cs_place_kernel(CsParams p)
+__global__ void __launch_bounds__(CS_THREADS, CS_BLOCKS_PER_SM) cs_place_kernel(CsParams p)
 {
     // per key the block's first position, then per (warp, key) the running
     // offset from it
     extern __shared__ uint32_t s_base[];
     uint16_t *s_off = reinterpret_cast<uint16_t *>(s_base + p.nkeys);
+    __shared__ uint8_t s_idx[CS_WARPS][32];  // lanes of the entries with pairs
     if (*p.n_eff == 0) return;  // nothing to place, or over capacity
     int64_t gw, beg, end;
     cs_segment(p, gw, beg, end);
@@ -654,13 +655,23 @@ __global__ void __launch_bounds__(CS_THREADS) cs_place_kernel(CsParams p)
     }
     __syncthreads();
     uint16_t *g = s_off + (threadIdx.x >> 5) * p.nkeys;
+    uint8_t *idx = s_idx[threadIdx.x >> 5];
+    const unsigned le = (2u << lane) - 1u;  // lanes <= this one
+    // the next 32 entries are loaded while the present ones are placed
+    uint32_t sv_next = 0;
+    uint64_t rc_next = 0;
+    if (beg + lane < end) {
+        sv_next = p.svals[beg + lane];
+        rc_next = p.rect[beg + lane];
+    }
     for (int64_t e0 = beg; e0 < end; e0 += 32) {
-        const int64_t i = e0 + lane;
-        uint32_t sv = 0;
-        uint64_t rc = 0;
-        if (i < end) {
-            sv = p.svals[i];
-            rc = p.rect[i];
+        const uint32_t sv = sv_next;
+        const uint64_t rc = rc_next;
+        sv_next = 0;
+        rc_next = 0;
+        if (e0 + 32 + lane < end) {
+            sv_next = p.svals[e0 + 32 + lane];
+            rc_next = p.rect[e0 + 32 + lane];
         }
         const int x0 = (int)(rc & 0xfff), x1 = (int)((rc >> 12) & 0xfff);
         const int y0 = (int)((rc >> 24) & 0xfff), y1 = (int)((rc >> 36) & 0xfff);
@@ -672,32 +683,37 @@ __global__ void __launch_bounds__(CS_THREADS) cs_place_kernel(CsParams p)
             const int y = __shfl_up_sync(0xffffffffu, inc, o);
             if (lane >= o) inc += y;
         }
-        const int off = inc - cnt;
         const int total = __shfl_sync(0xffffffffu, inc, 31);
-        // per entry: its first key, its Gaussian and 1/width for the slots
-        const int kfirst = (int)view * p.bins + y0 * p.bins_x + x0;
-        const uint32_t gi = sv - view * (uint32_t)p.n;
-        const float rw = cnt > 0 ? __frcp_rn((float)w) : 0.f;
+        // the entries with pairs, compacted: lane j holds the j-th one's first
+        // slot, first key and width, Gaussian and 1/width
+        const unsigned nz = __ballot_sync(0xffffffffu, cnt > 0);
+        const int nent = __popc(nz);
+        if (cnt > 0) idx[__popc(nz & lt)] = (uint8_t)lane;
+        __syncwarp();
+        const int src = lane < nent ? idx[lane] : 0;
+        __syncwarp();
+        const int c_off = __shfl_sync(0xffffffffu, inc - cnt, src);
+        const int c_kw = __shfl_sync(0xffffffffu, ((int)view * p.bins + y0 * p.bins_x + x0) | (w << 16), src);
+        const uint32_t c_gi = __shfl_sync(0xffffffffu, sv - view * (uint32_t)p.n, src);
+        const float c_rw = __shfl_sync(0xffffffffu, cnt > 0 ? __frcp_rn((float)w) : 0.f, src);
+        int before = 0;  // entries that start before this step's first slot
         for (int s0 = 0; s0 < total; s0 += 32) {
+            // the entry of pair slot o: the last one whose first slot is <= o
+            const bool starts = lane < nent && c_off >= s0 && c_off < s0 + 32;
+            const unsigned B = __reduce_or_sync(0xffffffffu, starts ? 1u << (c_off - s0) : 0u);
+            const int j = max(0, before + __popc(B & le) - 1);
+            before += __popc(B);
             const int o = s0 + lane;
-            // the entry of pair slot o: the last lane whose offset is <= o
-            int src = 0;
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const int cand = src + step;
-                if (__shfl_sync(0xffffffffu, off, cand) <= o) src = cand;
-            }
-            const int so = __shfl_sync(0xffffffffu, off, src);
-            const int sw = __shfl_sync(0xffffffffu, w, src);
-            const int sk = __shfl_sync(0xffffffffu, kfirst, src);
-            const float srw = __shfl_sync(0xffffffffu, rw, src);
-            const uint32_t sgi = __shfl_sync(0xffffffffu, gi, src);
+            const int so = __shfl_sync(0xffffffffu, c_off, j);
+            const int skw = __shfl_sync(0xffffffffu, c_kw, j);
+            const float srw = __shfl_sync(0xffffffffu, c_rw, j);
+            const uint32_t sgi = __shfl_sync(0xffffffffu, c_gi, j);
             const bool valid = o < total;
             int key = -1;
             if (valid) {
-                const int local = o - so;
+                const int local = o - so, sw = skw >> 16;
                 const int dy = cs_div(local, srw);  // local < bins <= 2048, sw <= bins_x
-                key = sk + dy * p.bins_x + (local - dy * sw);
+                key = (skw & 0xffff) + dy * p.bins_x + (local - dy * sw);
             }
             const unsigned peers = __match_any_sync(0xffffffffu, key);
             uint32_t pos = 0;
@@ -709,7 +725,7 @@ __global__ void __launch_bounds__(CS_THREADS) cs_place_kernel(CsParams p)
                 p.vals[pos] = sgi;
                 if (p.keys)
                     p.keys[pos] = ((uint64_t)(uint32_t)key << 32) |
-                                  __float_as_uint(p.depth[(int64_t)(sk / p.bins) * p.n + sgi]);
+                                  __float_as_uint(p.depth[(int64_t)((skw & 0xffff) / p.bins) * p.n + sgi]);
             }
         }
     }
