@@ -420,31 +420,36 @@ __global__ void keys64_kernel(const uint32_t *tk, const uint32_t *vals, const in
 }
 
 // ------------------------------------------- stage 2 as a counting sort
-// When the keys' difference grids fit in shared memory, stage 2 sorts the
-// pairs by key without materialising them: every warp owns a contiguous
-// segment of the depth-ordered entries.
-//  - count: each warp adds every entry's bin rectangle to a 2-D difference
-//    grid of its view ((bins_y + 1) x (bins_x + 1) cells: +1 at two corners,
-//    -1 at the other two); prefix sums along rows and columns turn the grid
-//    into the warp's pair count per key, written (16 bits) to
-//    wcnt[warp][key]; the block's counts per key go to hist[key][block], and
-//    every entry's bin rectangle and view, packed, to rect[entry].
+// When the per-warp key tables fit in shared memory, stage 2 sorts the pairs
+// by key without materialising them.  Every warp owns a contiguous segment of
+// the depth-ordered entries and walks their pairs in order, 32 pair slots per
+// step (an entry's pairs are its bin rectangle, row by row):
+//  - count: each slot adds one to its key's 16-bit counter in the warp's
+//    table (two counters per 32-bit word; a warp's count of one key is at
+//    most its CS_MAX_ENTRIES entries).  The block then writes, per key, each
+//    warp's exclusive prefix over the block's warps to wpre[warp][key] and
+//    the block's total to hist[key][block], and every entry's bin rectangle
+//    and view, packed, to rect[entry].
 //  - scan: per key, exclusive over the blocks (scan_digit_rows_kernel), then
-//    over the keys, giving each (block, key) its first position and each key
-//    its range, the total and the capacity check.
+//    over the keys (cs_keys_kernel), giving each (block, key) its first
+//    position, each key its range, the total and the capacity check.
 //  - place: each block keeps per key its first position (32 bits) and per
 //    (warp, key) a running offset from it (16 bits: a block's count of one
-//    key stays below 2^16), and each warp walks its entries' pairs in order,
-//    32 per step, each placed at its key's running position (ranks within a
-//    step by __match_any_sync).
+//    key is below 2^16), and each warp walks its pairs again, each placed at
+//    its key's running position; within a step the slots of one key are
+//    ranked by lane (__match_any_sync), which a step whose slots all belong to
+//    one entry (distinct keys) skips.
 // Every list then holds its pairs in the entries' depth order: the same
 // result as the stable key sort, bit for bit.
 constexpr int CS_WARPS = 16;
 constexpr int CS_THREADS = CS_WARPS * 32;
-constexpr int CS_MAX_CELLS = 2048;       // grid cells per warp: 16 x 2048 x 4 B = 128 KB of shared memory
-constexpr int CS_MIN_ENTRIES = 64;       // entries per warp at least (bounds the count table)
+constexpr int CS_MAX_KEYS = 2048;        // keys V * bins at most (16-bit tables: 64 KB per block)
+constexpr int CS_MIN_ENTRIES = 64;       // entries per warp at least (bounds the count tables)
 constexpr int CS_MAX_ENTRIES = 4095;     // entries per warp at most: CS_WARPS x 4095 < 2^16 per block and key
 constexpr int CS_BLOCKS_PER_SM = 4;
+
+// Keys padded to a multiple of 8, so a warp's 16-bit row is whole 16-byte words.
+inline int cs_pad_keys(int64_t nkeys) { return (int)((nkeys + 7) & ~int64_t(7)); }
 
 // Warps of the counting sort for NV entries on this device (a multiple of
 // CS_WARPS), and the bound of that number used to size the workspace
@@ -468,21 +473,20 @@ struct CsParams {
     const float *depth;
     int64_t NV, n;
     float inv_n, inv_bin;    // 1/n and 1/bin, rounded to FP32
-    int tx, ty, bin, bins_x, bins_y, bins, V;
-    int gx, cells;           // grid row length bins_x + 1; cells per warp V (bins_y + 1) (bins_x + 1)
-    int nkeys;               // V * bins
+    int tx, ty, bin, bins_x, bins, V;
+    int nkeys, kp;           // V * bins, and padded to a multiple of 8
     int64_t NW;              // warps, G = NW / CS_WARPS blocks
     uint32_t *hist;          // [nkeys][G] block counts -> prefixes, then per key [nkeys] totals -> bases
-    uint16_t *wcnt;          // [NW][nkeys] warp counts
+    uint16_t *wpre;          // [NW][kp] warp offsets within the block
     uint64_t *rect;          // [NV] packed bin rectangle and view of every entry
     const int64_t *n_eff;
     uint32_t *vals;
     uint64_t *keys;          // optional
 };
 
-__device__ __forceinline__ void cs_segment(const CsParams &p, int64_t &gw, int64_t &beg, int64_t &end)
+__device__ __forceinline__ void cs_segment(const CsParams &p, int64_t &beg, int64_t &end)
 {
-    gw = (int64_t)blockIdx.x * CS_WARPS + (threadIdx.x >> 5);
+    const int64_t gw = (int64_t)blockIdx.x * CS_WARPS + (threadIdx.x >> 5);
     const int64_t per = (p.NV + p.NW - 1) / p.NW;
     beg = min(p.NV, gw * per);
     end = min(p.NV, beg + per);
@@ -506,11 +510,12 @@ __device__ __forceinline__ uint32_t cs_view(const CsParams &p, uint32_t sv)
     return v;
 }
 
-// Bin rectangle of entry sv (empty for a culled entry): bin_rect() with the
-// divisions by bin taken by cs_div (tiles < 2^12).
-__device__ __forceinline__ void cs_rect(const CsParams &p, uint32_t sv, int &x0, int &y0, int &x1, int &y1)
+// Packed bin rectangle and view of entry sv (an empty rectangle for a culled
+// entry): bin_rect() with the divisions by bin taken by cs_div (tiles < 2^12);
+// x0, x1, y0, y1 in 12 bits each (bins <= 1024 a side), the view above them.
+__device__ __forceinline__ uint64_t cs_rect(const CsParams &p, uint32_t sv)
 {
-    x0 = y0 = x1 = y1 = 0;
+    int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
     const int r = p.radius[sv];
     if (r > 0) {
         const float2 m = p.mean2d[sv];
@@ -523,76 +528,117 @@ __device__ __forceinline__ void cs_rect(const CsParams &p, uint32_t sv, int &x0,
             y1 = cs_div(b1 - 1, p.inv_bin) + 1;
         }
     }
-}
-
-// Packed rectangle: x0, x1, y0, y1 in 12 bits each (bins <= 1024 a side),
-// the view in the top 16 bits.
-__device__ __forceinline__ uint64_t cs_pack(int x0, int y0, int x1, int y1, uint32_t view)
-{
     return (uint64_t)x0 | ((uint64_t)x1 << 12) | ((uint64_t)y0 << 24) | ((uint64_t)y1 << 36) |
-           ((uint64_t)view << 48);
+           ((uint64_t)cs_view(p, sv) << 48);
 }
 
-// Grid cell of key (view, bin): the prefix sums leave the count of bin (x, y)
-// of view v at cell v (bins_y + 1) gx + y gx + x.
-__device__ __forceinline__ int cs_cell(const CsParams &p, int key)
-{
-    const int v = key / p.bins, b = key - v * p.bins;
-    const int y = b / p.bins_x, x = b - y * p.bins_x;
-    return (v * (p.bins_y + 1) + y) * p.gx + x;
-}
+// 32 entries of a warp's segment (one per lane), compacted: lane j < nent
+// holds the j-th entry with pairs: its first slot, first key | width << 16,
+// Gaussian index and 1/width.
+struct CsChunk {
+    int total, nent, off, kw;
+    uint32_t gi;
+    float rw;
+};
 
-__global__ void __launch_bounds__(CS_THREADS) cs_count_kernel(CsParams p)
+__device__ __forceinline__ CsChunk cs_chunk(const CsParams &p, uint32_t sv, uint64_t rc, uint8_t *idx)
 {
-    extern __shared__ int s_grid[];  // [CS_WARPS][cells]
-    int64_t gw, beg, end;
-    cs_segment(p, gw, beg, end);
     const int lane = threadIdx.x & 31;
-    int *g = s_grid + (threadIdx.x >> 5) * p.cells;
-    for (int c = lane; c < p.cells; c += 32) g[c] = 0;
+    const int x0 = (int)(rc & 0xfff), x1 = (int)((rc >> 12) & 0xfff);
+    const int y0 = (int)((rc >> 24) & 0xfff), y1 = (int)((rc >> 36) & 0xfff);
+    const uint32_t view = (uint32_t)(rc >> 48);
+    const int w = x1 - x0, cnt = w * (y1 - y0);
+    int inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    CsChunk c;
+    c.total = __shfl_sync(0xffffffffu, inc, 31);
+    const unsigned nz = __ballot_sync(0xffffffffu, cnt > 0);
+    c.nent = __popc(nz);
+    if (cnt > 0) idx[__popc(nz & ((1u << lane) - 1u))] = (uint8_t)lane;
     __syncwarp();
-    for (int64_t i = beg + lane; i < end; i += 32) {
-        const uint32_t sv = p.svals[i];
-        int x0, y0, x1, y1;
-        cs_rect(p, sv, x0, y0, x1, y1);
-        const uint32_t view = cs_view(p, sv);
-        p.rect[i] = cs_pack(x0, y0, x1, y1, view);
-        if (x1 > x0) {
-            int *v = g + (int)view * (p.bins_y + 1) * p.gx;
-            atomicAdd(v + y0 * p.gx + x0, 1);
-            atomicAdd(v + y0 * p.gx + x1, -1);
-            atomicAdd(v + y1 * p.gx + x0, -1);
-            atomicAdd(v + y1 * p.gx + x1, 1);
+    const int src = lane < c.nent ? idx[lane] : 0;
+    __syncwarp();
+    c.off = __shfl_sync(0xffffffffu, inc - cnt, src);
+    c.kw = __shfl_sync(0xffffffffu, ((int)view * p.bins + y0 * p.bins_x + x0) | (w << 16), src);
+    c.gi = __shfl_sync(0xffffffffu, sv - view * (uint32_t)p.n, src);
+    c.rw = __shfl_sync(0xffffffffu, cnt > 0 ? __frcp_rn((float)w) : 0.f, src);
+    return c;
+}
+
+// Key of pair slot s0 + lane of a chunk (-1 past its end) and the slot's
+// entry j (compacted; `before` counts the entries that start before s0 and
+// is advanced past this step).  single: every slot of the step belongs to one
+// entry.
+__device__ __forceinline__ int cs_slot(const CsParams &p, const CsChunk &c, int s0, int &before, int &j,
+                                       bool &single)
+{
+    const int lane = threadIdx.x & 31;
+    // the entry of slot o: the last one whose first slot is <= o
+    const bool starts = lane < c.nent && c.off >= s0 && c.off < s0 + 32;
+    const unsigned B = __reduce_or_sync(0xffffffffu, starts ? 1u << (c.off - s0) : 0u);
+    j = max(0, before + __popc(B & ((2u << lane) - 1u)) - 1);
+    before += __popc(B);
+    single = (B & ~1u) == 0u;
+    const int so = __shfl_sync(0xffffffffu, c.off, j);
+    const int skw = __shfl_sync(0xffffffffu, c.kw, j);
+    const float srw = __shfl_sync(0xffffffffu, c.rw, j);
+    const int o = s0 + lane;
+    if (o >= c.total) return -1;
+    const int local = o - so, sw = skw >> 16;
+    const int dy = cs_div(local, srw);  // local < bins <= CS_MAX_KEYS, sw <= bins_x
+    return (skw & 0xffff) + dy * p.bins_x + (local - dy * sw);
+}
+
+__global__ void __launch_bounds__(CS_THREADS, CS_BLOCKS_PER_SM) cs_count_kernel(CsParams p)
+{
+    extern __shared__ uint32_t s_cnt[];      // [CS_WARPS][kp / 2]: two 16-bit counters a word
+    __shared__ uint8_t s_idx[CS_WARPS][32];  // lanes of the entries with pairs
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kw2 = p.kp >> 1;
+    uint32_t *cnt = s_cnt + warp * kw2;
+    for (int k = lane; k < kw2; k += 32) cnt[k] = 0u;
+    __syncwarp();
+    int64_t beg, end;
+    cs_segment(p, beg, end);
+    for (int64_t e0 = beg; e0 < end; e0 += 32) {
+        const int64_t i = e0 + lane;
+        uint32_t sv = 0;
+        uint64_t rc = 0;
+        if (i < end) {
+            sv = p.svals[i];
+            rc = cs_rect(p, sv);
+            p.rect[i] = rc;
         }
-    }
-    __syncwarp();
-    // prefix sums along the rows, then down the columns, of every view's grid
-    const int rows = p.V * (p.bins_y + 1);
-    for (int r = lane; r < rows; r += 32) {
-        int run = 0;
-        int *row = g + r * p.gx;
-        for (int x = 0; x < p.gx; ++x) row[x] = (run += row[x]);
-    }
-    __syncwarp();
-    for (int c = lane; c < p.V * p.gx; c += 32) {
-        int *col = g + (c / p.gx) * (p.bins_y + 1) * p.gx + c % p.gx;
-        int run = 0;
-        for (int y = 0; y <= p.bins_y; ++y) col[y * p.gx] = (run += col[y * p.gx]);
+        const CsChunk c = cs_chunk(p, sv, rc, s_idx[warp]);
+        int before = 0;
+        for (int s0 = 0; s0 < c.total; s0 += 32) {
+            int j;
+            bool single;
+            const int key = cs_slot(p, c, s0, before, j, single);
+            if (key >= 0) atomicAdd(&cnt[key >> 1], 1u << ((key & 1) << 4));
+        }
     }
     __syncthreads();
-    // per key: the warps' counts (16 bits: at most CS_MAX_ENTRIES) and the block's
+    // per pair of keys: each warp's offset within the block (exclusive over
+    // the warps, both halves at once: no half exceeds 2^16 - 1) and the
+    // block's counts
     const int G = (int)(p.NW / CS_WARPS);
-    uint16_t *wc = p.wcnt + (int64_t)blockIdx.x * CS_WARPS * p.nkeys;
-    for (int key = threadIdx.x; key < p.nkeys; key += CS_THREADS) {
-        const int c = cs_cell(p, key);
-        uint32_t sum = 0;
-#pragma unroll 4
+    uint32_t *pre = reinterpret_cast<uint32_t *>(p.wpre) + (int64_t)blockIdx.x * CS_WARPS * kw2;
+    for (int k2 = threadIdx.x; k2 < kw2; k2 += CS_THREADS) {
+        uint32_t run = 0;
+#pragma unroll
         for (int w = 0; w < CS_WARPS; ++w) {
-            const uint32_t x = (uint32_t)s_grid[w * p.cells + c];
-            wc[(int64_t)w * p.nkeys + key] = (uint16_t)x;
-            sum += x;
+            const uint32_t x = s_cnt[w * kw2 + k2];
+            pre[(int64_t)w * kw2 + k2] = run;
+            run += x;
         }
-        p.hist[(int64_t)key * G + blockIdx.x] = sum;
+        const int key = 2 * k2;
+        if (key < p.nkeys) p.hist[(int64_t)key * G + blockIdx.x] = run & 0xffffu;
+        if (key + 1 < p.nkeys) p.hist[(int64_t)(key + 1) * G + blockIdx.x] = run >> 16;
     }
 }
 
@@ -626,37 +672,18 @@ __global__ void __launch_bounds__(SCAN_THREADS) cs_keys_kernel(uint32_t *tot, in
     }
 }
 
-__global__ void __launch_bounds__(CS_THREADS, CS_BLOCKS_PER_SM) cs_place_kernel(CsParams p)
+__global__ void __launch_bounds__(CS_THREADS) cs_place_kernel(CsParams p)
 {
     // per key the block's first position, then per (warp, key) the running
     // offset from it
-    extern __shared__ uint32_t s_base[];
-    uint16_t *s_off = reinterpret_cast<uint16_t *>(s_base + p.nkeys);
+    extern __shared__ __align__(16) uint32_t s_base[];
+    uint16_t *s_off = reinterpret_cast<uint16_t *>(s_base + p.kp);
     __shared__ uint8_t s_idx[CS_WARPS][32];  // lanes of the entries with pairs
-    if (*p.n_eff == 0) return;  // nothing to place, or over capacity
-    int64_t gw, beg, end;
-    cs_segment(p, gw, beg, end);
-    const int lane = threadIdx.x & 31;
+    if (*p.n_eff == 0) return;               // nothing to place, or over capacity
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    {
-        const int G = (int)(p.NW / CS_WARPS);
-        const uint32_t *base = p.hist + (int64_t)p.nkeys * G;
-        const uint16_t *wc = p.wcnt + (int64_t)blockIdx.x * CS_WARPS * p.nkeys;
-        for (int key = threadIdx.x; key < p.nkeys; key += CS_THREADS) {
-            s_base[key] = base[key] + p.hist[(int64_t)key * G + blockIdx.x];
-            uint32_t run = 0;
-#pragma unroll 4
-            for (int w = 0; w < CS_WARPS; ++w) {
-                const uint32_t c = wc[(int64_t)w * p.nkeys + key];
-                s_off[w * p.nkeys + key] = (uint16_t)run;
-                run += c;
-            }
-        }
-    }
-    __syncthreads();
-    uint16_t *g = s_off + (threadIdx.x >> 5) * p.nkeys;
-    uint8_t *idx = s_idx[threadIdx.x >> 5];
-    const unsigned le = (2u << lane) - 1u;  // lanes <= this one
+    int64_t beg, end;
+    cs_segment(p, beg, end);
     // the next 32 entries are loaded while the present ones are placed
     uint32_t sv_next = 0;
     uint64_t rc_next = 0;
@@ -664,6 +691,18 @@ __global__ void __launch_bounds__(CS_THREADS, CS_BLOCKS_PER_SM) cs_place_kernel(
         sv_next = p.svals[beg + lane];
         rc_next = p.rect[beg + lane];
     }
+    {
+        const int G = (int)(p.NW / CS_WARPS);
+        const uint32_t *base = p.hist + (int64_t)p.nkeys * G;
+        for (int key = threadIdx.x; key < p.nkeys; key += CS_THREADS)
+            s_base[key] = base[key] + p.hist[(int64_t)key * G + blockIdx.x];
+        // the warp's own row of offsets, 16 bytes a lane
+        const uint4 *src = reinterpret_cast<const uint4 *>(p.wpre + ((int64_t)blockIdx.x * CS_WARPS + warp) * p.kp);
+        uint4 *dst = reinterpret_cast<uint4 *>(s_off + warp * p.kp);
+        for (int k = lane; k < (p.kp >> 3); k += 32) dst[k] = src[k];
+    }
+    __syncthreads();
+    uint16_t *g = s_off + warp * p.kp;
     for (int64_t e0 = beg; e0 < end; e0 += 32) {
         const uint32_t sv = sv_next;
         const uint64_t rc = rc_next;
@@ -673,49 +712,16 @@ __global__ void __launch_bounds__(CS_THREADS, CS_BLOCKS_PER_SM) cs_place_kernel(
             sv_next = p.svals[e0 + 32 + lane];
             rc_next = p.rect[e0 + 32 + lane];
         }
-        const int x0 = (int)(rc & 0xfff), x1 = (int)((rc >> 12) & 0xfff);
-        const int y0 = (int)((rc >> 24) & 0xfff), y1 = (int)((rc >> 36) & 0xfff);
-        const uint32_t view = (uint32_t)(rc >> 48);
-        const int w = x1 - x0, cnt = w * (y1 - y0);
-        int inc = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
-        }
-        const int total = __shfl_sync(0xffffffffu, inc, 31);
-        // the entries with pairs, compacted: lane j holds the j-th one's first
-        // slot, first key and width, Gaussian and 1/width
-        const unsigned nz = __ballot_sync(0xffffffffu, cnt > 0);
-        const int nent = __popc(nz);
-        if (cnt > 0) idx[__popc(nz & lt)] = (uint8_t)lane;
-        __syncwarp();
-        const int src = lane < nent ? idx[lane] : 0;
-        __syncwarp();
-        const int c_off = __shfl_sync(0xffffffffu, inc - cnt, src);
-        const int c_kw = __shfl_sync(0xffffffffu, ((int)view * p.bins + y0 * p.bins_x + x0) | (w << 16), src);
-        const uint32_t c_gi = __shfl_sync(0xffffffffu, sv - view * (uint32_t)p.n, src);
-        const float c_rw = __shfl_sync(0xffffffffu, cnt > 0 ? __frcp_rn((float)w) : 0.f, src);
-        int before = 0;  // entries that start before this step's first slot
-        for (int s0 = 0; s0 < total; s0 += 32) {
-            // the entry of pair slot o: the last one whose first slot is <= o
-            const bool starts = lane < nent && c_off >= s0 && c_off < s0 + 32;
-            const unsigned B = __reduce_or_sync(0xffffffffu, starts ? 1u << (c_off - s0) : 0u);
-            const int j = max(0, before + __popc(B & le) - 1);
-            before += __popc(B);
-            const int o = s0 + lane;
-            const int so = __shfl_sync(0xffffffffu, c_off, j);
-            const int skw = __shfl_sync(0xffffffffu, c_kw, j);
-            const float srw = __shfl_sync(0xffffffffu, c_rw, j);
-            const uint32_t sgi = __shfl_sync(0xffffffffu, c_gi, j);
-            const bool valid = o < total;
-            int key = -1;
-            if (valid) {
-                const int local = o - so, sw = skw >> 16;
-                const int dy = cs_div(local, srw);  // local < bins <= 2048, sw <= bins_x
-                key = (skw & 0xffff) + dy * p.bins_x + (local - dy * sw);
-            }
-            const unsigned peers = __match_any_sync(0xffffffffu, key);
+        const CsChunk c = cs_chunk(p, sv, rc, s_idx[warp]);
+        int before = 0;
+        for (int s0 = 0; s0 < c.total; s0 += 32) {
+            int j;
+            bool single;
+            const int key = cs_slot(p, c, s0, before, j, single);
+            const uint32_t sgi = __shfl_sync(0xffffffffu, c.gi, j);
+            const bool valid = key >= 0;
+            // slots of one key in this step, ranked by lane
+            const unsigned peers = single ? 1u << lane : __match_any_sync(0xffffffffu, key);
             uint32_t pos = 0;
             if (valid) pos = s_base[key] + g[key] + __popc(peers & lt);
             __syncwarp();
@@ -725,7 +731,7 @@ __global__ void __launch_bounds__(CS_THREADS, CS_BLOCKS_PER_SM) cs_place_kernel(
                 p.vals[pos] = sgi;
                 if (p.keys)
                     p.keys[pos] = ((uint64_t)(uint32_t)key << 32) |
-                                  __float_as_uint(p.depth[(int64_t)((skw & 0xffff) / p.bins) * p.n + sgi]);
+                                  __float_as_uint(p.depth[(int64_t)(key / p.bins) * p.n + sgi]);
             }
         }
     }
@@ -740,7 +746,7 @@ struct BinWs {
     int64_t *n_eff;
     uint32_t *tk[2], *tv;
     uint64_t *rect;    // counting sort; shares its space with the emit path's buffers
-    uint16_t *wcnt;
+    uint16_t *wpre;
     size_t bytes;
 };
 
@@ -761,7 +767,7 @@ static BinWs carve(void *base, int64_t NV, int64_t cap)
     // the radix passes' digit counts, or the counting sort's per-block key counts
     const int64_t cw = cs_warps_bound(NV);
     const size_t hist_words = std::max<size_t>((size_t)RADIX * SORT_BLOCKS_MAX + RADIX,
-                                               (size_t)CS_MAX_CELLS * (cw / CS_WARPS + 1));
+                                               (size_t)CS_MAX_KEYS * (cw / CS_WARPS + 1));
     w.hist = reinterpret_cast<uint32_t *>(take(4 * hist_words));
     w.n_eff = reinterpret_cast<int64_t *>(take(64));
     // stage 2 takes one of two paths: their buffers share one region
@@ -774,7 +780,7 @@ static BinWs carve(void *base, int64_t NV, int64_t cap)
     const size_t emit_end = o;
     o = region;
     w.rect = reinterpret_cast<uint64_t *>(take(8 * NV));
-    w.wcnt = reinterpret_cast<uint16_t *>(take(2 * (size_t)CS_MAX_CELLS * cw));
+    w.wpre = reinterpret_cast<uint16_t *>(take(2 * (size_t)CS_MAX_KEYS * cw));
     w.bytes = std::max(emit_end, o);
     return w;
 }
@@ -856,10 +862,8 @@ extern "C" gs_status gs_bin_sort(const gs_projected *proj, int64_t n, int V, int
         cur ^= 1;
     }
     const uint32_t *svals = w.dv[cur];
-    // ---- stage 2 as a counting sort when the keys' grids fit in shared memory
-    const int bins_y = bins_y_of(H, bin), gx = bins_x + 1;
-    const int cells = V * (bins_y + 1) * gx;
-    if (cells <= CS_MAX_CELLS) {
+    // ---- stage 2 as a counting sort when the per-warp key tables fit in shared memory
+    if (nkeys <= CS_MAX_KEYS) {
         CsParams cp{};
         cp.svals = svals;
         cp.mean2d = reinterpret_cast<const float2 *>(proj->mean2d);
@@ -867,28 +871,26 @@ extern "C" gs_status gs_bin_sort(const gs_projected *proj, int64_t n, int V, int
         cp.depth = proj->depth;
         cp.NV = NV;
         cp.n = n;
+        cp.inv_n = 1.0f / (float)n;
+        cp.inv_bin = 1.0f / (float)bin;
         cp.tx = tx;
         cp.ty = ty;
         cp.bin = bin;
         cp.bins_x = bins_x;
-        cp.bins_y = bins_y;
         cp.bins = bins;
         cp.V = V;
-        cp.gx = gx;
-        cp.cells = cells;
         cp.nkeys = (int)nkeys;
-        cp.inv_n = 1.0f / (float)n;
-        cp.inv_bin = 1.0f / (float)bin;
+        cp.kp = cs_pad_keys(nkeys);
         cp.NW = cs_warps(NV, num_sms());
         const int G = (int)(cp.NW / CS_WARPS);
         cp.hist = w.hist;
-        cp.wcnt = w.wcnt;
+        cp.wpre = w.wpre;
         cp.rect = w.rect;
         cp.n_eff = w.n_eff;
         cp.vals = vals;
         cp.keys = keys;
-        const int smem_count = CS_WARPS * cells * (int)sizeof(int);
-        const int smem_place = (int)nkeys * (int)(sizeof(uint32_t) + CS_WARPS * sizeof(uint16_t));
+        const int smem_count = CS_WARPS * (cp.kp / 2) * (int)sizeof(uint32_t);
+        const int smem_place = cp.kp * (int)(sizeof(uint32_t) + CS_WARPS * sizeof(uint16_t));
         set_smem_limit((const void *)cs_count_kernel, smem_count, st);
         set_smem_limit((const void *)cs_place_kernel, smem_place, st);
         note_launch();
