@@ -122,11 +122,20 @@ __global__ void __launch_bounds__(SORT_THREADS, 4) radix_scatter_kernel(SortPass
     __shared__ uint32_t s_k[SORT_TILE], s_v[SORT_TILE];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;
+    const int64_t n = pass_n(s);
     int64_t beg, end;
-    block_range(pass_n(s), s.G, blockIdx.x, beg, end);
+    block_range(n, s.G, blockIdx.x, beg, end);
     {
         // digit base = exclusive scan of the digit totals (RADIX == threads)
         uint32_t tot = s.hist[(int64_t)RADIX * s.G + tid];
+        // one digit holds every item: the pass keeps the order, a copy
+        if (__syncthreads_or((int64_t)tot == n)) {
+            for (int64_t i = beg + tid; i < end; i += SORT_THREADS) {
+                s.kout[i] = s.kin[i];
+                s.vout[i] = s.vin[i];
+            }
+            return;
+        }
         uint32_t inc = tot;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {

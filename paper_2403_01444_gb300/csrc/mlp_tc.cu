@@ -37,14 +37,16 @@ struct FwdSmem {
     uint32_t tmem;
 };
 
+// The backward's buffers are shared between the stages of a tile where
+// their lives do not overlap, so that two CTAs fit on an SM (about 110 KB
+// each): a1 holds the encoding (stage 1) then the output gradient G
+// (stage 2); hbuf holds H1, dH2 and dH1 in turn; AT holds [H2^T; dH2^T]
+// until the stage-3 MMAs (dW3 among them) have read it, then [dH1^T; dH2^T].
 struct BwdSmem {
-    bf16 AT[192 * TM];  // rows: H2^T (0..63), dH2^T (64..127), dH1^T (128..191); K = tile rows
+    bf16 AT[128 * TM];  // A of the weight-gradient MMAs; K = tile rows
     bf16 BT[112 * TM];  // rows: H1^T (0..63), enc^T (64..95), G^T (96..111)
-    bf16 a1[TM * 32];
-    bf16 h1a[TM * 64];
-    bf16 g2a[TM * 64];
-    bf16 g1a[TM * 64];
-    bf16 ga[TM * 16];
+    bf16 a1[TM * 32];   // enc (K = 32), then G (K = 16)
+    bf16 hbuf[TM * 64]; // H1, dH2, dH1 (K = 64)
     bf16 w1[64 * 32];   // [out][in]
     bf16 w2[64 * 64];
     bf16 w3t[64 * 16];  // [hidden][out], out padded to 16
@@ -53,6 +55,8 @@ struct BwdSmem {
     unsigned long long mbar;
     uint32_t tmem;
 };
+// two CTAs an SM: 228 KB of shared memory, 1 KB reserved per CTA, 1 KB of alignment slack
+static_assert(2 * (sizeof(BwdSmem) + 1024 + 1024) <= 228 * 1024, "backward tile buffers too large");
 
 // Arguments of the MLP kernels.  The standalone MLP reads encodings and
 // writes raw outputs; the fused cache kernels (FUSED = true) also encode the
@@ -373,7 +377,7 @@ __global__ void __launch_bounds__(TM, 4) mlp_tc_fwd_kernel(TcParams p)
 }
 
 template <typename ET, bool FUSED>
-__global__ void __launch_bounds__(TM) mlp_tc_bwd_kernel(TcParams p)
+__global__ void __launch_bounds__(TM, 2) mlp_tc_bwd_kernel(TcParams p)
 {
     extern __shared__ unsigned char smem_raw[];
     BwdSmem &S = *aligned_smem<BwdSmem>(smem_raw);
@@ -412,8 +416,8 @@ __global__ void __launch_bounds__(TM) mlp_tc_bwd_kernel(TcParams p)
     const uint32_t id64 = idesc_bf16_f32(128, 64), id32 = idesc_bf16_f32(128, 32);
     const uint32_t id96 = idesc_bf16_f32(128, 96), id16 = idesc_bf16_f32(128, 16);
     const uint32_t sAT = smem_u32(S.AT), sBT = smem_u32(S.BT);
-    const uint32_t sa1 = smem_u32(S.a1), sh1 = smem_u32(S.h1a), sg2 = smem_u32(S.g2a);
-    const uint32_t sg1 = smem_u32(S.g1a), sga = smem_u32(S.ga);
+    const uint32_t sa1 = smem_u32(S.a1), sga = sa1;
+    const uint32_t sh1 = smem_u32(S.hbuf), sg2 = sh1, sg1 = sh1;
     const uint32_t sw1 = smem_u32(S.w1), sw2 = smem_u32(S.w2), sw3t = smem_u32(S.w3t);
     const uint32_t sw2t = smem_u32(S.w2t), sw1t = smem_u32(S.w1t);
     const float scale = d_scale ? *d_scale : 1.f;
@@ -443,8 +447,6 @@ __global__ void __launch_bounds__(TM) mlp_tc_bwd_kernel(TcParams p)
 #pragma unroll
             for (int q = 0; q < 7; ++q) g[q] *= scale;
         }
-        st_chunk8(S.ga, t, 0, 16, g);
-        st_chunk8(S.ga, t, 8, 16, g + 8);
 #pragma unroll
         for (int q = 0; q < 16; ++q) S.BT[kmajor_off(96 + q, t, TM)] = __float2bfloat16_rn(g[q]);
         publish_smem();
@@ -469,7 +471,10 @@ __global__ void __launch_bounds__(TM) mlp_tc_bwd_kernel(TcParams p)
             else m1hi |= (uint32_t)pos << (k - 32);
         }
 #pragma unroll
-        for (int c = 0; c < 8; ++c) st_chunk8(S.h1a, t, 8 * c, 64, v + 8 * c);
+        for (int c = 0; c < 8; ++c) st_chunk8(S.hbuf, t, 8 * c, 64, v + 8 * c);
+        // G over the encoding, which stage 1 has read
+        st_chunk8(S.a1, t, 0, 16, g);
+        st_chunk8(S.a1, t, 8, 16, g + 8);
 #pragma unroll
         for (int j = 0; j < 64; ++j) S.BT[kmajor_off(j, t, TM)] = __float2bfloat16_rn(v[j]);
         publish_smem();
@@ -504,7 +509,7 @@ __global__ void __launch_bounds__(TM) mlp_tc_bwd_kernel(TcParams p)
             v[k] = pos ? v[k] : 0.f;
         }
 #pragma unroll
-        for (int c = 0; c < 8; ++c) st_chunk8(S.g2a, t, 8 * c, 64, v + 8 * c);
+        for (int c = 0; c < 8; ++c) st_chunk8(S.hbuf, t, 8 * c, 64, v + 8 * c);
 #pragma unroll
         for (int j = 0; j < 64; ++j) S.AT[kmajor_off(64 + j, t, TM)] = __float2bfloat16_rn(v[j]);
         publish_smem();
@@ -514,6 +519,12 @@ __global__ void __launch_bounds__(TM) mlp_tc_bwd_kernel(TcParams p)
             for (int ks = 0; ks < 4; ++ks)
                 mma_bf16(D0, desc_kmajor(sg2 + 256 * ks, 128, 1024), desc_kmajor(sw2t + 256 * ks, 128, 1024),
                          id64, ks > 0);
+            // dW3^T += H2^T G (rows 64..127 of this product are unused)
+            const uint32_t acc0 = done_tiles > 0 ? 1u : 0u;
+#pragma unroll
+            for (int ks = 0; ks < 8; ++ks)
+                mma_bf16(DW3, desc_kmajor(sAT + 256 * ks, 128, 2048),
+                         desc_kmajor(sBT + 12 * 2048 + 256 * ks, 128, 2048), id16, ks > 0 ? 1u : acc0);
             mma_commit(mbar);
         }
         if (!(ok = wait_mma(mbar, phase, p.wait_tries))) break;
@@ -526,9 +537,10 @@ __global__ void __launch_bounds__(TM) mlp_tc_bwd_kernel(TcParams p)
             v[k] = pos ? v[k] : 0.f;
         }
 #pragma unroll
-        for (int c = 0; c < 8; ++c) st_chunk8(S.g1a, t, 8 * c, 64, v + 8 * c);
+        for (int c = 0; c < 8; ++c) st_chunk8(S.hbuf, t, 8 * c, 64, v + 8 * c);
+        // dH1^T over H2^T, which the stage-3 MMAs have read
 #pragma unroll
-        for (int j = 0; j < 64; ++j) S.AT[kmajor_off(128 + j, t, TM)] = __float2bfloat16_rn(v[j]);
+        for (int j = 0; j < 64; ++j) S.AT[kmajor_off(j, t, TM)] = __float2bfloat16_rn(v[j]);
         publish_smem();
         if (t == 0) {
             fence_after_sync();
@@ -537,17 +549,12 @@ __global__ void __launch_bounds__(TM) mlp_tc_bwd_kernel(TcParams p)
             for (int ks = 0; ks < 4; ++ks)
                 mma_bf16(D0, desc_kmajor(sg1 + 256 * ks, 128, 1024), desc_kmajor(sw1t + 256 * ks, 128, 1024),
                          id32, ks > 0);
-            // [dW2 | . ; . | dW1] += [dH2^T ; dH1^T] [H1 | enc], K = the tile's rows
+            // [. | dW1 ; dW2 | .] += [dH1^T ; dH2^T] [H1 | enc], K = the tile's rows
             const uint32_t acc0 = done_tiles > 0 ? 1u : 0u;
 #pragma unroll
             for (int ks = 0; ks < 8; ++ks)
-                mma_bf16(DW, desc_kmajor(sAT + 8 * 2048 + 256 * ks, 128, 2048),
-                         desc_kmajor(sBT + 256 * ks, 128, 2048), id96, ks > 0 ? 1u : acc0);
-            // dW3^T += H2^T G (rows 64..127 of this product are unused)
-#pragma unroll
-            for (int ks = 0; ks < 8; ++ks)
-                mma_bf16(DW3, desc_kmajor(sAT + 256 * ks, 128, 2048),
-                         desc_kmajor(sBT + 12 * 2048 + 256 * ks, 128, 2048), id16, ks > 0 ? 1u : acc0);
+                mma_bf16(DW, desc_kmajor(sAT + 256 * ks, 128, 2048), desc_kmajor(sBT + 256 * ks, 128, 2048),
+                         id96, ks > 0 ? 1u : acc0);
             mma_commit(mbar);
         }
         if (!(ok = wait_mma(mbar, phase, p.wait_tries))) break;
@@ -572,23 +579,23 @@ __global__ void __launch_bounds__(TM) mlp_tc_bwd_kernel(TcParams p)
     if (ok && done_tiles > 0) {
         float v[16];
         if (warp < 2) {
-            const int j = t;  // dW2 row (output unit) j, dW3 column j
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                tmem_ld16(DW + lane + 16 * c, v);
-#pragma unroll
-                for (int i = 0; i < 16; ++i) atomicAdd(dW + 2048 + j * 64 + 16 * c + i, v[i]);
-            }
-            tmem_ld16(DW3 + lane, v);
-#pragma unroll
-            for (int o = 0; o < 7; ++o) atomicAdd(dW + 6144 + o * 64 + j, v[o]);
-        } else {
-            const int j = t - 64;  // dW1 row j
+            const int j = t;  // dW1 row (hidden unit) j, dW3 column j
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
                 tmem_ld16(DW + lane + 64 + 16 * c, v);
 #pragma unroll
                 for (int i = 0; i < 16; ++i) atomicAdd(dW + j * 32 + 16 * c + i, v[i]);
+            }
+            tmem_ld16(DW3 + lane, v);
+#pragma unroll
+            for (int o = 0; o < 7; ++o) atomicAdd(dW + 6144 + o * 64 + j, v[o]);
+        } else {
+            const int j = t - 64;  // dW2 row (output unit) j
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                tmem_ld16(DW + lane + 16 * c, v);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) atomicAdd(dW + 2048 + j * 64 + 16 * c + i, v[i]);
             }
         }
     }
@@ -638,7 +645,7 @@ static gs_status launch_bwd(TcParams p, cudaStream_t s)
 {
     p.wait_tries = s_wait_tries.load();
     const size_t smem = sizeof(BwdSmem) + 1024;
-    const int grid = (int)std::min<int64_t>(ceil_div(p.n, TM), num_sms());
+    const int grid = (int)std::min<int64_t>(ceil_div(p.n, TM), num_sms() * 2);
     set_smem_limit((const void *)mlp_tc_bwd_kernel<ET, FUSED>, (int)smem, s);
     note_launch();
     mlp_tc_bwd_kernel<ET, FUSED><<<grid, TM, smem, s>>>(p);
