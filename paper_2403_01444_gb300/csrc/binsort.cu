@@ -130,7 +130,26 @@ __global__ void __launch_bounds__(SORT_THREADS, 4) radix_scatter_kernel(SortPass
         uint32_t tot = s.hist[(int64_t)RADIX * s.G + tid];
         // one digit holds every item: the pass keeps the order, a copy
         if (__syncthreads_or((int64_t)tot == n)) {
-            for (int64_t i = beg + tid; i < end; i += SORT_THREADS) {
+            // 16 bytes a load where the buffers allow it (beg is a multiple
+            // of SORT_TILE; a caller's vals may be only 4-byte aligned), all
+            // of a thread's loads before its stores
+            const bool vec = ((reinterpret_cast<uintptr_t>(s.kin) | reinterpret_cast<uintptr_t>(s.vin) |
+                               reinterpret_cast<uintptr_t>(s.kout) | reinterpret_cast<uintptr_t>(s.vout)) &
+                              15) == 0;
+            const int64_t n4 = vec ? max((int64_t)0, end - beg) >> 2 : 0;
+            const uint4 *k4 = reinterpret_cast<const uint4 *>(s.kin + beg);
+            const uint4 *v4 = reinterpret_cast<const uint4 *>(s.vin + beg);
+            uint4 *ko = reinterpret_cast<uint4 *>(s.kout + beg);
+            uint4 *vo = reinterpret_cast<uint4 *>(s.vout + beg);
+            for (int64_t i0 = 0; i0 < n4; i0 += 2 * SORT_THREADS) {
+                const int64_t i = i0 + tid, j = i + SORT_THREADS;
+                uint4 a = {}, b = {}, c = {}, d = {};
+                if (i < n4) { a = k4[i]; b = v4[i]; }
+                if (j < n4) { c = k4[j]; d = v4[j]; }
+                if (i < n4) { ko[i] = a; vo[i] = b; }
+                if (j < n4) { ko[j] = c; vo[j] = d; }
+            }
+            for (int64_t i = beg + 4 * n4 + tid; i < end; i += SORT_THREADS) {
                 s.kout[i] = s.kin[i];
                 s.vout[i] = s.vin[i];
             }

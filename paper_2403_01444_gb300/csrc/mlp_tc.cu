@@ -577,14 +577,26 @@ __global__ void __launch_bounds__(TM, 2) mlp_tc_bwd_kernel(TcParams p)
         __syncthreads();
     }
     if (ok && done_tiles > 0) {
+        // one FP32 atomic per weight per CTA, four at a time where dW is
+        // 16-byte aligned (the rows of dW1 and dW2 are contiguous)
+        const bool v4 = (reinterpret_cast<uintptr_t>(dW) & 15) == 0;
+        auto add16 = [&](float *dst, const float *v) {
+            if (v4) {
+#pragma unroll
+                for (int i = 0; i < 16; i += 4)
+                    atomicAdd(reinterpret_cast<float4 *>(dst + i), make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]));
+            } else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) atomicAdd(dst + i, v[i]);
+            }
+        };
         float v[16];
         if (warp < 2) {
             const int j = t;  // dW1 row (hidden unit) j, dW3 column j
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
                 tmem_ld16(DW + lane + 64 + 16 * c, v);
-#pragma unroll
-                for (int i = 0; i < 16; ++i) atomicAdd(dW + j * 32 + 16 * c + i, v[i]);
+                add16(dW + j * 32 + 16 * c, v);
             }
             tmem_ld16(DW3 + lane, v);
 #pragma unroll
@@ -594,8 +606,7 @@ __global__ void __launch_bounds__(TM, 2) mlp_tc_bwd_kernel(TcParams p)
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 tmem_ld16(DW + lane + 16 * c, v);
-#pragma unroll
-                for (int i = 0; i < 16; ++i) atomicAdd(dW + 2048 + j * 64 + 16 * c + i, v[i]);
+                add16(dW + 2048 + j * 64 + 16 * c, v);
             }
         }
     }
