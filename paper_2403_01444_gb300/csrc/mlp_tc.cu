@@ -221,14 +221,52 @@ __device__ __forceinline__ void apply_bwd_row(const TcParams &p, int64_t row, fl
 }
 
 // W1 | W2 | W3 (bf16, [out][in] row-major) into K-major B operands.
-__device__ __forceinline__ void load_weights_fwd(const bf16 *w, bf16 *w1, bf16 *w2, bf16 *w3)
+// The BF16 weights (W1 [64][32], W2 [64][64], W3 [7][64] as stored, 6592
+// values) staged in shared memory 16 bytes a load, every load of a thread
+// issued before its stores: K-major W1 and W2 (the B operands of the forward
+// products) and, for the backward, K-major W1^T, W2^T and W3^T (outputs
+// padded to 16 with zeros).
+template <bool BWD>
+__device__ __forceinline__ void stage_weights(const bf16 *w, bf16 *w1, bf16 *w2, bf16 *w3t, bf16 *w2t,
+                                              bf16 *w1t)
 {
-    for (int e = threadIdx.x; e < 64 * 32; e += blockDim.x) w1[kmajor_off(e >> 5, e & 31, 32)] = w[e];
-    for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x)
-        w2[kmajor_off(e >> 6, e & 63, 64)] = w[2048 + e];
-    for (int e = threadIdx.x; e < 16 * 64; e += blockDim.x) {
-        int o = e >> 6, j = e & 63;
-        w3[kmajor_off(o, j, 64)] = o < 7 ? w[6144 + o * 64 + j] : __float2bfloat16(0.f);
+    constexpr int NQ = 6592 / 8;
+    constexpr int PER = (NQ + TM - 1) / TM;
+    const uint4 *src = reinterpret_cast<const uint4 *>(w);
+    uint4 q[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int k = threadIdx.x + i * TM;
+        q[i] = k < NQ ? src[k] : make_uint4(0u, 0u, 0u, 0u);
+    }
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int k = threadIdx.x + i * TM;
+        if (k >= NQ) continue;
+        const int e0 = 8 * k;
+        const bf16 *h = reinterpret_cast<const bf16 *>(&q[i]);
+        if (e0 < 2048) {
+            const int j = e0 >> 5, i0 = e0 & 31;  // W1[j][i0 .. i0 + 7]
+            *reinterpret_cast<uint4 *>(w1 + kmajor_off(j, i0, 32)) = q[i];
+            if (BWD) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) w1t[kmajor_off(i0 + c, j, 64)] = h[c];
+            }
+        } else if (e0 < 6144) {
+            const int f = e0 - 2048, j = f >> 6, k0 = f & 63;  // W2[j][k0 .. k0 + 7]
+            *reinterpret_cast<uint4 *>(w2 + kmajor_off(j, k0, 64)) = q[i];
+            if (BWD) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) w2t[kmajor_off(k0 + c, j, 64)] = h[c];
+            }
+        } else if (BWD) {
+            const int f = e0 - 6144, o = f >> 6, j0 = f & 63;  // W3[o][j0 .. j0 + 7]
+#pragma unroll
+            for (int c = 0; c < 8; ++c) w3t[kmajor_off(j0 + c, o, 16)] = h[c];
+        }
+    }
+    if (BWD) {
+        for (int e = threadIdx.x; e < 64 * 9; e += TM) w3t[kmajor_off(e / 9, 7 + e % 9, 16)] = __float2bfloat16(0.f);
     }
 }
 
@@ -260,9 +298,12 @@ __global__ void __launch_bounds__(TM, 4) mlp_tc_fwd_kernel(TcParams p)
     const bf16 *w = p.w;
     float *raw7 = p.raw7;
     const int t = threadIdx.x, warp = t >> 5;
-    for (int e = t; e < 64 * 32; e += TM) S.w1[kmajor_off(e >> 5, e & 31, 32)] = w[e];
-    for (int e = t; e < 64 * 64; e += TM) S.w2[kmajor_off(e >> 6, e & 63, 64)] = w[2048 + e];
-    for (int e = t; e < 7 * 64; e += TM) S.w3f[e] = p.w3f[e];
+    stage_weights<false>(w, S.w1, S.w2, nullptr, nullptr, nullptr);
+    if ((reinterpret_cast<uintptr_t>(p.w3f) & 15) == 0) {
+        if (t < 7 * 64 / 4) reinterpret_cast<float4 *>(S.w3f)[t] = reinterpret_cast<const float4 *>(p.w3f)[t];
+    } else {
+        for (int e = t; e < 7 * 64; e += TM) S.w3f[e] = p.w3f[e];
+    }
     const uint32_t mbar = smem_u32(&S.mbar);
     if (t == 0) mbar_init(mbar, 1);
     if (warp == 0) {
@@ -387,20 +428,7 @@ __global__ void __launch_bounds__(TM, 2) mlp_tc_bwd_kernel(TcParams p)
     const float *d_raw7 = p.d_raw7, *d_scale = p.d_scale;
     float *dW = p.dW, *d_enc = p.d_enc;
     const int t = threadIdx.x, warp = t >> 5;
-    load_weights_fwd(w, S.w1, S.w2, S.w3t);  // w3t slot reused below; rewritten transposed
-    __syncthreads();
-    for (int e = t; e < 64 * 16; e += TM) {
-        int j = e >> 4, o = e & 15;
-        S.w3t[kmajor_off(j, o, 16)] = o < 7 ? w[6144 + o * 64 + j] : __float2bfloat16(0.f);
-    }
-    for (int e = t; e < 64 * 64; e += TM) {
-        int j = e >> 6, k = e & 63;  // W2[j][k] -> w2t[k][j]
-        S.w2t[kmajor_off(k, j, 64)] = w[2048 + e];
-    }
-    for (int e = t; e < 64 * 32; e += TM) {
-        int j = e >> 5, i = e & 31;  // W1[j][i] -> w1t[i][j]
-        S.w1t[kmajor_off(i, j, 64)] = w[e];
-    }
+    stage_weights<true>(w, S.w1, S.w2, S.w3t, S.w2t, S.w1t);
     const uint32_t mbar = smem_u32(&S.mbar);
     if (t == 0) mbar_init(mbar, 1);
     if (warp == 0) {
