@@ -443,12 +443,12 @@ def run_ours(args):
         gs3.gs_bin_sort(r.proj, G.n, Vb, W, H, r.bin, r.capacity, r.vals, r.ranges, None, r.d_count, r.d_err, r.ws)
         E("t3")
         gs3.gs_raster_fwd(r.proj, G.n, Vb, W, H, r.bin, r.bg, r.vals, r.ranges, r.img, r.T_final, r.last,
-                          stats[0:2] if count_pairs else None)
+                          stats[0:2] if count_pairs else None, lists=r.lists)
         E("t4")
         st.loss(r.img, tg)
         E("t5")
         gs3.gs_raster_bwd(r.proj, G.n, Vb, W, H, r.bin, r.bg, r.vals, r.ranges, r.T_final, r.last,
-                          st.loss.d_img, r.grads, None, stats[2:4] if count_pairs else None)
+                          st.loss.d_img, r.grads, None, stats[2:4] if count_pairs else None, lists=r.lists)
         E("t6")
         gs3.gs_project_bwd(G, cd, Vb, W, H, r.grads, r.d_mean, r.d_quat, st.mean_t, st.quat_t)
         E("t7")

@@ -268,6 +268,21 @@ GS_API gs_status gs_bin_sort_noalloc(const gs_projected *proj, int64_t n, int V,
 
 /* ------------------------------------------------------------ compositing */
 
+/* The records a compositing forward staged for each tile, in list order (the
+ * per-tile lists of Section 3.2 after the footprint tests, up to where the
+ * tile's pixels stopped): for tile t of view v (i = v * tiles + t, tiles =
+ * ceil(W/16) * ceil(H/16), t = tile_y * ceil(W/16) + tile_x),
+ * rec[2 * (i * cap + j)] is the Gaussian index and rec[2 * (i * cap + j) + 1]
+ * the position in the bin's list of its j-th staged record, j < count[i];
+ * count[i] = -1 when the tile staged more than cap records.  Device memory
+ * owned by the caller: rec uint32[V * tiles * cap * 2] (8-byte aligned),
+ * count int32[V * tiles]; 1 <= cap <= 2^20. */
+typedef struct {
+    uint32_t *rec;
+    int32_t *count;
+    int32_t cap;
+} gs_tile_lists;
+
 /* Front-to-back alpha compositing (Section 3.2, Eq. 4), one 16x16 tile per
  * block.  Per pixel, over its tile's sorted list: power = -(A dx^2 + C dy^2)/2
  * - B dx dy with (dx, dy) = pixel centre - mean2d; skip if power > 0;
@@ -279,10 +294,12 @@ GS_API gs_status gs_bin_sort_noalloc(const gs_projected *proj, int64_t n, int V,
  * alpha-ellipse cannot reach 1/255 at any pixel centre of a tile (a margin
  * of 0.01 in the quadratic form) is not staged for that tile: every pixel
  * would skip it, so results are unchanged.  d_stats (device uint64[2], or
- * NULL) accumulates the (pixel, Gaussian) pairs evaluated and added. */
+ * NULL) accumulates the (pixel, Gaussian) pairs evaluated and added.  lists
+ * (or NULL) receives each tile's staged records for gs_raster_bwd. */
 GS_API gs_status gs_raster_fwd(const gs_projected *proj, int64_t n, int V, int W, int H, int bin,
                         const float *bg, const uint32_t *vals, const uint32_t *ranges, float *img,
-                        float *T_final, int32_t *last, uint64_t *d_stats, gs_stream stream);
+                        float *T_final, int32_t *last, uint64_t *d_stats, const gs_tile_lists *lists,
+                        gs_stream stream);
 
 /* Reverse of gs_raster_fwd: walks each pixel's list back to front from
  * `last`, recomputing T_i = T_{i+1} / (1 - alpha_i) from T_final (no per-pair
@@ -291,11 +308,15 @@ GS_API gs_status gs_raster_fwd(const gs_projected *proj, int64_t n, int V, int W
  * Overwrites grads[V][N][8] = dL/d(u, v, A, B, C, r, g, b) and, when non-NULL,
  * d_opacity[V][N].  bg is a host array of 3 floats.  d_stats (device
  * uint64[2], or NULL) accumulates the pairs walked and the pairs that had
- * contributed. */
+ * contributed.  lists (or NULL): written by the gs_raster_fwd call on the same
+ * proj, n, V, W, H, bin, vals and ranges; the reverse then stages a tile's
+ * records from its list instead of testing its bin's list again (a tile with
+ * count -1 is tested as without lists).  Results are the same either way. */
 GS_API gs_status gs_raster_bwd(const gs_projected *proj, int64_t n, int V, int W, int H, int bin,
                         const float *bg, const uint32_t *vals, const uint32_t *ranges,
                         const float *T_final, const int32_t *last, const float *d_img,
-                        float *grads, float *d_opacity, uint64_t *d_stats, gs_stream stream);
+                        float *grads, float *d_opacity, uint64_t *d_stats,
+                        const gs_tile_lists *lists, gs_stream stream);
 
 /* ------------------------------------------------------------------- loss */
 

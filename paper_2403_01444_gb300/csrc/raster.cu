@@ -61,6 +61,11 @@ struct RasterParams {
     float *grads;
     float *d_opacity;
     unsigned long long *stats;  // optional: [tested, contributing] (pixel, Gaussian) pairs
+    // optional per-tile lists of staged records (Gaussian, list position):
+    // written by the forward, read by the reverse
+    uint2 *tl_rec;
+    int32_t *tl_cnt;
+    int tl_cap;
 };
 
 // Add this thread's pair counts to the optional statistics words.
@@ -237,19 +242,26 @@ __global__ void __launch_bounds__(NT) raster_fwd2_kernel(RasterParams p)
     int last[2] = {0, 0};
     bool done[2] = {!in0, !in1};
     uint32_t n_tested = 0, n_contrib = 0;
+    const int64_t tg = (int64_t)view * gridDim.x + tile;  // the tile's list
+    int staged = 0;
     for (int base = 0; base < total; base += NT) {
         if (__syncthreads_count(done[0] && done[1]) == NT) break;
         const int k = base + tid;
         int64_t o = 0;
+        uint32_t g = 0;
         bool keep = false;
         float2 m;
         float4 co;
         if (k < total) {
-            o = vb + p.vals[range.x + k];
+            g = p.vals[range.x + k];
+            o = vb + g;
             keep = keep_record<BINNED>(p, o, tx_t, ty_t, m, co);
         }
         int cnt;
         const int slot = compact_slot<NT>(keep, s_wcnt, cnt);
+        if (slot >= 0 && p.tl_rec && staged + slot < p.tl_cap)
+            p.tl_rec[tg * p.tl_cap + staged + slot] = make_uint2(g, (uint32_t)k);
+        staged += cnt;
         if (slot >= 0) {
             s_xy[slot] = make_float4(m.x, m.y, -__log2f(255.f * co.w), 0.f);
             s_co[slot] = scale_conic(co);
@@ -305,6 +317,7 @@ __global__ void __launch_bounds__(NT) raster_fwd2_kernel(RasterParams p)
         }
     }
     if (STATS) flush_stats(p.stats, n_tested, n_contrib);
+    if (p.tl_rec && tid == 0) p.tl_cnt[tg] = staged <= p.tl_cap ? staged : -1;
     const int64_t HW = (int64_t)p.H * p.W;
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
@@ -486,21 +499,41 @@ __global__ void __launch_bounds__(NT) raster_bwd2_kernel(RasterParams p)
     __syncthreads();
     const int maxlast = s_max;
     uint32_t n_tested = 0, n_contrib = 0;
-    for (int hi = maxlast; hi > 0; hi -= NT) {
+    // with the forward's list of the tile, its records are staged straight
+    // from it (list order is position order; the few past maxlast are
+    // skipped by the position test); otherwise the bin's list is tested again
+    const int64_t tg = (int64_t)view * gridDim.x + tile;
+    const int listed = p.tl_rec ? p.tl_cnt[tg] : -1;
+    for (int hi = listed >= 0 ? listed : maxlast; hi > 0; hi -= NT) {
         const int lo = max(0, hi - NT);
-        const int k = lo + tid;
         int64_t o = 0;
         uint32_t g = 0;
+        int k = 0;
         bool keep = false;
         float2 m;
         float4 co;
-        if (k < hi) {
-            g = p.vals[range.x + k];
-            o = vb + g;
-            keep = keep_record<BINNED>(p, o, tx_t, ty_t, m, co);
+        int cnt, slot;
+        if (listed >= 0) {
+            if (lo + tid < hi) {
+                const uint2 e = p.tl_rec[tg * p.tl_cap + lo + tid];
+                g = e.x;
+                k = (int)e.y;
+                o = vb + g;
+                m = p.mean2d[o];
+                co = p.conic_op[o];
+                keep = true;
+            }
+            cnt = hi - lo;
+            slot = keep ? tid : -1;
+        } else {
+            k = lo + tid;
+            if (k < hi) {
+                g = p.vals[range.x + k];
+                o = vb + g;
+                keep = keep_record<BINNED>(p, o, tx_t, ty_t, m, co);
+            }
+            slot = compact_slot<NT>(keep, s_wcnt, cnt);
         }
-        int cnt;
-        const int slot = compact_slot<NT>(keep, s_wcnt, cnt);
         if (slot >= 0) {
             s_g[slot] = g;
             s_xy[slot] = make_float4(m.x, m.y, -__log2f(255.f * co.w), 0.f);
@@ -577,8 +610,16 @@ __global__ void __launch_bounds__(NT) raster_bwd2_kernel(RasterParams p)
 
 static gs_status fill(const gs_projected *proj, int64_t n, int V, int W, int H, int bin,
                       const float *bg, const uint32_t *vals, const uint32_t *ranges,
-                      RasterParams &p)
+                      const gs_tile_lists *lists, RasterParams &p)
 {
+    if (lists) {
+        GS_REQUIRE(lists->rec && lists->count && lists->cap >= 1 && lists->cap <= (1 << 20),
+                   "raster: tile lists need rec, count and 1 <= cap <= 2^20");
+        GS_REQUIRE(aligned(lists->rec, 8) && aligned(lists->count, 4), "raster: misaligned tile lists");
+        p.tl_rec = reinterpret_cast<uint2 *>(lists->rec);
+        p.tl_cnt = lists->count;
+        p.tl_cap = lists->cap;
+    }
     GS_REQUIRE(proj && vals && ranges, "raster: null argument");
     GS_REQUIRE(n >= 0 && V >= 1 && V <= GS_MAX_VIEWS, "raster: bad n or V");
     GS_REQUIRE(W > 0 && H > 0 && W <= 16384 && H <= 16384, "raster: bad image size");
@@ -623,10 +664,11 @@ using namespace gs3;
 extern "C" gs_status gs_raster_fwd(const gs_projected *proj, int64_t n, int V, int W, int H,
                                    int bin, const float *bg, const uint32_t *vals,
                                    const uint32_t *ranges, float *img, float *T_final,
-                                   int32_t *last, uint64_t *d_stats, gs_stream stream)
+                                   int32_t *last, uint64_t *d_stats, const gs_tile_lists *lists,
+                                   gs_stream stream)
 {
     RasterParams p{};
-    gs_status st = fill(proj, n, V, W, H, bin, bg, vals, ranges, p);
+    gs_status st = fill(proj, n, V, W, H, bin, bg, vals, ranges, lists, p);
     if (st != GS_OK) return st;
     GS_REQUIRE(img && T_final && last, "gs_raster_fwd: null output");
     p.img = img;
@@ -651,10 +693,11 @@ extern "C" gs_status gs_raster_bwd(const gs_projected *proj, int64_t n, int V, i
                                    int bin, const float *bg, const uint32_t *vals,
                                    const uint32_t *ranges, const float *T_final,
                                    const int32_t *last, const float *d_img, float *grads,
-                                   float *d_opacity, uint64_t *d_stats, gs_stream stream)
+                                   float *d_opacity, uint64_t *d_stats, const gs_tile_lists *lists,
+                                   gs_stream stream)
 {
     RasterParams p{};
-    gs_status st = fill(proj, n, V, W, H, bin, bg, vals, ranges, p);
+    gs_status st = fill(proj, n, V, W, H, bin, bg, vals, ranges, lists, p);
     if (st != GS_OK) return st;
     GS_REQUIRE(T_final && last && d_img && (grads || n == 0), "gs_raster_bwd: null argument");
     GS_REQUIRE(aligned(grads, 16), "gs_raster_bwd: grads must be 16-byte aligned");

@@ -31,6 +31,7 @@ STAGE1_LR_FINAL = 0.01
 STAGE1_EPS = 1e-6
 WARMUP_EPS = 1e-15
 DEFAULT_BIN = 4             # tiles per bin side of the binned pair lists (autotuned best at 1352x1014)
+TILE_LIST_CAP = 1024        # staged records a tile keeps for the reverse (more: the reverse re-tests its bin list)
 
 
 def _i32(*shape, device="cuda"):
@@ -64,6 +65,9 @@ class Rasterizer:
         self.img = _f32(V, 3, H, W, device=device)
         self.T_final = _f32(V, H, W, device=device)
         self.last = _i32(V, H, W, device=device)
+        # the records each tile's forward staged, for the reverse
+        self.lists = gs3.TileLists(V, W, H, TILE_LIST_CAP, device)
+        self._listed = False
         self.set_n(n)
         self.set_capacity(capacity)
 
@@ -88,19 +92,24 @@ class Rasterizer:
         ws = gs3.gs_bin_sort_workspace_size(self.n_max, self.V, self.W, self.H, self.capacity)
         self.ws = torch.empty(ws, dtype=torch.uint8, device=self.device)
 
-    def forward(self, g: Gaussians, cams_dev, mean=None, quat=None, stream=None, keys=None):
+    def forward(self, g: Gaussians, cams_dev, mean=None, quat=None, stream=None, keys=None,
+                lists: bool = True):
+        """lists: keep each tile's staged records for backward() (a render
+        with no reverse to follow can leave them out)."""
         V, W, H, n = self.V, self.W, self.H, self.n
         gs3.gs_project(g, cams_dev, V, W, H, self.proj, mean, quat, stream, self.d_err)
         gs3.gs_bin_sort(self.proj, n, V, W, H, self.bin, self.capacity, self.vals, self.ranges, keys,
                         self.d_count, self.d_err, self.ws, stream)
         gs3.gs_raster_fwd(self.proj, n, V, W, H, self.bin, self.bg, self.vals, self.ranges, self.img,
-                          self.T_final, self.last, None, stream)
+                          self.T_final, self.last, None, stream, lists=self.lists if lists else None)
+        self._listed = lists
         return self.img
 
     def backward(self, g: Gaussians, cams_dev, d_img, mean=None, quat=None, stream=None):
         V, W, H, n = self.V, self.W, self.H, self.n
         gs3.gs_raster_bwd(self.proj, n, V, W, H, self.bin, self.bg, self.vals, self.ranges,
-                          self.T_final, self.last, d_img, self.grads, None, None, stream)
+                          self.T_final, self.last, d_img, self.grads, None, None, stream,
+                          lists=self.lists if self._listed else None)
         gs3.gs_project_bwd(g, cams_dev, V, W, H, self.grads, self.d_mean, self.d_quat, mean, quat,
                            stream)
         return self.d_mean, self.d_quat
@@ -441,7 +450,7 @@ class Stage2:
         self.loss(r.img, target, stream)
         d_op = self._d_op[:V * n]
         gs3.gs_raster_bwd(r.proj, n, V, W, H, r.bin, r.bg, r.vals, r.ranges, r.T_final, r.last,
-                          self.loss.d_img, r.grads, d_op, None, stream)
+                          self.loss.d_img, r.grads, d_op, None, stream, lists=r.lists)
         gs3.gs_project_bwd_full(g, cams_dev, V, W, H, r.grads, d_op, self.n_fixed, self.n_add,
                                 self.d_mean, self.d_quat, self.d_scale, self.d_ologit, self.d_sh,
                                 stream)
@@ -846,7 +855,7 @@ class Renderer:
                       stream)
         if self.sh_rot is not None:
             gs3.gs_sh_rotate(g.quat, self.quat_t, g.sh, n, g.sh_deg, self.sh_rot, stream)
-        return self.raster.forward(self.g_rot, cams_dev, self.mean_t, self.quat_t, stream)
+        return self.raster.forward(self.g_rot, cams_dev, self.mean_t, self.quat_t, stream, lists=False)
 
     def capture(self, cams_dev):
         side = torch.cuda.Stream()

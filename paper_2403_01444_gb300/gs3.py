@@ -56,6 +56,10 @@ class GsProjected(ctypes.Structure):
                 ("depth", c_void_p), ("radius", c_void_p), ("tiles_touched", c_void_p)]
 
 
+class GsTileLists(ctypes.Structure):
+    _fields_ = [("rec", c_void_p), ("count", c_void_p), ("cap", ctypes.c_int32)]
+
+
 class GsHashgrid(ctypes.Structure):
     _fields_ = [("levels", c_int32), ("features", c_int32), ("log2_table", c_int32),
                 ("n_min", c_int32), ("n_max", c_int32), ("aabb", c_float * 6)]
@@ -260,20 +264,40 @@ def _bg(bg):
     return a
 
 
+class TileLists:
+    """gs_tile_lists: each tile's staged records (Gaussian, list position),
+    written by gs_raster_fwd and read by gs_raster_bwd; cap records a tile."""
+
+    def __init__(self, V: int, W: int, H: int, cap: int = 1024, device="cuda"):
+        tiles = ((W + 15) // 16) * ((H + 15) // 16)
+        self.cap = int(cap)
+        self.rec = torch.zeros(V * tiles * self.cap * 2, dtype=torch.int32, device=device)
+        self.count = torch.full((V * tiles,), -1, dtype=torch.int32, device=device)
+
+    def struct(self) -> GsTileLists:
+        return GsTileLists(_ptr(self.rec), _ptr(self.count), self.cap)
+
+
+def _lists(lists: Optional[TileLists]):
+    return None if lists is None else ctypes.byref(lists.struct())
+
+
 def gs_raster_fwd(proj: Projected, n, V, W, H, bin, bg, vals, ranges, img, T_final, last,
-                  stats=None, stream=None):
+                  stats=None, stream=None, lists: Optional[TileLists] = None):
     po = proj.struct()
+    tl = _lists(lists)
     _check("gs_raster_fwd", lib().gs_raster_fwd(
         ctypes.byref(po), c_int64(n), c_int(V), c_int(W), c_int(H), c_int(bin), _bg(bg), _ptr(vals), _ptr(ranges),
-        _ptr(img), _ptr(T_final), _ptr(last), _ptr(stats), _stream(stream)))
+        _ptr(img), _ptr(T_final), _ptr(last), _ptr(stats), tl, _stream(stream)))
 
 
 def gs_raster_bwd(proj: Projected, n, V, W, H, bin, bg, vals, ranges, T_final, last, d_img, grads,
-                  d_opacity=None, stats=None, stream=None):
+                  d_opacity=None, stats=None, stream=None, lists: Optional[TileLists] = None):
     po = proj.struct()
+    tl = _lists(lists)
     _check("gs_raster_bwd", lib().gs_raster_bwd(
         ctypes.byref(po), c_int64(n), c_int(V), c_int(W), c_int(H), c_int(bin), _bg(bg), _ptr(vals), _ptr(ranges),
-        _ptr(T_final), _ptr(last), _ptr(d_img), _ptr(grads), _ptr(d_opacity), _ptr(stats),
+        _ptr(T_final), _ptr(last), _ptr(d_img), _ptr(grads), _ptr(d_opacity), _ptr(stats), tl,
         _stream(stream)))
 
 

@@ -50,12 +50,22 @@ def test_binning_and_compositing_reject_bad_arguments(L):
     _fails(L, L.gs_bin_sort(byref(p), c_int64(10), 1, 64, 48, 0, c_int64(100), FAKE, FAKE, None,
                             FAKE, FAKE, FAKE, c_size_t(1 << 20), None), "bin")
     _fails(L, L.gs_raster_fwd(byref(p), c_int64(10), 1, 64, 48, 65, None, FAKE, FAKE, FAKE, FAKE,
-                              FAKE, None, None), "bin")
+                              FAKE, None, None, None), "bin")
     # views outside 1..GS_MAX_VIEWS, image too large
     _fails(L, L.gs_raster_fwd(byref(p), c_int64(10), 0, 64, 48, 1, None, FAKE, FAKE, FAKE, FAKE,
-                              FAKE, None, None), "bad n or V")
+                              FAKE, None, None, None), "bad n or V")
     _fails(L, L.gs_raster_fwd(byref(p), c_int64(10), 1, 20000, 48, 1, None, FAKE, FAKE, FAKE, FAKE,
-                              FAKE, None, None), "image size")
+                              FAKE, None, None, None), "image size")
+
+
+def test_compositing_rejects_bad_tile_lists(L):
+    p = _proj()
+    for lists, words in ((gs3.GsTileLists(FAKE, FAKE, 0), "cap"), (gs3.GsTileLists(None, FAKE, 16), "rec"),
+                         (gs3.GsTileLists(c_void_p(0x10004), FAKE, 16), "misaligned")):
+        _fails(L, L.gs_raster_fwd(byref(p), c_int64(10), 1, 64, 48, 1, None, FAKE, FAKE, FAKE, FAKE,
+                                  FAKE, None, byref(lists), None), words)
+        _fails(L, L.gs_raster_bwd(byref(p), c_int64(10), 1, 64, 48, 1, None, FAKE, FAKE, FAKE, FAKE,
+                                  FAKE, FAKE, None, None, byref(lists), None), words)
 
 
 def test_binning_rejects_wrapping_entry_counts(L):

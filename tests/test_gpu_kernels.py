@@ -201,6 +201,59 @@ def test_binned_raster_equals_per_tile(bin):
     assert rel_err(o2.cpu().numpy(), o1.cpu().numpy()) <= 1e-5
 
 
+@pytest.mark.parametrize("bin,cap", [(1, "all"), (4, "all"), (4, "half")])
+def test_reverse_from_tile_lists_equals_retested(bin, cap):
+    """The reverse staged from the forward's per-tile lists (gs_tile_lists)
+    equals the reverse that tests the bin's list again: the same gradients (to
+    the order of the FP32 atomics).  Each list holds records of its tile's
+    bin list in position order.  With room for every tile's records all
+    tiles are listed; with a cap at the median count the tiles with more
+    staged records say so (count -1) and take the re-testing path, the
+    others the list."""
+    V, N, W, H = 2, 3000, 300, 170
+    rec = scenes.random_projected(V, N, W, H, np.random.default_rng(52))
+    p = projected_from_records(rec)
+    r, _ = gpu_bin_sort(p, N, V, W, H, keys=False, bin=bin)
+    bg = (0.1, 0.2, 0.3)
+    gs3.gs_raster_fwd(p, N, V, W, H, bin, bg, r.vals, r.ranges, r.img, r.T_final, r.last)
+    img = r.img.clone()
+    full = gs3.TileLists(V, W, H, 4096, DEV)  # above N: room for any tile
+    gs3.gs_raster_fwd(p, N, V, W, H, bin, bg, r.vals, r.ranges, r.img, r.T_final, r.last, lists=full)
+    torch.cuda.synchronize()
+    assert torch.equal(img, r.img)  # writing the lists leaves the forward as it is
+    staged = full.count.cpu().numpy()
+    assert (staged >= 0).all()
+    cap = 4096 if cap == "all" else max(1, int(np.median(staged)))
+    lists = gs3.TileLists(V, W, H, cap, DEV)
+    gs3.gs_raster_fwd(p, N, V, W, H, bin, bg, r.vals, r.ranges, r.img, r.T_final, r.last, lists=lists)
+    torch.cuda.synchronize()
+    cnt = lists.count.cpu().numpy()
+    np.testing.assert_array_equal(cnt, np.where(staged <= cap, staged, -1))
+    recs = lists.rec.cpu().numpy().view(np.uint32).reshape(-1, cap, 2)
+    vals, ranges = r.vals.cpu().numpy().view(np.uint32), r.ranges.cpu().numpy().view(np.uint32)
+    tx, ty = math.ceil(W / 16), math.ceil(H / 16)
+    bins_x, bins = math.ceil(tx / bin), math.ceil(tx / bin) * math.ceil(ty / bin)
+    assert (cnt > 0).any()
+    if cap < 4096:
+        assert (cnt == -1).any()
+    for i in np.nonzero(cnt > 0)[0]:
+        v, t_ = divmod(int(i), tx * ty)
+        start = int(ranges[v * bins + (t_ // tx // bin) * bins_x + (t_ % tx) // bin, 0])
+        e = recs[i, :cnt[i]]
+        assert np.all(np.diff(e[:, 1].astype(np.int64)) > 0)
+        np.testing.assert_array_equal(vals[start + e[:, 1]], e[:, 0])
+    d_img = t(np.random.default_rng(53).normal(size=(V, 3, H, W)))
+    g1, g2 = torch.zeros(V, N, 8, device=DEV), torch.zeros(V, N, 8, device=DEV)
+    o1, o2 = torch.zeros(V, N, device=DEV), torch.zeros(V, N, device=DEV)
+    gs3.gs_raster_bwd(p, N, V, W, H, bin, bg, r.vals, r.ranges, r.T_final, r.last, d_img, g1, o1)
+    gs3.gs_raster_bwd(p, N, V, W, H, bin, bg, r.vals, r.ranges, r.T_final, r.last, d_img, g2, o2,
+                      lists=lists)
+    torch.cuda.synchronize()
+    assert float(g1.abs().max()) > 0
+    assert rel_err(g2.cpu().numpy(), g1.cpu().numpy()) <= 1e-5
+    assert rel_err(o2.cpu().numpy(), o1.cpu().numpy()) <= 1e-5
+
+
 # ------------------------------------------------------------------ projection
 def _proj_scene(seed, N=3000, deg=3, W=200, H=150):
     rng = np.random.default_rng(seed)
