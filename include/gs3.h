@@ -401,7 +401,8 @@ GS_API gs_status ntc_warmup_loss(const float *raw7, int64_t n, float *d_raw7, fl
 
 /* ------------------------------------------------------------- optimiser */
 
-/* Sets d_state->found_inf = 1 if any of g[n] is not finite. */
+/* Sets d_state->found_inf = 1 if any of g[n] is not finite.  g must be
+ * 16-byte aligned (GS_ERR_INVALID_ARG otherwise). */
 GS_API gs_status gs_check_finite(const float *g, int64_t n, gs_train_state *d_state, gs_stream stream);
 
 /* Bias-corrected Adam (Suppl. A) on p[n] with gradient g * (1 / loss_scale)

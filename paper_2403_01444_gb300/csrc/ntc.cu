@@ -334,12 +334,24 @@ __global__ void __launch_bounds__(256) warmup_kernel(const float *raw7, int64_t 
 }
 
 // ----------------------------------------------------------- optimiser
-__global__ void check_finite_kernel(const float *g, int64_t n, gs_train_state *st)
+// Sixteen values per thread as four float4 loads, all in flight at once
+// (g 16-byte aligned); block 0 also takes the scalar tail.
+__global__ void __launch_bounds__(256) check_finite_kernel(const float *g, int64_t n, gs_train_state *st)
 {
+    const int64_t n4 = n / 4;
+    const float4 *g4 = reinterpret_cast<const float4 *>(g);
+    const int64_t q0 = (int64_t)blockIdx.x * blockDim.x * 4 + threadIdx.x;
+    float4 q[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int64_t i = q0 + (int64_t)k * blockDim.x;
+        q[k] = i < n4 ? g4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     bool bad = false;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        bad |= !isfinite(g[i]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) bad |= !(isfinite(q[k].x) && isfinite(q[k].y) && isfinite(q[k].z) && isfinite(q[k].w));
+    if (blockIdx.x == 0)
+        for (int64_t i = 4 * n4 + threadIdx.x; i < n; i += blockDim.x) bad |= !isfinite(g[i]);
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) st->found_inf = 1;
 }
 
@@ -610,7 +622,8 @@ extern "C" gs_status gs_check_finite(const float *g, int64_t n, gs_train_state *
     GS_REQUIRE(d_state && n >= 0, "gs_check_finite: null state or negative n");
     if (n == 0) return GS_OK;
     GS_REQUIRE(g, "gs_check_finite: null argument");
-    int blocks = (int)std::min<int64_t>(ceil_div(n, 256), num_sms() * 8);
+    GS_REQUIRE(aligned(g, 16), "gs_check_finite: g must be 16-byte aligned");
+    const int blocks = (int)std::max<int64_t>(ceil_div(n / 4, 256 * 4), 1);
     note_launch();
     check_finite_kernel<<<blocks, 256, 0, as_stream(stream)>>>(g, n, d_state);
     return launch_status("gs_check_finite");

@@ -467,6 +467,23 @@ def test_adam_parity_skip_and_shadow():
     assert s.loss_scale == 128.0 and s.found_inf == 0 and s.step == 5
 
 
+@pytest.mark.parametrize("n", [1, 7, 4099, 70001])
+def test_check_finite_sees_every_position(n):
+    """gs_check_finite flags a non-finite value wherever it is: the vector
+    body, the scalar tail, the last block; a finite array leaves the flag."""
+    st = gs3.new_train_state(1.0)
+    g = torch.ones(n, device=DEV)
+    gs3.gs_check_finite(g, st)
+    assert gs3.read_train_state(st).found_inf == 0
+    for pos in sorted({0, n // 2, n - 1, max(0, n - 5)}):
+        for bad in (float("nan"), float("inf"), -float("inf")):
+            st = gs3.new_train_state(1.0)
+            g = torch.ones(n, device=DEV)
+            g[pos] = bad
+            gs3.gs_check_finite(g, st)
+            assert gs3.read_train_state(st).found_inf == 1, (n, pos, bad)
+
+
 def test_adam_rate_schedule():
     """The rate decays exponentially from lr to lr * ratio over decay_steps
     applied updates and stays there; a skipped update does not advance it."""
