@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(LTHREADS, SSIM_FWD_MIN_BLOCKS)
 }
 
 #ifndef SSIM_BWD_MIN_BLOCKS
-#define SSIM_BWD_MIN_BLOCKS 3
+#define SSIM_BWD_MIN_BLOCKS 4  // 62 registers, no spills
 #endif
 __global__ void __launch_bounds__(LTHREADS, SSIM_BWD_MIN_BLOCKS) ssim_bwd_kernel(LossParams p)
 {
