@@ -18,6 +18,24 @@ constexpr int BWD_CHUNK = BWD_CHUNK_RECORDS;  // records per backward reduction 
 #define FWD_UNROLL 8
 #endif
 constexpr int kBwdUnroll = BWD_UNROLL, kFwdUnroll = FWD_UNROLL;
+// Optional minimum blocks per SM for the compositing kernels' launch bounds
+// (0: none, the compiler's register choice).
+#ifndef FWD_MIN_BLOCKS
+#define FWD_MIN_BLOCKS 0
+#endif
+#ifndef BWD_MIN_BLOCKS
+#define BWD_MIN_BLOCKS 0
+#endif
+#if FWD_MIN_BLOCKS > 0
+#define FWD_BOUNDS __launch_bounds__(128, FWD_MIN_BLOCKS)
+#else
+#define FWD_BOUNDS __launch_bounds__(128)
+#endif
+#if BWD_MIN_BLOCKS > 0
+#define BWD_BOUNDS __launch_bounds__(128, BWD_MIN_BLOCKS)
+#else
+#define BWD_BOUNDS __launch_bounds__(128)
+#endif
 #ifndef RASTER_WARP_BLOCKS
 #define RASTER_WARP_BLOCKS 1     // 1: each warp owns a compact block of the tile; 0: rows
 #endif
@@ -218,7 +236,7 @@ __device__ __forceinline__ int compact_slot(bool keep, int *s_wcnt, int &count)
 // colour), two lanes of a register pair per instruction.  The arithmetic of an
 // added pixel is the scalar one, rounding for rounding.
 template <bool BINNED, bool STATS>
-__global__ void __launch_bounds__(NT) raster_fwd2_kernel(RasterParams p)
+__global__ void FWD_BOUNDS raster_fwd2_kernel(RasterParams p)
 {
     __shared__ float4 s_xy[NT];
     __shared__ float4 s_co[NT];
@@ -442,7 +460,7 @@ __device__ __forceinline__ bool unblend_pair(PixBwd2 &P, int pos, float4 co, flo
 }
 
 template <bool WANT_OP, bool BINNED, bool STATS>
-__global__ void __launch_bounds__(NT) raster_bwd2_kernel(RasterParams p)
+__global__ void BWD_BOUNDS raster_bwd2_kernel(RasterParams p)
 {
     constexpr int NW = NT / 32;
     constexpr int NV = WANT_OP ? 9 : 8;
