@@ -84,6 +84,18 @@ def test_full_size_view_render_and_gradients(cfg_index, view, record_property):
     got = rast.grads.cpu().numpy()
     for sl in (slice(0, 2), slice(2, 5), slice(5, 8)):
         assert rel_err(got[..., sl], grads[..., sl]) <= 1e-3
+    # the reverse staged from the forward's per-tile lists (as the training
+    # step runs it) gives the same gradients, to the order of the FP32 atomics;
+    # the densest tiles of the 1M-Gaussian view overflow the list (about 2 %)
+    # and take the re-testing path
+    listed = int((rast.lists.count >= 0).sum()) / rast.lists.count.numel()
+    record_property("listed_tiles", listed)
+    assert listed > 0.9, listed
+    gs3.gs_raster_bwd(rast.proj, g.n, 1, W, H, rast.bin, rast.bg, rast.vals, rast.ranges,
+                      rast.T_final, rast.last, torch.from_numpy(d_img.astype(np.float32)).to(DEV),
+                      rast.grads, lists=rast.lists)
+    torch.cuda.synchronize()
+    assert rel_err(rast.grads.cpu().numpy(), got) <= 1e-5
 
 
 def test_full_resolution_binning_bit_exact():
