@@ -6,12 +6,13 @@
 //   1. the V*N (view, Gaussian) entries are sorted by depth bits -- 4
 //      byte-digit passes on the FP32 depth bits, stable, so equal depths keep
 //      the index order (the views interleave; stage 2's key holds the view);
+//      a pass whose digit is the same for every entry is a copy;
 //   2. the pairs of every entry's bins are ordered on the (view * bins + bin)
 //      key alone, stably, so each list keeps its entries' depth order.  When
-//      the keys' difference grids fit in shared memory this is a counting
-//      sort that writes each pair once, straight to its place; otherwise the
-//      pairs are emitted in entry order and radix-sorted on the key,
-//      ceil(log2(V * bins) / 8) byte passes.
+//      the per-warp key tables fit in shared memory (V * bins <= CS_MAX_KEYS)
+//      this is a counting sort that writes each pair once, straight to its
+//      place; otherwise the pairs are emitted in entry order and radix-sorted
+//      on the key, ceil(log2(V * bins) / 8) byte passes.
 // A bin is bin x bin tiles.  With bin = 1 the lists are the per-tile lists;
 // with larger bins every tile of a bin shares the bin's depth-ordered list and
 // the compositing kernels keep, on the fly, the entries whose footprint
