@@ -375,14 +375,26 @@ __device__ __forceinline__ float adam_rate(const gs_adam &hp, int t)
     return hp.lr * exp2f(f * log2f(hp.lr_final_ratio));
 }
 
-// Sixteen parameters per thread: four float4 groups, strided by the block
-// size so that every load is coalesced, all loaded before any is stored (16
-// loads in flight per thread); block 0 also takes the scalar tail.  The
-// arithmetic per parameter is adam_one's.
-constexpr int ADAM_GROUPS = 4;
+// ADAM_GROUPS float4 groups of parameters per thread, strided by the block
+// size so that every load is coalesced, all loaded before any is stored;
+// block 0 also takes the scalar tail.  The arithmetic per parameter is
+// adam_one's.  One group (4 parameters, 49 registers, many resident blocks)
+// measured faster on the 3.3M-parameter table than four (130 registers).
+#ifndef ADAM_GROUPS_N
+#define ADAM_GROUPS_N 1  // one float4 per thread (49 registers) measured fastest after an L2 flush
+#endif
+#ifndef ADAM_MIN_BLOCKS
+#define ADAM_MIN_BLOCKS 0
+#endif
+#if ADAM_MIN_BLOCKS > 0
+#define ADAM_BOUNDS __launch_bounds__(256, ADAM_MIN_BLOCKS)
+#else
+#define ADAM_BOUNDS __launch_bounds__(256)
+#endif
+constexpr int ADAM_GROUPS = ADAM_GROUPS_N;
 
 template <int SHADOW>
-__global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ p, float *__restrict__ g,
+__global__ void ADAM_BOUNDS adam_kernel(float *__restrict__ p, float *__restrict__ g,
                                                    float *__restrict__ m, float *__restrict__ v,
                                                    int64_t n, gs_adam hp,
                                                    const gs_train_state *__restrict__ st,
