@@ -336,16 +336,31 @@ GS_API gs_status gs_loss_l1_dssim(const float *img, const float *target, int pla
 /* Number of table entries (rows) of the grid; < 0 on invalid arguments. */
 GS_API int64_t ntc_hashgrid_entries(const gs_hashgrid *grid);
 
+/* The order in which the encoding kernels visit the Gaussians, for locality
+ * in the table: order[n] = the Gaussians sorted by the Morton code (10 bits
+ * an axis) of their mean within the grid's box, ties by index.  Any
+ * permutation of 0..n-1 gives the same encodings; this one makes the 32
+ * Gaussians of a warp neighbours, so at the coarse levels their corners fall
+ * in few table rows.  ws: scratch of ntc_spatial_order_workspace_size(n)
+ * bytes, 256-byte aligned; order is device uint32[n]. */
+GS_API size_t ntc_spatial_order_workspace_size(int64_t n);
+GS_API gs_status ntc_spatial_order(const float *mean, int64_t n, const gs_hashgrid *grid, uint32_t *order,
+                                   void *ws, size_t ws_bytes, gs_stream stream);
+
 /* enc[n][L*F] = per level, trilinear interpolation of the 8 corner features
  * around the normalised mean (Section 4.1).  table_dtype: GS_F16 or GS_F32;
- * enc_dtype: GS_F32 or GS_BF16. */
+ * enc_dtype: GS_F32 or GS_BF16.  order (device uint32[n], or NULL for 0..n-1):
+ * a permutation of the Gaussians giving the order of the work (for example
+ * ntc_spatial_order's); the results are the same for any. */
 GS_API gs_status ntc_encode_fwd(const float *mean, int64_t n, const gs_hashgrid *grid, const void *table,
-                         int table_dtype, void *enc, int enc_dtype, gs_stream stream);
+                         int table_dtype, void *enc, int enc_dtype, const uint32_t *order, gs_stream stream);
 
 /* d_table[entries][F] += trilinear-weighted scatter of d_enc[n][L*F]
- * (FP32 atomics; the caller zeroes d_table between steps -- adam_step does). */
+ * (FP32 atomics; the caller zeroes d_table between steps -- adam_step does).
+ * order: as for ntc_encode_fwd (the sums differ only in the order of the
+ * atomic additions). */
 GS_API gs_status ntc_encode_bwd(const float *mean, int64_t n, const gs_hashgrid *grid, const float *d_enc,
-                         float *d_table, gs_stream stream);
+                         float *d_table, const uint32_t *order, gs_stream stream);
 
 /* raw7[n][7] = W3 relu(W2 relu(W1 enc)) (Section 4.1 Eq. 5).  enc_dtype
  * GS_F32 or GS_BF16. */

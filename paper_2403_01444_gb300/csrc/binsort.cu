@@ -23,6 +23,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "sort.cuh"
 
 namespace gs3 {
 
@@ -824,6 +825,31 @@ static gs_status run_pass(SortPass s, int64_t grid_items_hint, cudaStream_t st)
     note_launch();
     radix_scatter_kernel<<<s.G, SORT_THREADS, 0, st>>>(s);
     return launch_status("radix pass");
+}
+
+size_t radix_sort_hist_words() { return (size_t)RADIX * SORT_BLOCKS_MAX + RADIX; }
+
+gs_status radix_sort_pairs(uint32_t *k[2], uint32_t *v[2], int64_t n, int bits, uint32_t *hist, int &cur,
+                           cudaStream_t st)
+{
+    cur = 0;
+    const int G = (int)std::min<int64_t>(sort_blocks(), std::max<int64_t>(1, ceil_div(n, SORT_TILE)));
+    for (int shift = 0; shift < bits; shift += 8) {
+        SortPass s{};
+        s.kin = k[cur];
+        s.vin = v[cur];
+        s.kout = k[cur ^ 1];
+        s.vout = v[cur ^ 1];
+        s.d_n = nullptr;
+        s.n_host = n;
+        s.shift = shift;
+        s.hist = hist;
+        s.G = G;
+        gs_status e = run_pass(s, n, st);
+        if (e != GS_OK) return e;
+        cur ^= 1;
+    }
+    return GS_OK;
 }
 
 }  // namespace gs3

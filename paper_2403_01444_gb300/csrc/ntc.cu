@@ -11,6 +11,7 @@
 
 #include "common.cuh"
 #include "ntc.cuh"
+#include "sort.cuh"
 
 namespace gs3 {
 
@@ -68,38 +69,72 @@ __device__ __forceinline__ float2 load_feat<float>(const float *table, uint32_t 
     return reinterpret_cast<const float2 *>(table)[row];
 }
 
-// One thread per (Gaussian, level): threadIdx.x is the level, threadIdx.y
-// the Gaussian within the block, so a Gaussian's levels gather in parallel
-// and its 2L outputs are written by adjacent threads.
-template <typename TT, typename ET>
-__global__ void __launch_bounds__(128) encode_fwd_kernel(const float *mean, int64_t n, GridParams g,
-                                                         const TT *table, ET *enc)
+// The encoding kernels work on blocks of 32 Gaussians with one warp per level
+// (ENC_THREADS = 32 x kMaxLevels threads; warps at l >= L idle): a warp's
+// lanes gather the same level for 32 Gaussians, so when the Gaussians are in
+// spatial order (ntc_spatial_order) the coarse levels' corners of a warp
+// fall in a few table rows.  Block b takes the Gaussians order[32 b ..
+// 32 b + 31] (the identity without an order); an order entry >= n is
+// skipped.  Rows of the encoding and of its gradient pass through shared
+// memory so that global accesses are whole rows.
+constexpr int ENC_G = 32;
+constexpr int ENC_THREADS = 32 * kMaxLevels;
+
+__device__ __forceinline__ int64_t enc_row(const uint32_t *order, int64_t j, int64_t n)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.y + threadIdx.y;
-    const int l = threadIdx.x;
-    if (i >= n || l >= g.L) return;
-    const float3 m = make_float3(mean[3 * i], mean[3 * i + 1], mean[3 * i + 2]);
-    uint32_t idx[8];
-    float w[8];
-    level_corners(g, l, m, idx, w);
-    float2 t[8];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) t[c] = load_feat<TT>(table, idx[c]);
-    float f0 = 0.f, f1 = 0.f;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        f0 = fmaf(w[c], t[c].x, f0);
-        f1 = fmaf(w[c], t[c].y, f1);
-    }
-    store2(enc + i * (int64_t)(2 * g.L) + 2 * l, f0, f1);
+    if (j >= n) return -1;
+    const int64_t i = order ? (int64_t)order[j] : j;
+    return i < n ? i : -1;
 }
 
-__global__ void __launch_bounds__(128) encode_bwd_kernel(const float *mean, int64_t n, GridParams g,
-                                                         const float *d_enc, float *d_table)
+template <typename TT, typename ET>
+__global__ void __launch_bounds__(ENC_THREADS) encode_fwd_kernel(const float *mean, int64_t n, GridParams g,
+                                                                 const TT *table, ET *enc,
+                                                                 const uint32_t *order)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.y + threadIdx.y;
+    __shared__ float s_out[ENC_G][2 * kMaxLevels + 1];
+    const int lane = threadIdx.x & 31, l = threadIdx.x >> 5;
+    const int64_t j0 = (int64_t)blockIdx.x * ENC_G;
+    const int64_t i = enc_row(order, j0 + lane, n);
+    if (i >= 0 && l < g.L) {
+        const float3 m = make_float3(mean[3 * i], mean[3 * i + 1], mean[3 * i + 2]);
+        uint32_t idx[8];
+        float w[8];
+        level_corners(g, l, m, idx, w);
+        float2 t[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) t[c] = load_feat<TT>(table, idx[c]);
+        float f0 = 0.f, f1 = 0.f;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            f0 = fmaf(w[c], t[c].x, f0);
+            f1 = fmaf(w[c], t[c].y, f1);
+        }
+        s_out[lane][2 * l] = f0;
+        s_out[lane][2 * l + 1] = f1;
+    }
+    __syncthreads();
+    // row r of the block: threads 16 r .. 16 r + 15 write its 2L values in pairs
+    const int r = threadIdx.x >> 4, q = threadIdx.x & 15;
+    const int64_t ir = enc_row(order, j0 + r, n);
+    if (ir >= 0 && q < g.L) store2(enc + ir * (int64_t)(2 * g.L) + 2 * q, s_out[r][2 * q], s_out[r][2 * q + 1]);
+}
+
+// Reverse: one thread per (Gaussian, level), threadIdx.x the level and
+// threadIdx.y the Gaussian (block b takes order[8 b ..], the identity
+// without an order).  A Gaussian no view saw has a zero gradient and its
+// threads return at once; the lanes of a warp scatter into different levels'
+// tables.  (The level-major mapping with in-warp combining of the coarse
+// levels' atomics was slower here, where most gradients are zero.)
+constexpr int ENC_BWD_G = 8;
+
+__global__ void __launch_bounds__(128) encode_bwd_kernel(const float *mean, int64_t n, GridParams g,
+                                                         const float *d_enc, float *d_table,
+                                                         const uint32_t *order)
+{
+    const int64_t i = enc_row(order, (int64_t)blockIdx.x * blockDim.y + threadIdx.y, n);
     const int l = threadIdx.x;
-    if (i >= n || l >= g.L) return;
+    if (i < 0 || l >= g.L) return;
     const float2 gg = reinterpret_cast<const float2 *>(d_enc + i * (int64_t)(2 * g.L))[l];
     if (gg.x == 0.f && gg.y == 0.f) return;
     const float3 m = make_float3(mean[3 * i], mean[3 * i + 1], mean[3 * i + 2]);
@@ -111,8 +146,31 @@ __global__ void __launch_bounds__(128) encode_bwd_kernel(const float *mean, int6
         atomicAdd(reinterpret_cast<float2 *>(d_table) + idx[c], make_float2(w[c] * gg.x, w[c] * gg.y));
 }
 
-// Block shape of the encoding kernels: (levels, Gaussians per block).
-static dim3 encode_block(const GridParams &g) { return dim3(g.L, std::max(1, 128 / g.L)); }
+// Morton code (10 bits an axis) of every mean within the grid's box, and the
+// identity as the values to sort.
+__device__ __forceinline__ uint32_t spread10(uint32_t x)
+{
+    x &= 0x3ffu;
+    x = (x | (x << 16)) & 0x30000ffu;
+    x = (x | (x << 8)) & 0x300f00fu;
+    x = (x | (x << 4)) & 0x30c30c3u;
+    x = (x | (x << 2)) & 0x9249249u;
+    return x;
+}
+
+__global__ void morton_kernel(const float *mean, int64_t n, GridParams g, uint32_t *code, uint32_t *idx)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t q[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float x = (mean[3 * i + k] - g.amin[k]) / g.ext[k];
+        q[k] = (uint32_t)(fminf(fmaxf(x, 0.f), 1.f) * 1023.f);
+    }
+    code[i] = spread10(q[0]) | (spread10(q[1]) << 1) | (spread10(q[2]) << 2);
+    idx[i] = (uint32_t)i;
+}
 
 // ------------------------------------------------------------ MLP (SIMT)
 template <typename ET>
@@ -494,7 +552,7 @@ extern "C" int64_t ntc_hashgrid_entries(const gs_hashgrid *grid)
 
 extern "C" gs_status ntc_encode_fwd(const float *mean, int64_t n, const gs_hashgrid *grid,
                                    const void *table, int table_dtype, void *enc, int enc_dtype,
-                                   gs_stream stream)
+                                   const uint32_t *order, gs_stream stream)
 {
     GridParams g;
     int64_t total;
@@ -504,25 +562,27 @@ extern "C" gs_status ntc_encode_fwd(const float *mean, int64_t n, const gs_hashg
     GS_REQUIRE(n >= 0, "ntc_encode_fwd: negative n");
     if (n == 0) return GS_OK;
     GS_REQUIRE(mean && table && enc, "ntc_encode_fwd: null argument");
-    const dim3 blk = encode_block(g);
-    const unsigned blocks = (unsigned)ceil_div(n, blk.y);
+    const unsigned blocks = (unsigned)ceil_div(n, ENC_G);
     cudaStream_t s = as_stream(stream);
     note_launch();
     if (table_dtype == GS_F16 && enc_dtype == GS_F32)
-        encode_fwd_kernel<__half, float><<<blocks, blk, 0, s>>>(mean, n, g, (const __half *)table, (float *)enc);
+        encode_fwd_kernel<__half, float><<<blocks, ENC_THREADS, 0, s>>>(mean, n, g, (const __half *)table,
+                                                                        (float *)enc, order);
     else if (table_dtype == GS_F16)
-        encode_fwd_kernel<__half, __nv_bfloat16><<<blocks, blk, 0, s>>>(mean, n, g, (const __half *)table,
-                                                                        (__nv_bfloat16 *)enc);
+        encode_fwd_kernel<__half, __nv_bfloat16><<<blocks, ENC_THREADS, 0, s>>>(
+            mean, n, g, (const __half *)table, (__nv_bfloat16 *)enc, order);
     else if (enc_dtype == GS_F32)
-        encode_fwd_kernel<float, float><<<blocks, blk, 0, s>>>(mean, n, g, (const float *)table, (float *)enc);
+        encode_fwd_kernel<float, float><<<blocks, ENC_THREADS, 0, s>>>(mean, n, g, (const float *)table,
+                                                                      (float *)enc, order);
     else
-        encode_fwd_kernel<float, __nv_bfloat16><<<blocks, blk, 0, s>>>(mean, n, g, (const float *)table,
-                                                                      (__nv_bfloat16 *)enc);
+        encode_fwd_kernel<float, __nv_bfloat16><<<blocks, ENC_THREADS, 0, s>>>(
+            mean, n, g, (const float *)table, (__nv_bfloat16 *)enc, order);
     return launch_status("ntc_encode_fwd");
 }
 
 extern "C" gs_status ntc_encode_bwd(const float *mean, int64_t n, const gs_hashgrid *grid,
-                                   const float *d_enc, float *d_table, gs_stream stream)
+                                   const float *d_enc, float *d_table, const uint32_t *order,
+                                   gs_stream stream)
 {
     GridParams g;
     int64_t total;
@@ -531,10 +591,46 @@ extern "C" gs_status ntc_encode_bwd(const float *mean, int64_t n, const gs_hashg
     if (n == 0) return GS_OK;
     GS_REQUIRE(mean && d_enc && d_table, "ntc_encode_bwd: null argument");
     GS_REQUIRE(aligned(d_table, 8) && aligned(d_enc, 8), "ntc_encode_bwd: misaligned");
-    const dim3 blk = encode_block(g);
     note_launch();
-    encode_bwd_kernel<<<(unsigned)ceil_div(n, blk.y), blk, 0, as_stream(stream)>>>(mean, n, g, d_enc, d_table);
+    const dim3 blk(g.L, ENC_BWD_G);
+    encode_bwd_kernel<<<(unsigned)ceil_div(n, ENC_BWD_G), blk, 0, as_stream(stream)>>>(mean, n, g, d_enc, d_table,
+                                                                                      order);
     return launch_status("ntc_encode_bwd");
+}
+
+extern "C" size_t ntc_spatial_order_workspace_size(int64_t n)
+{
+    if (n < 0 || n > (int64_t(1) << 32) - 1) return 0;
+    const size_t a = ((size_t)4 * std::max<int64_t>(n, 1) + 255) & ~size_t(255);
+    return 3 * a + ((radix_sort_hist_words() * 4 + 255) & ~size_t(255));
+}
+
+extern "C" gs_status ntc_spatial_order(const float *mean, int64_t n, const gs_hashgrid *grid,
+                                      uint32_t *order, void *ws, size_t ws_bytes, gs_stream stream)
+{
+    GridParams g;
+    int64_t total;
+    GS_REQUIRE(grid_params(grid, g, total), "ntc_spatial_order: invalid hash grid");
+    GS_REQUIRE(n >= 0 && n <= (int64_t(1) << 32) - 1, "ntc_spatial_order: n out of range");
+    if (n == 0) return GS_OK;
+    GS_REQUIRE(mean && order && ws, "ntc_spatial_order: null argument");
+    GS_REQUIRE(aligned(ws, 256), "ntc_spatial_order: workspace must be 256-byte aligned");
+    const size_t need = ntc_spatial_order_workspace_size(n);
+    GS_REQUIRE(ws_bytes >= need, "ntc_spatial_order: workspace too small (%zu < %zu)", ws_bytes, need);
+    const size_t a = ((size_t)4 * n + 255) & ~size_t(255);
+    char *w = reinterpret_cast<char *>(ws);
+    // the values start in `order` and end there: 30 key bits take four passes
+    uint32_t *k[2] = {reinterpret_cast<uint32_t *>(w), reinterpret_cast<uint32_t *>(w + a)};
+    uint32_t *v[2] = {order, reinterpret_cast<uint32_t *>(w + 2 * a)};
+    uint32_t *hist = reinterpret_cast<uint32_t *>(w + 3 * a);
+    cudaStream_t s = as_stream(stream);
+    note_launch();
+    morton_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(mean, n, g, k[0], v[0]);
+    int cur = 0;
+    gs_status e = radix_sort_pairs(k, v, n, 30, hist, cur, s);
+    if (e != GS_OK) return e;
+    if (cur != 0) cudaMemcpyAsync(order, v[cur], sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s);
+    return launch_status("ntc_spatial_order");
 }
 
 extern "C" gs_status ntc_mlp_fwd(const void *enc, int enc_dtype, int64_t n, const gs_mlp *w,

@@ -257,6 +257,18 @@ class Stage1:
         self.state = gs3.new_train_state(loss_scale, device)
         self.aabb = list(ntc.grid.aabb)
         self.track = None  # (accum [n], denom [n]) while tracking view-space gradients
+        # the encoding kernels' order over the Gaussians (refresh_order); kept
+        # in place so that captured graphs read the refreshed order
+        self.visit = torch.empty(max(n, 1), dtype=torch.int32, device=device)[:n]
+        self._visit_ws = torch.empty(max(gs3.ntc_spatial_order_workspace_size(n), 1), dtype=torch.uint8,
+                                     device=device)
+        self.refresh_order()
+
+    def refresh_order(self, stream=None):
+        """Spatial order of the encoding kernels' work over the Gaussians (for
+        table locality; any permutation gives the same results).  Called when
+        the Gaussians' means change (each frame of a stream)."""
+        gs3.ntc_spatial_order(self.g.mean, self.g.n, self.ntc.grid, self.visit, self._visit_ws, stream)
 
     def track_viewspace(self, on: bool = True):
         """Start (zeroed) or stop accumulating the view-space positional
@@ -286,7 +298,7 @@ class Stage1:
             gs3.ntc_fused_fwd(g.mean, g.quat, n, ntc.grid, ntc.table.shadow, ntc.mlp_struct(), self.order,
                               self.mean_t, self.quat_t, self.raw7, self.enc, stream)
             return self.mean_t, self.quat_t
-        gs3.ntc_encode_fwd(g.mean, n, ntc.grid, ntc.table_for_encode(), self.enc, stream)
+        gs3.ntc_encode_fwd(g.mean, n, ntc.grid, ntc.table_for_encode(), self.enc, stream, order=self.visit)
         gs3.ntc_mlp_fwd(self.enc, n, ntc.mlp_struct(), self.raw7, stream)
         gs3.ntc_apply(g.mean, g.quat, self.raw7, n, self.aabb, self.order, self.mean_t, self.quat_t,
                       stream)
@@ -314,6 +326,8 @@ class Stage1:
                           self.d_raw7, stream)
         gs3.ntc_mlp_bwd(self.enc, n, ntc.mlp_struct(), self.d_raw7, self.loss_scale_view(),
                         ntc.mlp.g, self.d_enc, stream)
+        # the reverse runs in index order: in spatial order neighbouring
+        # Gaussians' atomics meet on the same table rows
         gs3.ntc_encode_bwd(g.mean, n, ntc.grid, self.d_enc, ntc.table.g, stream)
         return self.loss.d_loss
 
@@ -551,6 +565,7 @@ class Streamer:
         self.targets.copy_(targets)
         self.ntc.reset_to(*self.warm)
         st.reset_state()
+        st.refresh_order()  # the carried means moved
         if self.track is None:
             self.track = st.track_viewspace(True)
             st.track_viewspace(False)
@@ -808,11 +823,13 @@ def warmup(ntc: NTC, g: Gaussians, iters=3000, noise=0.01, extent=2.0, seed=0, s
     state = gs3.new_train_state(loss_scale, g.mean.device)
     scale_view = state[0:4].view(torch.float32)
     mu = torch.empty_like(g.mean)
+    # the noisy means stay near the Gaussians: their spatial order serves
+    visit = gs3.spatial_order(g.mean, n, ntc.grid, stream)
     for _ in range(iters):
         # the noise the method draws is an input of the kernels
         torch.randn(mu.shape, generator=gen, device=mu.device, out=mu)
         mu.mul_(noise * extent).add_(g.mean)
-        gs3.ntc_encode_fwd(mu, n, ntc.grid, ntc.table_for_encode(), enc, stream)
+        gs3.ntc_encode_fwd(mu, n, ntc.grid, ntc.table_for_encode(), enc, stream, order=visit)
         gs3.ntc_mlp_fwd(enc, n, ntc.mlp_struct(), raw7, stream)
         gs3.ntc_warmup_loss(raw7, n, d_raw7, d_loss, stream)
         gs3.ntc_mlp_bwd(enc, n, ntc.mlp_struct(), d_raw7, scale_view, ntc.mlp.g, d_enc, stream)
@@ -842,6 +859,7 @@ class Renderer:
         self.g_rot = (Gaussians(g.mean, g.quat, g.scale, g.opacity_logit, self.sh_rot, g.sh_deg)
                       if sh_rotation else g)
         self.enc = torch.zeros(n, 32, dtype=ntc.enc_dtype(), device=device)
+        self.visit = gs3.spatial_order(g.mean, n, ntc.grid)  # the Gaussians are fixed
         self.raw7 = _f32(n, 7, device=device)
         self.mean_t = _f32(n, 3, device=device)
         self.quat_t = _f32(n, 4, device=device)
@@ -849,7 +867,7 @@ class Renderer:
 
     def frame(self, cams_dev, stream=None):
         g, ntc, n = self.g, self.ntc, self.g.n
-        gs3.ntc_encode_fwd(g.mean, n, ntc.grid, ntc.table_for_encode(), self.enc, stream)
+        gs3.ntc_encode_fwd(g.mean, n, ntc.grid, ntc.table_for_encode(), self.enc, stream, order=self.visit)
         gs3.ntc_mlp_fwd(self.enc, n, ntc.mlp_struct(), self.raw7, stream)
         gs3.ntc_apply(g.mean, g.quat, self.raw7, n, self.aabb, self.order, self.mean_t, self.quat_t,
                       stream)

@@ -318,15 +318,36 @@ def ntc_hashgrid_entries(grid: GsHashgrid) -> int:
 _DT = {torch.float32: GS_F32, torch.float16: GS_F16, torch.bfloat16: GS_BF16}
 
 
-def ntc_encode_fwd(mean, n, grid: GsHashgrid, table, enc, stream=None):
+def ntc_encode_fwd(mean, n, grid: GsHashgrid, table, enc, stream=None, order=None):
     _check("ntc_encode_fwd", lib().ntc_encode_fwd(
         _ptr(mean), c_int64(n), ctypes.byref(grid), _ptr(table), c_int(_DT[table.dtype]), _ptr(enc),
-        c_int(_DT[enc.dtype]), _stream(stream)))
+        c_int(_DT[enc.dtype]), _ptr(order), _stream(stream)))
 
 
-def ntc_encode_bwd(mean, n, grid: GsHashgrid, d_enc, d_table, stream=None):
+def ntc_encode_bwd(mean, n, grid: GsHashgrid, d_enc, d_table, stream=None, order=None):
     _check("ntc_encode_bwd", lib().ntc_encode_bwd(
-        _ptr(mean), c_int64(n), ctypes.byref(grid), _ptr(d_enc), _ptr(d_table), _stream(stream)))
+        _ptr(mean), c_int64(n), ctypes.byref(grid), _ptr(d_enc), _ptr(d_table), _ptr(order), _stream(stream)))
+
+
+def ntc_spatial_order_workspace_size(n) -> int:
+    L = lib()
+    L.ntc_spatial_order_workspace_size.restype = ctypes.c_size_t
+    return int(L.ntc_spatial_order_workspace_size(c_int64(n)))
+
+
+def ntc_spatial_order(mean, n, grid: GsHashgrid, order, ws, stream=None):
+    _check("ntc_spatial_order", lib().ntc_spatial_order(
+        _ptr(mean), c_int64(n), ctypes.byref(grid), _ptr(order), _ptr(ws), ctypes.c_size_t(ws.numel()),
+        _stream(stream)))
+
+
+def spatial_order(mean, n, grid: GsHashgrid, stream=None):
+    """ntc_spatial_order of the first n means into a new int32[n] tensor
+    (the order's device words)."""
+    order = torch.empty(max(n, 1), dtype=torch.int32, device=mean.device)
+    ws = torch.empty(max(ntc_spatial_order_workspace_size(n), 1), dtype=torch.uint8, device=mean.device)
+    ntc_spatial_order(mean, n, grid, order, ws, stream)
+    return order[:n]
 
 
 def ntc_mlp_fwd(enc, n, mlp: GsMlp, raw7, stream=None):

@@ -17,7 +17,8 @@ def _declared():
 def test_header_declares_the_boundary():
     names = _declared()
     for want in ("gs_project", "gs_project_bwd", "gs_bin_sort", "gs_raster_fwd", "gs_raster_bwd",
-                 "gs_loss_l1_dssim", "ntc_encode_fwd", "ntc_encode_bwd", "ntc_mlp_fwd",
+                 "gs_loss_l1_dssim", "ntc_encode_fwd", "ntc_encode_bwd", "ntc_spatial_order",
+                 "ntc_spatial_order_workspace_size", "ntc_mlp_fwd",
                  "ntc_mlp_bwd", "ntc_apply", "ntc_apply_bwd", "adam_step"):
         assert want in names
 

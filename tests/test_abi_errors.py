@@ -100,14 +100,22 @@ def test_cache_and_optimiser_reject_bad_arguments(L):
     bad_grid = gs3.hashgrid()
     bad_grid.levels = 0
     _fails(L, L.ntc_encode_fwd(FAKE, c_int64(10), byref(bad_grid), FAKE, gs3.GS_F16, FAKE,
-                               gs3.GS_F32, None), "invalid hash grid")
+                               gs3.GS_F32, None, None), "invalid hash grid")
     good = gs3.hashgrid()
     _fails(L, L.ntc_encode_fwd(FAKE, c_int64(10), byref(good), FAKE, gs3.GS_BF16, FAKE, gs3.GS_F32,
-                               None), "table dtype")
+                               None, None), "table dtype")
     _fails(L, L.adam_step(FAKE, FAKE, FAKE, FAKE, c_int64(16), None, FAKE, None, gs3.GS_NONE, None),
            "adam_step")
     _fails(L, L.gs_sh_rotate(FAKE, FAKE, FAKE, c_int64(10), 4, FAKE, None), "sh_deg")
     # empty inputs are valid and do nothing (no device work either)
     assert L.gs_sh_rotate(FAKE, FAKE, FAKE, c_int64(0), 3, FAKE, None) == gs3.GS_OK
     assert L.ntc_encode_fwd(None, c_int64(0), byref(good), None, gs3.GS_F16, None, gs3.GS_F32,
-                            None) == gs3.GS_OK
+                            None, None) == gs3.GS_OK
+    L.ntc_spatial_order_workspace_size.restype = c_size_t
+    assert L.ntc_spatial_order_workspace_size(c_int64(-1)) == 0
+    need = L.ntc_spatial_order_workspace_size(c_int64(1000))
+    assert need > 0
+    _fails(L, L.ntc_spatial_order(FAKE, c_int64(1000), byref(good), FAKE, FAKE, c_size_t(need - 1), None),
+           "workspace too small")
+    _fails(L, L.ntc_spatial_order(FAKE, c_int64(1000), byref(bad_grid), FAKE, FAKE, c_size_t(need), None),
+           "invalid hash grid")

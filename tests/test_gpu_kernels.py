@@ -373,6 +373,50 @@ def test_encode_bwd_parity():
     assert_grad_close(dt.cpu().numpy(), want, rtol=1e-3)
 
 
+@pytest.mark.parametrize("n", [1, 33, 70001])
+def test_spatial_order_and_ordered_encoding(n):
+    """ntc_spatial_order: the Gaussians sorted stably by the Morton code of
+    their mean in the grid's box (10 bits an axis, as the definition: the
+    FP32 coordinate (m - min) / extent clamped to [0, 1] times 1023,
+    truncated), computed here in numpy; the encoding visited in that order is
+    the same, bit for bit, and its reverse the same to the order of the FP32
+    atomics."""
+    og, gg = _grid_pair()
+    rng = np.random.default_rng(n + 7)
+    mu = rng.uniform(-1.6, 1.6, size=(n, 3)).astype(np.float32)
+    mu[: n // 3] = mu[0]  # ties: equal codes keep the index order
+    amin = np.float32(gg.aabb[0:3]); ext = np.float32(gg.aabb[3:6]) - amin
+    x = np.clip((mu - amin) / ext, np.float32(0), np.float32(1)) * np.float32(1023)
+    q = x.astype(np.uint32)
+
+    def spread(v):
+        v = v.astype(np.uint64) & 0x3FF
+        v = (v | (v << 16)) & 0x30000FF
+        v = (v | (v << 8)) & 0x300F00F
+        v = (v | (v << 4)) & 0x30C30C3
+        v = (v | (v << 2)) & 0x9249249
+        return v
+
+    code = spread(q[:, 0]) | (spread(q[:, 1]) << 1) | (spread(q[:, 2]) << 2)
+    want = np.argsort(code, kind="stable")
+    order = gs3.spatial_order(t(mu), n, gg)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(order.cpu().numpy(), want)
+    table = rng.normal(0, 0.1, size=(og.n_entries, 2)).astype(np.float32)
+    e0 = torch.zeros(n, 32, device=DEV)
+    e1 = torch.zeros(n, 32, device=DEV)
+    gs3.ntc_encode_fwd(t(mu), n, gg, t(table), e0)
+    gs3.ntc_encode_fwd(t(mu), n, gg, t(table), e1, order=order)
+    d_enc = rng.normal(size=(n, 32)).astype(np.float32)
+    d0 = torch.zeros(og.n_entries, 2, device=DEV)
+    d1 = torch.zeros(og.n_entries, 2, device=DEV)
+    gs3.ntc_encode_bwd(t(mu), n, gg, t(d_enc), d0)
+    gs3.ntc_encode_bwd(t(mu), n, gg, t(d_enc), d1, order=order)
+    torch.cuda.synchronize()
+    assert torch.equal(e0, e1)
+    assert rel_err(d1.cpu().numpy(), d0.cpu().numpy()) <= 1e-5
+
+
 def _mlp(seed):
     rng = np.random.default_rng(seed)
     return [w.astype(np.float32) for w in scenes.random_mlp([32, 64, 64, 7], rng)], rng
