@@ -457,8 +457,10 @@ def run_ours(args):
                               r.d_mean, r.d_quat, st.loss_scale_view(), ntc.mlp.g, ntc.table.g)
         else:
             gs3.ntc_apply_bwd(G.mean, G.quat, st.raw7, G.n, st.aabb, st.order, r.d_mean, r.d_quat, st.d_raw7)
-            gs3.ntc_mlp_bwd(st.enc, G.n, ntc.mlp_struct(), st.d_raw7, st.loss_scale_view(), ntc.mlp.g, st.d_enc)
-            gs3.ntc_encode_bwd(G.mean, G.n, ntc.grid, st.d_enc, ntc.table.g)
+            gs3.ntc_active_rows(st.d_raw7, G.n, st.active, st.n_active)
+            gs3.ntc_mlp_bwd(st.enc, G.n, ntc.mlp_struct(), st.d_raw7, st.loss_scale_view(), ntc.mlp.g, st.d_enc,
+                            rows=st.active, d_rows=st.n_active)
+            gs3.ntc_encode_bwd(G.mean, G.n, ntc.grid, st.d_enc, ntc.table.g, order=st.active, d_count=st.n_active)
         E("t8")
         st.update()
         E("t9")

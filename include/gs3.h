@@ -358,9 +358,11 @@ GS_API gs_status ntc_encode_fwd(const float *mean, int64_t n, const gs_hashgrid 
 /* d_table[entries][F] += trilinear-weighted scatter of d_enc[n][L*F]
  * (FP32 atomics; the caller zeroes d_table between steps -- adam_step does).
  * order: as for ntc_encode_fwd (the sums differ only in the order of the
- * atomic additions). */
+ * atomic additions).  d_count (device int64, or NULL): only the rows
+ * order[0 .. *d_count) are scattered -- a row list such as ntc_active_rows'
+ * (needs order). */
 GS_API gs_status ntc_encode_bwd(const float *mean, int64_t n, const gs_hashgrid *grid, const float *d_enc,
-                         float *d_table, const uint32_t *order, gs_stream stream);
+                         float *d_table, const uint32_t *order, const int64_t *d_count, gs_stream stream);
 
 /* raw7[n][7] = W3 relu(W2 relu(W1 enc)) (Section 4.1 Eq. 5).  enc_dtype
  * GS_F32 or GS_BF16. */
@@ -369,10 +371,19 @@ GS_API gs_status ntc_mlp_fwd(const void *enc, int enc_dtype, int64_t n, const gs
 
 /* Reverse of ntc_mlp_fwd with d_raw7 multiplied by *d_scale (device float;
  * NULL = 1): dW[6592] += sum over rows (FP32), d_enc[n][32] = dL/d enc
- * (written when non-NULL). */
+ * (written when non-NULL).  rows / d_rows (both or neither): only the rows
+ * rows[0 .. *d_rows) are worked on and only their d_enc rows written (a row
+ * whose d_raw7 is zero adds nothing to dW and has a zero d_enc);
+ * ntc_active_rows gives such a list. */
 GS_API gs_status ntc_mlp_bwd(const void *enc, int enc_dtype, int64_t n, const gs_mlp *w,
                       const float *d_raw7, const float *d_scale, float *dW, float *d_enc,
-                      gs_stream stream);
+                      const uint32_t *rows, const int64_t *d_rows, gs_stream stream);
+
+/* The rows of d_raw7[n][7] with a nonzero (or non-finite) value: writes
+ * rows[0 .. *d_count) (device uint32[n]) in no particular order and *d_count
+ * (device int64). */
+GS_API gs_status ntc_active_rows(const float *d_raw7, int64_t n, uint32_t *rows, int64_t *d_count,
+                                 gs_stream stream);
 
 /* Transformation (Section 4.1): mean_out = mean + raw7[0:3];
  * quat_out = norm(quat) x norm(raw7[3:7]) (order 0, the paper's product) or

@@ -82,6 +82,9 @@ struct TcParams {
     Box box;
     int order;
     uint32_t wait_tries;  // polls of an MMA-completion wait before giving up
+    // reverse over a row list: slot k of the work is row rows[k], k < *d_rows
+    const uint32_t *rows;
+    const int64_t *d_rows;
 };
 
 template <typename T>
@@ -452,9 +455,12 @@ __global__ void __launch_bounds__(TM, 2) mlp_tc_bwd_kernel(TcParams p)
     uint32_t phase = 0;
     bool ok = true;
     int done_tiles = 0;
-    const int64_t ntiles = (n + TM - 1) / TM;
+    const int64_t nslots = p.d_rows ? *p.d_rows : n;
+    const int64_t ntiles = (nslots + TM - 1) / TM;
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        const int64_t row = tile * TM + t;
+        // a slot past the list is row n: every use below checks row < n
+        const int64_t slot = tile * TM + t;
+        const int64_t row = slot < nslots ? (p.rows ? (int64_t)p.rows[slot] : slot) : n;
         float v[64];
         // ---- stage the encoding and the scaled output gradient
         load_row32(enc, row, n, v);
@@ -708,7 +714,7 @@ gs_status mlp_tc_fwd(const void *enc, int enc_dtype, int64_t n, const gs_mlp *w,
 
 gs_status mlp_tc_bwd(const void *enc, int enc_dtype, int64_t n, const gs_mlp *w,
                      const float *d_raw7, const float *d_scale, float *dW, float *d_enc,
-                     cudaStream_t s)
+                     const uint32_t *rows, const int64_t *d_rows, cudaStream_t s)
 {
     gs_status st = check_common(enc, enc_dtype, w);
     if (st != GS_OK) return st;
@@ -721,6 +727,8 @@ gs_status mlp_tc_bwd(const void *enc, int enc_dtype, int64_t n, const gs_mlp *w,
     p.d_scale = d_scale;
     p.dW = dW;
     p.d_enc = d_enc;
+    p.rows = rows;
+    p.d_rows = d_rows;
     return enc_dtype == GS_BF16 ? launch_bwd<bf16, false>(p, s) : launch_bwd<float, false>(p, s);
 }
 

@@ -130,9 +130,11 @@ constexpr int ENC_BWD_G = 8;
 
 __global__ void __launch_bounds__(128) encode_bwd_kernel(const float *mean, int64_t n, GridParams g,
                                                          const float *d_enc, float *d_table,
-                                                         const uint32_t *order)
+                                                         const uint32_t *order, const int64_t *d_count)
 {
-    const int64_t i = enc_row(order, (int64_t)blockIdx.x * blockDim.y + threadIdx.y, n);
+    const int64_t j = (int64_t)blockIdx.x * blockDim.y + threadIdx.y;
+    if (d_count && j >= *d_count) return;
+    const int64_t i = enc_row(order, j, n);
     const int l = threadIdx.x;
     if (i < 0 || l >= g.L) return;
     const float2 gg = reinterpret_cast<const float2 *>(d_enc + i * (int64_t)(2 * g.L))[l];
@@ -144,6 +146,26 @@ __global__ void __launch_bounds__(128) encode_bwd_kernel(const float *mean, int6
 #pragma unroll
     for (int c = 0; c < 8; ++c)
         atomicAdd(reinterpret_cast<float2 *>(d_table) + idx[c], make_float2(w[c] * gg.x, w[c] * gg.y));
+}
+
+// The rows of d_raw7 with a nonzero (or non-finite) value, in no particular
+// order: a warp's rows get consecutive slots from one atomic on the count.
+__global__ void active_rows_kernel(const float *d_raw7, int64_t n, uint32_t *rows, unsigned long long *count)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    bool act = false;
+    if (i < n) {
+        const float *r = d_raw7 + 7 * i;
+#pragma unroll
+        for (int q = 0; q < 7; ++q) act |= r[q] != 0.f;
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, act);
+    if (b == 0u) return;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(count, (unsigned long long)__popc(b));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (act) rows[base + __popc(b & ((1u << lane) - 1u))] = (uint32_t)i;
 }
 
 // Morton code (10 bits an axis) of every mean within the grid's box, and the
@@ -221,7 +243,8 @@ template <typename ET>
 __global__ void __launch_bounds__(MB_ROWS) mlp_bwd_simt_kernel(const ET *enc, int64_t n,
                                                                const float *W, const float *d_raw7,
                                                                const float *d_scale, float *dW,
-                                                               float *d_enc)
+                                                               float *d_enc, const uint32_t *rows,
+                                                               const int64_t *d_rows)
 {
     extern __shared__ float smem[];
     float *sW = smem;
@@ -238,10 +261,13 @@ __global__ void __launch_bounds__(MB_ROWS) mlp_bwd_simt_kernel(const ET *enc, in
     float acc[MB_PER_THREAD];
 #pragma unroll
     for (int r = 0; r < MB_PER_THREAD; ++r) acc[r] = 0.f;
-    const int64_t nchunks = (n + MB_ROWS - 1) / MB_ROWS;
+    // with a row list, slot k of the work is row rows[k], k < *d_rows
+    const int64_t nslots = d_rows ? *d_rows : n;
+    const int64_t nchunks = (nslots + MB_ROWS - 1) / MB_ROWS;
     __syncthreads();
     for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-        int64_t i = ch * MB_ROWS + t;
+        const int64_t k = ch * MB_ROWS + t;
+        int64_t i = k < nslots ? (rows ? (int64_t)rows[k] : k) : n;
         bool ok = i < n;
         float *x = sX + t * MB_SX, *h1 = sH1 + t * MB_SH, *h2 = sH2 + t * MB_SH;
         float *g2 = sG2 + t * MB_SH, *g1 = sG1 + t * MB_SH, *go = sGO + t * MB_SO;
@@ -582,7 +608,7 @@ extern "C" gs_status ntc_encode_fwd(const float *mean, int64_t n, const gs_hashg
 
 extern "C" gs_status ntc_encode_bwd(const float *mean, int64_t n, const gs_hashgrid *grid,
                                    const float *d_enc, float *d_table, const uint32_t *order,
-                                   gs_stream stream)
+                                   const int64_t *d_count, gs_stream stream)
 {
     GridParams g;
     int64_t total;
@@ -593,9 +619,25 @@ extern "C" gs_status ntc_encode_bwd(const float *mean, int64_t n, const gs_hashg
     GS_REQUIRE(aligned(d_table, 8) && aligned(d_enc, 8), "ntc_encode_bwd: misaligned");
     note_launch();
     const dim3 blk(g.L, ENC_BWD_G);
+    GS_REQUIRE(d_count == nullptr || order, "ntc_encode_bwd: a count needs its row list (order)");
     encode_bwd_kernel<<<(unsigned)ceil_div(n, ENC_BWD_G), blk, 0, as_stream(stream)>>>(mean, n, g, d_enc, d_table,
-                                                                                      order);
+                                                                                      order, d_count);
     return launch_status("ntc_encode_bwd");
+}
+
+extern "C" gs_status ntc_active_rows(const float *d_raw7, int64_t n, uint32_t *rows, int64_t *d_count,
+                                    gs_stream stream)
+{
+    GS_REQUIRE(n >= 0 && n <= (int64_t(1) << 32) - 1, "ntc_active_rows: n out of range");
+    GS_REQUIRE(d_count, "ntc_active_rows: null count");
+    cudaStream_t s = as_stream(stream);
+    cudaMemsetAsync(d_count, 0, sizeof(int64_t), s);
+    if (n == 0) return launch_status("ntc_active_rows");
+    GS_REQUIRE(d_raw7 && rows, "ntc_active_rows: null argument");
+    note_launch();
+    active_rows_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(d_raw7, n, rows,
+                                                                 reinterpret_cast<unsigned long long *>(d_count));
+    return launch_status("ntc_active_rows");
 }
 
 extern "C" size_t ntc_spatial_order_workspace_size(int64_t n)
@@ -655,14 +697,15 @@ extern "C" gs_status ntc_mlp_fwd(const void *enc, int enc_dtype, int64_t n, cons
 
 extern "C" gs_status ntc_mlp_bwd(const void *enc, int enc_dtype, int64_t n, const gs_mlp *w,
                                 const float *d_raw7, const float *d_scale, float *dW, float *d_enc,
-                                gs_stream stream)
+                                const uint32_t *rows, const int64_t *d_rows, gs_stream stream)
 {
     GS_REQUIRE(w && dW && n >= 0, "ntc_mlp_bwd: null weights or negative n");
     GS_REQUIRE(enc_dtype == GS_F32 || enc_dtype == GS_BF16, "ntc_mlp_bwd: enc dtype");
+    GS_REQUIRE((rows == nullptr) == (d_rows == nullptr), "ntc_mlp_bwd: rows and d_rows go together");
     if (n == 0) return GS_OK;
     GS_REQUIRE(enc && d_raw7, "ntc_mlp_bwd: null argument");
     if (w->precision == GS_MLP_BF16)
-        return mlp_tc_bwd(enc, enc_dtype, n, w, d_raw7, d_scale, dW, d_enc, as_stream(stream));
+        return mlp_tc_bwd(enc, enc_dtype, n, w, d_raw7, d_scale, dW, d_enc, rows, d_rows, as_stream(stream));
     GS_REQUIRE(w->precision == GS_MLP_FP32 && w->w_f32, "ntc_mlp_bwd: bad precision / weights");
     cudaStream_t s = as_stream(stream);
     int blocks = (int)std::min<int64_t>(ceil_div(n, MB_ROWS), 2 * num_sms());
@@ -670,12 +713,12 @@ extern "C" gs_status ntc_mlp_bwd(const void *enc, int enc_dtype, int64_t n, cons
         set_smem_limit((const void *)mlp_bwd_simt_kernel<float>, (int)MB_SMEM, s);
         note_launch();
         mlp_bwd_simt_kernel<float><<<blocks, MB_ROWS, MB_SMEM, s>>>((const float *)enc, n, w->w_f32,
-                                                                    d_raw7, d_scale, dW, d_enc);
+                                                                    d_raw7, d_scale, dW, d_enc, rows, d_rows);
     } else {
         set_smem_limit((const void *)mlp_bwd_simt_kernel<__nv_bfloat16>, (int)MB_SMEM, s);
         note_launch();
         mlp_bwd_simt_kernel<__nv_bfloat16><<<blocks, MB_ROWS, MB_SMEM, s>>>(
-            (const __nv_bfloat16 *)enc, n, w->w_f32, d_raw7, d_scale, dW, d_enc);
+            (const __nv_bfloat16 *)enc, n, w->w_f32, d_raw7, d_scale, dW, d_enc, rows, d_rows);
     }
     return launch_status("ntc_mlp_bwd");
 }

@@ -116,6 +116,6 @@ gs_status mlp_tc_fwd(const void *enc, int enc_dtype, int64_t n, const gs_mlp *w,
                      cudaStream_t s);
 gs_status mlp_tc_bwd(const void *enc, int enc_dtype, int64_t n, const gs_mlp *w,
                      const float *d_raw7, const float *d_scale, float *dW, float *d_enc,
-                     cudaStream_t s);
+                     const uint32_t *rows, const int64_t *d_rows, cudaStream_t s);
 
 }  // namespace gs3

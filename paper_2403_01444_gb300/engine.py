@@ -251,6 +251,10 @@ class Stage1:
         self.quat_t = _f32(n, 4, device=device)
         self.d_raw7 = _f32(n, 7, device=device)
         self.d_enc = _f32(n, 32, device=device)
+        # the rows with a nonzero cache-output gradient (most Gaussians are
+        # seen by no view of a batch): the cache's reverse works on those only
+        self.active = torch.zeros(max(n, 1), dtype=torch.int32, device=device)
+        self.n_active = torch.zeros(1, dtype=torch.int64, device=device)
         if loss_scale is None:
             loss_scale = 2.0 ** 15 if ntc.precision == gs3.GS_MLP_BF16 else 1.0
         self.growth = growth_interval if ntc.precision == gs3.GS_MLP_BF16 else 0
@@ -324,11 +328,13 @@ class Stage1:
             return self.loss.d_loss
         gs3.ntc_apply_bwd(g.mean, g.quat, self.raw7, n, self.aabb, self.order, d_mean, d_quat,
                           self.d_raw7, stream)
+        gs3.ntc_active_rows(self.d_raw7, n, self.active, self.n_active, stream)
         gs3.ntc_mlp_bwd(self.enc, n, ntc.mlp_struct(), self.d_raw7, self.loss_scale_view(),
-                        ntc.mlp.g, self.d_enc, stream)
-        # the reverse runs in index order: in spatial order neighbouring
-        # Gaussians' atomics meet on the same table rows
-        gs3.ntc_encode_bwd(g.mean, n, ntc.grid, self.d_enc, ntc.table.g, stream)
+                        ntc.mlp.g, self.d_enc, stream, rows=self.active, d_rows=self.n_active)
+        # the reverse encoding over the same rows (not in spatial order: there
+        # neighbouring Gaussians' atomics would meet on the same table rows)
+        gs3.ntc_encode_bwd(g.mean, n, ntc.grid, self.d_enc, ntc.table.g, stream, order=self.active,
+                           d_count=self.n_active)
         return self.loss.d_loss
 
     def loss_scale_view(self):

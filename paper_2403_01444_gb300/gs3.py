@@ -324,9 +324,15 @@ def ntc_encode_fwd(mean, n, grid: GsHashgrid, table, enc, stream=None, order=Non
         c_int(_DT[enc.dtype]), _ptr(order), _stream(stream)))
 
 
-def ntc_encode_bwd(mean, n, grid: GsHashgrid, d_enc, d_table, stream=None, order=None):
+def ntc_encode_bwd(mean, n, grid: GsHashgrid, d_enc, d_table, stream=None, order=None, d_count=None):
     _check("ntc_encode_bwd", lib().ntc_encode_bwd(
-        _ptr(mean), c_int64(n), ctypes.byref(grid), _ptr(d_enc), _ptr(d_table), _ptr(order), _stream(stream)))
+        _ptr(mean), c_int64(n), ctypes.byref(grid), _ptr(d_enc), _ptr(d_table), _ptr(order), _ptr(d_count),
+        _stream(stream)))
+
+
+def ntc_active_rows(d_raw7, n, rows, d_count, stream=None):
+    _check("ntc_active_rows", lib().ntc_active_rows(_ptr(d_raw7), c_int64(n), _ptr(rows), _ptr(d_count),
+                                                    _stream(stream)))
 
 
 def ntc_spatial_order_workspace_size(n) -> int:
@@ -355,10 +361,10 @@ def ntc_mlp_fwd(enc, n, mlp: GsMlp, raw7, stream=None):
                                             ctypes.byref(mlp), _ptr(raw7), _stream(stream)))
 
 
-def ntc_mlp_bwd(enc, n, mlp: GsMlp, d_raw7, d_scale, dW, d_enc, stream=None):
+def ntc_mlp_bwd(enc, n, mlp: GsMlp, d_raw7, d_scale, dW, d_enc, stream=None, rows=None, d_rows=None):
     _check("ntc_mlp_bwd", lib().ntc_mlp_bwd(
         _ptr(enc), c_int(_DT[enc.dtype]), c_int64(n), ctypes.byref(mlp), _ptr(d_raw7), _ptr(d_scale),
-        _ptr(dW), _ptr(d_enc), _stream(stream)))
+        _ptr(dW), _ptr(d_enc), _ptr(rows), _ptr(d_rows), _stream(stream)))
 
 
 def _aabb(aabb):

@@ -444,6 +444,51 @@ def test_mlp_fp32_parity(n):
     assert_grad_close(denc.cpu().numpy() / 4.0, dx)
 
 
+@pytest.mark.parametrize("precision", [gs3.GS_MLP_FP32, gs3.GS_MLP_BF16])
+@pytest.mark.parametrize("n,frac", [(1, 1.0), (3000, 0.1), (70001, 0.12), (5000, 0.0)])
+def test_cache_reverse_over_active_rows(precision, n, frac):
+    """ntc_active_rows lists exactly the rows with a nonzero output gradient;
+    the MLP reverse and the reverse encoding over that list give the same
+    weight, encoding and table gradients as over all rows (rows whose gradient
+    is zero add nothing), to the order of the FP32 sums."""
+    Ws, rng = _mlp(n + 11)
+    og, gg = _grid_pair()
+    x = rng.normal(size=(n, 32)).astype(np.float32)
+    mu = rng.uniform(-1.4, 1.4, size=(n, 3)).astype(np.float32)
+    gout = rng.normal(size=(n, 7)).astype(np.float32)
+    gout[rng.uniform(size=n) >= frac] = 0.0
+    wflat = t(np.concatenate([w.ravel() for w in Ws]))
+    wb = wflat.to(torch.bfloat16)
+    mlp = gs3.mlp_struct(precision, wflat, wb if precision == gs3.GS_MLP_BF16 else None)
+    xe = t(x).to(torch.bfloat16) if precision == gs3.GS_MLP_BF16 else t(x)
+    rows = torch.zeros(n, dtype=torch.int32, device=DEV)
+    cnt = torch.zeros(1, dtype=torch.int64, device=DEV)
+    gs3.ntc_active_rows(t(gout), n, rows, cnt)
+    torch.cuda.synchronize()
+    m = int(cnt.item())
+    want_rows = np.nonzero(np.any(gout != 0, axis=1))[0]
+    assert m == len(want_rows)
+    np.testing.assert_array_equal(np.sort(rows[:m].cpu().numpy()), want_rows)
+    scale = torch.tensor([8.0], device=DEV)
+    out = {}
+    for key, kw in (("all", {}), ("listed", {"rows": rows, "d_rows": cnt})):
+        dW = torch.zeros(gs3.MLP_PARAMS, device=DEV)
+        denc = torch.zeros(n, 32, device=DEV)
+        dT = torch.zeros(og.n_entries, 2, device=DEV)
+        gs3.ntc_mlp_bwd(xe, n, mlp, t(gout), scale, dW, denc, **kw)
+        gs3.ntc_encode_bwd(t(mu), n, gg, denc, dT, order=kw.get("rows"), d_count=kw.get("d_rows"))
+        torch.cuda.synchronize()
+        out[key] = (dW.cpu().numpy(), denc.cpu().numpy(), dT.cpu().numpy())
+    (w0, e0, t0), (w1, e1, t1) = out["all"], out["listed"]
+    if m == 0:
+        assert not w1.any() and not e1.any() and not t1.any()
+        return
+    assert rel_err(w1, w0) <= 1e-5
+    np.testing.assert_array_equal(e1[want_rows], e0[want_rows])
+    assert not e0[np.setdiff1d(np.arange(n), want_rows)].any()
+    assert rel_err(t1, t0) <= 1e-5
+
+
 @pytest.mark.parametrize("order", [0, 1])
 def test_apply_parity(order):
     n = 1000
