@@ -132,20 +132,22 @@ __global__ void __launch_bounds__(128) encode_bwd_kernel(const float *mean, int6
                                                          const float *d_enc, float *d_table,
                                                          const uint32_t *order, const int64_t *d_count)
 {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.y + threadIdx.y;
-    if (d_count && j >= *d_count) return;
-    const int64_t i = enc_row(order, j, n);
+    // with a count the grid is a fixed size that strides over the list
+    const int64_t nj = d_count ? *d_count : n;
     const int l = threadIdx.x;
-    if (i < 0 || l >= g.L) return;
-    const float2 gg = reinterpret_cast<const float2 *>(d_enc + i * (int64_t)(2 * g.L))[l];
-    if (gg.x == 0.f && gg.y == 0.f) return;
-    const float3 m = make_float3(mean[3 * i], mean[3 * i + 1], mean[3 * i + 2]);
-    uint32_t idx[8];
-    float w[8];
-    level_corners(g, l, m, idx, w);
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; j < nj; j += (int64_t)gridDim.x * blockDim.y) {
+        const int64_t i = enc_row(order, j, n);
+        if (i < 0 || l >= g.L) continue;
+        const float2 gg = reinterpret_cast<const float2 *>(d_enc + i * (int64_t)(2 * g.L))[l];
+        if (gg.x == 0.f && gg.y == 0.f) continue;
+        const float3 m = make_float3(mean[3 * i], mean[3 * i + 1], mean[3 * i + 2]);
+        uint32_t idx[8];
+        float w[8];
+        level_corners(g, l, m, idx, w);
 #pragma unroll
-    for (int c = 0; c < 8; ++c)
-        atomicAdd(reinterpret_cast<float2 *>(d_table) + idx[c], make_float2(w[c] * gg.x, w[c] * gg.y));
+        for (int c = 0; c < 8; ++c)
+            atomicAdd(reinterpret_cast<float2 *>(d_table) + idx[c], make_float2(w[c] * gg.x, w[c] * gg.y));
+    }
 }
 
 // The rows of d_raw7 with a nonzero (or non-finite) value, in no particular
@@ -620,8 +622,10 @@ extern "C" gs_status ntc_encode_bwd(const float *mean, int64_t n, const gs_hashg
     note_launch();
     const dim3 blk(g.L, ENC_BWD_G);
     GS_REQUIRE(d_count == nullptr || order, "ntc_encode_bwd: a count needs its row list (order)");
-    encode_bwd_kernel<<<(unsigned)ceil_div(n, ENC_BWD_G), blk, 0, as_stream(stream)>>>(mean, n, g, d_enc, d_table,
-                                                                                      order, d_count);
+    // over a list of unknown length: 16 blocks an SM stride over it
+    const int64_t blocks = d_count ? std::min<int64_t>(ceil_div(n, ENC_BWD_G), (int64_t)num_sms() * 16)
+                                   : ceil_div(n, ENC_BWD_G);
+    encode_bwd_kernel<<<(unsigned)blocks, blk, 0, as_stream(stream)>>>(mean, n, g, d_enc, d_table, order, d_count);
     return launch_status("ntc_encode_bwd");
 }
 
