@@ -47,6 +47,13 @@ struct SortPass {
     int shift;
     uint32_t *hist;      // [RADIX][G]
     int G;
+    // optional: OR of the keys and OR of their complements.  A byte set in
+    // both differs between keys; a pass on any other byte keeps the order
+    // and is skipped whole.  Each pass then reads buffer kb/vb[f & 1], f the
+    // passes before it that are not skipped, and writes the other (kin,
+    // vin, kout, vout are set from them on the device).
+    const uint32_t *kor;
+    uint32_t *kb[2], *vb[2];
 };
 
 __device__ __forceinline__ int64_t pass_n(const SortPass &s) { return s.d_n ? *s.d_n : s.n_host; }
@@ -59,6 +66,30 @@ __device__ __forceinline__ void block_range(int64_t n, int G, int b, int64_t &be
     end = min(n, beg + per * SORT_TILE);
 }
 
+__device__ __forceinline__ bool byte_constant(const uint32_t *kor, int shift)
+{
+    return kor && (((kor[0] & kor[1]) >> shift) & (RADIX - 1)) == 0u;
+}
+
+// Passes on the bytes below `shift` that are not skipped (kor as in SortPass).
+__device__ __forceinline__ int passes_below(const uint32_t *kor, int shift)
+{
+    const uint32_t diff = kor[0] & kor[1];
+    int f = 0;
+    for (int sh = 0; sh < shift; sh += 8) f += ((diff >> sh) & (RADIX - 1)) != 0u;
+    return f;
+}
+
+__device__ __forceinline__ void pass_buffers(SortPass &s)
+{
+    if (!s.kor) return;
+    const bool odd = passes_below(s.kor, s.shift) & 1;  // selects, not an indexed (local) copy
+    s.kin = odd ? s.kb[1] : s.kb[0];
+    s.vin = odd ? s.vb[1] : s.vb[0];
+    s.kout = odd ? s.kb[0] : s.kb[1];
+    s.vout = odd ? s.vb[0] : s.vb[1];
+}
+
 __device__ __forceinline__ uint32_t digit_of(const SortPass &s, uint32_t k, uint32_t v)
 {
     return (k >> s.shift) & (RADIX - 1);
@@ -66,49 +97,152 @@ __device__ __forceinline__ uint32_t digit_of(const SortPass &s, uint32_t k, uint
 
 __global__ void __launch_bounds__(SORT_THREADS) radix_hist_kernel(SortPass s)
 {
+    if (byte_constant(s.kor, s.shift)) return;
+    pass_buffers(s);
     __shared__ uint32_t h[RADIX];
     h[threadIdx.x] = 0;
     __syncthreads();
     int64_t beg, end;
     block_range(pass_n(s), s.G, blockIdx.x, beg, end);
-    for (int64_t i = beg + threadIdx.x; i < end; i += SORT_THREADS) {
-        uint32_t d = (s.kin[i] >> s.shift) & (RADIX - 1);
-        atomicAdd(&h[d], 1u);
+    // a tile's loads in flight before its counts
+    for (int64_t t0 = beg; t0 < end; t0 += SORT_TILE) {
+        uint32_t d[SORT_ITEMS];
+#pragma unroll
+        for (int j = 0; j < SORT_ITEMS; ++j) {
+            const int64_t i = t0 + j * SORT_THREADS + threadIdx.x;
+            d[j] = i < end ? (s.kin[i] >> s.shift) & (RADIX - 1) : (uint32_t)RADIX;
+        }
+#pragma unroll
+        for (int j = 0; j < SORT_ITEMS; ++j)
+            if (d[j] < RADIX) atomicAdd(&h[d[j]], 1u);
     }
     __syncthreads();
     s.hist[threadIdx.x * s.G + blockIdx.x] = h[threadIdx.x];
 }
 
+// Key bases of the counting sort (exclusive scan, in place, of the key
+// totals tot[0..nkeys)), the range of every key (empty for an empty key, and
+// for all keys over capacity), the total and the capacity check; by one block.
+struct KeyBases {
+    uint32_t *done;      // rows finished (zeroed before); NULL: no key bases
+    int64_t capacity;
+    int64_t *d_count, *n_eff;
+    int32_t *d_err;
+    uint32_t *ranges;
+};
+
+__device__ __forceinline__ int64_t block_scan_i64(int64_t x, int64_t *s_warp, int64_t &total);
+
+__device__ __forceinline__ void key_bases(uint32_t *tot, int nkeys, KeyBases kb)
+{
+    __shared__ int64_t s_warp[32];
+    const int nt = (int)blockDim.x;
+    const int per = (nkeys + nt - 1) / nt;
+    const int beg = min(nkeys, (int)threadIdx.x * per), end = min(nkeys, beg + per);
+    int64_t sum = 0;
+    for (int k = beg; k < end; ++k) sum += __ldcg(tot + k);
+    int64_t total;
+    int64_t run = block_scan_i64(sum, s_warp, total);
+    const bool fits = total <= kb.capacity;
+    for (int k = beg; k < end; ++k) {
+        const uint32_t c = __ldcg(tot + k);
+        const bool some = fits && c > 0;
+        kb.ranges[2 * (int64_t)k] = some ? (uint32_t)run : 0u;
+        kb.ranges[2 * (int64_t)k + 1] = some ? (uint32_t)(run + c) : 0u;
+        tot[k] = (uint32_t)run;
+        run += c;
+    }
+    if (threadIdx.x == 0) {
+        *kb.d_count = total;
+        *kb.n_eff = fits ? total : 0;
+        if (!fits && kb.d_err) atomicCAS(kb.d_err, 0, (int32_t)GS_ERR_CAPACITY);
+    }
+}
+
+constexpr int ROW_ITEMS = 4;  // a row of up to SORT_THREADS x ROW_ITEMS counts is scanned in one step
+
 // Per row d (one block each; a digit of a radix pass or a key of the
 // counting sort): exclusive scan, in place, of the G block counts
-// hist[d][0..G), and the row's total in hist[rows * G + d].
-__global__ void __launch_bounds__(SORT_THREADS) scan_digit_rows_kernel(uint32_t *hist, int G, int rows)
+// hist[d][0..G), and the row's total in hist[rows * G + d].  Nothing for a
+// radix pass whose byte is constant (kor, shift as in SortPass).  With
+// kb.done, the block that finishes last also takes the key bases of the
+// totals (the others' rows and totals are fenced before they count).
+__global__ void __launch_bounds__(SORT_THREADS, 1) scan_digit_rows_kernel(uint32_t *hist, int G, int rows,
+                                                                      const uint32_t *kor, int shift,
+                                                                      KeyBases kb)
 {
+    if (byte_constant(kor, shift)) return;  // a radix pass that is skipped
     __shared__ uint32_t s_w[SORT_WARPS];
     __shared__ uint32_t s_carry;
+    __shared__ int s_last;
     const int d = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t *row = hist + (int64_t)d * G;
-    if (threadIdx.x == 0) s_carry = 0;
-    __syncthreads();
-    for (int base = 0; base < G; base += SORT_THREADS) {
-        int i = base + threadIdx.x;
-        uint32_t x = i < G ? row[i] : 0u;
-        uint32_t inc = x;
+    uint32_t total;
+    if (G <= SORT_THREADS * ROW_ITEMS) {
+        // each thread a run of up to ROW_ITEMS consecutive counts, all loaded at once
+        const int per = (G + SORT_THREADS - 1) / SORT_THREADS;
+        const int b0 = threadIdx.x * per;
+        uint32_t x[ROW_ITEMS];
+        uint32_t sum = 0u;
+#pragma unroll
+        for (int k = 0; k < ROW_ITEMS; ++k) {
+            x[k] = k < per && b0 + k < G ? row[b0 + k] : 0u;
+            sum += x[k];
+        }
+        uint32_t inc = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
             if (lane >= o) inc += y;
         }
         if (lane == 31) s_w[warp] = inc;
         __syncthreads();
-        uint32_t before = s_carry;
-        for (int w = 0; w < warp; ++w) before += s_w[w];
-        if (i < G) row[i] = before + inc - x;
+        uint32_t before = 0u;
+        total = 0u;
+#pragma unroll
+        for (int w = 0; w < SORT_WARPS; ++w) {
+            const uint32_t c = s_w[w];
+            before += w < warp ? c : 0u;
+            total += c;
+        }
+        uint32_t run = before + inc - sum;
+#pragma unroll
+        for (int k = 0; k < ROW_ITEMS; ++k) {
+            if (k < per && b0 + k < G) row[b0 + k] = run;
+            run += x[k];
+        }
+    } else {
+        if (threadIdx.x == 0) s_carry = 0;
         __syncthreads();
-        if (threadIdx.x == SORT_THREADS - 1) s_carry = before + inc;
-        __syncthreads();
+        for (int base = 0; base < G; base += SORT_THREADS) {
+            int i = base + threadIdx.x;
+            uint32_t x = i < G ? row[i] : 0u;
+            uint32_t inc = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            if (lane == 31) s_w[warp] = inc;
+            __syncthreads();
+            uint32_t before = s_carry;
+            for (int w = 0; w < warp; ++w) before += s_w[w];
+            if (i < G) row[i] = before + inc - x;
+            __syncthreads();
+            if (threadIdx.x == SORT_THREADS - 1) s_carry = before + inc;
+            __syncthreads();
+        }
+        total = s_carry;
     }
-    if (threadIdx.x == 0) hist[(int64_t)rows * G + d] = s_carry;
+    if (threadIdx.x == 0) hist[(int64_t)rows * G + d] = total;
+    if (kb.done == nullptr) return;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(kb.done, 1u) == (uint32_t)(rows - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    key_bases(hist + (int64_t)rows * G, rows, kb);
 }
 
 // Ranked scatter of one pass.  Each tile of SORT_TILE items is first put in
@@ -124,14 +258,30 @@ __global__ void __launch_bounds__(SORT_THREADS, 4) radix_scatter_kernel(SortPass
     __shared__ uint32_t s_k[SORT_TILE], s_v[SORT_TILE];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;
+    if (byte_constant(s.kor, s.shift)) return;
+    pass_buffers(s);
     const int64_t n = pass_n(s);
     int64_t beg, end;
     block_range(n, s.G, blockIdx.x, beg, end);
+    // the block's counts and the first tile's items are loaded before
+    // anything waits; each later tile's while the one before is written out
+    const uint32_t tot = s.hist[(int64_t)RADIX * s.G + tid];
+    const uint32_t mine = s.hist[(int64_t)tid * s.G + blockIdx.x];
+    uint32_t key[SORT_ITEMS], val[SORT_ITEMS];
+    auto load_tile = [&](int64_t t0) {
+#pragma unroll
+        for (int j = 0; j < SORT_ITEMS; ++j) {
+            const int64_t idx = t0 + (int64_t)warp * 32 * SORT_ITEMS + j * 32 + lane;
+            const bool ok = idx < end;
+            key[j] = ok ? s.kin[idx] : 0u;
+            val[j] = ok ? s.vin[idx] : 0u;
+        }
+    };
+    if (beg < end) load_tile(beg);
     {
         // digit base = exclusive scan of the digit totals (RADIX == threads)
-        uint32_t tot = s.hist[(int64_t)RADIX * s.G + tid];
         // one digit holds every item: the pass keeps the order, a copy
-        if (__syncthreads_or((int64_t)tot == n)) {
+        if (!s.kor && __syncthreads_or((int64_t)tot == n)) {
             // 16 bytes a load where the buffers allow it (beg is a multiple
             // of SORT_TILE; a caller's vals may be only 4-byte aligned), all
             // of a thread's loads before its stores
@@ -167,21 +317,21 @@ __global__ void __launch_bounds__(SORT_THREADS, 4) radix_scatter_kernel(SortPass
         __syncthreads();
         uint32_t before = 0;
         for (int w = 0; w < warp; ++w) before += s_tot[w];
-        s_off[tid] = before + inc - tot + s.hist[tid * s.G + blockIdx.x];
-        __syncthreads();
+        s_off[tid] = before + inc - tot + mine;
     }
     for (int64_t t0 = beg; t0 < end; t0 += SORT_TILE) {
         for (int k = tid; k < SORT_WARPS * RADIX; k += SORT_THREADS) (&s_wh[0][0])[k] = 0u;
         __syncthreads();
-        uint32_t key[SORT_ITEMS], val[SORT_ITEMS], rank[SORT_ITEMS], dig[SORT_ITEMS];
+        uint32_t rank[SORT_ITEMS], dig[SORT_ITEMS];
 #pragma unroll
         for (int j = 0; j < SORT_ITEMS; ++j) {
-            int64_t idx = t0 + (int64_t)warp * 32 * SORT_ITEMS + j * 32 + lane;
-            bool ok = idx < end;
-            key[j] = ok ? s.kin[idx] : 0u;
-            val[j] = ok ? s.vin[idx] : 0u;
-            uint32_t d = ok ? digit_of(s, key[j], val[j]) : (uint32_t)RADIX;
-            dig[j] = d;
+            const int64_t idx = t0 + (int64_t)warp * 32 * SORT_ITEMS + j * 32 + lane;
+            dig[j] = idx < end ? digit_of(s, key[j], val[j]) : (uint32_t)RADIX;
+        }
+#pragma unroll
+        for (int j = 0; j < SORT_ITEMS; ++j) {
+            const uint32_t d = dig[j];
+            const bool ok = d < RADIX;
             unsigned peers = __match_any_sync(0xffffffffu, d);
             uint32_t before = 0;
             if (ok) before = s_wh[warp][d];
@@ -224,6 +374,7 @@ __global__ void __launch_bounds__(SORT_THREADS, 4) radix_scatter_kernel(SortPass
             }
         }
         __syncthreads();
+        if (t0 + SORT_TILE < end) load_tile(t0 + SORT_TILE);
         const int cnt = (int)min((int64_t)SORT_TILE, end - t0);
         for (int i = tid; i < cnt; i += SORT_THREADS) {
             const uint32_t k = s_k[i], v = s_v[i];
@@ -238,14 +389,54 @@ __global__ void __launch_bounds__(SORT_THREADS, 4) radix_scatter_kernel(SortPass
 }
 
 // ---------------------------------------------------------------- stage 1
-__global__ void depth_keys_kernel(const float *depth, const int32_t *radius, int64_t NV,
-                                  uint32_t *k, uint32_t *v)
+// Keys (IEEE bits of the positive depths, which are monotone; culled entries
+// last) and values (the entry index) of the depth sort, with the first
+// pass's block counts hist[d][G] (the blocks of block_range) and the keys'
+// OR and complements' OR in kor[0..1] (zeroed before).
+__global__ void __launch_bounds__(SORT_THREADS) depth_keys_kernel(const float *depth, const int32_t *radius,
+                                                                  int64_t NV, int G, uint32_t *k, uint32_t *v,
+                                                                  uint32_t *hist, uint32_t *kor)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= NV) return;
-    // positive depths: IEEE bits are monotone; culled entries go last
-    k[i] = radius[i] > 0 ? __float_as_uint(depth[i]) : 0xffffffffu;
-    v[i] = (uint32_t)i;
+    __shared__ uint32_t h[RADIX];
+    __shared__ uint32_t s_or[2];
+    h[threadIdx.x] = 0u;
+    if (threadIdx.x < 2) s_or[threadIdx.x] = 0u;
+    __syncthreads();
+    int64_t beg, end;
+    block_range(NV, G, blockIdx.x, beg, end);
+    uint32_t o1 = 0u, o0 = 0u;
+    for (int64_t t0 = beg; t0 < end; t0 += SORT_TILE) {
+        uint32_t key[SORT_ITEMS];
+#pragma unroll
+        for (int j = 0; j < SORT_ITEMS; ++j) {
+            const int64_t i = t0 + j * SORT_THREADS + threadIdx.x;
+            key[j] = 0u;
+            if (i < end) key[j] = radius[i] > 0 ? __float_as_uint(depth[i]) : 0xffffffffu;
+        }
+#pragma unroll
+        for (int j = 0; j < SORT_ITEMS; ++j) {
+            const int64_t i = t0 + j * SORT_THREADS + threadIdx.x;
+            if (i < end) {
+                k[i] = key[j];
+                v[i] = (uint32_t)i;
+                o1 |= key[j];
+                o0 |= ~key[j];
+                atomicAdd(&h[key[j] & (RADIX - 1)], 1u);
+            }
+        }
+    }
+    o1 = __reduce_or_sync(0xffffffffu, o1);
+    o0 = __reduce_or_sync(0xffffffffu, o0);
+    if ((threadIdx.x & 31) == 0) {
+        atomicOr(&s_or[0], o1);
+        atomicOr(&s_or[1], o0);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * G + blockIdx.x] = h[threadIdx.x];
+    if (threadIdx.x == 0) {
+        if (s_or[0]) atomicOr(kor, s_or[0]);
+        if (s_or[1]) atomicOr(kor + 1, s_or[1]);
+    }
 }
 
 // Number of bins of every entry, in the sorted order (same rectangle rule as
@@ -461,7 +652,7 @@ __global__ void keys64_kernel(const uint32_t *tk, const uint32_t *vals, const in
 //    the block's total to hist[key][block], and every entry's bin rectangle
 //    and view, packed, to rect[entry].
 //  - scan: per key, exclusive over the blocks (scan_digit_rows_kernel), then
-//    over the keys (cs_keys_kernel), giving each (block, key) its first
+//    over the keys (by the scan's last block), giving each (block, key) its first
 //    position, each key its range, the total and the capacity check.
 //  - place: each block keeps per key its first position (32 bits) and per
 //    (warp, key) a running offset from it (16 bits: a block's count of one
@@ -477,6 +668,7 @@ constexpr int CS_MAX_KEYS = 2048;        // keys V * bins at most (16-bit tables
 constexpr int CS_MIN_ENTRIES = 64;       // entries per warp at least (bounds the count tables)
 constexpr int CS_MAX_ENTRIES = 4095;     // entries per warp at most: CS_WARPS x 4095 < 2^16 per block and key
 constexpr int CS_BLOCKS_PER_SM = 4;
+constexpr int CS_COUNT_MIN_BLOCKS = 3;   // count kernel: 42 registers, room for its loads run ahead
 
 // Keys padded to a multiple of 8, so a warp's 16-bit row is whole 16-byte words.
 inline int cs_pad_keys(int64_t nkeys) { return (int)((nkeys + 7) & ~int64_t(7)); }
@@ -498,6 +690,8 @@ inline int64_t cs_warps_bound(int64_t NV)
 
 struct CsParams {
     const uint32_t *svals;   // sorted (view, Gaussian) entries: view * n + g
+    const uint32_t *kor;     // with it, svals is sv[f & 1], f the depth passes not skipped
+    const uint32_t *sv[2];
     const float2 *mean2d;
     const int32_t *radius;
     const float *depth;
@@ -509,10 +703,17 @@ struct CsParams {
     uint32_t *hist;          // [nkeys][G] block counts -> prefixes, then per key [nkeys] totals -> bases
     uint16_t *wpre;          // [NW][kp] warp offsets within the block
     uint64_t *rect;          // [NV] packed bin rectangle and view of every entry
+    uint32_t *done;          // zeroed by the count kernel for the scan after it
     const int64_t *n_eff;
     uint32_t *vals;
     uint64_t *keys;          // optional
 };
+
+__device__ __forceinline__ const uint32_t *cs_svals(const CsParams &p)
+{
+    if (!p.kor) return p.svals;
+    return (passes_below(p.kor, 32) & 1) ? p.sv[1] : p.sv[0];
+}
 
 __device__ __forceinline__ void cs_segment(const CsParams &p, int64_t &beg, int64_t &end)
 {
@@ -543,12 +744,10 @@ __device__ __forceinline__ uint32_t cs_view(const CsParams &p, uint32_t sv)
 // Packed bin rectangle and view of entry sv (an empty rectangle for a culled
 // entry): bin_rect() with the divisions by bin taken by cs_div (tiles < 2^12);
 // x0, x1, y0, y1 in 12 bits each (bins <= 1024 a side), the view above them.
-__device__ __forceinline__ uint64_t cs_rect(const CsParams &p, uint32_t sv)
+__device__ __forceinline__ uint64_t cs_rect(const CsParams &p, uint32_t sv, int r, float2 m)
 {
     int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
-    const int r = p.radius[sv];
     if (r > 0) {
-        const float2 m = p.mean2d[sv];
         int a0, b0, a1, b1;
         tile_rect(m.x, m.y, r, p.tx, p.ty, a0, b0, a1, b1);
         if (a1 > a0 && b1 > b0) {
@@ -623,27 +822,40 @@ __device__ __forceinline__ int cs_slot(const CsParams &p, const CsChunk &c, int 
     return (skw & 0xffff) + dy * p.bins_x + (local - dy * sw);
 }
 
-__global__ void __launch_bounds__(CS_THREADS, CS_BLOCKS_PER_SM) cs_count_kernel(CsParams p)
+__global__ void __launch_bounds__(CS_THREADS, CS_COUNT_MIN_BLOCKS) cs_count_kernel(CsParams p)
 {
     extern __shared__ uint32_t s_cnt[];      // [CS_WARPS][kp / 2]: two 16-bit counters a word
     __shared__ uint8_t s_idx[CS_WARPS][32];  // lanes of the entries with pairs
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int kw2 = p.kp >> 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *p.done = 0u;
     uint32_t *cnt = s_cnt + warp * kw2;
     for (int k = lane; k < kw2; k += 32) cnt[k] = 0u;
     __syncwarp();
     int64_t beg, end;
     cs_segment(p, beg, end);
+    // loads run ahead of the counting: the entries two chunks ahead, the
+    // radii and means of the next chunk's entries
+    const uint32_t *svals = cs_svals(p);
+    uint32_t sv_a = beg + lane < end ? svals[beg + lane] : 0u;
+    uint32_t sv_b = beg + 32 + lane < end ? svals[beg + 32 + lane] : 0u;
+    int r_a = beg + lane < end ? p.radius[sv_a] : 0;
+    float2 m_a = r_a > 0 ? p.mean2d[sv_a] : make_float2(0.f, 0.f);
     for (int64_t e0 = beg; e0 < end; e0 += 32) {
         const int64_t i = e0 + lane;
-        uint32_t sv = 0;
+        const uint32_t sv = sv_a;
+        const int r = r_a;
+        const float2 m = m_a;
+        sv_a = sv_b;
+        r_a = e0 + 32 + lane < end ? p.radius[sv_a] : 0;
+        m_a = r_a > 0 ? p.mean2d[sv_a] : make_float2(0.f, 0.f);
+        sv_b = e0 + 64 + lane < end ? svals[e0 + 64 + lane] : 0u;
         uint64_t rc = 0;
         if (i < end) {
-            sv = p.svals[i];
-            rc = cs_rect(p, sv);
+            rc = cs_rect(p, sv, r, m);
             p.rect[i] = rc;
         }
-        const CsChunk c = cs_chunk(p, sv, rc, s_idx[warp]);
+        const CsChunk c = cs_chunk(p, i < end ? sv : 0u, rc, s_idx[warp]);
         int before = 0;
         for (int s0 = 0; s0 < c.total; s0 += 32) {
             int j;
@@ -672,36 +884,6 @@ __global__ void __launch_bounds__(CS_THREADS, CS_BLOCKS_PER_SM) cs_count_kernel(
     }
 }
 
-// Bases of the keys (exclusive scan of the totals hist[nkeys * G + key], in
-// place), the ranges of the non-empty keys, the total and the capacity check.
-__global__ void __launch_bounds__(SCAN_THREADS) cs_keys_kernel(uint32_t *tot, int nkeys, int64_t capacity,
-                                                               int64_t *d_count, int64_t *n_eff,
-                                                               int32_t *d_err, uint32_t *ranges)
-{
-    __shared__ int64_t s_warp[32];
-    const int per = (nkeys + SCAN_THREADS - 1) / SCAN_THREADS;
-    const int beg = threadIdx.x * per, end = min(nkeys, beg + per);
-    int64_t sum = 0;
-    for (int k = beg; k < end; ++k) sum += tot[k];
-    int64_t total;
-    int64_t run = block_scan_i64(sum, s_warp, total);
-    const bool fits = total <= capacity;
-    for (int k = beg; k < end; ++k) {
-        const uint32_t c = tot[k];
-        if (fits && c > 0) {
-            ranges[2 * (int64_t)k] = (uint32_t)run;
-            ranges[2 * (int64_t)k + 1] = (uint32_t)(run + c);
-        }
-        tot[k] = (uint32_t)run;
-        run += c;
-    }
-    if (threadIdx.x == 0) {
-        *d_count = total;
-        *n_eff = fits ? total : 0;
-        if (!fits && d_err) atomicCAS(d_err, 0, (int32_t)GS_ERR_CAPACITY);
-    }
-}
-
 __global__ void __launch_bounds__(CS_THREADS) cs_place_kernel(CsParams p)
 {
     // per key the block's first position, then per (warp, key) the running
@@ -715,10 +897,11 @@ __global__ void __launch_bounds__(CS_THREADS) cs_place_kernel(CsParams p)
     int64_t beg, end;
     cs_segment(p, beg, end);
     // the next 32 entries are loaded while the present ones are placed
+    const uint32_t *svals = cs_svals(p);
     uint32_t sv_next = 0;
     uint64_t rc_next = 0;
     if (beg + lane < end) {
-        sv_next = p.svals[beg + lane];
+        sv_next = svals[beg + lane];
         rc_next = p.rect[beg + lane];
     }
     {
@@ -739,7 +922,7 @@ __global__ void __launch_bounds__(CS_THREADS) cs_place_kernel(CsParams p)
         sv_next = 0;
         rc_next = 0;
         if (e0 + 32 + lane < end) {
-            sv_next = p.svals[e0 + 32 + lane];
+            sv_next = svals[e0 + 32 + lane];
             rc_next = p.rect[e0 + 32 + lane];
         }
         const CsChunk c = cs_chunk(p, sv, rc, s_idx[warp]);
@@ -774,6 +957,8 @@ struct BinWs {
     int32_t *cnt;
     uint32_t *hist;
     int64_t *n_eff;
+    uint32_t *kor;     // the depth keys' OR and their complements' OR
+    uint32_t *done;    // rows of the counting sort's scan finished
     uint32_t *tk[2], *tv;
     uint64_t *rect;    // counting sort; shares its space with the emit path's buffers
     uint16_t *wpre;
@@ -800,6 +985,8 @@ static BinWs carve(void *base, int64_t NV, int64_t cap)
                                                (size_t)CS_MAX_KEYS * (cw / CS_WARPS + 1));
     w.hist = reinterpret_cast<uint32_t *>(take(4 * hist_words));
     w.n_eff = reinterpret_cast<int64_t *>(take(64));
+    w.kor = reinterpret_cast<uint32_t *>(take(8));
+    w.done = reinterpret_cast<uint32_t *>(take(4));
     // stage 2 takes one of two paths: their buffers share one region
     const size_t region = o;
     w.offsets = reinterpret_cast<int64_t *>(take(8 * (NV + 1)));
@@ -815,13 +1002,15 @@ static BinWs carve(void *base, int64_t NV, int64_t cap)
     return w;
 }
 
-static gs_status run_pass(SortPass s, int64_t grid_items_hint, cudaStream_t st)
+// One radix pass; with counts false the block counts are already in s.hist.
+static gs_status run_pass(SortPass s, cudaStream_t st, bool counts = true)
 {
-    (void)grid_items_hint;
+    if (counts) {
+        note_launch();
+        radix_hist_kernel<<<s.G, SORT_THREADS, 0, st>>>(s);
+    }
     note_launch();
-    radix_hist_kernel<<<s.G, SORT_THREADS, 0, st>>>(s);
-    note_launch();
-    scan_digit_rows_kernel<<<RADIX, SORT_THREADS, 0, st>>>(s.hist, s.G, RADIX);
+    scan_digit_rows_kernel<<<RADIX, SORT_THREADS, 0, st>>>(s.hist, s.G, RADIX, s.kor, s.shift, KeyBases{});
     note_launch();
     radix_scatter_kernel<<<s.G, SORT_THREADS, 0, st>>>(s);
     return launch_status("radix pass");
@@ -845,7 +1034,7 @@ gs_status radix_sort_pairs(uint32_t *k[2], uint32_t *v[2], int64_t n, int bits, 
         s.shift = shift;
         s.hist = hist;
         s.G = G;
-        gs_status e = run_pass(s, n, st);
+        gs_status e = run_pass(s, st);
         if (e != GS_OK) return e;
         cur ^= 1;
     }
@@ -887,17 +1076,23 @@ extern "C" gs_status gs_bin_sort(const gs_projected *proj, int64_t n, int V, int
     const int bins_x = bins_x_of(W, bin);
     const int bins = bins_x * bins_y_of(H, bin);
     const int64_t nkeys = (int64_t)V * bins;
-    cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * nkeys, st);
+    // the counting sort writes every key's range; the other paths only the
+    // non-empty ones
+    if (NV == 0 || nkeys > CS_MAX_KEYS) cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * nkeys, st);
     if (NV == 0) {
         cudaMemsetAsync(d_count, 0, sizeof(int64_t), st);
         return launch_status("gs_bin_sort");
     }
-    // ---- stage 1: (view, depth) order of the V*N entries
-    note_launch();
-    depth_keys_kernel<<<(int)ceil_div(NV, 256), 256, 0, st>>>(proj->depth, proj->radius, NV,
-                                                              w.dk[0], w.dv[0]);
+    // ---- stage 1: (view, depth) order of the V*N entries; before the
+    // counting sort, the passes whose byte is the same in every key are
+    // skipped and the kernels find their buffers on the device
+    const bool cs = nkeys <= CS_MAX_KEYS;
     int cur = 0;
-    int Gd = (int)std::min<int64_t>(sort_blocks(), ceil_div(NV, SORT_TILE));
+    const int Gd = (int)std::min<int64_t>(sort_blocks(), ceil_div(NV, SORT_TILE));
+    cudaMemsetAsync(w.kor, 0, 2 * sizeof(uint32_t), st);
+    note_launch();
+    depth_keys_kernel<<<Gd, SORT_THREADS, 0, st>>>(proj->depth, proj->radius, NV, Gd, w.dk[0], w.dv[0], w.hist,
+                                                   w.kor);
     // depth order only: stage 2 sorts stably on a key that holds the view,
     // so each (view, bin) list needs its view's entries in (depth, index)
     // order, not the views grouped
@@ -912,15 +1107,25 @@ extern "C" gs_status gs_bin_sort(const gs_projected *proj, int64_t n, int V, int
         s.shift = 8 * pass;
         s.hist = w.hist;
         s.G = Gd;
-        gs_status e = run_pass(s, NV, st);
+        if (cs) {
+            s.kor = w.kor;
+            for (int b = 0; b < 2; ++b) {
+                s.kb[b] = w.dk[b];
+                s.vb[b] = w.dv[b];
+            }
+        }
+        gs_status e = run_pass(s, st, pass > 0);  // the keys kernel counted the first pass
         if (e != GS_OK) return e;
         cur ^= 1;
     }
     const uint32_t *svals = w.dv[cur];
     // ---- stage 2 as a counting sort when the per-warp key tables fit in shared memory
-    if (nkeys <= CS_MAX_KEYS) {
+    if (cs) {
         CsParams cp{};
         cp.svals = svals;
+        cp.kor = w.kor;
+        cp.sv[0] = w.dv[0];
+        cp.sv[1] = w.dv[1];
         cp.mean2d = reinterpret_cast<const float2 *>(proj->mean2d);
         cp.radius = proj->radius;
         cp.depth = proj->depth;
@@ -941,6 +1146,7 @@ extern "C" gs_status gs_bin_sort(const gs_projected *proj, int64_t n, int V, int
         cp.hist = w.hist;
         cp.wpre = w.wpre;
         cp.rect = w.rect;
+        cp.done = w.done;
         cp.n_eff = w.n_eff;
         cp.vals = vals;
         cp.keys = keys;
@@ -951,10 +1157,8 @@ extern "C" gs_status gs_bin_sort(const gs_projected *proj, int64_t n, int V, int
         note_launch();
         cs_count_kernel<<<G, CS_THREADS, smem_count, st>>>(cp);
         note_launch();
-        scan_digit_rows_kernel<<<(int)nkeys, SORT_THREADS, 0, st>>>(w.hist, G, (int)nkeys);
-        note_launch();
-        cs_keys_kernel<<<1, SCAN_THREADS, 0, st>>>(w.hist + (int64_t)nkeys * G, (int)nkeys, capacity, d_count,
-                                                   w.n_eff, d_err, ranges);
+        const KeyBases kb{w.done, capacity, d_count, w.n_eff, d_err, ranges};
+        scan_digit_rows_kernel<<<(int)nkeys, SORT_THREADS, 0, st>>>(w.hist, G, (int)nkeys, nullptr, 0, kb);
         note_launch();
         cs_place_kernel<<<G, CS_THREADS, smem_place, st>>>(cp);
         return launch_status("gs_bin_sort");
@@ -1006,7 +1210,7 @@ extern "C" gs_status gs_bin_sort(const gs_projected *proj, int64_t n, int V, int
         s.shift = 8 * pass;
         s.hist = w.hist;
         s.G = sort_blocks();
-        e = run_pass(s, 0, st);
+        e = run_pass(s, st);
         if (e != GS_OK) return e;
         kc ^= 1;
         vcur = s.vout;
