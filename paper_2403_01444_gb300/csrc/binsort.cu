@@ -90,6 +90,23 @@ __device__ __forceinline__ void pass_buffers(SortPass &s)
     s.vout = odd ? s.vb[0] : s.vb[1];
 }
 
+
+// Lanes whose value v (below 2^BITS) equals this lane's, among the lanes with
+// ok set (an empty set for a lane without): one ballot per bit.
+template <int BITS>
+__device__ __forceinline__ unsigned ballot_match(uint32_t v, bool ok)
+{
+    const unsigned okm = __ballot_sync(0xffffffffu, ok);
+    unsigned m = ok ? okm : 0u;
+#pragma unroll
+    for (int b = 0; b < BITS; ++b) {
+        const bool bit = (v >> b) & 1u;
+        const unsigned bb = __ballot_sync(0xffffffffu, bit);
+        m &= bit ? bb : ~bb;
+    }
+    return m;
+}
+
 __device__ __forceinline__ uint32_t digit_of(const SortPass &s, uint32_t k, uint32_t v)
 {
     return (k >> s.shift) & (RADIX - 1);
@@ -332,7 +349,7 @@ __global__ void __launch_bounds__(SORT_THREADS, 4) radix_scatter_kernel(SortPass
         for (int j = 0; j < SORT_ITEMS; ++j) {
             const uint32_t d = dig[j];
             const bool ok = d < RADIX;
-            unsigned peers = __match_any_sync(0xffffffffu, d);
+            unsigned peers = ballot_match<8>(d, ok);
             uint32_t before = 0;
             if (ok) before = s_wh[warp][d];
             __syncwarp();
@@ -658,8 +675,8 @@ __global__ void keys64_kernel(const uint32_t *tk, const uint32_t *vals, const in
 //    (warp, key) a running offset from it (16 bits: a block's count of one
 //    key is below 2^16), and each warp walks its pairs again, each placed at
 //    its key's running position; within a step the slots of one key are
-//    ranked by lane (__match_any_sync), which a step whose slots all belong to
-//    one entry (distinct keys) skips.
+//    ranked by lane (ballot_match: one ballot per key bit), which a step whose
+//    slots all belong to one entry (distinct keys) skips.
 // Every list then holds its pairs in the entries' depth order: the same
 // result as the stable key sort, bit for bit.
 constexpr int CS_WARPS = 16;
@@ -934,7 +951,7 @@ __global__ void __launch_bounds__(CS_THREADS) cs_place_kernel(CsParams p)
             const uint32_t sgi = __shfl_sync(0xffffffffu, c.gi, j);
             const bool valid = key >= 0;
             // slots of one key in this step, ranked by lane
-            const unsigned peers = single ? 1u << lane : __match_any_sync(0xffffffffu, key);
+            const unsigned peers = single ? 1u << lane : ballot_match<11>((uint32_t)key, valid);
             uint32_t pos = 0;
             if (valid) pos = s_base[key] + g[key] + __popc(peers & lt);
             __syncwarp();
