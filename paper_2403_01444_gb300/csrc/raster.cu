@@ -596,21 +596,30 @@ __global__ void BWD_BOUNDS raster_bwd2_kernel(RasterParams p)
             }
             __syncthreads();
             const int ccnt = chi - clo;
-            if (tid < 2 * ccnt) {
-                int j = tid >> 1, h = (tid & 1) * 4;
-                float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (tid < 4 * ccnt) {
+                // four threads a record, two moments each
+                const int j = tid >> 2, q = (tid & 3) * 2;
+                float2 sum = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int w = 0; w < NW; ++w) {
-                    const float4 a = s_part[w][j][h], b = s_part[w][j][h + 1];
-                    const float4 c = s_part[w][j][h + 2], d = s_part[w][j][h + 3];
+                    const float4 a = s_part[w][j][q], b = s_part[w][j][q + 1];
                     sum.x += (a.x + a.y) + (a.z + a.w);
                     sum.y += (b.x + b.y) + (b.z + b.w);
-                    sum.z += (c.x + c.y) + (c.z + c.w);
-                    sum.w += (d.x + d.y) + (d.z + d.w);
                 }
-                if (sum.x != 0.f || sum.y != 0.f || sum.z != 0.f || sum.w != 0.f)
-                    atomicAdd(reinterpret_cast<float4 *>(p.grads + 8 * (vb + s_g[clo + j]) + h),
-                              moments_to_grads(sum, unscale_conic(s_co[clo + j]), h));
+                if (sum.x != 0.f || sum.y != 0.f) {
+                    float2 gq;
+                    if (q == 0) {
+                        const float4 co = unscale_conic(s_co[clo + j]);
+                        gq = make_float2(fmaf(co.x, sum.x, co.y * sum.y), fmaf(co.z, sum.y, co.y * sum.x));
+                    } else if (q == 2) {
+                        gq = make_float2(-0.5f * sum.x, -sum.y);
+                    } else if (q == 4) {
+                        gq = make_float2(-0.5f * sum.x, sum.y);
+                    } else {
+                        gq = sum;
+                    }
+                    atomicAdd(reinterpret_cast<float2 *>(p.grads + 8 * (vb + s_g[clo + j]) + q), gq);
+                }
             }
             if (WANT_OP) {
                 for (int j = tid; j < ccnt; j += NT) {
