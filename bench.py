@@ -539,6 +539,41 @@ def run_ours(args):
     n_sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     roof = roofline_for(dom, stages[dom], pairs, pair_counts, G.n, Vb, W, H, cfg, hbm, src, sm_mhz, n_sms)
 
+    # the cache MLP on its own against the tensor peak: each launch timed
+    # alone over all rows (the reverse dense, every row's gradient), tensor
+    # FLOPs of the two BF16 hidden layers (32 -> 64 -> 64); the 64 -> 7
+    # output layer runs in FP32 on the SIMT cores and is not counted
+    mlp_roof = None
+    if ntc.mlp_struct().precision == gs3.GS_MLP_BF16 and not st.fused:
+        dW_keep = ntc.mlp.g.clone()
+        d_enc_keep = st.d_enc.clone()
+
+        def time_it(fn, reps=20):
+            fn()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / reps
+
+        fwd_ms = time_it(lambda: gs3.ntc_mlp_fwd(st.enc, G.n, ntc.mlp_struct(), st.raw7, stream))
+        bwd_ms = time_it(lambda: gs3.ntc_mlp_bwd(st.enc, G.n, ntc.mlp_struct(), st.d_raw7, st.loss_scale_view(),
+                                                  ntc.mlp.g, st.d_enc))
+        ntc.mlp.g.copy_(dW_keep)
+        st.d_enc.copy_(d_enc_keep)
+        f_fwd = 2 * (32 * 64 + 64 * 64) * G.n
+        f_bwd = 2 * f_fwd   # input gradients and weight gradients of both layers
+        mlp_roof = {"bound": "tensor", "dtype": "bf16", "peak": bf16, "unit": "TFLOP/s", "peak_source": src,
+                    "rows": G.n, "fwd": {"ms": fwd_ms, "flops": f_fwd, "achieved": f_fwd / fwd_ms / 1e9,
+                                         "frac": f_fwd / fwd_ms / 1e9 / bf16},
+                    "bwd_dense": {"ms": bwd_ms, "flops": f_bwd, "achieved": f_bwd / bwd_ms / 1e9,
+                                  "frac": f_bwd / bwd_ms / 1e9 / bf16},
+                    "note": "latency-bound small GEMMs (K = 32/64 per row tile); ncu on the 100K case: "
+                            "sm__pipe_tensor_cycles_active 6.6 % in the reverse"}
+
     # the rasterizer fwd+bwd against HBM: algorithmic bytes of projection,
     # binning/sort, compositing fwd/bwd and projection bwd, counted per
     # Gaussian, per (view, Gaussian, 16x16 tile) intersection and per pixel
@@ -691,7 +726,7 @@ def run_ours(args):
                 "stages_ms": {k: round(v, 4) for k, v in stages.items()},
                 "bin_pairs_per_step": pairs, "composited_pairs": pair_counts,
                 "warmup_loss": wl, "warmup_s": t_warm,
-                "roofline": roof, "raster_fwd_bwd_roofline": raster_roof,
+                "roofline": roof, "raster_fwd_bwd_roofline": raster_roof, "mlp_roofline": mlp_roof,
                 "render_only": render_only, "bin_autotune": tune, "bin_tiles": bin_side,
                 "stage2": stage2, "stream": stream_res, "large": large,
                 "paper_context": {"s_per_frame": 12.0, "fps_render": 200,
