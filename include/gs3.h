@@ -274,7 +274,9 @@ GS_API gs_status gs_bin_sort_noalloc(const gs_projected *proj, int64_t n, int V,
  * ceil(W/16) * ceil(H/16), t = tile_y * ceil(W/16) + tile_x),
  * rec[2 * (i * cap + j)] is the Gaussian index and rec[2 * (i * cap + j) + 1]
  * the position in the bin's list of its j-th staged record, j < count[i];
- * count[i] = -1 when the tile staged more than cap records.  Device memory
+ * the list ends at the last staged record that some pixel of the tile went
+ * through before it stopped (the records after it took part at no pixel);
+ * count[i] = -1 when that is more than cap records.  Device memory
  * owned by the caller: rec uint32[V * tiles * cap * 2] (8-byte aligned),
  * count int32[V * tiles]; 1 <= cap <= 2^20. */
 typedef struct {

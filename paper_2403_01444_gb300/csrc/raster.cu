@@ -262,6 +262,11 @@ __global__ void FWD_BOUNDS raster_fwd2_kernel(RasterParams p)
     uint32_t n_tested = 0, n_contrib = 0;
     const int64_t tg = (int64_t)view * gridDim.x + tile;  // the tile's list
     int staged = 0;
+    // the last batch's first list index, and how far into it this thread's
+    // pixels went (all of it unless both stopped)
+    int staged_prev = 0, jlast = 0;
+    __shared__ int s_jmax;
+    if (tid == 0) s_jmax = 0;
     for (int base = 0; base < total; base += NT) {
         if (__syncthreads_count(done[0] && done[1]) == NT) break;
         const int k = base + tid;
@@ -279,7 +284,9 @@ __global__ void FWD_BOUNDS raster_fwd2_kernel(RasterParams p)
         const int slot = compact_slot<NT>(keep, s_wcnt, cnt);
         if (slot >= 0 && p.tl_rec && staged + slot < p.tl_cap)
             p.tl_rec[tg * p.tl_cap + staged + slot] = make_uint2(g, (uint32_t)k);
+        staged_prev = staged;
         staged += cnt;
+        jlast = done[0] && done[1] ? 0 : cnt;
         if (slot >= 0) {
             s_xy[slot] = make_float4(m.x, m.y, -__log2f(255.f * co.w), 0.f);
             s_co[slot] = scale_conic(co);
@@ -317,6 +324,7 @@ __global__ void FWD_BOUNDS raster_fwd2_kernel(RasterParams p)
                 add1 = add1 && !stop1;
                 if (stop0) { alpha.x = 0.f; tT.x = Tv.x; }
                 if (stop1) { alpha.y = 0.f; tT.y = Tv.y; }
+                if (done[0] && done[1]) jlast = j + 1;
             }
             const float2 w = __fmul2_rn(alpha, Tv);
             const float4 ck = s_rgbk[j];
@@ -335,7 +343,17 @@ __global__ void FWD_BOUNDS raster_fwd2_kernel(RasterParams p)
         }
     }
     if (STATS) flush_stats(p.stats, n_tested, n_contrib);
-    if (p.tl_rec && tid == 0) p.tl_cnt[tg] = staged <= p.tl_cap ? staged : -1;
+    if (p.tl_rec) {
+        // records of the last batch past every thread's stop took part at no
+        // pixel (their positions are at or past every pixel's last): the list
+        // ends before them
+        if (jlast > 0) atomicMax(&s_jmax, jlast);
+        __syncthreads();
+        if (tid == 0) {
+            const int listed = staged_prev + s_jmax;
+            p.tl_cnt[tg] = listed <= p.tl_cap ? listed : -1;
+        }
+    }
     const int64_t HW = (int64_t)p.H * p.W;
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
