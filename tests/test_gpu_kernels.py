@@ -85,6 +85,41 @@ def test_bin_sort_bit_exact(V, N, W, H, seed):
     np.testing.assert_array_equal(r.ranges.cpu().numpy().view(np.uint32), ranges)
 
 
+@pytest.mark.parametrize("pattern", ["byte1", "bytes02", "all_equal", "all_vary"])
+def test_bin_sort_constant_depth_bytes(pattern):
+    """A depth-sort pass whose byte is the same in every key is skipped, and
+    each later pass finds the buffer holding the keys from the passes before
+    it that were not skipped.  Depths built bit by bit so that byte 1, or
+    bytes 0 and 2, or every byte (all equal: ties by index) is constant, and a
+    control where all four vary, give the oracle's keys, values and ranges
+    bit for bit.  No entry is culled here: a culled entry's key has every
+    byte 0xff and would make each byte vary."""
+    V, N, W, H = 2, 900, 200, 130
+    rng = np.random.default_rng(61)
+    rec = scenes.random_projected(V, N, W, H, rng)
+    rec["radius"] = np.maximum(rec["radius"], 1).astype(rec["radius"].dtype)
+    rb = lambda lo, hi: rng.integers(lo, hi + 1, size=(V, N)).astype(np.uint32)
+    top = np.where(rng.random((V, N)) < 0.5, 0x3F, 0x40).astype(np.uint32)  # positive depths 0.6 .. 4
+    if pattern == "byte1":
+        bits = (top << 24) | (rb(0x20, 0x7F) << 16) | (0x5A << 8) | rb(0, 255)  # three passes: odd
+    elif pattern == "bytes02":
+        bits = (top << 24) | (0x20 << 16) | (rb(0, 255) << 8) | 0x11  # the first pass skipped
+    elif pattern == "all_equal":
+        bits = np.full((V, N), 0x40400000, np.uint32)
+    else:
+        bits = (top << 24) | (rb(0x20, 0x7F) << 16) | (rb(0, 255) << 8) | rb(0, 255)
+    rec["depth"] = bits.astype(np.uint32).view(np.float32)
+    assert (rec["depth"] > 0).all()
+    p = projected_from_records(rec)
+    r, k = gpu_bin_sort(p, N, V, W, H)
+    count, keys, vals, ranges = oracle.bin_sort(rec["mean2d"], rec["radius"], rec["depth"], W, H)
+    assert count > 0 and r.count() == count
+    assert int(r.d_err.item()) == 0
+    np.testing.assert_array_equal(k[:count].cpu().numpy().view(np.uint64), keys)
+    np.testing.assert_array_equal(r.vals[:count].cpu().numpy().view(np.uint32), vals)
+    np.testing.assert_array_equal(r.ranges.cpu().numpy().view(np.uint32), ranges)
+
+
 def test_bin_sort_all_culled_and_capacity_overflow():
     V, N, W, H = 2, 400, 100, 60
     rec = scenes.random_projected(V, N, W, H, np.random.default_rng(9))
