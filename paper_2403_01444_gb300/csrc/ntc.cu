@@ -619,9 +619,9 @@ extern "C" gs_status ntc_encode_bwd(const float *mean, int64_t n, const gs_hashg
     if (n == 0) return GS_OK;
     GS_REQUIRE(mean && d_enc && d_table, "ntc_encode_bwd: null argument");
     GS_REQUIRE(aligned(d_table, 8) && aligned(d_enc, 8), "ntc_encode_bwd: misaligned");
+    GS_REQUIRE(d_count == nullptr || order, "ntc_encode_bwd: a count needs its row list (order)");
     note_launch();
     const dim3 blk(g.L, ENC_BWD_G);
-    GS_REQUIRE(d_count == nullptr || order, "ntc_encode_bwd: a count needs its row list (order)");
     // over a list of unknown length: 16 blocks an SM stride over it
     const int64_t blocks = d_count ? std::min<int64_t>(ceil_div(n, ENC_BWD_G), (int64_t)num_sms() * 16)
                                    : ceil_div(n, ENC_BWD_G);
@@ -634,10 +634,10 @@ extern "C" gs_status ntc_active_rows(const float *d_raw7, int64_t n, uint32_t *r
 {
     GS_REQUIRE(n >= 0 && n <= (int64_t(1) << 32) - 1, "ntc_active_rows: n out of range");
     GS_REQUIRE(d_count, "ntc_active_rows: null count");
+    GS_REQUIRE(n == 0 || (d_raw7 && rows), "ntc_active_rows: null argument");
     cudaStream_t s = as_stream(stream);
     cudaMemsetAsync(d_count, 0, sizeof(int64_t), s);
     if (n == 0) return launch_status("ntc_active_rows");
-    GS_REQUIRE(d_raw7 && rows, "ntc_active_rows: null argument");
     note_launch();
     active_rows_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(d_raw7, n, rows,
                                                                  reinterpret_cast<unsigned long long *>(d_count));

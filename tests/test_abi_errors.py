@@ -119,3 +119,12 @@ def test_cache_and_optimiser_reject_bad_arguments(L):
            "workspace too small")
     _fails(L, L.ntc_spatial_order(FAKE, c_int64(1000), byref(bad_grid), FAKE, FAKE, c_size_t(need), None),
            "invalid hash grid")
+    # the reverse over a list of active rows: the count goes with its list
+    _fails(L, L.ntc_encode_bwd(FAKE, c_int64(10), byref(good), FAKE, FAKE, None, FAKE, None),
+           "a count needs its row list")
+    _fails(L, L.ntc_active_rows(FAKE, c_int64(-1), FAKE, FAKE, None), "n out of range")
+    _fails(L, L.ntc_active_rows(FAKE, c_int64(10), FAKE, None, None), "null count")
+    _fails(L, L.ntc_active_rows(None, c_int64(10), FAKE, FAKE, None), "null argument")
+    mlp = gs3.GsMlp(gs3.GS_MLP_BF16, FAKE, FAKE)
+    _fails(L, L.ntc_mlp_bwd(FAKE, gs3.GS_BF16, c_int64(10), byref(mlp), FAKE, None, FAKE, FAKE, FAKE, None, None),
+           "rows and d_rows go together")
