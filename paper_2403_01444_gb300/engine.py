@@ -690,7 +690,7 @@ class Streamer:
     def checkpoint(self, path: str):
         """Everything a later run needs to continue the video from the next
         frame: the carried Gaussians (transformed means and rotations, SH as
-        rotated) and the cache's warm-up parameters."""
+        rotated, scales and opacities) and the cache's warm-up parameters."""
         g = self.g
         np.savez(path, frames_done=self.frames_done, mean=g.mean.cpu().numpy(),
                  quat=g.quat.cpu().numpy(), sh=g.sh.cpu().numpy(),
@@ -699,7 +699,9 @@ class Streamer:
                  warm_mlp=self.warm[1].cpu().numpy())
 
     def resume(self, path: str):
-        """Continue from a checkpoint written by checkpoint()."""
+        """Continue from a checkpoint written by checkpoint(): every field it
+        holds is restored; one of another scene (Gaussian count or SH degree)
+        is refused before anything changes."""
         d = np.load(path)
         dev = self.g.mean.device
         t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
@@ -709,6 +711,8 @@ class Streamer:
         self.g.mean.copy_(t(d["mean"]))
         self.g.quat.copy_(t(d["quat"]))
         self.g.sh.copy_(t(d["sh"]))
+        self.g.scale.copy_(t(d["scale"]))
+        self.g.opacity_logit.copy_(t(d["opacity_logit"]))
         self.warm = (t(d["warm_table"]), t(d["warm_mlp"]))
         self.frames_done = int(d["frames_done"])
 
