@@ -5,8 +5,12 @@
 // (Gaussian, tile) pair, the sort is split in two stable stages:
 //   1. the V*N (view, Gaussian) entries are sorted by depth bits -- 4
 //      byte-digit passes on the FP32 depth bits, stable, so equal depths keep
-//      the index order (the views interleave; stage 2's key holds the view);
-//      a pass whose digit is the same for every entry is a copy;
+//      the index order (the views interleave; stage 2's key holds the view).
+//      The keys kernel also writes the first pass's block counts and the OR
+//      of the keys and of their complements; before the counting sort, a
+//      pass on a byte that is the same in every key is skipped whole and the
+//      kernels of each pass find the buffer holding the keys from the parity
+//      of the passes before it that ran (elsewhere such a pass is a copy);
 //   2. the pairs of every entry's bins are ordered on the (view * bins + bin)
 //      key alone, stably, so each list keeps its entries' depth order.  When
 //      the per-warp key tables fit in shared memory (V * bins <= CS_MAX_KEYS)
@@ -19,7 +23,9 @@
 // rectangle holds their tile -- the same records in the same order as the
 // per-tile list, for far fewer pairs to sort.
 // All passes are of reduce-then-scan form (counts, one-block scans, ranked
-// scatter): no inter-block waits, deterministic output.
+// scatter): no inter-block waits, deterministic output.  Equal digits or
+// keys within a warp are found with one ballot per bit (ballot_match), which
+// measured faster here than __match_any_sync.
 #include <algorithm>
 
 #include "common.cuh"
